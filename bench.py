@@ -1,0 +1,309 @@
+"""Throughput of the RTG all-pairs r-NN build on GB300 (one JSON line on stdout).
+
+Workload (the configuration the metric is quoted on): n = 100,000 points i.i.d. uniform in
+[0,1]^6 stored FP64, r for an expected ball population of 2 ln n (r = 0.18829), m = 8 seeded
+random rotations + shifts, cell side c = r, seed 0.  One step = one complete build: all m
+grids keyed, grouped, enumerated, deduplicated and assembled into the device CSR.
+
+  value : unique reported pairs per second of device time, points resident in HBM, L2
+          flushed (512 MB write) between steps
+  e2e   : the same metric through the C ABI with host buffers: points copied in from pinned
+          host memory and the CSR copied back inside the timed region
+  --impl reference : the CPU oracle (test infrastructure) timed on the host cores on the
+          same workload
+Multi-GPU (torchrun): replicas only; every rank builds its own roadmap, no collective on
+the data path; value = pairs of all ranks / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reported r-NN pairs/s and roadmap builds/s at recall R; p50/p99 build latency"
+WORKLOAD = {"workload": "rtg_all_pairs n=100000 d=6 fp64 uniform[0,1]^6 r=2lnn-degree m=8 c=r seed0",
+            "n": 100000, "d": 6, "m": 8, "points": "uniform [0,1]^6, fp64", "cell_side": "r",
+            "seed": 0, "l2": "flushed between steps (512 MB write)"}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload():
+    from paper_1409_8112_gb300 import gen
+    n, d, m = WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["m"]
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(0, n, d)
+    T = gen.transforms(0, d, m, r)
+    return pts, T, r
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# Algorithmic bytes per build for each timed phase (lower-bound model):
+#   sort  : upfront histogram reads the N keys once; each pass reads and writes N (key, index)
+#   count : reads the N sorted (key, index) pairs and gathers each point's padded FP32 row
+def phase_bytes(n, d, m, key_bytes, passes, dpad):
+    N = n * m
+    return {
+        "sort": N * key_bytes + passes * 2 * N * (key_bytes + 4),
+        "count": N * (key_bytes + 4) + N * dpad * 4,
+    }
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1409_8112_gb300 import rtg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pts, T, r = workload()
+    n, d = pts.shape
+    m = T.shape[0]
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(local, stream=stream.cuda_stream)
+    dev_pts = torch.from_numpy(pts).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # recall against the exact set (device brute force), outside the timed region
+    exact = ctx.brute_force(dev_pts, r, count_only=True)
+    exact_pairs = exact.nnz
+    exact.release()
+
+    for _ in range(args.warmup):
+        res = ctx.all_pairs(dev_pts, r, T, r, timing=True)
+        res.release()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, phases, pairs, launches = [], [], None, None
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.all_pairs(dev_pts, r, T, r, timing=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = res.stats
+        phases.append(st["phase_us"])
+        pairs, launches = res.nnz, st["launches"]
+        key_bytes = 8 if st["key_bits"] > 32 else 4
+        passes = st["sort_passes"]
+        res.release()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall_s = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = pairs * args.steps * ws / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned) and the CSR copied back
+    import torch as _t
+    host_pts = _t.from_numpy(pts).pin_memory()
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2) + 1):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.all_pairs(host_pts, r, T, r)
+        row_ptr, col = res.download()
+        t1 = time.perf_counter()
+        res.release()
+        if k > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_value = pairs / (np.mean(e2e_ms) / 1e3)
+    h2d = pts.nbytes + T.nbytes
+    d2h = row_ptr.nbytes + col.nbytes
+
+    # roofline of the dominant phase (per-phase device events over the timed region)
+    mean_phase = {p: float(np.mean([ph[p] for ph in phases])) for p in phases[0]}
+    pb = phase_bytes(n, d, m, key_bytes, passes, 8 if d <= 8 else 16)
+    dom = max(pb, key=lambda p: mean_phase[p])
+    peak, peak_kind = measured_peaks()
+    achieved = pb[dom] / (mean_phase[dom] * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "algorithmic_bytes": pb[dom], "launch_us": round(mean_phase[dom], 2)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic", "config": WORKLOAD,
+        "builds_per_s": round(args.steps * ws / (total_ms / 1e3), 2),
+        "pairs_per_build": pairs, "exact_pairs": exact_pairs,
+        "recall": round(pairs / exact_pairs, 5) if exact_pairs else 1.0,
+        "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+        "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+        "wall_s_timed_region": round(wall_s, 3),
+        "phase_us": {p: round(v, 2) for p, v in mean_phase.items()},
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 1), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(float(np.mean(e2e_ms)), 4)},
+        "clocks": clk, "gpu_launches": launches * args.steps,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pts, T, r, budget_s=args.cpu_seconds)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(pts, T, r, budget_s=12.0):
+    """The oracle as it stands, single-threaded, on whole builds of the same workload."""
+    import oracle
+    times, pairs = [], 0
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        res = oracle.rtg(pts, r, T, r)
+        times.append(time.perf_counter() - t0)
+        pairs = res.csr.nnz
+        if time.perf_counter() - t_start > budget_s or len(times) >= 20:
+            break
+    return {"value": round(pairs / float(np.median(times)), 1), "unit": "pairs/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{len(times)} complete builds of the bench workload (n=100000, d=6, m=8), "
+                      f"median {np.median(times):.3f} s each"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    pts, T, r = workload()
+    for _ in range(args.warmup):
+        oracle.rtg(pts, r, T, r)
+    times, pairs = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = oracle.rtg(pts, r, T, r)
+        times.append(time.perf_counter() - t0)
+        pairs = res.csr.nnz
+    total = float(np.sum(times))
+    value = pairs * args.steps / total
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": WORKLOAD, "impl": "reference",
+        "cpu_baseline": {"value": round(value, 1), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} complete builds of the bench workload"},
+        "e2e": {"value": round(value, 1), "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/* rtg.h - C ABI of the GB300 library for all-pairs r-nearest-neighbour reporting with
+ * randomly transformed grids (RTG).
+ *
+ * Method (Kleinbort, Salzman, Halperin, arXiv:1409.8112):
+ *   Problem (Sec. I): given n points P in R^d and a radius r, report every pair {p, q} of P
+ *   at Euclidean distance at most r.
+ *   Alg. 1 (Sec. III): repeat m times: place a grid of cell side c under a random shift
+ *   (and, in the second algorithm of Sec. III, a random rotation), associate every point
+ *   with the cell it lies in, and report the pairs inside each non-empty cell that are at
+ *   distance at most r.  Pairs found by several grids are reported once (Sec. III-B).
+ *
+ * Exact arithmetic contract (what makes the output a unique integer set):
+ *   grid t is the row-major d x d matrix R_t followed by the shift s_t (m*(d*d+d) doubles);
+ *   rotated coordinate  y_k = fma-chain: acc = s_k; acc = fma(R_t[k][l], p_l, acc), l=0..d-1
+ *   cell coordinate     q_k = floor(y_k / c)          (IEEE double division)
+ *   squared distance    s = 0; e = p_a[l] - p_b[l]; s = fma(e, e, s), l = 0..d-1, on the
+ *                       original (unrotated) coordinates; FP32 input is widened exactly
+ *   reported            s <= fl(r * r)
+ * The library reaches this FP64 result bit for bit while doing its bulk arithmetic in
+ * FP32: every decision whose FP32 value lies within a proven error bound of the boundary
+ * is recomputed in FP64 with the sequence above.
+ *
+ * Output: the upper-triangular CSR of the reported set: row i lists every j > i with
+ * {i, j} reported, ascending.  With RTG_FLAG_SYMMETRIC both (i, j) and (j, i) are stored
+ * (the "store each pair twice" extension of Sec. III-B for multiple r-NN queries).
+ *
+ * Errors: every entry point returns an rtg_status; nothing is thrown across the ABI.
+ * rtg_last_error() gives a text for the last failure on a context.  One context serialises
+ * its synchronous calls on its own stream; distinct contexts are independent.
+ */
+#ifndef RTG_H
+#define RTG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RTG_OK = 0,
+  RTG_E_INVALID = 1,        /* bad argument (sizes, non-finite values, null pointers) */
+  RTG_E_NOMEM = 2,          /* device allocation failed */
+  RTG_E_BUDGET = 3,         /* the request does not fit the context's memory budget */
+  RTG_E_KEY_OVERFLOW = 4,   /* a grid's cell index range needs more than 64 key bits */
+  RTG_E_CUDA = 5,           /* a CUDA call failed; see rtg_last_error */
+  RTG_E_TIMEOUT = 6,        /* a bounded device or host wait ran out */
+  RTG_PENDING = 7,          /* rtg_poll: the build is not finished yet */
+  RTG_E_UNKNOWN_TICKET = 8, /* rtg_poll/rtg_wait: no such ticket */
+  RTG_E_INTERNAL = 9        /* a device-side consistency check failed */
+} rtg_status;
+
+/* Flags. */
+#define RTG_FLAG_SHIFT_ONLY 1u /* rtg_transforms_generate: R = identity (Alg. 1 as printed) */
+#define RTG_FLAG_SYMMETRIC 2u  /* rtg_all_pairs: store (i,j) and (j,i) */
+#define RTG_FLAG_TIMING 4u     /* rtg_all_pairs: fill rtg_stats.phase_us (adds events) */
+
+/* Point coordinate types. */
+#define RTG_DTYPE_F64 0
+#define RTG_DTYPE_F32 1
+
+#define RTG_MAX_DIM 16   /* d in [1, RTG_MAX_DIM] */
+#define RTG_MAX_GRIDS 64 /* m in [1, RTG_MAX_GRIDS] */
+
+typedef struct rtg_ctx rtg_ctx;
+
+typedef struct {
+  int device;                /* CUDA device ordinal */
+  uint64_t mem_budget_bytes; /* cap on device memory the context may hold; 0 = no cap */
+  void* stream;              /* cudaStream_t to run on, or NULL for a private stream */
+  uint32_t flags;            /* reserved, pass 0 */
+} rtg_config;
+
+/* Per-build counters (all exact integers unless noted). */
+typedef struct {
+  int64_t candidates[RTG_MAX_GRIDS]; /* grid t: sum over non-empty cells of C(size, 2) */
+  int64_t total_candidates;          /* sum of the above */
+  int64_t owned_candidates;          /* candidates whose pair first shares a cell in grid t */
+  int64_t near_wall;     /* (point, grid) pairs with a coordinate within 1e-12 of a wall */
+  int64_t near_r;        /* distinct co-located pairs with |dist - r| <= 1e-12 r */
+  int64_t key_rechecks;  /* coordinates whose cell index was recomputed in FP64 */
+  int64_t dist_rechecks; /* pairs whose distance test was recomputed in FP64 */
+  int64_t large_cells;   /* cells handled by the tiled large-cell path */
+  int64_t max_cell;      /* largest cell population over all grids */
+  int64_t pairs;         /* unique reported pairs (= upper-triangular nnz) */
+  int32_t key_bits;      /* bits of the (grid, cell) sort key */
+  int32_t sort_passes;   /* radix passes run */
+  int32_t launches;      /* kernels this build launched */
+  int32_t reserved;
+  double phase_us[8];    /* with RTG_FLAG_TIMING: prep, key, sort, count, scan, write,
+                            rowsort, total (microseconds, device events) */
+} rtg_stats;
+
+typedef struct {
+  int64_t n;         /* number of points (rows) */
+  int64_t nnz;       /* stored entries: pairs, or 2 * pairs when symmetric */
+  int64_t* row_ptr;  /* device pointer, n + 1 entries */
+  int32_t* col;      /* device pointer, nnz entries, ascending within each row */
+  int32_t symmetric; /* 1 if both (i,j) and (j,i) are stored */
+  uint64_t handle;   /* library bookkeeping; 0 = empty */
+  rtg_stats stats;
+} rtg_csr;
+
+/* Create a context on cfg->device.  *out receives the context or NULL on failure. */
+rtg_status rtg_create(const rtg_config* cfg, rtg_ctx** out);
+
+/* Destroy a context; releases every CSR it still owns.  NULL is allowed. */
+void rtg_destroy(rtg_ctx* ctx);
+
+/* Text for the last failure on ctx (or for context-less calls if ctx is NULL).  Valid until
+ * the next call on that context. */
+const char* rtg_last_error(const rtg_ctx* ctx);
+
+/* Name of a status code. */
+const char* rtg_status_string(rtg_status s);
+
+/* Draw m grid transforms for Alg. 1 / its rotated variant (Sec. III): R_t Haar-distributed
+ * on O(d) (QR of a seeded standard Gaussian matrix with diag(R) made positive; identity
+ * with RTG_FLAG_SHIFT_ONLY) and s_t uniform in [0, cell_side)^d.  out (host) receives
+ * m*(d*d+d) doubles, R_t row-major then s_t.  Deterministic in (seed, d, m, cell_side,
+ * flags).  RTG_E_INVALID for d outside [1,16], m < 1, cell_side <= 0 or out == NULL. */
+rtg_status rtg_transforms_generate(uint64_t seed, int d, int m, double cell_side,
+                                   uint32_t flags, double* out);
+
+/* Alg. 1 (Sec. III) over all m grids, with the pairs merged and deduplicated into a CSR
+ * (Sec. III-B).  Synchronous: returns when the CSR is complete on the device.
+ *   points     n x d row-major, dtype RTG_DTYPE_F64 or RTG_DTYPE_F32; a device pointer if
+ *              points_on_device, else a host pointer (copied in).  Caller-owned, read-only.
+ *   r          reporting radius (> 0, finite)
+ *   transforms host pointer, m*(d*d+d) doubles as produced by rtg_transforms_generate
+ *   cell_side  grid cell side c (> 0, finite); the paper takes c = c~ r with c~ > 1
+ *   flags      RTG_FLAG_SYMMETRIC, RTG_FLAG_TIMING
+ *   out        receives a library-owned device CSR; free it with rtg_release
+ * Errors: RTG_E_INVALID (n < 0 or n >= 2^31, d outside [1,16], m outside [1,64], r or c not
+ * positive and finite, a non-finite coordinate or transform entry), RTG_E_KEY_OVERFLOW,
+ * RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT.  n in {0, 1} gives an empty CSR. */
+rtg_status rtg_all_pairs(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
+                         int64_t n, int d, double r, const double* transforms, int m,
+                         double cell_side, uint32_t flags, rtg_csr* out);
+
+/* The exact all-pairs r-NN set of Sec. I (every pair {i, j} with s <= fl(r * r), s as in
+ * the arithmetic contract above) by checking all n(n-1)/2 pairs on the device in tiles; the
+ * recall denominator for Alg. 1 and an exact reference.  Same argument conventions and
+ * errors as rtg_all_pairs (no transforms).  With count_only != 0 only out->nnz and
+ * out->stats.pairs are set (no device memory is returned beyond the row pointers). */
+rtg_status rtg_brute_force(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
+                           int64_t n, int d, double r, uint32_t flags, int count_only,
+                           rtg_csr* out);
+
+/* Free the device memory of a CSR returned by this context and zero *csr. */
+rtg_status rtg_release(rtg_ctx* ctx, rtg_csr* csr);
+
+/* Copy a CSR to host arrays (row_ptr: n + 1 entries, col: nnz entries).  Synchronous. */
+rtg_status rtg_csr_download(rtg_ctx* ctx, const rtg_csr* csr, int64_t* row_ptr, int32_t* col);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTG_H */

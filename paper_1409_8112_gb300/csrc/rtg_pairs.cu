@@ -1,0 +1,723 @@
+// In-cell pair enumeration and CSR assembly (Alg. 1 lines 8-9 and the dedupe of Sec. III-B
+// of arXiv:1409.8112).
+//
+// After the sort every (grid, cell) is a run of equal keys.  A block owns the cells whose
+// first position lies in its slice of kSlice sorted positions: it finds them with adjacent
+// key comparisons, stages their points (FP32, padded rows) in shared memory and walks all
+// pairs (a < b) of every cell with at most kSmax points as one flat candidate range.  Cells
+// with more points go to the tiled large-cell kernel.
+//
+// Dedupe without an auxiliary set: the distance test does not depend on the grid, so pair
+// {i, j} is reported by grid t iff it is within r and shares a cell in t.  The pair is
+// therefore emitted only by the first grid that puts i and j in one cell; a candidate in
+// grid t is dropped when key_mat[i][t'] == key_mat[j][t'] for some t' < t.  The check runs
+// before the distance (the filtering use of the auxiliary structure in Sec. III-B).
+//
+// Distance: FP32 on the staged rows; a pair is decided in FP32 only when the FP32 squared
+// distance is outside [s_lo, s_hi], the proven error band around fl(r*r) (see the plan
+// kernel); otherwise the FP64 reference sequence decides.
+//
+// Each enumeration runs twice: COUNT (per-row counts, statistics, large-cell list), then,
+// after the row-pointer scan, WRITE (columns into their rows).  Rows are sorted at the end.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "rtg_internal.cuh"
+
+namespace rtg {
+
+namespace {
+
+constexpr int kSlice = 1024;
+constexpr int kSmax = 128;
+constexpr int kPairThreads = 256;
+constexpr int kStage = kSlice + kSmax;
+constexpr int kKeyWin = kSlice + kSmax + 2;
+constexpr unsigned int kUnknown = 0xffffffffu;
+constexpr int kTL = 128;  // large-cell tile
+constexpr unsigned int kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ double load_coord(const void* pts, int dtype, long long i, int d,
+                                             int l) {
+  return dtype == 0 ? __ldg((const double*)pts + i * d + l)
+                    : (double)__ldg((const float*)pts + i * d + l);
+}
+
+// FP64 reference squared distance (fixed order, fused multiply-add, original coordinates).
+__device__ __noinline__ double exact_dist2(const void* pts, int dtype, long long i, long long j,
+                                           int d) {
+  double s = 0.0;
+  for (int l = 0; l < d; ++l) {
+    const double e = __dsub_rn(load_coord(pts, dtype, i, d, l), load_coord(pts, dtype, j, d, l));
+    s = __fma_rn(e, e, s);
+  }
+  return s;
+}
+
+__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int* total,
+                                                        unsigned int* sbuf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sbuf[warp] = x;
+  __syncthreads();
+  unsigned int wpre = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    const unsigned int c = sbuf[w];
+    if (w < warp) wpre += c;
+    tot += c;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + x - v;
+}
+
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v,
+                                                                unsigned long long* total,
+                                                                unsigned long long* sbuf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sbuf[warp] = x;
+  __syncthreads();
+  unsigned long long wpre = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    const unsigned long long c = sbuf[w];
+    if (w < warp) wpre += c;
+    tot += c;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + x - v;
+}
+
+// Per-thread tallies of the COUNT pass.
+struct Tally {
+  unsigned int owned = 0, rechecks = 0, near_r = 0, pairs = 0;
+  bool overflow = false;
+};
+
+// The decision for one candidate pair (i < j) of grid t.  Returns true if it is reported.
+template <typename K, int DPAD, bool WRITE>
+__device__ __forceinline__ void visit_pair(unsigned int i, unsigned int j, int t, const float* pa,
+                                           const float* pb, const K* __restrict__ key_mat,
+                                           const Plan* __restrict__ P, const void* pts,
+                                           int dtype, unsigned int* row_cnt,
+                                           const long long* __restrict__ row_ptr, int* col,
+                                           long long col_cap, int symmetric, Tally& tl) {
+  const int m = P->m;
+  const K* ki = key_mat + (size_t)i * m;
+  const K* kj = key_mat + (size_t)j * m;
+  for (int u = 0; u < t; ++u)
+    if (__ldg(ki + u) == __ldg(kj + u)) return;  // an earlier grid owns this pair
+  ++tl.owned;
+  float sf = 0.0f;
+#pragma unroll
+  for (int l = 0; l < DPAD; ++l) {
+    const float e = pa[l] - pb[l];
+    sf = fmaf(e, e, sf);
+  }
+  bool keep;
+  if (P->filter_on && sf < P->s_lo) {
+    keep = true;
+  } else if (P->filter_on && sf > P->s_hi) {
+    keep = false;
+  } else {
+    const double s = exact_dist2(pts, dtype, i, j, P->d);
+    keep = s <= P->rr;
+    ++tl.rechecks;
+    if (!WRITE && fabs(__dsub_rn(__dsqrt_rn(s), P->r)) <= __dmul_rn(1e-12, P->r)) ++tl.near_r;
+  }
+  if (!keep) return;
+  ++tl.pairs;
+  if (!WRITE) {
+    atomicAdd(&row_cnt[i], 1u);
+    if (symmetric) atomicAdd(&row_cnt[j], 1u);
+  } else {
+    const long long pi = row_ptr[i] + atomicAdd(&row_cnt[i], 1u);
+    if (pi < col_cap) col[pi] = (int)j; else tl.overflow = true;
+    if (symmetric) {
+      const long long pj = row_ptr[j] + atomicAdd(&row_cnt[j], 1u);
+      if (pj < col_cap) col[pj] = (int)i; else tl.overflow = true;
+    }
+  }
+}
+
+template <bool WRITE>
+__device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigned int* sbuf) {
+  if (WRITE) {
+    if (__syncthreads_or(tl.overflow) && threadIdx.x == 0) atomicOr(&st->errors, kErrColOverflow);
+    return;
+  }
+  unsigned int tot;
+  block_excl_scan(tl.owned, &tot, sbuf);
+  if (threadIdx.x == 0 && tot) atomicAdd(&st->owned_candidates, (unsigned long long)tot);
+  block_excl_scan(tl.rechecks, &tot, sbuf);
+  if (threadIdx.x == 0 && tot) atomicAdd(&st->dist_rechecks, (unsigned long long)tot);
+  block_excl_scan(tl.near_r, &tot, sbuf);
+  if (threadIdx.x == 0 && tot) atomicAdd(&st->near_r, (unsigned long long)tot);
+  block_excl_scan(tl.pairs, &tot, sbuf);
+  if (threadIdx.x == 0 && tot) atomicAdd(&st->pairs, (unsigned long long)tot);
+}
+
+template <typename K>
+__device__ __forceinline__ int grid_of(K key, int B, int m) {
+  return m > 1 ? (int)(key >> B) : 0;
+}
+
+template <typename K, int DPAD, bool WRITE>
+__global__ void __launch_bounds__(kPairThreads) k_pairs_small(
+    const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N,
+    const float* __restrict__ pf, const void* __restrict__ pts, int dtype,
+    const K* __restrict__ key_mat, const Plan* __restrict__ P, Status* st, unsigned int* row_cnt,
+    const long long* __restrict__ row_ptr, int* col, long long col_cap, LargeCell* large,
+    unsigned int large_cap, int symmetric) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* s_pt = reinterpret_cast<float*>(smem);                      // kStage * DPAD
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_pt + kStage * DPAD);  // kStage
+  K* s_key = reinterpret_cast<K*>(s_idx + kStage);                     // kKeyWin
+  unsigned int* c_start = reinterpret_cast<unsigned int*>(s_key + kKeyWin);  // kSlice + 1
+  unsigned int* c_cand = c_start + kSlice + 1;                                // kSlice + 1
+  unsigned char* c_grid = reinterpret_cast<unsigned char*>(c_cand + kSlice + 1);  // kSlice
+  __shared__ unsigned int s_end, s_ncells, s_total, s_stage_lo, s_stage_hi;
+  __shared__ unsigned int sbuf[kPairThreads / 32];
+  __shared__ unsigned long long s_gcand[kMaxGrids];
+  __shared__ unsigned long long s_maxcell;
+
+  const int tid = threadIdx.x;
+  const long long lo = (long long)blockIdx.x * kSlice;
+  const long long hi = min(lo + kSlice, N);
+  const long long win_end = min(hi + kSmax + 1, N);
+  const int B = P->key_bits, m = P->m;
+
+  for (long long x = lo - 1 + tid; x < win_end; x += kPairThreads)
+    if (x >= 0) s_key[x - lo + 1] = skeys[x];
+  if (tid == 0) {
+    s_end = kUnknown;
+    s_maxcell = 0;
+  }
+  if (!WRITE)
+    for (int g = tid; g < kMaxGrids; g += kPairThreads) s_gcand[g] = 0;
+  __syncthreads();
+  auto is_head = [&](long long x) -> bool {
+    return x == 0 || s_key[x - lo + 1] != s_key[x - lo];
+  };
+  for (long long x = hi + tid; x < win_end; x += kPairThreads)
+    if (is_head(x)) atomicMin(&s_end, (unsigned int)(x - lo));
+  // compact the heads in [lo, hi): four consecutive positions per thread
+  constexpr int kPer = kSlice / kPairThreads;
+  unsigned int flags = 0, cnt = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const long long x = lo + tid * kPer + q;
+    if (x < hi && is_head(x)) {
+      flags |= 1u << q;
+      ++cnt;
+    }
+  }
+  unsigned int ncells;
+  unsigned int w = block_excl_scan(cnt, &ncells, sbuf);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q)
+    if (flags & (1u << q)) c_start[w++] = (unsigned int)(tid * kPer + q);
+  if (tid == 0) {
+    s_ncells = ncells;
+    const unsigned int end_rel =
+        s_end != kUnknown ? s_end : (win_end == N ? (unsigned int)(N - lo) : kUnknown);
+    c_start[ncells] = end_rel;
+  }
+  __syncthreads();
+  if (ncells == 0) return;
+  // classify cells
+  for (unsigned int e = tid; e < ncells; e += kPairThreads) {
+    const unsigned int st_rel = c_start[e], en = c_start[e + 1];
+    const K key = s_key[st_rel + 1];
+    const int g = grid_of(key, B, m);
+    c_grid[e] = (unsigned char)g;
+    unsigned long long size = en == kUnknown ? 0ull : (unsigned long long)(en - st_rel);
+    unsigned int cand = 0;
+    if (en == kUnknown || size > (unsigned long long)kSmax) {
+      if (!WRITE) {
+        if (en == kUnknown) {
+          // the run continues past the window: first position with a larger key
+          long long a = win_end, b = N;
+          while (a < b) {
+            const long long mid = (a + b) >> 1;
+            if (skeys[mid] == key) a = mid + 1; else b = mid;
+          }
+          size = (unsigned long long)(a - (lo + st_rel));
+        }
+        const unsigned long long slot = atomicAdd(&st->large_cells, 1ull);
+        if (slot < large_cap) {
+          large[slot].start = (unsigned long long)(lo + st_rel);
+          large[slot].size = (unsigned int)size;
+          large[slot].grid = (unsigned int)g;
+        } else {
+          atomicOr(&st->errors, kErrLargeOverflow);
+        }
+        atomicAdd(&s_gcand[g], size * (size - 1) / 2);
+        atomicMax(&s_maxcell, size);
+      }
+    } else {
+      cand = (unsigned int)(size * (size - 1) / 2);
+      if (!WRITE) {
+        if (cand) atomicAdd(&s_gcand[g], (unsigned long long)cand);
+        atomicMax(&s_maxcell, size);
+      }
+    }
+    c_cand[e] = cand;
+  }
+  __syncthreads();
+  // exclusive scan of the candidate counts (ncells <= kSlice)
+  {
+    unsigned int v[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const unsigned int e = tid * kPer + q;
+      v[q] = e < ncells ? c_cand[e] : 0u;
+      sum += v[q];
+    }
+    unsigned int total;
+    unsigned int run = block_excl_scan(sum, &total, sbuf);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const unsigned int e = tid * kPer + q;
+      if (e < ncells) c_cand[e] = run;
+      run += v[q];
+    }
+    if (tid == 0) {
+      c_cand[ncells] = total;
+      s_total = total;
+      s_stage_lo = c_start[0];
+      const unsigned int last = ncells - 1;
+      const unsigned int en = c_start[ncells];
+      const bool last_small = en != kUnknown && en - c_start[last] <= (unsigned int)kSmax;
+      unsigned int shi = last_small ? en : c_start[last];
+      if (shi > s_stage_lo + kStage) shi = s_stage_lo + kStage;
+      s_stage_hi = shi;
+    }
+  }
+  __syncthreads();
+  if (!WRITE) {
+    if (tid < m && s_gcand[tid]) atomicAdd(&st->candidates[tid], s_gcand[tid]);
+    if (tid == 0 && s_maxcell) atomicMax(&st->max_cell, s_maxcell);
+  }
+  const unsigned int T = s_total;
+  Tally tl;
+  if (T > 0) {
+    const unsigned int stage_lo = s_stage_lo, nstage = s_stage_hi - s_stage_lo;
+    for (unsigned int x = tid; x < nstage; x += kPairThreads) {
+      const uint32_t idx = svals[lo + stage_lo + x];
+      s_idx[x] = idx;
+      const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
+      float4* dst = reinterpret_cast<float4*>(s_pt + (size_t)x * DPAD);
+#pragma unroll
+      for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+    }
+    __syncthreads();
+    for (unsigned int c = tid; c < T; c += kPairThreads) {
+      int el = 0, eh = (int)ncells - 1;
+      while (el < eh) {
+        const int mid = (el + eh + 1) >> 1;
+        if (c_cand[mid] <= c) el = mid; else eh = mid - 1;
+      }
+      const unsigned int l = c - c_cand[el];
+      unsigned int b = (unsigned int)((1.0f + sqrtf(8.0f * (float)l + 1.0f)) * 0.5f);
+      while (b * (b - 1) / 2 > l) --b;
+      while ((b + 1) * b / 2 <= l) ++b;
+      const unsigned int a = l - b * (b - 1) / 2;
+      const unsigned int xa = c_start[el] + a - stage_lo, xb = c_start[el] + b - stage_lo;
+      const unsigned int ia = s_idx[xa], ib = s_idx[xb];
+      const unsigned int i = min(ia, ib), j = max(ia, ib);
+      visit_pair<K, DPAD, WRITE>(i, j, c_grid[el], s_pt + (size_t)xa * DPAD,
+                                 s_pt + (size_t)xb * DPAD, key_mat, P, pts, dtype, row_cnt,
+                                 row_ptr, col, col_cap, symmetric, tl);
+    }
+  }
+  flush_tally<WRITE>(tl, st, sbuf);
+}
+
+// Job offsets for the large cells: cell e has ceil(size / kTL) row tiles.
+__global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restrict__ large,
+                                                      unsigned int cap, Status* st,
+                                                      unsigned long long* job_off) {
+  __shared__ unsigned long long sbuf[32];
+  __shared__ unsigned long long carry;
+  const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (unsigned long long base = 0; base < L; base += blockDim.x) {
+    const unsigned long long e = base + threadIdx.x;
+    const unsigned long long v = e < L ? (large[e].size + kTL - 1) / kTL : 0;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan64(v, &tot, sbuf);
+    if (e < L) job_off[e] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    job_off[L] = carry;
+    st->large_jobs = carry;
+  }
+}
+
+template <typename K, int DPAD, bool WRITE>
+__global__ void __launch_bounds__(kPairThreads) k_pairs_large(
+    const uint32_t* __restrict__ svals, const float* __restrict__ pf, const void* __restrict__ pts,
+    int dtype, const K* __restrict__ key_mat, const Plan* __restrict__ P, Status* st,
+    const LargeCell* __restrict__ large, unsigned int cap, const unsigned long long* job_off,
+    unsigned int* row_cnt, const long long* __restrict__ row_ptr, int* col, long long col_cap,
+    int symmetric) {
+  __shared__ __align__(16) float sa[kTL * DPAD];
+  __shared__ __align__(16) float sb[kTL * DPAD];
+  __shared__ uint32_t ia[kTL], ib[kTL];
+  __shared__ unsigned int sbuf[kPairThreads / 32];
+  const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
+  const unsigned long long J = L ? job_off[L] : 0;
+  Tally tl;
+  for (unsigned long long job = blockIdx.x; job < J; job += gridDim.x) {
+    long long el = 0, eh = (long long)L - 1;
+    while (el < eh) {
+      const long long mid = (el + eh + 1) >> 1;
+      if (job_off[mid] <= job) el = mid; else eh = mid - 1;
+    }
+    const LargeCell cell = large[el];
+    const unsigned int s = cell.size;
+    const unsigned int a0 = (unsigned int)(job - job_off[el]) * kTL;
+    const unsigned int na = min((unsigned int)kTL, s - a0);
+    __syncthreads();
+    for (unsigned int x = threadIdx.x; x < na; x += blockDim.x) {
+      const uint32_t idx = svals[cell.start + a0 + x];
+      ia[x] = idx;
+      const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
+      float4* dst = reinterpret_cast<float4*>(sa + x * DPAD);
+#pragma unroll
+      for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+    }
+    for (unsigned int b0 = a0; b0 < s; b0 += kTL) {
+      const unsigned int nb = min((unsigned int)kTL, s - b0);
+      __syncthreads();
+      for (unsigned int x = threadIdx.x; x < nb; x += blockDim.x) {
+        const uint32_t idx = svals[cell.start + b0 + x];
+        ib[x] = idx;
+        const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
+        float4* dst = reinterpret_cast<float4*>(sb + x * DPAD);
+#pragma unroll
+        for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+      }
+      __syncthreads();
+      for (unsigned int q = threadIdx.x; q < na * nb; q += blockDim.x) {
+        const unsigned int x = q / nb, y = q % nb;
+        if (a0 + x >= b0 + y) continue;
+        const unsigned int i = min(ia[x], ib[y]), j = max(ia[x], ib[y]);
+        visit_pair<K, DPAD, WRITE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD, key_mat,
+                                   P, pts, dtype, row_cnt, row_ptr, col, col_cap, symmetric, tl);
+      }
+    }
+  }
+  flush_tally<WRITE>(tl, st, sbuf);
+}
+
+// Row counts -> row pointers (exclusive scan, single pass with decoupled look-back); the
+// counts are reset to zero so that the WRITE pass can use them as fill cursors.
+constexpr int kScanItems = 16;
+constexpr int kScanTile = 256 * kScanItems;
+
+__global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, long long* row_ptr, int n,
+                                              unsigned long long* lookback,
+                                              unsigned int* tile_counter, Status* st,
+                                              unsigned int tiles) {
+  __shared__ unsigned long long sbuf[8];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned int s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const unsigned int tile = s_tile;
+  const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned int v[kScanItems];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = base + q < n ? row_cnt[base + q] : 0u;
+    sum += v[q];
+  }
+  unsigned long long total;
+  const unsigned long long ex = block_excl_scan64(sum, &total, sbuf);
+  if (threadIdx.x == 0) {
+    const unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kMask = (1ull << 62) - 1;
+    unsigned long long excl = 0;
+    if (tile == 0) {
+      *reinterpret_cast<volatile unsigned long long*>(lookback) = kPre | total;
+    } else {
+      *reinterpret_cast<volatile unsigned long long*>(lookback + tile) = kAgg | total;
+      long long p = (long long)tile - 1;
+      unsigned int spins = 0;
+      while (p >= 0) {
+        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(lookback + p);
+        if ((w >> 62) == 0) {
+          if (++spins > kSpinLimit) {
+            atomicOr(&st->errors, kErrTimeout);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += w & kMask;
+        if ((w >> 62) == 2) break;
+        --p;
+      }
+      *reinterpret_cast<volatile unsigned long long*>(lookback + tile) = kPre | (excl + total);
+    }
+    s_base = excl;
+    if (tile == tiles - 1) {
+      row_ptr[n] = (long long)(excl + total);
+      st->nnz = excl + total;
+    }
+  }
+  __syncthreads();
+  unsigned long long run = s_base + ex;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    if (base + q < n) {
+      row_ptr[base + q] = (long long)run;
+      row_cnt[base + q] = 0u;
+    }
+    run += v[q];
+  }
+}
+
+__device__ __forceinline__ int bitonic32(int v, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int other = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      v = (lower == up) ? min(v, other) : max(v, other);
+    }
+  }
+  return v;
+}
+
+// One warp per row: rows of at most 32 entries are sorted in registers; longer rows are
+// queued for the block kernel.
+__global__ void __launch_bounds__(256) k_rowsort_warp(const long long* __restrict__ row_ptr,
+                                                      int* col, int n, unsigned int* long_rows,
+                                                      unsigned int* long_count) {
+  const int lane = threadIdx.x & 31;
+  const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const long long b = row_ptr[row], e = row_ptr[row + 1], len = e - b;
+  if (len <= 1) return;
+  if (len <= 32) {
+    int v = lane < len ? col[b + lane] : INT_MAX;
+    v = bitonic32(v, lane);
+    if (lane < len) col[b + lane] = v;
+  } else if (lane == 0) {
+    long_rows[atomicAdd(long_count, 1u)] = (unsigned int)row;
+  }
+}
+
+constexpr int kRowSmem = 8192;
+
+__global__ void __launch_bounds__(256) k_rowsort_long(const long long* __restrict__ row_ptr,
+                                                      int* col,
+                                                      const unsigned int* __restrict__ long_rows,
+                                                      const unsigned int* long_count) {
+  __shared__ int buf[kRowSmem];
+  const unsigned int cnt = *long_count;
+  for (unsigned int k = blockIdx.x; k < cnt; k += gridDim.x) {
+    const unsigned int row = long_rows[k];
+    const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
+    long long L = 1;
+    while (L < len) L <<= 1;
+    __syncthreads();
+    if (L <= kRowSmem) {
+      for (long long x = threadIdx.x; x < L; x += blockDim.x) buf[x] = x < len ? col[b + x] : INT_MAX;
+      __syncthreads();
+      for (long long kk = 2; kk <= L; kk <<= 1) {
+        for (long long j = kk >> 1; j > 0; j >>= 1) {
+          for (long long x = threadIdx.x; x < L; x += blockDim.x) {
+            const long long y = x ^ j;
+            if (y > x) {
+              const bool asc = (x & kk) == 0;
+              const int u = buf[x], w = buf[y];
+              if (asc ? (u > w) : (u < w)) {
+                buf[x] = w;
+                buf[y] = u;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (long long x = threadIdx.x; x < len; x += blockDim.x) col[b + x] = buf[x];
+    } else {
+      // Sorting network whose every comparator puts the smaller value at the lower index,
+      // so positions at or past len behave as +infinity without being stored.
+      int* a = col + b;
+      for (long long kk = 2; kk <= L; kk <<= 1) {
+        for (long long j = kk >> 1; j > 0; j >>= 1) {
+          for (long long x = threadIdx.x; x < L; x += blockDim.x) {
+            const long long y = (j == (kk >> 1)) ? (x ^ (kk - 1)) : (x ^ j);
+            if (y > x && y < len) {
+              const int u = a[x], w = a[y];
+              if (u > w) {
+                a[x] = w;
+                a[y] = u;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+}
+
+// Exact set of Sec. I: every pair (i < j) checked, in 128 x 128 tiles (bi <= bj), with the
+// same FP32 filter and FP64 recheck as the in-cell path.
+constexpr int kBT = 128;
+
+template <int DPAD, bool WRITE>
+__global__ void __launch_bounds__(kPairThreads) k_brute(
+    const float* __restrict__ pf, const void* __restrict__ pts, int dtype,
+    const Plan* __restrict__ P, Status* st, int n, unsigned int* row_cnt,
+    const long long* __restrict__ row_ptr, int* col, long long col_cap, int symmetric) {
+  __shared__ __align__(16) float sa[kBT * DPAD];
+  __shared__ __align__(16) float sb[kBT * DPAD];
+  __shared__ unsigned int sbuf[kPairThreads / 32];
+  const long long nt = ((long long)n + kBT - 1) / kBT;
+  const long long jobs = nt * (nt + 1) / 2;
+  Tally tl;
+  for (long long job = blockIdx.x; job < jobs; job += gridDim.x) {
+    long long bj = (long long)((sqrt(8.0 * (double)job + 1.0) - 1.0) * 0.5);
+    while (bj * (bj + 1) / 2 > job) --bj;
+    while ((bj + 1) * (bj + 2) / 2 <= job) ++bj;
+    const long long bi = job - bj * (bj + 1) / 2;
+    const long long i0 = bi * kBT, j0 = bj * kBT;
+    const int na = (int)min((long long)kBT, n - i0), nb = (int)min((long long)kBT, n - j0);
+    __syncthreads();
+    for (int x = threadIdx.x; x < 2 * kBT; x += blockDim.x) {
+      const bool first = x < kBT;
+      const int xx = first ? x : x - kBT;
+      const int cnt = first ? na : nb;
+      float* dst = (first ? sa : sb) + xx * DPAD;
+      if (xx < cnt) {
+        const float4* src = reinterpret_cast<const float4*>(pf + (size_t)((first ? i0 : j0) + xx) * DPAD);
+#pragma unroll
+        for (int v = 0; v < DPAD / 4; ++v) reinterpret_cast<float4*>(dst)[v] = __ldg(src + v);
+      }
+    }
+    __syncthreads();
+    const int y = threadIdx.x % kBT;
+    if (y < nb) {
+      for (int x = threadIdx.x / kBT; x < na; x += kPairThreads / kBT) {
+        const long long i = i0 + x, j = j0 + y;
+        if (i >= j) continue;
+        visit_pair<uint32_t, DPAD, WRITE>((unsigned int)i, (unsigned int)j, 0, sa + x * DPAD,
+                                          sb + y * DPAD, nullptr, P, pts, dtype, row_cnt,
+                                          row_ptr, col, col_cap, symmetric, tl);
+      }
+    }
+  }
+  flush_tally<WRITE>(tl, st, sbuf);
+}
+
+template <int DPAD>
+void brute_impl(const BuildArgs& a, bool write, cudaStream_t s) {
+  const unsigned blocks = (unsigned)(8 * a.num_sms);
+  if (write)
+    k_brute<DPAD, true><<<blocks, kPairThreads, 0, s>>>(a.pf, a.pts, a.dtype, a.plan, a.st, a.n,
+                                                        a.row_cnt, a.row_ptr, a.col, a.col_cap,
+                                                        a.symmetric);
+  else
+    k_brute<DPAD, false><<<blocks, kPairThreads, 0, s>>>(a.pf, a.pts, a.dtype, a.plan, a.st, a.n,
+                                                         a.row_cnt, nullptr, nullptr, 0,
+                                                         a.symmetric);
+}
+
+template <typename K, int DPAD>
+void pairs_impl(const BuildArgs& a, int sorted_buf, bool write, cudaStream_t s) {
+  const long long N = (long long)a.n * a.m;
+  const unsigned blocks = (unsigned)((N + kSlice - 1) / kSlice);
+  const size_t smem = (size_t)kStage * DPAD * 4 + (size_t)kStage * 4 + (size_t)kKeyWin * sizeof(K) +
+                      (size_t)(kSlice + 1) * 8 + kSlice;
+  const K* sk = (const K*)a.keys[sorted_buf];
+  const uint32_t* sv = a.vals[sorted_buf];
+  unsigned int large_blocks = (unsigned)(4 * a.num_sms);
+  if (write) {
+    cudaFuncSetAttribute(k_pairs_small<K, DPAD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_pairs_small<K, DPAD, true><<<blocks, kPairThreads, smem, s>>>(
+        sk, sv, N, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.row_cnt, a.row_ptr,
+        a.col, a.col_cap, a.large, a.large_cap, a.symmetric);
+    k_pairs_large<K, DPAD, true><<<large_blocks, kPairThreads, 0, s>>>(
+        sv, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.large, a.large_cap,
+        a.large_job_off, a.row_cnt, a.row_ptr, a.col, a.col_cap, a.symmetric);
+  } else {
+    cudaFuncSetAttribute(k_pairs_small<K, DPAD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_pairs_small<K, DPAD, false><<<blocks, kPairThreads, smem, s>>>(
+        sk, sv, N, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.row_cnt, nullptr,
+        nullptr, 0, a.large, a.large_cap, a.symmetric);
+    k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
+    k_pairs_large<K, DPAD, false><<<large_blocks, kPairThreads, 0, s>>>(
+        sv, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.large, a.large_cap,
+        a.large_job_off, a.row_cnt, nullptr, nullptr, 0, a.symmetric);
+  }
+}
+
+}  // namespace
+
+int launch_pairs(const BuildArgs& a, int sorted_buf, bool write, cudaStream_t s) {
+  if (a.key64) {
+    switch (a.dpad) {
+      case 4: pairs_impl<unsigned long long, 4>(a, sorted_buf, write, s); break;
+      case 8: pairs_impl<unsigned long long, 8>(a, sorted_buf, write, s); break;
+      default: pairs_impl<unsigned long long, 16>(a, sorted_buf, write, s); break;
+    }
+  } else {
+    switch (a.dpad) {
+      case 4: pairs_impl<uint32_t, 4>(a, sorted_buf, write, s); break;
+      case 8: pairs_impl<uint32_t, 8>(a, sorted_buf, write, s); break;
+      default: pairs_impl<uint32_t, 16>(a, sorted_buf, write, s); break;
+    }
+  }
+  return write ? 2 : 3;
+}
+
+int launch_brute(const BuildArgs& a, bool write, cudaStream_t s) {
+  switch (a.dpad) {
+    case 4: brute_impl<4>(a, write, s); break;
+    case 8: brute_impl<8>(a, write, s); break;
+    default: brute_impl<16>(a, write, s); break;
+  }
+  return 1;
+}
+
+void launch_scan(const BuildArgs& a, cudaStream_t s) {
+  const unsigned tiles = (unsigned)((a.n + kScanTile - 1) / kScanTile);
+  cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
+  k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.row_ptr, a.n, a.scan_lookback, &a.st->scan_tiles,
+                               a.st, tiles);
+}
+
+int launch_rowsort(const BuildArgs& a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((a.n + 7) / 8);
+  unsigned int* long_count = &a.st->long_rows;
+  k_rowsort_warp<<<blocks, 256, 0, s>>>(a.row_ptr, a.col, a.n, a.row_cnt, long_count);
+  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.row_ptr, a.col, a.row_cnt, long_count);
+  return 2;
+}
+
+}  // namespace rtg

@@ -1,0 +1,299 @@
+"""Python binding of the RTG C ABI (include/rtg.h).
+
+Argument marshalling only: every step of a build runs in the CUDA library
+``_build/librtg.so``.  The functions ``rtg_*`` mirror the C entry points one to one;
+``Context`` is a small convenience wrapper over them.  If the library cannot be loaded the
+import fails loudly: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+RTG_OK = 0
+RTG_E_INVALID = 1
+RTG_E_NOMEM = 2
+RTG_E_BUDGET = 3
+RTG_E_KEY_OVERFLOW = 4
+RTG_E_CUDA = 5
+RTG_E_TIMEOUT = 6
+RTG_PENDING = 7
+RTG_E_UNKNOWN_TICKET = 8
+RTG_E_INTERNAL = 9
+
+RTG_FLAG_SHIFT_ONLY = 1
+RTG_FLAG_SYMMETRIC = 2
+RTG_FLAG_TIMING = 4
+
+RTG_DTYPE_F64 = 0
+RTG_DTYPE_F32 = 1
+
+RTG_MAX_DIM = 16
+RTG_MAX_GRIDS = 64
+
+PHASES = ("prep", "key", "sort", "count", "scan", "write", "rowsort", "total")
+
+
+class rtg_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class rtg_stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64 * RTG_MAX_GRIDS),
+                ("total_candidates", ctypes.c_int64), ("owned_candidates", ctypes.c_int64),
+                ("near_wall", ctypes.c_int64), ("near_r", ctypes.c_int64),
+                ("key_rechecks", ctypes.c_int64), ("dist_rechecks", ctypes.c_int64),
+                ("large_cells", ctypes.c_int64), ("max_cell", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("key_bits", ctypes.c_int32),
+                ("sort_passes", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("phase_us", ctypes.c_double * 8)]
+
+
+class rtg_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("symmetric", ctypes.c_int32), ("handle", ctypes.c_uint64),
+                ("stats", rtg_stats)]
+
+
+class RTGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+# Every function the header declares, with its ctypes signature.
+_SIGNATURES = {
+    "rtg_create": (ctypes.c_int, [ctypes.POINTER(rtg_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "rtg_destroy": (None, [ctypes.c_void_p]),
+    "rtg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "rtg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rtg_transforms_generate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_double, ctypes.c_uint32,
+                                               ctypes.c_void_p]),
+    "rtg_all_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_uint32,
+                                     ctypes.POINTER(rtg_csr)]),
+    "rtg_brute_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_uint32, ctypes.c_int,
+                                       ctypes.POINTER(rtg_csr)]),
+    "rtg_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr)]),
+    "rtg_csr_download": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"RTG CUDA library missing: {path}")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def status_name(s: int) -> str:
+    return lib().rtg_status_string(s).decode()
+
+
+def _check(status: int, ctx=None):
+    if status != RTG_OK:
+        msg = lib().rtg_last_error(ctx).decode(errors="replace")
+        raise RTGError(status, msg)
+
+
+# ---- thin 1:1 wrappers ---------------------------------------------------------------------
+
+def rtg_create(device: int = 0, mem_budget_bytes: int = 0, stream: int | None = None):
+    cfg = rtg_config(device, mem_budget_bytes, stream or None, 0)
+    out = ctypes.c_void_p()
+    _check(lib().rtg_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def rtg_destroy(ctx) -> None:
+    lib().rtg_destroy(ctx)
+
+
+def rtg_transforms_generate(seed: int, d: int, m: int, cell_side: float,
+                            flags: int = 0) -> np.ndarray:
+    out = np.zeros((m, d * d + d), dtype=np.float64)
+    _check(lib().rtg_transforms_generate(seed, d, m, cell_side, flags, out.ctypes.data))
+    return out
+
+
+def rtg_all_pairs(ctx, points_ptr: int, dtype: int, on_device: bool, n: int, d: int, r: float,
+                  transforms: np.ndarray, m: int, cell_side: float, flags: int = 0) -> rtg_csr:
+    T = np.ascontiguousarray(transforms, dtype=np.float64)
+    out = rtg_csr()
+    st = lib().rtg_all_pairs(ctx, points_ptr, dtype, 1 if on_device else 0, n, d, r,
+                             T.ctypes.data, m, cell_side, flags, ctypes.byref(out))
+    _check(st, ctx)
+    return out
+
+
+def rtg_brute_force(ctx, points_ptr: int, dtype: int, on_device: bool, n: int, d: int,
+                    r: float, flags: int = 0, count_only: bool = False) -> rtg_csr:
+    out = rtg_csr()
+    st = lib().rtg_brute_force(ctx, points_ptr, dtype, 1 if on_device else 0, n, d, r, flags,
+                               1 if count_only else 0, ctypes.byref(out))
+    _check(st, ctx)
+    return out
+
+
+def rtg_release(ctx, csr: rtg_csr) -> None:
+    _check(lib().rtg_release(ctx, ctypes.byref(csr)), ctx)
+
+
+def rtg_csr_download(ctx, csr: rtg_csr):
+    row_ptr = np.zeros(csr.n + 1, dtype=np.int64)
+    col = np.zeros(max(csr.nnz, 0), dtype=np.int32)
+    _check(lib().rtg_csr_download(ctx, ctypes.byref(csr), row_ptr.ctypes.data,
+                                  col.ctypes.data if csr.nnz > 0 else None), ctx)
+    return row_ptr, col
+
+
+# ---- convenience -----------------------------------------------------------------------------
+
+def stats_dict(s: rtg_stats, m: int) -> dict:
+    return {
+        "candidates": [int(s.candidates[t]) for t in range(m)],
+        "total_candidates": int(s.total_candidates),
+        "owned_candidates": int(s.owned_candidates),
+        "near_wall": int(s.near_wall), "near_r": int(s.near_r),
+        "key_rechecks": int(s.key_rechecks), "dist_rechecks": int(s.dist_rechecks),
+        "large_cells": int(s.large_cells), "max_cell": int(s.max_cell),
+        "pairs": int(s.pairs), "key_bits": int(s.key_bits), "sort_passes": int(s.sort_passes),
+        "launches": int(s.launches),
+        "phase_us": {p: float(s.phase_us[i]) for i, p in enumerate(PHASES)},
+    }
+
+
+def _points_arg(points):
+    """(pointer, dtype code, on_device, n, d, keepalive) for a numpy array or CUDA tensor."""
+    if hasattr(points, "data_ptr") and hasattr(points, "is_cuda"):
+        import torch
+        if points.dim() != 2:
+            raise ValueError("points must be (n, d)")
+        if points.dtype == torch.float64:
+            code = RTG_DTYPE_F64
+        elif points.dtype == torch.float32:
+            code = RTG_DTYPE_F32
+        else:
+            raise TypeError("points must be float64 or float32")
+        p = points.contiguous()
+        if not p.is_cuda:
+            p = p.numpy()
+            return p.ctypes.data, code, False, p.shape[0], p.shape[1], p
+        torch.cuda.current_stream(p.device).synchronize()
+        return p.data_ptr(), code, True, p.shape[0], p.shape[1], p
+    p = np.ascontiguousarray(points)
+    if p.ndim != 2:
+        raise ValueError("points must be (n, d)")
+    if p.dtype == np.float64:
+        code = RTG_DTYPE_F64
+    elif p.dtype == np.float32:
+        code = RTG_DTYPE_F32
+    else:
+        raise TypeError("points must be float64 or float32")
+    return p.ctypes.data, code, False, p.shape[0], p.shape[1], p
+
+
+class Result:
+    """A device CSR owned by the library; ``download()`` copies it to numpy."""
+
+    def __init__(self, ctx: "Context", csr: rtg_csr, m: int):
+        self._ctx = ctx
+        self.csr = csr
+        self.m = m
+
+    @property
+    def n(self) -> int:
+        return int(self.csr.n)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.csr.nnz)
+
+    @property
+    def stats(self) -> dict:
+        return stats_dict(self.csr.stats, self.m)
+
+    def download(self):
+        return rtg_csr_download(self._ctx.handle, self.csr)
+
+    def release(self):
+        if self.csr.handle:
+            rtg_release(self._ctx.handle, self.csr)
+
+    def __del__(self):
+        try:
+            if self._ctx.handle is not None and self.csr.handle:
+                lib().rtg_release(self._ctx.handle, ctypes.byref(self.csr))
+        except Exception:
+            pass
+
+
+class Context:
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: int | None = None):
+        self.handle = rtg_create(device, mem_budget_bytes, stream)
+
+    def close(self):
+        if self.handle is not None:
+            rtg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def all_pairs(self, points, r: float, transforms: np.ndarray, cell_side: float,
+                  symmetric: bool = False, timing: bool = False) -> Result:
+        ptr, code, on_dev, n, d, keep = _points_arg(points)
+        T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
+        if T.size % (d * d + d) != 0:
+            raise ValueError("transforms must hold m * (d*d + d) values")
+        m = T.size // (d * d + d)
+        flags = (RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0)
+        csr = rtg_all_pairs(self.handle, ptr, code, on_dev, n, d, float(r), T, m,
+                            float(cell_side), flags)
+        del keep
+        return Result(self, csr, m)
+
+    def brute_force(self, points, r: float, symmetric: bool = False,
+                    count_only: bool = False) -> Result:
+        """Exact set of Sec. I on the device (all pairs checked)."""
+        ptr, code, on_dev, n, d, keep = _points_arg(points)
+        flags = RTG_FLAG_SYMMETRIC if symmetric else 0
+        csr = rtg_brute_force(self.handle, ptr, code, on_dev, n, d, float(r), flags, count_only)
+        del keep
+        return Result(self, csr, 0)

@@ -1,0 +1,239 @@
+"""GPU library vs the CPU oracle, element by element, through the C ABI.
+
+The bar is bit-exact equality of the CSR (row pointers and columns) and of the exact
+integer statistics (per-grid candidate counts, largest cell, near-wall and near-r counts)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1409_8112_gb300 import gen, rtg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rtg.Context(0)
+    yield c
+    c.close()
+
+
+def run_and_compare(ctx, pts, r, T, c, symmetric=False, on_device=False, check_stats=True):
+    arg = pts
+    if on_device:
+        import torch
+        arg = torch.from_numpy(pts).cuda()
+    res = ctx.all_pairs(arg, r, T, c, symmetric=symmetric)
+    rp, col = res.download()
+    ref = oracle.rtg(pts, r, T, c)
+    want_rp, want_col = ref.csr.row_ptr, ref.csr.col
+    if symmetric:
+        p = ref.csr.pairs()
+        both = np.concatenate([p, p[:, ::-1]])
+        order = np.lexsort((both[:, 1], both[:, 0]))
+        both = both[order]
+        want_rp = np.zeros(len(pts) + 1, dtype=np.int64)
+        np.add.at(want_rp, both[:, 0] + 1, 1)
+        want_rp = np.cumsum(want_rp)
+        want_col = both[:, 1].astype(np.int32)
+    assert len(rp) == len(want_rp)
+    assert np.array_equal(rp, want_rp), "row pointers differ"
+    assert np.array_equal(col, want_col), "columns differ"
+    st = res.stats
+    if check_stats:
+        m = len(ref.stats)
+        assert st["candidates"] == [s["candidates"] for s in ref.stats]
+        assert st["max_cell"] == max(s["max_cell"] for s in ref.stats)
+        assert st["near_wall"] == sum(s["near_wall"] for s in ref.stats)
+        assert st["near_r"] == ref.near_r
+        assert st["pairs"] == ref.csr.nnz
+        assert len(st["candidates"]) == m
+    res.release()
+    return st, ref
+
+
+def test_config1_n2000_d3(ctx):
+    pts = gen.points_uniform(0, 2000, 3)
+    T = gen.transforms(0, 3, 5, 0.1)
+    st, ref = run_and_compare(ctx, pts, 0.1, T, 0.1)
+    assert ref.csr.nnz > 4000
+
+
+def test_config2_n100k_d6(ctx):
+    n, d, m = 100000, 6, 8
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(0, n, d)
+    T = gen.transforms(0, d, m, r)
+    st, ref = run_and_compare(ctx, pts, r, T, r)
+    assert ref.csr.nnz > 400000
+
+
+def test_config2_points_on_device_and_symmetric(ctx):
+    n, d, m = 20000, 6, 8
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(3, n, d)
+    T = gen.transforms(3, d, m, r)
+    run_and_compare(ctx, pts, r, T, r, on_device=True)
+    run_and_compare(ctx, pts, r, T, r, symmetric=True, check_stats=False)
+
+
+def test_fp32_points(ctx):
+    n, d, m = 200000, 6, 8
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(1, n, d, np.float32)
+    T = gen.transforms(1, d, m, r)
+    run_and_compare(ctx, pts, r, T, r)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 8, 9, 12, 16])
+def test_dimensions(ctx, d):
+    n = 3001
+    r = gen.radius_for_degree(n, d, 10.0)
+    pts = gen.points_uniform(10 + d, n, d)
+    T = gen.transforms(20 + d, d, 4, 1.3 * r)
+    run_and_compare(ctx, pts, r, T, 1.3 * r)
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 64])
+def test_grid_counts(ctx, m):
+    n, d = 5000, 3
+    r = gen.radius_for_degree(n, d, 12.0)
+    pts = gen.points_uniform(5, n, d)
+    T = gen.transforms(6, d, m, r)
+    run_and_compare(ctx, pts, r, T, r)
+
+
+def test_shift_only_table2_parameters(ctx):
+    n, d, m, ct = 12800, 3, 20, 1.15
+    r = gen.radius_fmt(n, d)
+    pts = gen.points_uniform(1000, n, d)
+    T = gen.transforms(2000, d, m, ct * r, flags=gen.SHIFT_ONLY)
+    run_and_compare(ctx, pts, r, T, ct * r)
+
+
+def test_clustered_points_use_large_cells(ctx):
+    # a Gaussian mixture with sigma well below the cell side gives cells of hundreds of points
+    n, d, m = 20000, 3, 4
+    pts = gen.points_mixture(9, n, d, k=4, sigma=0.01, dtype=np.float64)
+    r = 0.05
+    T = gen.transforms(9, d, m, r)
+    st, ref = run_and_compare(ctx, pts, r, T, r)
+    assert st["large_cells"] > 0 and st["max_cell"] > 128
+
+
+def test_all_points_identical(ctx):
+    pts = np.full((700, 4), 0.3)
+    T = gen.transforms(2, 4, 3, 0.1)
+    st, ref = run_and_compare(ctx, pts, 0.1, T, 0.1)
+    assert ref.csr.nnz == 700 * 699 // 2
+
+
+def test_single_cell_equals_brute_force(ctx):
+    n, d = 3000, 3
+    pts = gen.points_uniform(4, n, d)
+    c = 8.0 * np.sqrt(d)
+    T = gen.transforms(4, d, 2, c)
+    T[:, d * d:] = c / 2
+    r = 0.08
+    res = ctx.all_pairs(pts, r, T, c)
+    rp, col = res.download()
+    ex = oracle.brute(pts, r)
+    assert np.array_equal(rp, ex.row_ptr) and np.array_equal(col, ex.col)
+
+
+def test_wide_keys_use_64_bits(ctx):
+    n, d, m = 4000, 6, 3
+    pts = gen.points_uniform(8, n, d)
+    r = 0.02
+    T = gen.transforms(8, d, m, r)
+    st, _ = run_and_compare(ctx, pts, r, T, r)
+    assert st["key_bits"] > 32
+
+
+def test_offset_and_negative_coordinates(ctx):
+    n, d = 8000, 4
+    pts = gen.points_uniform(12, n, d) * 3.0 - 17.5
+    r = 0.3
+    T = gen.transforms(12, d, 5, 1.2 * r)
+    run_and_compare(ctx, pts, r, T, 1.2 * r)
+
+
+def test_walls_and_exact_radius_go_through_fp64(ctx):
+    # dyadic points on a 1/8 lattice: every coordinate lies on a wall of the shift-only
+    # grid with zero shift, and many pairs are exactly at distance r = 0.625
+    g = np.arange(0, 1, 0.125)
+    pts = np.array(np.meshgrid(g, g, g)).reshape(3, -1).T.copy()
+    T = np.array([[1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0]], dtype=np.float64)
+    T = np.concatenate([T, gen.transforms(3, 3, 2, 0.625)])
+    st, ref = run_and_compare(ctx, pts, 0.625, T, 0.625)
+    assert st["near_wall"] > 0 and st["near_r"] > 0
+
+
+def test_empty_and_tiny_inputs(ctx):
+    T = gen.transforms(1, 3, 2, 0.1)
+    for n in (0, 1, 2, 3, 33):
+        pts = gen.points_uniform(n, n, 3) * 0.05
+        run_and_compare(ctx, pts, 0.1, T, 0.1)
+
+
+def test_errors(ctx):
+    T = gen.transforms(1, 3, 2, 0.1)
+    pts = gen.points_uniform(0, 100, 3)
+    bad = pts.copy()
+    bad[5, 1] = np.nan
+    with pytest.raises(rtg.RTGError) as e:
+        ctx.all_pairs(bad, 0.1, T, 0.1)
+    assert e.value.status == rtg.RTG_E_INVALID
+    with pytest.raises(rtg.RTGError) as e:
+        ctx.all_pairs(pts, -0.1, T, 0.1)
+    assert e.value.status == rtg.RTG_E_INVALID
+    d = 16
+    T16 = gen.transforms(1, d, 2, 1e-3)
+    with pytest.raises(rtg.RTGError) as e:
+        ctx.all_pairs(gen.points_uniform(0, 100, d), 1e-3, T16, 1e-3)
+    assert e.value.status == rtg.RTG_E_KEY_OVERFLOW
+    # the context stays usable after every error
+    run_and_compare(ctx, pts, 0.1, T, 0.1)
+
+
+def test_budget():
+    small = rtg.Context(0, mem_budget_bytes=1 << 16)
+    pts = gen.points_uniform(0, 20000, 3)
+    T = gen.transforms(1, 3, 4, 0.05)
+    with pytest.raises(rtg.RTGError) as e:
+        small.all_pairs(pts, 0.05, T, 0.05)
+    assert e.value.status == rtg.RTG_E_BUDGET
+    small.close()
+
+
+def test_repeatable(ctx):
+    n, d = 30000, 6
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(2, n, d)
+    T = gen.transforms(2, d, 8, r)
+    a = ctx.all_pairs(pts, r, T, r).download()
+    b = ctx.all_pairs(pts, r, T, r).download()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("d,n", [(1, 2000), (3, 3001), (6, 4099), (12, 2500)])
+def test_brute_force_matches_oracle(ctx, d, n):
+    pts = gen.points_uniform(40 + d, n, d)
+    r = gen.radius_for_degree(n, d, 15.0)
+    res = ctx.brute_force(pts, r)
+    rp, col = res.download()
+    ex = oracle.brute(pts, r)
+    assert np.array_equal(rp, ex.row_ptr) and np.array_equal(col, ex.col)
+    assert res.stats["pairs"] == ex.nnz
+
+
+def test_brute_force_count_config2_and_recall(ctx):
+    n, d, m = 100000, 6, 8
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(0, n, d)
+    cnt = ctx.brute_force(pts, r, count_only=True)
+    ex = oracle.exact_grid(pts, r)
+    assert cnt.nnz == ex.nnz
+    T = gen.transforms(0, d, m, r)
+    res = ctx.all_pairs(pts, r, T, r)
+    assert 0.5 < res.nnz / cnt.nnz < 0.6

@@ -197,7 +197,7 @@ def test_errors(ctx):
 
 
 def test_budget():
-    small = rtg.Context(0, mem_budget_bytes=1 << 16)
+    small = rtg.Context(0, mem_budget_bytes=1 << 20)
     pts = gen.points_uniform(0, 20000, 3)
     T = gen.transforms(1, 3, 4, 0.05)
     with pytest.raises(rtg.RTGError) as e:

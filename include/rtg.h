@@ -147,6 +147,27 @@ rtg_status rtg_brute_force(rtg_ctx* ctx, const void* points, int dtype, int poin
                            int64_t n, int d, double r, uint32_t flags, int count_only,
                            rtg_csr* out);
 
+/* Exact pair count without any device allocation.  The paper has no counterpart: this is for
+ * callers that cannot allocate device memory, such as a planner's control loop that runs
+ * under a fixed memory plan or a latency budget, or a plug-in inside a host application that
+ * owns every device allocation (rtg_create itself allocates, so such callers have no
+ * context).  It counts the pairs {i, j} with s <= fl(r * r) (the same set and arithmetic as
+ * rtg_brute_force) and writes the count to *count (host).
+ *   points  device pointer, n x d row-major, dtype RTG_DTYPE_F64 or RTG_DTYPE_F32, n <= 65536
+ *   stream  cudaStream_t to run on (NULL = legacy default stream); the call synchronises it
+ * Scratch: one file-scope device array of about 4.4 MiB (status counters, plan, FP32 rows of
+ * up to 65536 points with d <= 16, row counts), held by every GPU that loads the library
+ * until the process exits.  The first call on a device, with that device current, looks up
+ * the array's device address; make that first call before any stream capture.  Every call on
+ * a device shares the array and leaves its contents behind: calls that overlap on the GPU
+ * (from different streams or threads) race and give undefined counts.  Nothing here calls
+ * cudaMalloc, cudaFree or an allocating library routine.
+ * Errors: RTG_E_INVALID (n > 65536, d outside [1,16], r not positive and finite, NULL
+ * pointers, a non-finite coordinate), RTG_E_CUDA, RTG_E_TIMEOUT; text via
+ * rtg_last_error(NULL). */
+rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int64_t n, int d, double r,
+                                   void* stream, uint64_t* count);
+
 /* Free the device memory of a CSR returned by this context and zero *csr. */
 rtg_status rtg_release(rtg_ctx* ctx, rtg_csr* csr);
 

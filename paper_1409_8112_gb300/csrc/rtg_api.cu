@@ -29,6 +29,8 @@ struct DevBuf {
 
 }  // namespace
 
+void rtg::set_last_error(const char* msg) { g_err = msg; }
+
 struct rtg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

@@ -164,4 +164,7 @@ int launch_rowsort(const BuildArgs& a, cudaStream_t s);
 
 size_t sort_tiles_for(long long N, bool key64);
 
+// Text returned by rtg_last_error(NULL) on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace rtg

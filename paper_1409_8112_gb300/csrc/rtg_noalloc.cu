@@ -1,0 +1,103 @@
+// Exact pair count for callers that cannot allocate device memory.
+//
+// A motion-planning control loop that runs under a fixed memory plan or a hard latency
+// budget, or a plug-in that lives inside a host application which owns every device
+// allocation, cannot call cudaMalloc (nor create an rtg_ctx, which allocates).  For them,
+// rtg_brute_count_noalloc counts the pairs at distance <= r with the same kernels as
+// rtg_brute_force, but its scratch (status counters, plan, FP32 point rows, row counts) is one
+// file-scope device array of fixed size, held by every GPU that loads the library until the
+// process exits.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "rtg.h"
+#include "rtg_internal.cuh"
+
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = 65536;
+constexpr size_t kStatusBytes = (sizeof(rtg::Status) + 255) & ~size_t(255);
+constexpr size_t kPlanBytes = (sizeof(rtg::Plan) + 255) & ~size_t(255);
+constexpr size_t kRowsBytes = (size_t)kNoAllocMaxPoints * rtg::kMaxDim * 4;  // FP32 rows, dpad <= 16
+constexpr size_t kCountBytes = (size_t)kNoAllocMaxPoints * 4;
+constexpr size_t kScratchBytes = kStatusBytes + kPlanBytes + kRowsBytes + kCountBytes;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// the message is readable with rtg_last_error(NULL)
+rtg_status fail(rtg_status s, const char* msg) {
+  rtg::set_last_error(msg);
+  return s;
+}
+
+}  // namespace
+
+extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int64_t n, int d,
+                                              double r, void* stream, uint64_t* count) {
+  if (!count) return fail(RTG_E_INVALID, "count is NULL");
+  if (dtype != RTG_DTYPE_F64 && dtype != RTG_DTYPE_F32) return fail(RTG_E_INVALID, "bad dtype");
+  if (n < 0 || n > kNoAllocMaxPoints)
+    return fail(RTG_E_INVALID, "n exceeds the 65536-point limit of the static scratch");
+  if (d < 1 || d > RTG_MAX_DIM) return fail(RTG_E_INVALID, "d must be in [1, 16]");
+  if (!(r > 0.0) || !std::isfinite(r)) return fail(RTG_E_INVALID, "r must be > 0 and finite");
+  if (n > 0 && !points) return fail(RTG_E_INVALID, "points is NULL");
+  *count = 0;
+  if (n < 2) return RTG_OK;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail(RTG_E_CUDA, "no current CUDA device");
+  void* base = nullptr;
+  {
+    // once per device, with that device current: the device address of the scratch array
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+      if (e != cudaSuccess) return fail(RTG_E_CUDA, cudaGetErrorString(e));
+      g_scratch_addr[dev] = p;
+    }
+    base = g_scratch_addr[dev];
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(RTG_E_CUDA, "cudaDeviceGetAttribute failed");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  rtg::BuildArgs a{};
+  a.pts = points;
+  a.dtype = dtype;
+  a.n = (int)n;
+  a.d = d;
+  a.m = 0;
+  a.dpad = rtg::dpad_for(d);
+  a.r = r;
+  a.c = 1.0;
+  a.st = (rtg::Status*)base;
+  a.plan = (rtg::Plan*)((char*)base + kStatusBytes);
+  a.pf = (float*)((char*)base + kStatusBytes + kPlanBytes);
+  a.row_cnt = (unsigned int*)((char*)base + kStatusBytes + kPlanBytes + kRowsBytes);
+  a.num_sms = sms;
+  // the counters and the bounding box must start at zero; every other region is fully
+  // rewritten (plan, point rows) or only incremented and never read (row counts)
+  if (cudaMemsetAsync(a.st, 0, sizeof(rtg::Status), s) != cudaSuccess)
+    return fail(RTG_E_CUDA, "cudaMemsetAsync failed");
+  rtg::launch_prep(a, s);
+  rtg::launch_plan(a, 64, s);
+  rtg::launch_brute(a, false, s);
+  rtg::Status h;
+  cudaError_t e = cudaMemcpyAsync(&h, a.st, sizeof(rtg::Status), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(RTG_E_CUDA, cudaGetErrorString(e));
+  if (h.errors & rtg::kErrNonFinite) return fail(RTG_E_INVALID, "non-finite point coordinate");
+  if (h.errors & rtg::kErrTimeout) return fail(RTG_E_TIMEOUT, "a bounded device wait ran out");
+  if (h.errors) return fail(RTG_E_INTERNAL, "device error flags set");
+  *count = h.pairs;
+  return RTG_OK;
+}

@@ -87,6 +87,9 @@ _SIGNATURES = {
                                        ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_uint32, ctypes.c_int,
                                        ctypes.POINTER(rtg_csr)]),
+    "rtg_brute_count_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                               ctypes.POINTER(ctypes.c_uint64)]),
     "rtg_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr)]),
     "rtg_csr_download": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
                                         ctypes.c_void_p, ctypes.c_void_p]),
@@ -160,6 +163,15 @@ def rtg_brute_force(ctx, points_ptr: int, dtype: int, on_device: bool, n: int, d
                                1 if count_only else 0, ctypes.byref(out))
     _check(st, ctx)
     return out
+
+
+def rtg_brute_count_noalloc(points_ptr: int, dtype: int, n: int, d: int, r: float,
+                            stream: int | None = None) -> int:
+    """Exact pair count with no device allocation (static scratch; n <= 65536)."""
+    out = ctypes.c_uint64(0)
+    _check(lib().rtg_brute_count_noalloc(points_ptr, dtype, n, d, r, stream or None,
+                                         ctypes.byref(out)))
+    return int(out.value)
 
 
 def rtg_release(ctx, csr: rtg_csr) -> None:

@@ -1,0 +1,41 @@
+"""rtg_brute_count_noalloc (the entry point for callers that cannot allocate device memory,
+e.g. a planner loop under a fixed memory plan) against rtg_brute_force's exact count.
+
+Kept in a file of its own that pytest collects last, so a run that stops at the first
+failure has already run every other test.  It must pass alone in a fresh process too."""
+import numpy as np
+import pytest
+
+from paper_1409_8112_gb300 import gen, rtg
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_count_matches_brute_force_on_consecutive_calls():
+    import torch
+
+    stream = torch.cuda.current_stream()
+    # two calls in a row on different inputs (the second smaller, so stale scratch from the
+    # first call would show), each against the existing entry point
+    cases = [(60000, 6, np.float64, 1), (9000, 3, np.float32, 2)]
+    with rtg.Context(0) as ctx:
+        for n, d, dt, seed in cases:
+            pts = gen.points_uniform(seed, n, d, dt)
+            r = gen.radius_for_degree(n, d, 12.0)
+            dev = torch.from_numpy(pts).cuda()
+            stream.synchronize()
+            code = rtg.RTG_DTYPE_F64 if dt == np.float64 else rtg.RTG_DTYPE_F32
+            got = rtg.rtg_brute_count_noalloc(dev.data_ptr(), code, n, d, r, stream.cuda_stream)
+            ref = ctx.brute_force(dev, r, count_only=True)
+            assert got == ref.nnz and got > 0
+            ref.release()
+
+
+def test_noalloc_rejects_sizes_beyond_the_static_limit():
+    import torch
+
+    dev = torch.zeros((65537, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(rtg.RTGError) as e:
+        rtg.rtg_brute_count_noalloc(dev.data_ptr(), rtg.RTG_DTYPE_F64, 65537, 3, 0.1)
+    assert e.value.status == rtg.RTG_E_INVALID
+    assert "65536" in rtg.lib().rtg_last_error(None).decode()

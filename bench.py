@@ -117,12 +117,13 @@ def measured_peaks():
 
 # Algorithmic bytes per build for each timed phase (lower-bound model):
 #   sort  : upfront histogram reads the N keys once; each pass reads and writes N (key, index)
-#   count : reads the N sorted (key, index) pairs and gathers each point's padded FP32 row
-def phase_bytes(n, d, m, key_bytes, passes, dpad):
+#   pairs : reads the N sorted (key, index) pairs, gathers each point's padded FP32 row and
+#           writes 8 bytes per reported pair
+def phase_bytes(n, d, m, key_bytes, passes, dpad, pairs):
     N = n * m
     return {
         "sort": N * key_bytes + passes * 2 * N * (key_bytes + 4),
-        "count": N * (key_bytes + 4) + N * dpad * 4,
+        "pairs": N * (key_bytes + 4) + N * dpad * 4 + 8 * pairs,
     }
 
 
@@ -206,7 +207,7 @@ def run_ours(args):
 
     # roofline of the dominant phase (per-phase device events over the timed region)
     mean_phase = {p: float(np.mean([ph[p] for ph in phases])) for p in phases[0]}
-    pb = phase_bytes(n, d, m, key_bytes, passes, 8 if d <= 8 else 16)
+    pb = phase_bytes(n, d, m, key_bytes, passes, 8 if d <= 8 else 16, pairs)
     dom = max(pb, key=lambda p: mean_phase[p])
     peak, peak_kind = measured_peaks()
     achieved = pb[dom] / (mean_phase[dom] * 1e-6) / 1e9

@@ -54,6 +54,8 @@ typedef enum {
 #define RTG_FLAG_SHIFT_ONLY 1u /* rtg_transforms_generate: R = identity (Alg. 1 as printed) */
 #define RTG_FLAG_SYMMETRIC 2u  /* rtg_all_pairs: store (i,j) and (j,i) */
 #define RTG_FLAG_TIMING 4u     /* rtg_all_pairs: fill rtg_stats.phase_us (adds events) */
+#define RTG_FLAG_TWO_PASS 8u   /* enumerate twice (count, then write in place) instead of
+                                  holding a pair buffer: less memory, more time */
 
 /* Point coordinate types. */
 #define RTG_DTYPE_F64 0
@@ -86,9 +88,9 @@ typedef struct {
   int32_t key_bits;      /* bits of the (grid, cell) sort key */
   int32_t sort_passes;   /* radix passes run */
   int32_t launches;      /* kernels this build launched */
-  int32_t reserved;
-  double phase_us[8];    /* with RTG_FLAG_TIMING: prep, key, sort, count, scan, write,
-                            rowsort, total (microseconds, device events) */
+  int32_t attempts;      /* 1, or more when a launch assumption had to be corrected */
+  double phase_us[8];    /* with RTG_FLAG_TIMING: prep+plan, keys, sort, pairs, scan,
+                            scatter (or write), rowsort, total (microseconds, device events) */
 } rtg_stats;
 
 typedef struct {
@@ -100,6 +102,16 @@ typedef struct {
   uint64_t handle;   /* library bookkeeping; 0 = empty */
   rtg_stats stats;
 } rtg_csr;
+
+/* One roadmap of a batch. */
+typedef struct {
+  const void* points;        /* n x d row-major (host or device, as the call says) */
+  int64_t n;
+  int d;                     /* in [1, 16] */
+  double r;                  /* reporting radius */
+  double cell_side;          /* grid cell side c */
+  const double* transforms;  /* host, m*(d*d+d) doubles (R_t row-major, then s_t) */
+} rtg_instance;
 
 /* Create a context on cfg->device.  *out receives the context or NULL on failure. */
 rtg_status rtg_create(const rtg_config* cfg, rtg_ctx** out);
@@ -137,6 +149,18 @@ rtg_status rtg_transforms_generate(uint64_t seed, int d, int m, double cell_side
 rtg_status rtg_all_pairs(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
                          int64_t n, int d, double r, const double* transforms, int m,
                          double cell_side, uint32_t flags, rtg_csr* out);
+
+/* Alg. 1 (Sec. III) for a batch of independent roadmaps in one build (one sequence of kernel
+ * launches for all of them): every instance has its own points, n, d, r, cell side and m
+ * transforms (m, dtype and points_on_device are common).  out receives the block-diagonal
+ * CSR over the concatenated points: instance b owns rows and columns
+ * [row_offsets[b], row_offsets[b+1]), and its block is exactly what rtg_all_pairs returns
+ * for it alone, shifted by row_offsets[b].  row_offsets (host, count + 1 entries) may be
+ * NULL.  Errors as rtg_all_pairs; RTG_E_INVALID also for count outside [1, 65535] or
+ * sum(n) * m >= 2^31. */
+rtg_status rtg_batch_all_pairs(rtg_ctx* ctx, const rtg_instance* items, int count, int m,
+                               int dtype, int points_on_device, uint32_t flags, rtg_csr* out,
+                               int64_t* row_offsets);
 
 /* The exact all-pairs r-NN set of Sec. I (every pair {i, j} with s <= fl(r * r), s as in
  * the arithmetic contract above) by checking all n(n-1)/2 pairs on the device in tiles; the

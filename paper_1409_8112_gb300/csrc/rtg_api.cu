@@ -1,21 +1,33 @@
 // C ABI of the RTG library (declared in include/rtg.h): contexts, workspace, and the
-// orchestration of one build of Alg. 1 (arXiv:1409.8112, Sec. III) on the device.
+// orchestration of one build of Alg. 1 (arXiv:1409.8112, Sec. III) for a batch of roadmaps.
+//
+// A build is one fixed sequence of kernels on the context's stream with a single host
+// synchronisation at the end.  Three launch decisions depend on the data: the key width
+// (32 or 64 bits), the number of radix passes and the size of the pair buffer.  They are
+// taken from the last build of the same shape; the device checks them (kErrKeyBits,
+// kErrPairOverflow) and on a miss the build is run again with the values the device
+// reported.  The first build of a shape reads the key width back once before sorting.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <unordered_map>
+#include <vector>
 
 #include "gen/rtg_gen.h"
 #include "rtg.h"
 #include "rtg_internal.cuh"
 
 using rtg::BuildArgs;
-using rtg::Plan;
+using rtg::GridPlan;
+using rtg::Inst;
+using rtg::InstPlan;
 using rtg::Status;
 
 namespace {
@@ -25,6 +37,14 @@ thread_local std::string g_err;
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
+};
+
+// Launch decisions remembered per shape (sum n, instances, grids, dtype, widest d, flags).
+using ShapeKey = std::tuple<long long, int, int, int, int, int, int>;
+struct ShapeGuess {
+  bool key64 = true;
+  int passes = rtg::kMaxPasses;
+  long long pair_cap = 0;
 };
 
 }  // namespace
@@ -39,8 +59,8 @@ struct rtg_ctx {
   int num_sms = 0;
   std::mutex mu;
   std::string err;
-  DevBuf status_plan, T64, pts, pf, key_mat, keys0, keys1, vals0, vals1, lookback, hist,
-      digit_off, row_cnt, scan_lb, large, large_job;
+  DevBuf status, inst, iplan, gplan, bases, bbox, T64, pts, pf, key_mat, keys0, keys1, vals0,
+      vals1, lookback, hist, digit_off, row_cnt, scan_lb, large, large_job, pair_buf;
   Status* h_status = nullptr;  // pinned
   cudaEvent_t ev[8] = {};
   unsigned int epoch = 1;
@@ -48,6 +68,9 @@ struct rtg_ctx {
   size_t out_bytes = 0;
   uint64_t next_handle = 1;
   std::unordered_map<uint64_t, size_t> live;  // CSR handle -> bytes
+  std::map<ShapeKey, ShapeGuess> guesses;
+  std::vector<Inst> h_inst;
+  std::vector<double> h_T;
 };
 
 namespace {
@@ -76,6 +99,7 @@ rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
     return fail(c, RTG_E_BUDGET, "workspace of " + std::to_string(bytes) +
                                      " bytes exceeds the memory budget");
   if (b.p) {
+    cudaStreamSynchronize(c->stream);
     cudaFree(b.p);
     c->ws_bytes -= b.cap;
     b.p = nullptr;
@@ -108,8 +132,8 @@ rtg_status alloc_out(rtg_ctx* c, size_t bytes, void** p) {
 }
 
 rtg_status read_status(rtg_ctx* c) {
-  RTG_CUDA(c, cudaMemcpyAsync(c->h_status, c->status_plan.p, sizeof(Status),
-                              cudaMemcpyDeviceToHost, c->stream));
+  RTG_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(Status), cudaMemcpyDeviceToHost,
+                              c->stream));
   RTG_CUDA(c, cudaStreamSynchronize(c->stream));
   return RTG_OK;
 }
@@ -119,7 +143,7 @@ rtg_status check_errors(rtg_ctx* c, unsigned int mask) {
   if (!e) return RTG_OK;
   if (e & rtg::kErrNonFinite) return fail(c, RTG_E_INVALID, "non-finite point coordinate");
   if (e & rtg::kErrKeyOverflow)
-    return fail(c, RTG_E_KEY_OVERFLOW, "cell index range of a grid needs more than 64 bits");
+    return fail(c, RTG_E_KEY_OVERFLOW, "the cell index ranges need more than 64 key bits");
   if (e & rtg::kErrTimeout) return fail(c, RTG_E_TIMEOUT, "a bounded device wait ran out");
   if (e & rtg::kErrKeyRange)
     return fail(c, RTG_E_INTERNAL, "a cell index fell outside the planned key range");
@@ -139,23 +163,359 @@ void release_out(rtg_ctx* c, rtg_csr* csr) {
   std::memset(csr, 0, sizeof(*csr));
 }
 
-rtg_status validate(int dtype, int64_t n, int d, double r, const double* T, int m, double c,
-                    const void* points) {
+rtg_status validate_common(int dtype, int64_t n, int d, double r, double c, const void* points) {
   if (dtype != RTG_DTYPE_F64 && dtype != RTG_DTYPE_F32)
     return fail(nullptr, RTG_E_INVALID, "dtype must be RTG_DTYPE_F64 or RTG_DTYPE_F32");
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(nullptr, RTG_E_INVALID, "n out of range");
   if (d < 1 || d > RTG_MAX_DIM) return fail(nullptr, RTG_E_INVALID, "d must be in [1, 16]");
-  if (m < 1 || m > RTG_MAX_GRIDS) return fail(nullptr, RTG_E_INVALID, "m must be in [1, 64]");
   if (!(r > 0.0) || !std::isfinite(r)) return fail(nullptr, RTG_E_INVALID, "r must be > 0");
   if (!(c > 0.0) || !std::isfinite(c)) return fail(nullptr, RTG_E_INVALID, "cell_side must be > 0");
-  if (!T) return fail(nullptr, RTG_E_INVALID, "transforms is NULL");
   if (n > 0 && !points) return fail(nullptr, RTG_E_INVALID, "points is NULL");
+  return RTG_OK;
+}
+
+rtg_status validate_transforms(const double* T, int d, int m) {
+  if (!T) return fail(nullptr, RTG_E_INVALID, "transforms is NULL");
   const size_t tn = (size_t)m * (d * d + d);
   for (size_t x = 0; x < tn; ++x)
     if (!std::isfinite(T[x])) return fail(nullptr, RTG_E_INVALID, "non-finite transform entry");
-  if ((int64_t)n * m >= (int64_t(1) << 31))
-    return fail(nullptr, RTG_E_INVALID, "n * m must be below 2^31");
   return RTG_OK;
+}
+
+struct Request {
+  const rtg_instance* items;
+  int count;
+  int m;  // 0: brute force (count must be 1)
+  int dtype;
+  int points_on_device;
+  uint32_t flags;
+  bool count_only;
+};
+
+// The whole build.  On success *out holds the block-diagonal CSR of the batch.
+rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
+  cudaStream_t st = c->stream;
+  const bool timing = (q.flags & RTG_FLAG_TIMING) != 0;
+  const int sym = (q.flags & RTG_FLAG_SYMMETRIC) ? 1 : 0;
+  const int B = q.count, m = q.m;
+  const size_t esz = q.dtype == RTG_DTYPE_F64 ? 8 : 4;
+  rtg_status s;
+
+  // ---- instance table and packed transforms (host) ----
+  c->h_inst.assign(B, Inst{});
+  long long p0 = 0, blk0 = 0, T0 = 0;
+  int maxd = 1;
+  for (int b = 0; b < B; ++b) {
+    const rtg_instance& it = q.items[b];
+    Inst& I = c->h_inst[b];
+    I.pts = it.points;
+    I.p0 = p0;
+    I.T0 = T0;
+    I.n = (int)it.n;
+    I.d = it.d;
+    I.r = it.r;
+    I.c = m > 0 ? it.cell_side : 1.0;
+    I.blk0 = blk0;
+    p0 += it.n;
+    blk0 += (it.n + rtg::kPointBlock - 1) / rtg::kPointBlock;
+    T0 += (long long)m * (it.d * it.d + it.d);
+    maxd = std::max(maxd, it.d);
+  }
+  const long long n_total = p0;
+  out->n = n_total;
+  out->symmetric = sym;
+  if (n_total * std::max(m, 1) >= (1LL << 31))
+    return fail(c, RTG_E_INVALID, "total points times grids must be below 2^31");
+  if (m > 0 && B * (long long)m > 65535)
+    return fail(c, RTG_E_INVALID, "instances times grids must be at most 65535");
+  if (n_total == 0) {
+    void* rp = nullptr;
+    if ((s = alloc_out(c, sizeof(int64_t), &rp)) != RTG_OK) return s;
+    RTG_CUDA(c, cudaMemsetAsync(rp, 0, sizeof(int64_t), st));
+    RTG_CUDA(c, cudaStreamSynchronize(st));
+    out->row_ptr = (int64_t*)rp;
+    out->handle = c->next_handle++;
+    c->live[out->handle] = sizeof(int64_t);
+    return RTG_OK;
+  }
+  const int dpad = rtg::dpad_for(maxd);
+  const long long N = n_total * m;
+  if (m > 0) {
+    c->h_T.resize((size_t)T0);
+    for (int b = 0; b < B; ++b) {
+      const rtg_instance& it = q.items[b];
+      std::memcpy(c->h_T.data() + c->h_inst[b].T0, it.transforms,
+                  sizeof(double) * (size_t)m * (it.d * it.d + it.d));
+    }
+  }
+
+  // ---- workspace ----
+  const size_t stat_bytes = (sizeof(Status) + 255) & ~size_t(255);
+  if ((s = ensure(c, c->status, stat_bytes)) != RTG_OK) return s;
+  if ((s = ensure(c, c->inst, sizeof(Inst) * B)) != RTG_OK) return s;
+  if ((s = ensure(c, c->iplan, sizeof(InstPlan) * B)) != RTG_OK) return s;
+  if ((s = ensure(c, c->bbox, sizeof(unsigned long long) * B * rtg::kMaxDim * 2)) != RTG_OK) return s;
+  if (m > 0) {
+    if ((s = ensure(c, c->gplan, sizeof(GridPlan) * (size_t)B * m)) != RTG_OK) return s;
+    if ((s = ensure(c, c->bases, sizeof(unsigned long long) * ((size_t)B * m + 1))) != RTG_OK) return s;
+    if ((s = ensure(c, c->T64, sizeof(double) * (size_t)T0)) != RTG_OK) return s;
+  }
+  if ((s = ensure(c, c->pf, (size_t)n_total * dpad * 4)) != RTG_OK) return s;
+  if ((s = ensure(c, c->row_cnt, (size_t)n_total * 4)) != RTG_OK) return s;
+  if ((s = ensure(c, c->scan_lb, ((size_t)n_total / 4096 + 2) * 8)) != RTG_OK) return s;
+  if (!q.points_on_device) {
+    if ((s = ensure(c, c->pts, (size_t)n_total * maxd * esz + 16 * (size_t)B)) != RTG_OK) return s;
+    size_t off = 0;
+    for (int b = 0; b < B; ++b) {
+      const size_t bytes = (size_t)q.items[b].n * q.items[b].d * esz;
+      if (bytes)
+        RTG_CUDA(c, cudaMemcpyAsync((char*)c->pts.p + off, q.items[b].points, bytes,
+                                    cudaMemcpyHostToDevice, st));
+      c->h_inst[b].pts = (char*)c->pts.p + off;
+      off += (bytes + 15) & ~size_t(15);
+    }
+  }
+  RTG_CUDA(c, cudaMemcpyAsync(c->inst.p, c->h_inst.data(), sizeof(Inst) * B,
+                              cudaMemcpyHostToDevice, st));
+  if (m > 0)
+    RTG_CUDA(c, cudaMemcpyAsync(c->T64.p, c->h_T.data(), sizeof(double) * (size_t)T0,
+                                cudaMemcpyHostToDevice, st));
+
+  BuildArgs a{};
+  a.B = B;
+  a.m = m;
+  a.dtype = q.dtype;
+  a.dpad = dpad;
+  a.symmetric = sym;
+  a.n_total = n_total;
+  a.blocks = blk0;
+  a.inst = (const Inst*)c->inst.p;
+  a.iplan = (InstPlan*)c->iplan.p;
+  a.gplan = (GridPlan*)c->gplan.p;
+  a.bases = (unsigned long long*)c->bases.p;
+  a.bbox = (unsigned long long*)c->bbox.p;
+  a.T64 = (const double*)c->T64.p;
+  a.st = (Status*)c->status.p;
+  a.pf = (float*)c->pf.p;
+  a.row_cnt = (unsigned int*)c->row_cnt.p;
+  a.scan_lookback = (unsigned long long*)c->scan_lb.p;
+  a.num_sms = c->num_sms;
+
+  const ShapeKey key{n_total, B, m, q.dtype, maxd, sym, q.count_only ? 1 : 0};
+  auto git = c->guesses.find(key);
+  const bool known = git != c->guesses.end();
+  ShapeGuess g = known ? git->second : ShapeGuess{};
+  const bool two_pass_flag = (q.flags & RTG_FLAG_TWO_PASS) != 0;
+
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    int launches = 0;
+    a.key64 = g.key64;
+    a.passes = g.passes;
+    if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[0], st));
+    RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
+    RTG_CUDA(c, cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st));
+    RTG_CUDA(c, cudaMemsetAsync(a.row_cnt, 0, (size_t)n_total * 4, st));
+    rtg::launch_prep(a, st);
+    rtg::launch_plan(a, st);
+    launches += m > 0 ? 3 : 2;
+    if (m > 0 && !known && attempt == 0) {
+      // first build of this shape: read the key width back once
+      if ((s = read_status(c)) != RTG_OK) return s;
+      if ((s = check_errors(c, rtg::kErrNonFinite | rtg::kErrKeyOverflow)) != RTG_OK) return s;
+      const int bits = (int)c->h_status->sort_bits;
+      g.key64 = bits > 32;
+      g.passes = (bits + rtg::kRadixBits - 1) / rtg::kRadixBits;
+      a.key64 = g.key64;
+      a.passes = g.passes;
+    }
+    if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[1], st));
+    int sorted = 0;
+    if (m > 0) {
+      const size_t ksz = a.key64 ? 8 : 4;
+      if ((s = ensure(c, c->key_mat, (size_t)N * ksz)) != RTG_OK) return s;
+      if ((s = ensure(c, c->keys0, (size_t)N * ksz)) != RTG_OK) return s;
+      if ((s = ensure(c, c->keys1, (size_t)N * ksz)) != RTG_OK) return s;
+      if ((s = ensure(c, c->vals0, (size_t)N * 4)) != RTG_OK) return s;
+      if ((s = ensure(c, c->vals1, (size_t)N * 4)) != RTG_OK) return s;
+      if ((s = ensure(c, c->lookback, rtg::sort_tiles_for(N, a.key64) * rtg::kRadix * 8, true)) !=
+          RTG_OK)
+        return s;
+      if ((s = ensure(c, c->hist, rtg::kMaxPasses * rtg::kRadix * 4, true)) != RTG_OK) return s;
+      if ((s = ensure(c, c->digit_off, rtg::kMaxPasses * rtg::kRadix * 4)) != RTG_OK) return s;
+      const unsigned int large_cap = (unsigned int)(N / 129 + 1);
+      if ((s = ensure(c, c->large, (size_t)large_cap * sizeof(rtg::LargeCell))) != RTG_OK) return s;
+      if ((s = ensure(c, c->large_job, ((size_t)large_cap + 1) * 8)) != RTG_OK) return s;
+      a.key_mat = c->key_mat.p;
+      a.keys[0] = c->keys0.p;
+      a.keys[1] = c->keys1.p;
+      a.vals[0] = (uint32_t*)c->vals0.p;
+      a.vals[1] = (uint32_t*)c->vals1.p;
+      a.lookback = (unsigned long long*)c->lookback.p;
+      a.hist = (unsigned int*)c->hist.p;
+      a.digit_off = (unsigned int*)c->digit_off.p;
+      a.large = (rtg::LargeCell*)c->large.p;
+      a.large_cap = large_cap;
+      a.large_job_off = (unsigned long long*)c->large_job.p;
+      a.epoch = c->epoch;
+      c->epoch += rtg::kMaxPasses;
+      if ((c->epoch & 0x3fffffffu) < rtg::kMaxPasses) c->epoch = 1;
+      rtg::launch_keys(a, st);
+      launches += 1;
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
+      sorted = rtg::launch_sort(a, st);
+      launches += (a.passes > 0 && N > 1) ? 1 + a.passes : 0;
+    } else if (timing) {
+      RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
+    }
+    if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[3], st));
+
+    // output row pointers
+    void* rp = nullptr;
+    if ((s = alloc_out(c, sizeof(int64_t) * (n_total + 1), &rp)) != RTG_OK) return s;
+    out->row_ptr = (int64_t*)rp;
+    out->col = nullptr;
+    out->handle = c->next_handle++;
+    c->live[out->handle] = sizeof(int64_t) * (n_total + 1);
+    a.row_ptr = (long long*)rp;
+
+    // pair buffer for EMIT; COUNT then WRITE when asked, when only counting, or when the buffer
+    // would not fit the budget
+    if (g.pair_cap <= 0) g.pair_cap = std::max<long long>(4096, n_total * 16);
+    bool two_pass = two_pass_flag || q.count_only;
+    if (!two_pass) {
+      const size_t need = (size_t)g.pair_cap * 8;
+      if (c->budget && total_held(c) - c->pair_buf.cap + need + need / (sym ? 1 : 2) > c->budget)
+        two_pass = true;
+    }
+    auto pairs = [&](rtg::Mode mode) {
+      return m > 0 ? rtg::launch_pairs(a, sorted, mode, st) : rtg::launch_brute(a, mode, st);
+    };
+    if (!two_pass) {
+      if ((s = ensure(c, c->pair_buf, (size_t)g.pair_cap * 8)) != RTG_OK) return s;
+      a.pair_buf = (unsigned long long*)c->pair_buf.p;
+      a.pair_cap = g.pair_cap;
+      launches += pairs(rtg::kEmit);
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
+      rtg::launch_scan(a, st);
+      launches += 1;
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[5], st));
+      const long long ccap = a.pair_cap * (sym ? 2 : 1);
+      void* cp = nullptr;
+      if ((s = alloc_out(c, sizeof(int32_t) * (size_t)ccap, &cp)) != RTG_OK) {
+        release_out(c, out);
+        return s;
+      }
+      out->col = (int32_t*)cp;
+      c->live[out->handle] += sizeof(int32_t) * (size_t)ccap;
+      a.col = (int*)cp;
+      a.col_cap = ccap;
+      launches += rtg::launch_scatter(a, st);
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
+      launches += rtg::launch_rowsort(a, st);
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
+      RTG_CUDA(c, cudaGetLastError());
+      if ((s = read_status(c)) != RTG_OK) {
+        release_out(c, out);
+        return s;
+      }
+    } else {
+      launches += pairs(rtg::kCount);
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
+      rtg::launch_scan(a, st);
+      launches += 1;
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[5], st));
+      RTG_CUDA(c, cudaGetLastError());
+      if ((s = read_status(c)) != RTG_OK) {
+        release_out(c, out);
+        return s;
+      }
+      if (!(c->h_status->errors & rtg::kErrKeyBits) && !q.count_only && c->h_status->nnz > 0) {
+        const long long nnz = (long long)c->h_status->nnz;
+        void* cp = nullptr;
+        if ((s = alloc_out(c, sizeof(int32_t) * (size_t)nnz, &cp)) != RTG_OK) {
+          release_out(c, out);
+          return s;
+        }
+        out->col = (int32_t*)cp;
+        c->live[out->handle] += sizeof(int32_t) * (size_t)nnz;
+        a.col = (int*)cp;
+        a.col_cap = nnz;
+        launches += pairs(rtg::kWrite);
+        if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
+        launches += rtg::launch_rowsort(a, st);
+        if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
+        RTG_CUDA(c, cudaGetLastError());
+        if ((s = read_status(c)) != RTG_OK) {
+          release_out(c, out);
+          return s;
+        }
+      } else if (timing) {
+        RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
+        RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
+        RTG_CUDA(c, cudaEventSynchronize(c->ev[7]));
+      }
+    }
+    const Status& h = *c->h_status;
+    const unsigned int retry = rtg::kErrKeyBits | rtg::kErrPairOverflow;
+    if (h.errors & retry) {
+      // the launch assumptions were too small: take the device's values and run again
+      release_out(c, out);
+      if (h.errors & rtg::kErrKeyBits) {
+        g.key64 = h.sort_bits > 32;
+        g.passes = (int)((h.sort_bits + rtg::kRadixBits - 1) / rtg::kRadixBits);
+      }
+      if (h.errors & rtg::kErrPairOverflow)
+        g.pair_cap = (long long)((double)h.emitted * 1.05) + 4096;
+      continue;
+    }
+    if ((s = check_errors(c, ~0u)) != RTG_OK) {
+      release_out(c, out);
+      return s;
+    }
+    // remember the launch decisions for the next build of this shape
+    if (m > 0) {
+      g.key64 = h.sort_bits > 32;
+      g.passes = (int)((h.sort_bits + rtg::kRadixBits - 1) / rtg::kRadixBits);
+    }
+    if (!two_pass)
+      g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
+    c->guesses[key] = g;
+
+    out->n = n_total;
+    out->symmetric = sym;
+    out->nnz = q.count_only ? (long long)h.pairs * (sym ? 2 : 1) : (long long)h.nnz;
+    rtg_stats& S = out->stats;
+    std::memset(&S, 0, sizeof(S));
+    long long tc = 0;
+    for (int t = 0; t < m && t < RTG_MAX_GRIDS; ++t) {
+      S.candidates[t] = (int64_t)h.candidates[t];
+      tc += (long long)h.candidates[t];
+    }
+    S.total_candidates = tc;
+    S.owned_candidates = (int64_t)h.owned_candidates;
+    S.near_wall = (int64_t)h.near_wall;
+    S.near_r = (int64_t)h.near_r;
+    S.key_rechecks = (int64_t)h.key_rechecks;
+    S.dist_rechecks = (int64_t)h.dist_rechecks;
+    S.large_cells = (int64_t)h.large_cells;
+    S.max_cell = (int64_t)h.max_cell;
+    S.pairs = (int64_t)h.pairs;
+    S.key_bits = (int32_t)h.sort_bits;
+    S.sort_passes = m > 0 ? a.passes : 0;
+    S.launches = launches;
+    S.attempts = attempt + 1;
+    if (timing) {
+      float ms;
+      // prep+plan, keys, sort, pairs, scan, scatter/write, rowsort, total
+      const int idx[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {0, 7}};
+      for (int p = 0; p < 8; ++p) {
+        cudaEventElapsedTime(&ms, c->ev[idx[p][0]], c->ev[idx[p][1]]);
+        S.phase_us[p] = 1000.0 * ms;
+      }
+    }
+    return RTG_OK;
+  }
+  return fail(c, RTG_E_INTERNAL, "launch assumptions did not converge");
 }
 
 }  // namespace
@@ -223,8 +583,7 @@ rtg_status rtg_create(const rtg_config* cfg, rtg_ctx** out) {
   if ((e = cudaMallocHost(&c->h_status, sizeof(Status))) != cudaSuccess) return bail(e);
   for (auto& ev : c->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e);
-  rtg_status s =
-      ensure(c, c->status_plan, ((sizeof(Status) + 255) & ~size_t(255)) + sizeof(Plan), true);
+  rtg_status s = ensure(c, c->status, (sizeof(Status) + 255) & ~size_t(255), true);
   if (s != RTG_OK) {
     std::string msg = c->err;
     rtg_destroy(c);
@@ -238,10 +597,11 @@ void rtg_destroy(rtg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  DevBuf* bufs[] = {&c->status_plan, &c->T64,     &c->pts,     &c->pf,      &c->key_mat,
-                    &c->keys0,       &c->keys1,   &c->vals0,   &c->vals1,   &c->lookback,
-                    &c->hist,        &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
-                    &c->large_job};
+  DevBuf* bufs[] = {&c->status,    &c->inst,      &c->iplan,   &c->gplan,   &c->bases,
+                    &c->bbox,      &c->T64,       &c->pts,     &c->pf,      &c->key_mat,
+                    &c->keys0,     &c->keys1,     &c->vals0,   &c->vals1,   &c->lookback,
+                    &c->hist,      &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
+                    &c->large_job, &c->pair_buf};
   for (DevBuf* b : bufs) free_buf(c, *b);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
@@ -267,263 +627,53 @@ rtg_status rtg_csr_download(rtg_ctx* c, const rtg_csr* csr, int64_t* row_ptr, in
                                 cudaMemcpyDeviceToHost, c->stream));
   else
     std::memset(row_ptr, 0, sizeof(int64_t) * (csr->n + 1));
-  if (csr->nnz > 0)
+  if (csr->nnz > 0 && csr->col)
     RTG_CUDA(c, cudaMemcpyAsync(col, csr->col, sizeof(int32_t) * csr->nnz, cudaMemcpyDeviceToHost,
                                 c->stream));
   RTG_CUDA(c, cudaStreamSynchronize(c->stream));
   return RTG_OK;
 }
 
-}  // extern "C"
-
-namespace {
-
-// Validate, copy inputs in, run prep + plan and read the plan's key width back.
-// m == 0 prepares a brute-force build (no grids).
-rtg_status begin_build(rtg_ctx* c, const void* points, int dtype, int points_on_device, int64_t n,
-                       int d, double r, const double* transforms, int m, double cell_side,
-                       uint32_t flags, BuildArgs& a, int& launches) {
-  cudaStream_t st = c->stream;
-  const int dpad = rtg::dpad_for(d);
-  const size_t esz = dtype == RTG_DTYPE_F64 ? 8 : 4;
-  rtg_status s;
-  if (m > 0) {
-    const size_t tbytes = sizeof(double) * (size_t)m * (d * d + d);
-    if ((s = ensure(c, c->T64, tbytes)) != RTG_OK) return s;
-    RTG_CUDA(c, cudaMemcpyAsync(c->T64.p, transforms, tbytes, cudaMemcpyHostToDevice, st));
-  }
-  if ((s = ensure(c, c->pf, (size_t)n * dpad * 4)) != RTG_OK) return s;
-  if ((s = ensure(c, c->row_cnt, (size_t)n * 4)) != RTG_OK) return s;
-  if ((s = ensure(c, c->scan_lb, ((size_t)n / 4096 + 2) * 8)) != RTG_OK) return s;
-  const void* dpts = points;
-  if (!points_on_device) {
-    if ((s = ensure(c, c->pts, (size_t)n * d * esz)) != RTG_OK) return s;
-    RTG_CUDA(c, cudaMemcpyAsync(c->pts.p, points, (size_t)n * d * esz, cudaMemcpyHostToDevice, st));
-    dpts = c->pts.p;
-  }
-  a = BuildArgs{};
-  a.pts = dpts;
-  a.dtype = dtype;
-  a.n = (int)n;
-  a.d = d;
-  a.m = m;
-  a.dpad = dpad;
-  a.r = r;
-  a.c = cell_side;
-  a.T64 = (const double*)c->T64.p;
-  a.flags = flags;
-  a.symmetric = (flags & RTG_FLAG_SYMMETRIC) ? 1 : 0;
-  a.st = (Status*)c->status_plan.p;
-  a.plan = (Plan*)((char*)c->status_plan.p + ((sizeof(Status) + 255) & ~size_t(255)));
-  a.pf = (float*)c->pf.p;
-  a.row_cnt = (unsigned int*)c->row_cnt.p;
-  a.scan_lookback = (unsigned long long*)c->scan_lb.p;
-  a.num_sms = c->num_sms;
-  RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
-  RTG_CUDA(c, cudaMemsetAsync(a.row_cnt, 0, (size_t)n * 4, st));
-  rtg::launch_prep(a, st);
-  rtg::launch_plan(a, 64, st);
-  launches += 2;
-  RTG_CUDA(c, cudaGetLastError());
-  if ((s = read_status(c)) != RTG_OK) return s;
-  return check_errors(c, rtg::kErrNonFinite | rtg::kErrKeyOverflow);
-}
-
-// After the COUNT pass: scan, allocate the columns, WRITE pass, row sort.
-// `write_pass` launches the WRITE enumeration and returns its kernel count.
-template <typename WritePass>
-rtg_status finish_build(rtg_ctx* c, BuildArgs& a, rtg_csr* out, bool count_only, int& launches,
-                        bool timing, WritePass write_pass) {
-  cudaStream_t st = c->stream;
-  rtg_status s;
-  rtg::launch_scan(a, st);
-  launches += 1;
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[5], st));
-  RTG_CUDA(c, cudaGetLastError());
-  if ((s = read_status(c)) != RTG_OK || (s = check_errors(c, ~0u)) != RTG_OK) return s;
-  const long long nnz = (long long)c->h_status->nnz;
-  out->nnz = nnz;
-  if (count_only) {
-    if (timing) {
-      RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
-      RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
-    }
-    return RTG_OK;
-  }
-  void* cp = nullptr;
-  if ((s = alloc_out(c, sizeof(int32_t) * (size_t)nnz, &cp)) != RTG_OK) return s;
-  out->col = (int32_t*)cp;
-  c->live[out->handle] += sizeof(int32_t) * (size_t)nnz;
-  a.col = (int*)cp;
-  a.col_cap = nnz;
-  if (nnz > 0) launches += write_pass(a);
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
-  if (nnz > 0) launches += rtg::launch_rowsort(a, st);
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
-  RTG_CUDA(c, cudaGetLastError());
-  if ((s = read_status(c)) != RTG_OK) return s;
-  return check_errors(c, ~0u);
-}
-
-void fill_stats(rtg_ctx* c, const BuildArgs& a, rtg_csr* out, int launches, bool timing) {
-  const Status& h = *c->h_status;
-  rtg_stats& S = out->stats;
-  long long tc = 0;
-  for (int t = 0; t < a.m; ++t) {
-    S.candidates[t] = (int64_t)h.candidates[t];
-    tc += (long long)h.candidates[t];
-  }
-  S.total_candidates = tc;
-  S.owned_candidates = (int64_t)h.owned_candidates;
-  S.near_wall = (int64_t)h.near_wall;
-  S.near_r = (int64_t)h.near_r;
-  S.key_rechecks = (int64_t)h.key_rechecks;
-  S.dist_rechecks = (int64_t)h.dist_rechecks;
-  S.large_cells = (int64_t)h.large_cells;
-  S.max_cell = (int64_t)h.max_cell;
-  S.pairs = (int64_t)h.pairs;
-  S.key_bits = a.sort_bits;
-  S.sort_passes = a.sort_bits <= 0 ? 0 : (a.sort_bits + rtg::kRadixBits - 1) / rtg::kRadixBits;
-  S.launches = launches;
-  if (timing) {
-    float ms;
-    const int idx[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {0, 7}};
-    for (int p = 0; p < 8; ++p) {
-      cudaEventElapsedTime(&ms, c->ev[idx[p][0]], c->ev[idx[p][1]]);
-      S.phase_us[p] = 1000.0 * ms;
-    }
-  }
-}
-
-rtg_status empty_csr(rtg_ctx* c, int64_t n, rtg_csr* out) {
-  void* rp = nullptr;
-  rtg_status s;
-  if ((s = alloc_out(c, sizeof(int64_t) * (n + 1), &rp)) != RTG_OK) return s;
-  RTG_CUDA(c, cudaMemsetAsync(rp, 0, sizeof(int64_t) * (n + 1), c->stream));
-  RTG_CUDA(c, cudaStreamSynchronize(c->stream));
-  out->row_ptr = (int64_t*)rp;
-  out->handle = c->next_handle++;
-  c->live[out->handle] = sizeof(int64_t) * (n + 1);
-  return RTG_OK;
-}
-
-rtg_status alloc_row_ptr(rtg_ctx* c, BuildArgs& a, rtg_csr* out) {
-  void* rp = nullptr;
-  rtg_status s;
-  if ((s = alloc_out(c, sizeof(int64_t) * (a.n + 1), &rp)) != RTG_OK) return s;
-  out->row_ptr = (int64_t*)rp;
-  out->handle = c->next_handle++;
-  c->live[out->handle] = sizeof(int64_t) * (a.n + 1);
-  a.row_ptr = (long long*)rp;
-  return RTG_OK;
-}
-
-rtg_status all_pairs_impl(rtg_ctx* c, const void* points, int dtype, int points_on_device,
-                          int64_t n, int d, double r, const double* transforms, int m,
-                          double cell_side, uint32_t flags, rtg_csr* out) {
-  cudaStream_t st = c->stream;
-  const bool timing = (flags & RTG_FLAG_TIMING) != 0;
-  out->n = n;
-  out->symmetric = (flags & RTG_FLAG_SYMMETRIC) ? 1 : 0;
-  if (n == 0) return empty_csr(c, n, out);
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[0], st));
-  BuildArgs a;
-  int launches = 0;
-  rtg_status s = begin_build(c, points, dtype, points_on_device, n, d, r, transforms, m, cell_side,
-                             flags, a, launches);
-  if (s != RTG_OK) return s;
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[1], st));
-  const long long N = n * (long long)m;
-  a.sort_bits = (int)c->h_status->key_bits + (int)c->h_status->grid_bits;
-  a.key64 = a.sort_bits > 32;
-  const size_t ksz = a.key64 ? 8 : 4;
-  if ((s = ensure(c, c->key_mat, (size_t)N * ksz)) != RTG_OK) return s;
-  if ((s = ensure(c, c->keys0, (size_t)N * ksz)) != RTG_OK) return s;
-  if ((s = ensure(c, c->keys1, (size_t)N * ksz)) != RTG_OK) return s;
-  if ((s = ensure(c, c->vals0, (size_t)N * 4)) != RTG_OK) return s;
-  if ((s = ensure(c, c->vals1, (size_t)N * 4)) != RTG_OK) return s;
-  if ((s = ensure(c, c->lookback, rtg::sort_tiles_for(N, a.key64) * rtg::kRadix * 8, true)) !=
-      RTG_OK)
-    return s;
-  if ((s = ensure(c, c->hist, rtg::kMaxPasses * rtg::kRadix * 4, true)) != RTG_OK) return s;
-  if ((s = ensure(c, c->digit_off, rtg::kMaxPasses * rtg::kRadix * 4)) != RTG_OK) return s;
-  const unsigned int large_cap = (unsigned int)(N / 129 + 1);
-  if ((s = ensure(c, c->large, (size_t)large_cap * sizeof(rtg::LargeCell))) != RTG_OK) return s;
-  if ((s = ensure(c, c->large_job, ((size_t)large_cap + 1) * 8)) != RTG_OK) return s;
-  a.key_mat = c->key_mat.p;
-  a.keys[0] = c->keys0.p;
-  a.keys[1] = c->keys1.p;
-  a.vals[0] = (uint32_t*)c->vals0.p;
-  a.vals[1] = (uint32_t*)c->vals1.p;
-  a.lookback = (unsigned long long*)c->lookback.p;
-  a.hist = (unsigned int*)c->hist.p;
-  a.digit_off = (unsigned int*)c->digit_off.p;
-  a.large = (rtg::LargeCell*)c->large.p;
-  a.large_cap = large_cap;
-  a.large_job_off = (unsigned long long*)c->large_job.p;
-  a.epoch = c->epoch;
-  c->epoch += rtg::kMaxPasses;
-  if ((c->epoch & 0x3fffffffu) < rtg::kMaxPasses) c->epoch = 1;
-  if ((s = alloc_row_ptr(c, a, out)) != RTG_OK) return s;
-
-  rtg::launch_keys(a, st);
-  launches += 1;
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
-  const int sorted = rtg::launch_sort(a, st);
-  launches += a.sort_bits > 0 && N > 1 ? 1 + (a.sort_bits + rtg::kRadixBits - 1) / rtg::kRadixBits : 0;
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[3], st));
-  launches += rtg::launch_pairs(a, sorted, false, st);
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
-  s = finish_build(c, a, out, false, launches, timing,
-                   [&](BuildArgs& b) { return rtg::launch_pairs(b, sorted, true, st); });
-  if (s != RTG_OK) return s;
-  fill_stats(c, a, out, launches, timing);
-  return RTG_OK;
-}
-
-rtg_status brute_impl(rtg_ctx* c, const void* points, int dtype, int points_on_device, int64_t n,
-                      int d, double r, uint32_t flags, int count_only, rtg_csr* out) {
-  cudaStream_t st = c->stream;
-  const bool timing = (flags & RTG_FLAG_TIMING) != 0;
-  out->n = n;
-  out->symmetric = (flags & RTG_FLAG_SYMMETRIC) ? 1 : 0;
-  if (n == 0) return empty_csr(c, n, out);
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[0], st));
-  BuildArgs a;
-  int launches = 0;
-  rtg_status s = begin_build(c, points, dtype, points_on_device, n, d, r, nullptr, 0, 1.0, flags,
-                             a, launches);
-  if (s != RTG_OK) return s;
-  if (timing) {
-    RTG_CUDA(c, cudaEventRecord(c->ev[1], st));
-    RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
-    RTG_CUDA(c, cudaEventRecord(c->ev[3], st));
-  }
-  if ((s = alloc_row_ptr(c, a, out)) != RTG_OK) return s;
-  launches += rtg::launch_brute(a, false, st);
-  if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
-  s = finish_build(c, a, out, count_only != 0, launches, timing,
-                   [&](BuildArgs& b) { return rtg::launch_brute(b, true, st); });
-  if (s != RTG_OK) return s;
-  fill_stats(c, a, out, launches, timing);
-  return RTG_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
 rtg_status rtg_all_pairs(rtg_ctx* c, const void* points, int dtype, int points_on_device, int64_t n,
                          int d, double r, const double* transforms, int m, double cell_side,
                          uint32_t flags, rtg_csr* out) {
   if (!c || !out) return fail(c, RTG_E_INVALID, "NULL context or output");
   std::memset(out, 0, sizeof(*out));
-  rtg_status s = validate(dtype, n, d, r, transforms, m, cell_side, points);
+  rtg_status s = validate_common(dtype, n, d, r, cell_side, points);
+  if (s == RTG_OK && (m < 1 || m > RTG_MAX_GRIDS))
+    s = fail(nullptr, RTG_E_INVALID, "m must be in [1, 64]");
+  if (s == RTG_OK) s = validate_transforms(transforms, d, m);
   if (s != RTG_OK) return fail(c, s, g_err);
   std::lock_guard<std::mutex> lk(c->mu);
   RTG_CUDA(c, cudaSetDevice(c->device));
-  s = all_pairs_impl(c, points, dtype, points_on_device, n, d, r, transforms, m, cell_side, flags,
-                     out);
+  rtg_instance it{points, n, d, r, cell_side, transforms};
+  Request q{&it, 1, m, dtype, points_on_device, flags, false};
+  s = build(c, q, out);
+  if (s != RTG_OK) release_out(c, out);
+  return s;
+}
+
+rtg_status rtg_batch_all_pairs(rtg_ctx* c, const rtg_instance* items, int count, int m, int dtype,
+                               int points_on_device, uint32_t flags, rtg_csr* out,
+                               int64_t* row_offsets) {
+  if (!c || !out || (count > 0 && !items)) return fail(c, RTG_E_INVALID, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (count < 1 || count > 65535) return fail(c, RTG_E_INVALID, "count must be in [1, 65535]");
+  if (m < 1 || m > RTG_MAX_GRIDS) return fail(c, RTG_E_INVALID, "m must be in [1, 64]");
+  long long off = 0;
+  for (int b = 0; b < count; ++b) {
+    const rtg_instance& it = items[b];
+    rtg_status s = validate_common(dtype, it.n, it.d, it.r, it.cell_side, it.points);
+    if (s == RTG_OK) s = validate_transforms(it.transforms, it.d, m);
+    if (s != RTG_OK) return fail(c, s, "instance " + std::to_string(b) + ": " + g_err);
+    if (row_offsets) row_offsets[b] = off;
+    off += it.n;
+  }
+  if (row_offsets) row_offsets[count] = off;
+  std::lock_guard<std::mutex> lk(c->mu);
+  RTG_CUDA(c, cudaSetDevice(c->device));
+  Request q{items, count, m, dtype, points_on_device, flags, false};
+  rtg_status s = build(c, q, out);
   if (s != RTG_OK) release_out(c, out);
   return s;
 }
@@ -533,14 +683,13 @@ rtg_status rtg_brute_force(rtg_ctx* c, const void* points, int dtype, int points
                            rtg_csr* out) {
   if (!c || !out) return fail(c, RTG_E_INVALID, "NULL context or output");
   std::memset(out, 0, sizeof(*out));
-  const double T1[2] = {1.0, 0.0};
-  rtg_status s = validate(dtype, n, 1, r, T1, 1, 1.0, points);
-  if (s == RTG_OK && (d < 1 || d > RTG_MAX_DIM))
-    s = fail(nullptr, RTG_E_INVALID, "d must be in [1, 16]");
+  rtg_status s = validate_common(dtype, n, d, r, 1.0, points);
   if (s != RTG_OK) return fail(c, s, g_err);
   std::lock_guard<std::mutex> lk(c->mu);
   RTG_CUDA(c, cudaSetDevice(c->device));
-  s = brute_impl(c, points, dtype, points_on_device, n, d, r, flags, count_only, out);
+  rtg_instance it{points, n, d, r, 1.0, nullptr};
+  Request q{&it, 1, 0, dtype, points_on_device, flags, count_only != 0};
+  s = build(c, q, out);
   if (s != RTG_OK) release_out(c, out);
   return s;
 }

@@ -1,19 +1,23 @@
 // Internal declarations shared by the CUDA translation units of the RTG library.
 //
-// Pipeline of one build (Alg. 1 of arXiv:1409.8112 over all m grids at once):
-//   prep   : FP32 copy of the points (padded rows) + per-axis bounding box
-//   plan   : per grid, the cell-index range over the bounding box (mixed-radix key layout)
-//            and the FP32 error bounds that decide when FP64 must be used
-//   keys   : y = R p + s and q = floor(y / c) per point and grid (Alg. 1 lines 4-7),
-//            packed into an exact integer key; composite (grid, cell) sort keys
-//   sort   : LSD radix sort (onesweep: one upfront histogram, one kernel per digit)
-//   count  : per cell, all pairs (Alg. 1 lines 8-9); a pair is owned by the first grid
-//            that puts both points in one cell, which removes duplicates across grids
-//            without an auxiliary set (Sec. III-B); owned pairs at distance <= r are
-//            counted per row
-//   scan   : row counts -> CSR row pointers
-//   write  : the same enumeration, writing columns into their rows
-//   rowsort: each row's columns sorted ascending
+// One build processes a batch of B >= 1 roadmaps ("instances"), each with its own points,
+// radius r, cell side c and m grid transforms (Alg. 1 of arXiv:1409.8112 per instance), in one
+// fixed sequence of kernels over the concatenated points:
+//   prep    : FP32 copy of the points (padded rows) + per-instance bounding box
+//   plan    : per (instance, grid, axis) the cell-index range (mixed-radix key layout) and the
+//             FP32 error bound of the cell index; per instance the distance-filter band;
+//             composite key bases so that every (instance, grid) owns a disjoint key range
+//   keys    : y = R p + s and q = floor(y / c) per point and grid (Alg. 1 lines 4-7), packed
+//             into base(instance, grid) + mixed-radix cell key
+//   sort    : LSD radix sort (onesweep) of the composite keys with global point indices
+//   pairs   : per cell, all pairs (Alg. 1 lines 8-9); a pair is owned by the first grid that
+//             puts both points in one cell (dedupe of Sec. III-B without an auxiliary set);
+//             owned pairs at distance <= r are emitted to a pair buffer with row counts
+//             (EMIT), or counted and later written in place (COUNT then WRITE)
+//   scan    : row counts -> CSR row pointers
+//   scatter : pair buffer -> columns in their rows
+//   rowsort : each row's columns ascending
+// The CSR of a batch is block diagonal over the global point indices.
 #pragma once
 
 #include <cstdint>
@@ -28,28 +32,32 @@ constexpr int kMaxGrids = 64;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
+constexpr int kPointBlock = 128;  // points per block in the per-point kernels
 
 // Bits of Status::errors.
 enum : uint32_t {
-  kErrKeyOverflow = 1u,    // cell index range needs more than 64 bits
-  kErrTimeout = 2u,        // a bounded spin ran out
-  kErrColOverflow = 4u,    // more pairs than the column buffer holds
-  kErrNonFinite = 8u,      // a coordinate is NaN or infinite
-  kErrKeyBits = 16u,       // key wider than the launch assumed (host must redo)
-  kErrKeyRange = 32u,      // a cell index fell outside the planned range (internal)
-  kErrLargeOverflow = 64u  // large-cell list full (internal)
+  kErrKeyOverflow = 1u,     // composite key range needs more than 64 bits
+  kErrTimeout = 2u,         // a bounded spin ran out
+  kErrColOverflow = 4u,     // more pairs than the output holds (host re-runs bigger)
+  kErrNonFinite = 8u,       // a coordinate is NaN or infinite
+  kErrKeyBits = 16u,        // key wider than the launch assumed (host re-runs)
+  kErrKeyRange = 32u,       // a cell index fell outside the planned range (internal)
+  kErrLargeOverflow = 64u,  // large-cell list full (internal)
+  kErrPairOverflow = 128u   // pair buffer too small (host re-runs bigger)
 };
 
-// Device-side counters and bounding box; zeroed at the start of every build.
+// Enumeration modes.
+enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2 };
+
+// Device-side counters; zeroed at the start of every build.
 struct Status {
-  unsigned long long bbox_max[kMaxDim];   // sortable encoding of the per-axis maximum
-  unsigned long long bbox_nmin[kMaxDim];  // complement of the encoding of the minimum
   unsigned int errors;
-  unsigned int key_bits;   // widest per-grid cell key (bits)
-  unsigned int grid_bits;  // bits for the grid index
+  unsigned int sort_bits;  // bits of the composite key (set by the plan)
   unsigned int hist_ticket;
-  unsigned long long nnz;  // stored CSR entries
-  unsigned long long pairs;
+  unsigned int scan_tiles;
+  unsigned long long nnz;      // stored CSR entries (set by the scan)
+  unsigned long long pairs;    // reported pairs
+  unsigned long long emitted;  // slots claimed in the pair buffer
   unsigned long long candidates[kMaxGrids];
   unsigned long long owned_candidates;
   unsigned long long near_wall;
@@ -60,30 +68,45 @@ struct Status {
   unsigned long long large_jobs;
   unsigned long long max_cell;
   unsigned int sort_tiles[kMaxPasses];
-  unsigned int scan_tiles;
   unsigned int long_rows;  // rows queued for the block row sort
+  unsigned int pad;
 };
 
-// Per-build plan written by the plan kernel.
-struct Plan {
-  int n, d, m, dtype;
-  double c, r, rr;           // rr = fl(r * r)
-  float inv_c;               // fl32(1 / c)
-  float s_lo, s_hi;          // FP32 squared-distance thresholds (accept below, reject above)
-  int filter_on;             // 0: every candidate is decided in FP64
-  int key_bits, grid_bits;   // B_max, ceil(log2 m)
-  long long qlo[kMaxGrids][kMaxDim];
-  unsigned long long ext[kMaxGrids][kMaxDim];
-  unsigned long long stride[kMaxGrids][kMaxDim];
-  float Rf[kMaxGrids][kMaxDim * kMaxDim];  // rows padded to kMaxDim, zero beyond d
-  float sf[kMaxGrids][kMaxDim];
-  float E[kMaxGrids][kMaxDim];             // key error bound in cell units (rounded up)
+// One roadmap of a batch (filled on the host).
+struct Inst {
+  const void* pts;  // device, n x d row-major, FP64 or FP32
+  long long p0;     // first global point index
+  long long T0;     // first double of its m transforms in the packed transform array
+  int n, d;
+  double r, c;
+  long long blk0;   // first block of this instance in the per-point kernels
+};
+
+// Per-instance results of the plan.
+struct InstPlan {
+  double rr;         // fl(r * r), the reporting threshold
+  float s_lo, s_hi;  // FP32 squared-distance band (decide in FP32 outside it)
+  int filter_on;     // 0: decide every candidate in FP64
+  float inv_c;       // fl32(1 / c)
+};
+
+// Per (instance, grid) key layout and FP32 rotation.
+struct GridPlan {
+  float Rf[kMaxDim * kMaxDim];  // rows padded to kMaxDim, zero beyond d
+  float sf[kMaxDim];
+  float E[kMaxDim];  // bound on |FP32 y/c - FP64 y/c| (rounded up), plus near-wall margin
+  long long qlo[kMaxDim];
+  unsigned long long ext[kMaxDim];
+  unsigned long long stride[kMaxDim];
+  unsigned long long base;   // first composite key of this (instance, grid)
+  unsigned long long range;  // number of cell keys (product of extents)
 };
 
 struct LargeCell {
   unsigned long long start;  // first sorted position
   unsigned int size;
-  unsigned int grid;
+  unsigned short grid;
+  unsigned short inst;
 };
 
 // ---- sortable encodings of doubles (monotone) --------------------------------------------
@@ -115,51 +138,55 @@ __host__ __device__ inline double dec_double(unsigned long long e) {
 
 inline int dpad_for(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : 16); }
 
-// ---- launch wrappers (defined in the .cu files) -------------------------------------------
+// ---- launch arguments ----------------------------------------------------------------------
 struct BuildArgs {
-  // inputs
-  const void* pts;  // device, n x d, dtype
-  int dtype;
-  int n, d, m, dpad;
-  double r, c;
-  const double* T64;  // device, m * (d*d + d)
-  uint32_t flags;
+  int B;              // instances
+  int m;              // grids per instance (0: brute force)
+  int dtype;          // 0 FP64, 1 FP32 (common to the batch)
+  int dpad;           // padded row width (common to the batch)
   int symmetric;
-  // workspace
+  long long n_total;  // sum of n
+  long long blocks;   // per-point kernel blocks (sum of ceil(n / kPointBlock))
+  const Inst* inst;   // device, B entries
+  InstPlan* iplan;    // device, B entries
+  GridPlan* gplan;    // device, B * m entries
+  unsigned long long* bases;  // device, B * m composite key bases (ascending)
+  unsigned long long* bbox;  // device, B * kMaxDim * 2 (max, complement of min)
+  const double* T64;         // device, packed transforms
   Status* st;
-  Plan* plan;
-  float* pf;            // n x dpad
-  void* key_mat;        // n x m keys
-  void* keys[2];        // N composite keys, ping-pong
-  uint32_t* vals[2];    // N point indices, ping-pong
+  float* pf;          // n_total x dpad
+  void* key_mat;      // n_total x m keys
+  void* keys[2];      // N composite keys, ping-pong
+  uint32_t* vals[2];  // N global point indices, ping-pong
   unsigned long long* lookback;  // sort look-back words (tiles * 256)
   unsigned int* hist;            // kMaxPasses * 256 digit counts
   unsigned int* digit_off;       // kMaxPasses * 256 exclusive digit offsets
-  unsigned int* row_cnt;         // n
+  unsigned int* row_cnt;         // n_total
   unsigned long long* scan_lookback;
   LargeCell* large;
   unsigned int large_cap;
   unsigned long long* large_job_off;  // large_cap + 1
-  // outputs
-  long long* row_ptr;  // n + 1
+  unsigned long long* pair_buf;       // EMIT: (i << 32) | j
+  long long pair_cap;
+  long long* row_ptr;  // n_total + 1
   int* col;
   long long col_cap;
-  // launch decisions
   bool key64;
-  int sort_bits;       // bits of the composite key
+  int passes;          // radix passes launched
   unsigned int epoch;  // look-back epoch base for this build's sort passes
   int num_sms;
 };
 
 void launch_prep(const BuildArgs& a, cudaStream_t s);
-void launch_plan(const BuildArgs& a, int assumed_bits, cudaStream_t s);
+void launch_plan(const BuildArgs& a, cudaStream_t s);
 void launch_keys(const BuildArgs& a, cudaStream_t s);
-// returns 0 if the sorted data ended in buffer 0, 1 if in buffer 1
+// returns the ping-pong buffer (0 or 1) that holds the sorted data
 int launch_sort(const BuildArgs& a, cudaStream_t s);
-// The launch_* functions that return int return the number of kernels they launched.
-int launch_pairs(const BuildArgs& a, int sorted_buf, bool write, cudaStream_t s);
-int launch_brute(const BuildArgs& a, bool write, cudaStream_t s);
+// the launch_* functions returning int return the number of kernels they launched
+int launch_pairs(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s);
+int launch_brute(const BuildArgs& a, Mode mode, cudaStream_t s);
 void launch_scan(const BuildArgs& a, cudaStream_t s);
+int launch_scatter(const BuildArgs& a, cudaStream_t s);
 int launch_rowsort(const BuildArgs& a, cudaStream_t s);
 
 size_t sort_tiles_for(long long N, bool key64);

@@ -1,5 +1,5 @@
 // Point preparation, per-build plan and the transform+key kernel (Alg. 1 lines 4-7 of
-// arXiv:1409.8112, for the rotated + shifted grids of Sec. III).
+// arXiv:1409.8112, for the rotated + shifted grids of Sec. III), for a batch of instances.
 //
 // The cell index of a point in grid t is q_k = floor(y_k / c) with y = R_t p + s_t, where the
 // reference value is the FP64 fma chain acc = s_k; acc = fma(R[k][l], p_l, acc) followed by an
@@ -28,168 +28,116 @@ __device__ __forceinline__ double load_coord(const void* pts, int dtype, long lo
                     : (double)__ldg((const float*)pts + i * d + l);
 }
 
+// Instance owning block `blk` of a per-point kernel (blk0 ascending): binary search by one
+// thread, broadcast through shared memory.
+__device__ __forceinline__ int block_instance(const Inst* inst, int B, long long blk,
+                                              int* s_b) {
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (inst[mid].blk0 <= blk) lo = mid; else hi = mid - 1;
+    }
+    *s_b = lo;
+  }
+  __syncthreads();
+  return *s_b;
+}
+
 template <int DPAD>
-__global__ void __launch_bounds__(256) k_prep(const void* __restrict__ pts, int dtype, int n,
-                                              int d, float* __restrict__ pf, Status* st) {
+__global__ void __launch_bounds__(kPointBlock) k_prep(const Inst* __restrict__ inst, int B,
+                                                      int dtype, float* __restrict__ pf,
+                                                      unsigned long long* bbox, Status* st) {
+  __shared__ int s_b;
+  __shared__ double smn[kPointBlock / 32][DPAD], smx[kPointBlock / 32][DPAD];
+  const int b = block_instance(inst, B, blockIdx.x, &s_b);
+  const Inst I = inst[b];
+  const long long i = (blockIdx.x - I.blk0) * (long long)kPointBlock + threadIdx.x;
+  const int d = I.d;
   double mn[DPAD], mx[DPAD];
+  bool bad = false;
+  float row[DPAD];
 #pragma unroll
   for (int l = 0; l < DPAD; ++l) {
     mn[l] = DBL_MAX;
     mx[l] = -DBL_MAX;
+    row[l] = 0.0f;
   }
-  bool bad = false;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    float row[DPAD];
+  if (i < I.n) {
 #pragma unroll
     for (int l = 0; l < DPAD; ++l) {
       if (l < d) {
-        double x = load_coord(pts, dtype, i, d, l);
+        const double x = load_coord(I.pts, dtype, i, d, l);
         bad |= !isfinite(x);
-        mn[l] = fmin(mn[l], x);
-        mx[l] = fmax(mx[l], x);
+        mn[l] = x;
+        mx[l] = x;
         row[l] = __double2float_rn(x);
-      } else {
-        row[l] = 0.0f;
       }
     }
-    float4* dst = reinterpret_cast<float4*>(pf + i * DPAD);
+    float4* dst = reinterpret_cast<float4*>(pf + (I.p0 + i) * DPAD);
 #pragma unroll
     for (int v = 0; v < DPAD / 4; ++v)
       dst[v] = make_float4(row[4 * v], row[4 * v + 1], row[4 * v + 2], row[4 * v + 3]);
   }
-  // block reduction of the bounding box, then one atomic per axis per block
-  __shared__ double smn[8][DPAD], smx[8][DPAD];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int l = 0; l < DPAD; ++l) {
-    double a = mn[l], b = mx[l];
+    double a = mn[l], c = mx[l];
     for (int o = 16; o > 0; o >>= 1) {
       a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+      c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
     }
     if (lane == 0) {
       smn[warp][l] = a;
-      smx[warp][l] = b;
+      smx[warp][l] = c;
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->errors, kErrNonFinite);
   if (threadIdx.x < d) {
     const int l = threadIdx.x;
-    double a = smn[0][l], b = smx[0][l];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    double a = smn[0][l], c = smx[0][l];
+    for (int w = 1; w < kPointBlock / 32; ++w) {
       a = fmin(a, smn[w][l]);
-      b = fmax(b, smx[w][l]);
+      c = fmax(c, smx[w][l]);
     }
-    if (a <= b) {  // the block saw at least one point
-      atomicMax(&st->bbox_nmin[l], ~enc_double(a));
-      atomicMax(&st->bbox_max[l], enc_double(b));
+    if (a <= c) {
+      atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 0], enc_double(c));
+      atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 1], ~enc_double(a));
     }
   }
 }
 
-// One block.  Threads (t, k) fill the key layout and the FP32 data of grid t, axis k.
-__global__ void __launch_bounds__(1024) k_plan(Plan* P, Status* st, const double* T64, int n,
-                                               int d, int m, int dtype, double r, double c,
-                                               int assumed_bits) {
-  __shared__ double lo[kMaxDim], hi[kMaxDim], M[kMaxDim];
-  __shared__ unsigned int bits_t[kMaxGrids];
-  const int tid = threadIdx.x;
-  if (tid < kMaxDim) {
-    double a = 0.0, b = 0.0;
-    if (tid < d && n > 0) {
-      a = dec_double(~st->bbox_nmin[tid]);
-      b = dec_double(st->bbox_max[tid]);
-    }
-    lo[tid] = a;
-    hi[tid] = b;
-    M[tid] = fmax(fabs(a), fabs(b));
+// Thread (b, t, k): key layout of axis k of grid t of instance b; thread (b, 0, 0) also sets
+// the instance's distance band.
+__global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst, int B, int m,
+                                                   int dtype, const double* __restrict__ T64,
+                                                   const unsigned long long* __restrict__ bbox,
+                                                   InstPlan* iplan, GridPlan* gplan) {
+  const int mm = m > 0 ? m : 1;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)B * mm * kMaxDim) return;
+  const int b = (int)(idx / (mm * kMaxDim));
+  const int t = (int)(idx / kMaxDim % mm);
+  const int k = (int)(idx % kMaxDim);
+  const Inst I = inst[b];
+  const int d = I.d;
+  double M[kMaxDim];
+  for (int l = 0; l < kMaxDim; ++l) M[l] = 0.0;
+  double lo[kMaxDim], hi[kMaxDim];
+  for (int l = 0; l < d; ++l) {
+    hi[l] = I.n > 0 ? dec_double(bbox[((size_t)b * kMaxDim + l) * 2 + 0]) : 0.0;
+    lo[l] = I.n > 0 ? dec_double(~bbox[((size_t)b * kMaxDim + l) * 2 + 1]) : 0.0;
+    M[l] = fmax(fabs(lo[l]), fabs(hi[l]));
   }
-  __syncthreads();
-  const int stride = d * d + d;
-  for (int idx = tid; idx < m * kMaxDim; idx += blockDim.x) {
-    const int t = idx / kMaxDim, k = idx % kMaxDim;
-    if (k >= d) {
-      for (int l = 0; l < kMaxDim; ++l) P->Rf[t][k * kMaxDim + l] = 0.0f;
-      P->sf[t][k] = 0.0f;
-      P->E[t][k] = 0.0f;
-      P->qlo[t][k] = 0;
-      P->ext[t][k] = 1;
-      continue;
-    }
-    const double* R = T64 + (size_t)t * stride;
-    const double* s = R + d * d;
-    double ymin = s[k], ymax = s[k], A = fabs(s[k]);
-    for (int l = 0; l < kMaxDim; ++l) {
-      if (l < d) {
-        const double rkl = R[k * d + l];
-        const double a = rkl * lo[l], b = rkl * hi[l];
-        ymin += fmin(a, b);
-        ymax += fmax(a, b);
-        A += fabs(rkl) * M[l];
-        P->Rf[t][k * kMaxDim + l] = __double2float_rn(rkl);
-      } else {
-        P->Rf[t][k * kMaxDim + l] = 0.0f;
-      }
-    }
-    P->sf[t][k] = __double2float_rn(s[k]);
-    // Two cells of margin on each side absorb every rounding difference between these sums
-    // and the per-point fma chains (both are far below one cell).
-    const double qmin = floor(ymin / c) - 2.0, qmax = floor(ymax / c) + 2.0;
-    if (!(qmin > -4.0e18 && qmax < 4.0e18)) {
-      atomicOr(&st->errors, kErrKeyOverflow);
-      P->qlo[t][k] = 0;
-      P->ext[t][k] = 1;
-    } else {
-      P->qlo[t][k] = (long long)qmin;
-      P->ext[t][k] = (unsigned long long)((long long)qmax - (long long)qmin + 1);
-    }
-    const double E = (double)(d + 6) * 0x1.0p-24 * A / c * (1.0 + 1e-6) + 3e-12 / c;
-    P->E[t][k] = __double2float_ru(E);
-  }
-  __syncthreads();
-  if (tid < m) {
-    const int t = tid;
-    unsigned long long strd = 1;
-    bool of = false;
-    for (int k = 0; k < kMaxDim; ++k) {
-      if (k < d) {
-        P->stride[t][k] = strd;
-        const unsigned long long e = P->ext[t][k];
-        if (__umul64hi(strd, e) != 0) of = true;
-        strd *= e;
-      } else {
-        P->stride[t][k] = 0;
-      }
-    }
-    bits_t[t] = of ? 65u : (strd <= 1 ? 0u : 64u - (unsigned)__clzll((long long)(strd - 1)));
-  }
-  __syncthreads();
-  if (tid == 0) {
-    unsigned int B = 0;
-    for (int t = 0; t < m; ++t) B = max(B, bits_t[t]);
-    const unsigned int gb = m <= 1 ? 0u : 32u - (unsigned)__clz(m - 1);
-    if (B > 64 || B + gb > 64) atomicOr(&st->errors, kErrKeyOverflow);
-    if ((int)(B + gb) > assumed_bits) atomicOr(&st->errors, kErrKeyBits);
-    st->key_bits = B;
-    st->grid_bits = gb;
-    P->key_bits = (int)B;
-    P->grid_bits = (int)gb;
-    P->n = n;
-    P->d = d;
-    P->m = m;
-    P->dtype = dtype;
-    P->c = c;
-    P->r = r;
-    const double rr = __dmul_rn(r, r);
-    P->rr = rr;
-    P->inv_c = __double2float_rn(1.0 / c);
-    // Distance filter.  With S the exact squared distance and e_f the FP32 differences,
+  if (t == 0 && k == 0) {
+    // Distance band.  With S the exact squared distance and e_f the FP32 differences,
     // |fl32-chain(e_f) - S| <= 2|eta| sqrt(S) + |eta|^2 + d 2^-24 (sqrt(S) + |eta|)^2 where
     // eta_l bounds |e_f,l - e_l|: 2^-24 (|p_a,l| + |p_b,l|) from rounding FP64 input to FP32
     // plus 2^-24 |e_l| from the FP32 subtraction.  Evaluated at S <= 2 rr; the FP64
     // reference chain adds (d + 3) 2^-53 S.  The 3e-12 rr term sends every pair within
     // 1e-12 r of r to FP64, where the near-r diagnostic is counted.
+    const double r = I.r;
+    const double rr = __dmul_rn(r, r);
     const double u32 = 0x1.0p-24, u64 = 0x1.0p-53;
     const double S2 = sqrt(2.0 * rr) * (1.0 + 1e-9);
     double eta2 = 0.0;
@@ -204,9 +152,130 @@ __global__ void __launch_bounds__(1024) k_plan(Plan* P, Status* st, const double
     const double Es = (E1 + (double)(d + 3) * u64 * 2.0 * rr + 3e-12 * rr) * 1.01;
     const bool on = isfinite(Es) && eta <= 1e-3 * r && rr > 0.0 && (rr - Es) > 0.0 &&
                     rr + Es < 1e30;
-    P->filter_on = on ? 1 : 0;
-    P->s_lo = on ? __double2float_rd(rr - Es) : 0.0f;
-    P->s_hi = on ? __double2float_ru(rr + Es) : 0.0f;
+    InstPlan ip;
+    ip.rr = rr;
+    ip.filter_on = on ? 1 : 0;
+    ip.s_lo = on ? __double2float_rd(rr - Es) : 0.0f;
+    ip.s_hi = on ? __double2float_ru(rr + Es) : 0.0f;
+    ip.inv_c = __double2float_rn(1.0 / I.c);
+    iplan[b] = ip;
+  }
+  if (m == 0) return;
+  GridPlan& G = gplan[(size_t)b * m + t];
+  if (k >= d) {
+    for (int l = 0; l < kMaxDim; ++l) G.Rf[k * kMaxDim + l] = 0.0f;
+    G.sf[k] = 0.0f;
+    G.E[k] = 0.0f;
+    G.qlo[k] = 0;
+    G.ext[k] = 1;
+    return;
+  }
+  const double c = I.c;
+  const double* R = T64 + I.T0 + (size_t)t * (d * d + d);
+  const double* s = R + d * d;
+  double ymin = s[k], ymax = s[k], A = fabs(s[k]);
+  for (int l = 0; l < kMaxDim; ++l) {
+    if (l < d) {
+      const double rkl = R[k * d + l];
+      const double a = rkl * lo[l], bb = rkl * hi[l];
+      ymin += fmin(a, bb);
+      ymax += fmax(a, bb);
+      A += fabs(rkl) * M[l];
+      G.Rf[k * kMaxDim + l] = __double2float_rn(rkl);
+    } else {
+      G.Rf[k * kMaxDim + l] = 0.0f;
+    }
+  }
+  G.sf[k] = __double2float_rn(s[k]);
+  // Two cells of margin on each side absorb every rounding difference between these sums
+  // and the per-point fma chains (both are far below one cell).
+  const double qmin = floor(ymin / c) - 2.0, qmax = floor(ymax / c) + 2.0;
+  if (!(qmin > -4.0e18 && qmax < 4.0e18)) {
+    G.qlo[k] = 0;
+    G.ext[k] = ~0ull;  // flagged as overflow by the range pass
+  } else {
+    G.qlo[k] = (long long)qmin;
+    G.ext[k] = (unsigned long long)((long long)qmax - (long long)qmin + 1);
+  }
+  const double E = (double)(d + 6) * 0x1.0p-24 * A / c * (1.0 + 1e-6) + 3e-12 / c;
+  G.E[k] = __double2float_ru(E);
+}
+
+// One block: strides and key range of every (instance, grid), their exclusive prefix (the
+// composite key bases), and the width of the composite key.
+__global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ inst, int B, int m,
+                                                      GridPlan* gplan,
+                                                      unsigned long long* bases, Status* st,
+                                                      int passes, int key64) {
+  __shared__ unsigned long long sbuf[32];
+  __shared__ unsigned long long carry;
+  __shared__ int overflow;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    overflow = 0;
+  }
+  __syncthreads();
+  const long long total_bt = (long long)B * m;
+  for (long long base = 0; base < total_bt; base += blockDim.x) {
+    const long long bt = base + threadIdx.x;
+    unsigned long long range = 0;
+    if (bt < total_bt) {
+      const int d = inst[bt / m].d;
+      GridPlan& G = gplan[bt];
+      unsigned long long strd = 1;
+      bool of = false;
+      for (int k = 0; k < kMaxDim; ++k) {
+        if (k < d) {
+          G.stride[k] = strd;
+          const unsigned long long e = G.ext[k];
+          if (e == ~0ull || __umul64hi(strd, e) != 0) of = true;
+          strd *= e;
+        } else {
+          G.stride[k] = 0;
+        }
+      }
+      if (of) {
+        atomicOr((unsigned int*)&overflow, 1u);
+        strd = 1;
+      }
+      G.range = strd;
+      range = strd;
+    }
+    // block exclusive scan of the ranges (with a carry across chunks)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long x = range;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sbuf[warp] = x;
+    __syncthreads();
+    unsigned long long wpre = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) wpre += sbuf[w];
+      tot += sbuf[w];
+    }
+    const unsigned long long ex = carry + wpre + x - range;
+    if (bt < total_bt) {
+      gplan[bt].base = ex;
+      bases[bt] = ex;
+      if (ex < carry) atomicOr((unsigned int*)&overflow, 1u);  // wrapped
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned long long nc = carry + tot;
+      if (nc < carry) overflow = 1;
+      carry = nc;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long total = carry;
+    const unsigned int bits = total <= 1 ? 0u : 64u - (unsigned)__clzll((long long)(total - 1));
+    st->sort_bits = bits;
+    if (overflow) atomicOr(&st->errors, kErrKeyOverflow);
+    const int need = (int)((bits + kRadixBits - 1) / kRadixBits);
+    if (need > passes || (!key64 && bits > 32)) atomicOr(&st->errors, kErrKeyBits);
   }
 }
 
@@ -224,42 +293,48 @@ __device__ __noinline__ long long exact_cell(const void* pts, int dtype, long lo
 }
 
 template <typename K, int DPAD>
-__global__ void __launch_bounds__(128) k_keys(const float* __restrict__ pf,
-                                              const void* __restrict__ pts, int dtype,
-                                              const double* __restrict__ T64,
-                                              const Plan* __restrict__ P, Status* st,
-                                              K* __restrict__ key_mat, K* __restrict__ comp,
-                                              uint32_t* __restrict__ vals, int n, int d, int m,
-                                              double c) {
+__global__ void __launch_bounds__(kPointBlock) k_keys(
+    const Inst* __restrict__ inst, int B, int m, int dtype, const float* __restrict__ pf,
+    const double* __restrict__ T64, const GridPlan* __restrict__ gplan,
+    const InstPlan* __restrict__ iplan, Status* st, K* __restrict__ key_mat,
+    K* __restrict__ comp, uint32_t* __restrict__ vals) {
+  __shared__ int s_b;
   extern __shared__ __align__(16) unsigned char smem[];
-  // layout: qlo, ext, stride (m*d 8-byte each), R (m*d*DPAD floats), s, E (m*d floats)
+  const int b = block_instance(inst, B, blockIdx.x, &s_b);
+  const Inst I = inst[b];
+  const int d = I.d;
+  // layout: qlo, ext, stride (m*d 8-byte each), base (m), R (m*d*DPAD floats), s, E (m*d)
   long long* sqlo = reinterpret_cast<long long*>(smem);
   unsigned long long* sext = reinterpret_cast<unsigned long long*>(sqlo + m * d);
   unsigned long long* sstr = sext + m * d;
-  float* sR = reinterpret_cast<float*>(sstr + m * d);
+  unsigned long long* sbase = sstr + m * d;
+  float* sR = reinterpret_cast<float*>(sbase + m);
   float* ss = sR + m * d * DPAD;
   float* sE = ss + m * d;
+  const GridPlan* Gb = gplan + (size_t)b * m;
   for (int x = threadIdx.x; x < m * d; x += blockDim.x) {
     const int t = x / d, k = x % d;
-    sqlo[x] = P->qlo[t][k];
-    sext[x] = P->ext[t][k];
-    sstr[x] = P->stride[t][k];
-    ss[x] = P->sf[t][k];
-    sE[x] = P->E[t][k];
+    sqlo[x] = Gb[t].qlo[k];
+    sext[x] = Gb[t].ext[k];
+    sstr[x] = Gb[t].stride[k];
+    ss[x] = Gb[t].sf[k];
+    sE[x] = Gb[t].E[k];
   }
+  for (int t = threadIdx.x; t < m; t += blockDim.x) sbase[t] = Gb[t].base;
   for (int x = threadIdx.x; x < m * d * DPAD; x += blockDim.x) {
     const int t = x / (d * DPAD), rem = x % (d * DPAD), k = rem / DPAD, l = rem % DPAD;
-    sR[x] = P->Rf[t][k * kMaxDim + l];
+    sR[x] = Gb[t].Rf[k * kMaxDim + l];
   }
   __syncthreads();
-  const int B = P->key_bits;
-  const float inv_c = P->inv_c;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const float inv_c = iplan[b].inv_c;
+  const double c = I.c;
+  const long long i = (blockIdx.x - I.blk0) * (long long)kPointBlock + threadIdx.x;
   unsigned int near_cnt = 0, rechecks = 0;
   bool range_err = false;
-  if (i < n) {
+  if (i < I.n) {
+    const long long g = I.p0 + i;
     float p[DPAD];
-    const float4* src = reinterpret_cast<const float4*>(pf + i * DPAD);
+    const float4* src = reinterpret_cast<const float4*>(pf + g * DPAD);
 #pragma unroll
     for (int v = 0; v < DPAD / 4; ++v) {
       const float4 q = src[v];
@@ -268,7 +343,7 @@ __global__ void __launch_bounds__(128) k_keys(const float* __restrict__ pf,
       p[4 * v + 2] = q.z;
       p[4 * v + 3] = q.w;
     }
-    const int stride = d * d + d;
+    const int tstride = d * d + d;
     for (int t = 0; t < m; ++t) {
       K key = 0;
       bool near = false;
@@ -284,7 +359,7 @@ __global__ void __launch_bounds__(128) k_keys(const float* __restrict__ pf,
         if (flo == fhi) {
           q = (long long)flo;
         } else {
-          q = exact_cell(pts, dtype, i, d, T64 + (size_t)t * stride, k, c, &near);
+          q = exact_cell(I.pts, dtype, i, d, T64 + I.T0 + (size_t)t * tstride, k, c, &near);
           ++rechecks;
         }
         long long off = q - sqlo[t * d + k];
@@ -294,9 +369,11 @@ __global__ void __launch_bounds__(128) k_keys(const float* __restrict__ pf,
         }
         key += (K)off * (K)sstr[t * d + k];
       }
-      key_mat[(size_t)i * m + t] = key;
-      comp[(size_t)t * n + i] = (m > 1 ? ((K)t << B) : (K)0) | key;
-      vals[(size_t)t * n + i] = (uint32_t)i;
+      key += (K)sbase[t];
+      key_mat[(size_t)g * m + t] = key;
+      const long long pos = I.p0 * m + (long long)t * I.n + i;
+      comp[pos] = key;
+      vals[pos] = (uint32_t)g;
       near_cnt += near ? 1u : 0u;
     }
   }
@@ -313,23 +390,17 @@ __global__ void __launch_bounds__(128) k_keys(const float* __restrict__ pf,
 
 template <int DPAD>
 void prep_impl(const BuildArgs& a, cudaStream_t s) {
-  const int threads = 256;
-  long long blocks = (a.n + threads - 1) / threads;
-  if (blocks > 4LL * a.num_sms) blocks = 4LL * a.num_sms;
-  if (blocks < 1) blocks = 1;
-  k_prep<DPAD><<<(unsigned)blocks, threads, 0, s>>>(a.pts, a.dtype, a.n, a.d, a.pf, a.st);
+  k_prep<DPAD><<<(unsigned)a.blocks, kPointBlock, 0, s>>>(a.inst, a.B, a.dtype, a.pf, a.bbox, a.st);
 }
 
 template <typename K, int DPAD>
-void keys_impl(const BuildArgs& a, cudaStream_t s) {
-  const int threads = 128;
-  const size_t smem = (size_t)a.m * a.d * (3 * 8 + (DPAD + 2) * 4);
+void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
+  const size_t smem = (size_t)a.m * maxd * (3 * 8 + (DPAD + 2) * 4) + (size_t)a.m * 8;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_keys<K, DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
-  k_keys<K, DPAD><<<blocks, threads, smem, s>>>(a.pf, a.pts, a.dtype, a.T64, a.plan, a.st,
-                                                (K*)a.key_mat, (K*)a.keys[0], a.vals[0], a.n,
-                                                a.d, a.m, a.c);
+  k_keys<K, DPAD><<<(unsigned)a.blocks, kPointBlock, smem, s>>>(
+      a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.st, (K*)a.key_mat,
+      (K*)a.keys[0], a.vals[0]);
 }
 
 }  // namespace
@@ -342,26 +413,28 @@ void launch_prep(const BuildArgs& a, cudaStream_t s) {
   }
 }
 
-void launch_plan(const BuildArgs& a, int assumed_bits, cudaStream_t s) {
-  int threads = a.m * kMaxDim;
-  if (threads < 64) threads = 64;
-  if (threads > 1024) threads = 1024;
-  k_plan<<<1, threads, 0, s>>>(a.plan, a.st, a.T64, a.n, a.d, a.m, a.dtype, a.r, a.c,
-                               assumed_bits);
+void launch_plan(const BuildArgs& a, cudaStream_t s) {
+  const long long threads = (long long)a.B * (a.m > 0 ? a.m : 1) * kMaxDim;
+  k_plan_axes<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a.inst, a.B, a.m, a.dtype, a.T64,
+                                                              a.bbox, a.iplan, a.gplan);
+  if (a.m > 0)
+    k_plan_ranges<<<1, 1024, 0, s>>>(a.inst, a.B, a.m, a.gplan, a.bases, a.st, a.passes,
+                                     a.key64 ? 1 : 0);
 }
 
 void launch_keys(const BuildArgs& a, cudaStream_t s) {
+  const int maxd = a.dpad;  // rows staged per grid never exceed the padded width
   if (a.key64) {
     switch (a.dpad) {
-      case 4: keys_impl<unsigned long long, 4>(a, s); break;
-      case 8: keys_impl<unsigned long long, 8>(a, s); break;
-      default: keys_impl<unsigned long long, 16>(a, s); break;
+      case 4: keys_impl<unsigned long long, 4>(a, maxd, s); break;
+      case 8: keys_impl<unsigned long long, 8>(a, maxd, s); break;
+      default: keys_impl<unsigned long long, 16>(a, maxd, s); break;
     }
   } else {
     switch (a.dpad) {
-      case 4: keys_impl<uint32_t, 4>(a, s); break;
-      case 8: keys_impl<uint32_t, 8>(a, s); break;
-      default: keys_impl<uint32_t, 16>(a, s); break;
+      case 4: keys_impl<uint32_t, 4>(a, maxd, s); break;
+      case 8: keys_impl<uint32_t, 8>(a, maxd, s); break;
+      default: keys_impl<uint32_t, 16>(a, maxd, s); break;
     }
   }
 }

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "rtg.h"
@@ -19,10 +20,13 @@ namespace {
 
 constexpr int64_t kNoAllocMaxPoints = 65536;
 constexpr size_t kStatusBytes = (sizeof(rtg::Status) + 255) & ~size_t(255);
-constexpr size_t kPlanBytes = (sizeof(rtg::Plan) + 255) & ~size_t(255);
+constexpr size_t kInstBytes = (sizeof(rtg::Inst) + 255) & ~size_t(255);
+constexpr size_t kIPlanBytes = (sizeof(rtg::InstPlan) + 255) & ~size_t(255);
+constexpr size_t kBoxBytes = rtg::kMaxDim * 2 * 8;
 constexpr size_t kRowsBytes = (size_t)kNoAllocMaxPoints * rtg::kMaxDim * 4;  // FP32 rows, dpad <= 16
 constexpr size_t kCountBytes = (size_t)kNoAllocMaxPoints * 4;
-constexpr size_t kScratchBytes = kStatusBytes + kPlanBytes + kRowsBytes + kCountBytes;
+constexpr size_t kScratchBytes =
+    kStatusBytes + kInstBytes + kIPlanBytes + kBoxBytes + kRowsBytes + kCountBytes;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -70,28 +74,39 @@ extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int
     return fail(RTG_E_CUDA, "cudaDeviceGetAttribute failed");
   cudaStream_t s = (cudaStream_t)stream;
 
+  char* p = (char*)base;
   rtg::BuildArgs a{};
-  a.pts = points;
-  a.dtype = dtype;
-  a.n = (int)n;
-  a.d = d;
+  a.B = 1;
   a.m = 0;
+  a.dtype = dtype;
   a.dpad = rtg::dpad_for(d);
-  a.r = r;
-  a.c = 1.0;
-  a.st = (rtg::Status*)base;
-  a.plan = (rtg::Plan*)((char*)base + kStatusBytes);
-  a.pf = (float*)((char*)base + kStatusBytes + kPlanBytes);
-  a.row_cnt = (unsigned int*)((char*)base + kStatusBytes + kPlanBytes + kRowsBytes);
+  a.n_total = n;
+  a.blocks = (n + rtg::kPointBlock - 1) / rtg::kPointBlock;
+  a.st = (rtg::Status*)p;
+  a.inst = (const rtg::Inst*)(p + kStatusBytes);
+  a.iplan = (rtg::InstPlan*)(p + kStatusBytes + kInstBytes);
+  a.bbox = (unsigned long long*)(p + kStatusBytes + kInstBytes + kIPlanBytes);
+  a.pf = (float*)(p + kStatusBytes + kInstBytes + kIPlanBytes + kBoxBytes);
+  a.row_cnt = (unsigned int*)(p + kStatusBytes + kInstBytes + kIPlanBytes + kBoxBytes + kRowsBytes);
   a.num_sms = sms;
-  // the counters and the bounding box must start at zero; every other region is fully
-  // rewritten (plan, point rows) or only incremented and never read (row counts)
-  if (cudaMemsetAsync(a.st, 0, sizeof(rtg::Status), s) != cudaSuccess)
-    return fail(RTG_E_CUDA, "cudaMemsetAsync failed");
+  rtg::Inst I{};
+  I.pts = points;
+  I.n = (int)n;
+  I.d = d;
+  I.r = r;
+  I.c = 1.0;
+  // the counters and the bounding box must start at zero; the instance record is copied in;
+  // every other region is fully rewritten (plan, point rows) or only incremented and never
+  // read (row counts)
+  if (cudaMemsetAsync(a.st, 0, sizeof(rtg::Status), s) != cudaSuccess ||
+      cudaMemsetAsync(a.bbox, 0, kBoxBytes, s) != cudaSuccess ||
+      cudaMemcpyAsync((void*)a.inst, &I, sizeof(I), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(RTG_E_CUDA, "scratch set-up failed");
   rtg::launch_prep(a, s);
-  rtg::launch_plan(a, 64, s);
-  rtg::launch_brute(a, false, s);
+  rtg::launch_plan(a, s);
+  rtg::launch_brute(a, rtg::kCount, s);
   rtg::Status h;
+  std::memset(&h, 0, sizeof(h));
   cudaError_t e = cudaMemcpyAsync(&h, a.st, sizeof(rtg::Status), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(RTG_E_CUDA, cudaGetErrorString(e));

@@ -1,10 +1,10 @@
 // In-cell pair enumeration and CSR assembly (Alg. 1 lines 8-9 and the dedupe of Sec. III-B
-// of arXiv:1409.8112).
+// of arXiv:1409.8112), for a batch of instances.
 //
-// After the sort every (grid, cell) is a run of equal keys.  A block owns the cells whose
-// first position lies in its slice of kSlice sorted positions: it finds them with adjacent
-// key comparisons, stages their points (FP32, padded rows) in shared memory and walks all
-// pairs (a < b) of every cell with at most kSmax points as one flat candidate range.  Cells
+// After the sort every (instance, grid, cell) is a run of equal keys.  A block owns the cells
+// whose first position lies in its slice of kSlice sorted positions: it finds them with
+// adjacent key comparisons, stages their points (FP32, padded rows) in shared memory and walks
+// all pairs (a < b) of every cell with at most kSmax points as one flat candidate range.  Cells
 // with more points go to the tiled large-cell kernel.
 //
 // Dedupe without an auxiliary set: the distance test does not depend on the grid, so pair
@@ -17,8 +17,9 @@
 // distance is outside [s_lo, s_hi], the proven error band around fl(r*r) (see the plan
 // kernel); otherwise the FP64 reference sequence decides.
 //
-// Each enumeration runs twice: COUNT (per-row counts, statistics, large-cell list), then,
-// after the row-pointer scan, WRITE (columns into their rows).  Rows are sorted at the end.
+// Modes: EMIT writes reported pairs to a pair buffer (one atomic per warp) and counts rows;
+// after the scan, scatter places them.  COUNT then WRITE enumerates twice and needs no pair
+// buffer (for outputs too large to hold twice).  Rows are sorted at the end.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -98,26 +99,35 @@ __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long lo
   return wpre + x - v;
 }
 
-// Per-thread tallies of the COUNT pass.
+// Per-thread tallies.
 struct Tally {
   unsigned int owned = 0, rechecks = 0, near_r = 0, pairs = 0;
   bool overflow = false;
 };
 
-// The decision for one candidate pair (i < j) of grid t.  Returns true if it is reported.
-template <typename K, int DPAD, bool WRITE>
-__device__ __forceinline__ void visit_pair(unsigned int i, unsigned int j, int t, const float* pa,
-                                           const float* pb, const K* __restrict__ key_mat,
-                                           const Plan* __restrict__ P, const void* pts,
-                                           int dtype, unsigned int* row_cnt,
-                                           const long long* __restrict__ row_ptr, int* col,
-                                           long long col_cap, int symmetric, Tally& tl) {
-  const int m = P->m;
+// Where the pairs go.
+struct Sink {
+  unsigned int* row_cnt;
+  const long long* row_ptr;
+  int* col;
+  long long col_cap;
+  unsigned long long* pair_buf;
+  long long pair_cap;
+  unsigned long long* emitted;
+  int symmetric;
+};
+
+// Decide one candidate pair (i < j, global indices) of grid t of instance I.
+template <typename K, int DPAD, int MODE>
+__device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int t, const float* pa,
+                                            const float* pb, const K* __restrict__ key_mat, int m,
+                                            const Inst& I, const InstPlan& IP, int dtype,
+                                            Tally& tl) {
   const K* ki = key_mat + (size_t)i * m;
   const K* kj = key_mat + (size_t)j * m;
   for (int u = 0; u < t; ++u)
-    if (__ldg(ki + u) == __ldg(kj + u)) return;  // an earlier grid owns this pair
-  ++tl.owned;
+    if (__ldg(ki + u) == __ldg(kj + u)) return false;  // an earlier grid owns this pair
+  if (MODE != kWrite) ++tl.owned;
   float sf = 0.0f;
 #pragma unroll
   for (int l = 0; l < DPAD; ++l) {
@@ -125,37 +135,62 @@ __device__ __forceinline__ void visit_pair(unsigned int i, unsigned int j, int t
     sf = fmaf(e, e, sf);
   }
   bool keep;
-  if (P->filter_on && sf < P->s_lo) {
+  if (IP.filter_on && sf < IP.s_lo) {
     keep = true;
-  } else if (P->filter_on && sf > P->s_hi) {
+  } else if (IP.filter_on && sf > IP.s_hi) {
     keep = false;
   } else {
-    const double s = exact_dist2(pts, dtype, i, j, P->d);
-    keep = s <= P->rr;
-    ++tl.rechecks;
-    if (!WRITE && fabs(__dsub_rn(__dsqrt_rn(s), P->r)) <= __dmul_rn(1e-12, P->r)) ++tl.near_r;
+    const double s = exact_dist2(I.pts, dtype, (long long)i - I.p0, (long long)j - I.p0, I.d);
+    keep = s <= IP.rr;
+    if (MODE != kWrite) {
+      ++tl.rechecks;
+      if (fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r)) ++tl.near_r;
+    }
   }
-  if (!keep) return;
-  ++tl.pairs;
-  if (!WRITE) {
-    atomicAdd(&row_cnt[i], 1u);
-    if (symmetric) atomicAdd(&row_cnt[j], 1u);
+  if (keep && MODE != kWrite) ++tl.pairs;
+  return keep;
+}
+
+// Deliver a decided pair.  Called by all 32 lanes of a warp together (keep may be false).
+template <int MODE>
+__device__ __forceinline__ void deliver(bool keep, unsigned int i, unsigned int j, const Sink& sk,
+                                        Tally& tl) {
+  if (MODE == kEmit) {
+    const unsigned int mask = __ballot_sync(0xffffffffu, keep);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(sk.emitted, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (keep) {
+      const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1));
+      if ((long long)slot < sk.pair_cap) sk.pair_buf[slot] = ((unsigned long long)i << 32) | j;
+      else tl.overflow = true;
+      atomicAdd(&sk.row_cnt[i], 1u);
+      if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
+    }
+  } else if (MODE == kCount) {
+    if (keep) {
+      atomicAdd(&sk.row_cnt[i], 1u);
+      if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
+    }
   } else {
-    const long long pi = row_ptr[i] + atomicAdd(&row_cnt[i], 1u);
-    if (pi < col_cap) col[pi] = (int)j; else tl.overflow = true;
-    if (symmetric) {
-      const long long pj = row_ptr[j] + atomicAdd(&row_cnt[j], 1u);
-      if (pj < col_cap) col[pj] = (int)i; else tl.overflow = true;
+    if (keep) {
+      const long long pi = sk.row_ptr[i] + atomicAdd(&sk.row_cnt[i], 1u);
+      if (pi < sk.col_cap) sk.col[pi] = (int)j; else tl.overflow = true;
+      if (sk.symmetric) {
+        const long long pj = sk.row_ptr[j] + atomicAdd(&sk.row_cnt[j], 1u);
+        if (pj < sk.col_cap) sk.col[pj] = (int)i; else tl.overflow = true;
+      }
     }
   }
 }
 
-template <bool WRITE>
+template <int MODE>
 __device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigned int* sbuf) {
-  if (WRITE) {
-    if (__syncthreads_or(tl.overflow) && threadIdx.x == 0) atomicOr(&st->errors, kErrColOverflow);
-    return;
-  }
+  if (__syncthreads_or(tl.overflow) && threadIdx.x == 0)
+    atomicOr(&st->errors, MODE == kEmit ? kErrPairOverflow : kErrColOverflow);
+  if (MODE == kWrite) return;
   unsigned int tot;
   block_excl_scan(tl.owned, &tot, sbuf);
   if (threadIdx.x == 0 && tot) atomicAdd(&st->owned_candidates, (unsigned long long)tot);
@@ -167,26 +202,32 @@ __device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigne
   if (threadIdx.x == 0 && tot) atomicAdd(&st->pairs, (unsigned long long)tot);
 }
 
-template <typename K>
-__device__ __forceinline__ int grid_of(K key, int B, int m) {
-  return m > 1 ? (int)(key >> B) : 0;
+// (instance, grid) of a composite key: the last base <= key.
+__device__ __forceinline__ int find_bt(unsigned long long key,
+                                       const unsigned long long* __restrict__ bases, int nbt) {
+  int lo = 0, hi = nbt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(bases + mid) <= key) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
-template <typename K, int DPAD, bool WRITE>
+template <typename K, int DPAD, int MODE>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
     const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N,
-    const float* __restrict__ pf, const void* __restrict__ pts, int dtype,
-    const K* __restrict__ key_mat, const Plan* __restrict__ P, Status* st, unsigned int* row_cnt,
-    const long long* __restrict__ row_ptr, int* col, long long col_cap, LargeCell* large,
-    unsigned int large_cap, int symmetric) {
+    const float* __restrict__ pf, int dtype, const K* __restrict__ key_mat, int m,
+    const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
+    const unsigned long long* __restrict__ bases, int nbt, Status* st, Sink sk,
+    LargeCell* large, unsigned int large_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* s_pt = reinterpret_cast<float*>(smem);                      // kStage * DPAD
-  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_pt + kStage * DPAD);  // kStage
-  K* s_key = reinterpret_cast<K*>(s_idx + kStage);                     // kKeyWin
+  float* s_pt = reinterpret_cast<float*>(smem);                          // kStage * DPAD
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_pt + kStage * DPAD);    // kStage
+  K* s_key = reinterpret_cast<K*>(s_idx + kStage);                       // kKeyWin
   unsigned int* c_start = reinterpret_cast<unsigned int*>(s_key + kKeyWin);  // kSlice + 1
-  unsigned int* c_cand = c_start + kSlice + 1;                                // kSlice + 1
-  unsigned char* c_grid = reinterpret_cast<unsigned char*>(c_cand + kSlice + 1);  // kSlice
-  __shared__ unsigned int s_end, s_ncells, s_total, s_stage_lo, s_stage_hi;
+  unsigned int* c_cand = c_start + kSlice + 1;                               // kSlice + 1
+  unsigned int* c_bt = c_cand + kSlice + 1;                                  // kSlice
+  __shared__ unsigned int s_end, s_stage_lo, s_stage_hi, s_total;
   __shared__ unsigned int sbuf[kPairThreads / 32];
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned long long s_maxcell;
@@ -195,7 +236,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
   const long long lo = (long long)blockIdx.x * kSlice;
   const long long hi = min(lo + kSlice, N);
   const long long win_end = min(hi + kSmax + 1, N);
-  const int B = P->key_bits, m = P->m;
 
   for (long long x = lo - 1 + tid; x < win_end; x += kPairThreads)
     if (x >= 0) s_key[x - lo + 1] = skeys[x];
@@ -203,7 +243,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
     s_end = kUnknown;
     s_maxcell = 0;
   }
-  if (!WRITE)
+  if (MODE != kWrite)
     for (int g = tid; g < kMaxGrids; g += kPairThreads) s_gcand[g] = 0;
   __syncthreads();
   auto is_head = [&](long long x) -> bool {
@@ -211,7 +251,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
   };
   for (long long x = hi + tid; x < win_end; x += kPairThreads)
     if (is_head(x)) atomicMin(&s_end, (unsigned int)(x - lo));
-  // compact the heads in [lo, hi): four consecutive positions per thread
   constexpr int kPer = kSlice / kPairThreads;
   unsigned int flags = 0, cnt = 0;
 #pragma unroll
@@ -228,26 +267,24 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
   for (int q = 0; q < kPer; ++q)
     if (flags & (1u << q)) c_start[w++] = (unsigned int)(tid * kPer + q);
   if (tid == 0) {
-    s_ncells = ncells;
     const unsigned int end_rel =
         s_end != kUnknown ? s_end : (win_end == N ? (unsigned int)(N - lo) : kUnknown);
     c_start[ncells] = end_rel;
   }
   __syncthreads();
   if (ncells == 0) return;
-  // classify cells
   for (unsigned int e = tid; e < ncells; e += kPairThreads) {
     const unsigned int st_rel = c_start[e], en = c_start[e + 1];
     const K key = s_key[st_rel + 1];
-    const int g = grid_of(key, B, m);
-    c_grid[e] = (unsigned char)g;
+    const int bt = find_bt((unsigned long long)key, bases, nbt);
+    const int g = bt % m;
+    c_bt[e] = (unsigned int)bt;
     unsigned long long size = en == kUnknown ? 0ull : (unsigned long long)(en - st_rel);
     unsigned int cand = 0;
     if (en == kUnknown || size > (unsigned long long)kSmax) {
-      if (!WRITE) {
+      if (MODE != kWrite) {
         if (en == kUnknown) {
-          // the run continues past the window: first position with a larger key
-          long long a = win_end, b = N;
+          long long a = win_end, b = N;  // the run continues past the window
           while (a < b) {
             const long long mid = (a + b) >> 1;
             if (skeys[mid] == key) a = mid + 1; else b = mid;
@@ -258,7 +295,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
         if (slot < large_cap) {
           large[slot].start = (unsigned long long)(lo + st_rel);
           large[slot].size = (unsigned int)size;
-          large[slot].grid = (unsigned int)g;
+          large[slot].grid = (unsigned short)g;
+          large[slot].inst = (unsigned short)(bt / m);
         } else {
           atomicOr(&st->errors, kErrLargeOverflow);
         }
@@ -267,7 +305,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
       }
     } else {
       cand = (unsigned int)(size * (size - 1) / 2);
-      if (!WRITE) {
+      if (MODE != kWrite) {
         if (cand) atomicAdd(&s_gcand[g], (unsigned long long)cand);
         atomicMax(&s_maxcell, size);
       }
@@ -275,7 +313,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
     c_cand[e] = cand;
   }
   __syncthreads();
-  // exclusive scan of the candidate counts (ncells <= kSlice)
   {
     unsigned int v[kPer], sum = 0;
 #pragma unroll
@@ -305,7 +342,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
     }
   }
   __syncthreads();
-  if (!WRITE) {
+  if (MODE != kWrite) {
     if (tid < m && s_gcand[tid]) atomicAdd(&st->candidates[tid], s_gcand[tid]);
     if (tid == 0 && s_maxcell) atomicMax(&st->max_cell, s_maxcell);
   }
@@ -322,26 +359,36 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
       for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
     }
     __syncthreads();
-    for (unsigned int c = tid; c < T; c += kPairThreads) {
-      int el = 0, eh = (int)ncells - 1;
-      while (el < eh) {
-        const int mid = (el + eh + 1) >> 1;
-        if (c_cand[mid] <= c) el = mid; else eh = mid - 1;
+    const int lane = tid & 31;
+    for (unsigned int cb = tid & ~31u; cb < T; cb += kPairThreads) {
+      const unsigned int c = cb + lane;
+      bool keep = false;
+      unsigned int i = 0, j = 0;
+      if (c < T) {
+        int el = 0, eh = (int)ncells - 1;
+        while (el < eh) {
+          const int mid = (el + eh + 1) >> 1;
+          if (c_cand[mid] <= c) el = mid; else eh = mid - 1;
+        }
+        const unsigned int l = c - c_cand[el];
+        unsigned int b = (unsigned int)((1.0f + sqrtf(8.0f * (float)l + 1.0f)) * 0.5f);
+        while (b * (b - 1) / 2 > l) --b;
+        while ((b + 1) * b / 2 <= l) ++b;
+        const unsigned int a = l - b * (b - 1) / 2;
+        const unsigned int xa = c_start[el] + a - stage_lo, xb = c_start[el] + b - stage_lo;
+        const unsigned int ia = s_idx[xa], ib = s_idx[xb];
+        i = min(ia, ib);
+        j = max(ia, ib);
+        const unsigned int bt = c_bt[el];
+        const int inst_b = (int)(bt / m);
+        keep = decide_pair<K, DPAD, MODE>(i, j, (int)(bt % m), s_pt + (size_t)xa * DPAD,
+                                          s_pt + (size_t)xb * DPAD, key_mat, m, inst[inst_b],
+                                          iplan[inst_b], dtype, tl);
       }
-      const unsigned int l = c - c_cand[el];
-      unsigned int b = (unsigned int)((1.0f + sqrtf(8.0f * (float)l + 1.0f)) * 0.5f);
-      while (b * (b - 1) / 2 > l) --b;
-      while ((b + 1) * b / 2 <= l) ++b;
-      const unsigned int a = l - b * (b - 1) / 2;
-      const unsigned int xa = c_start[el] + a - stage_lo, xb = c_start[el] + b - stage_lo;
-      const unsigned int ia = s_idx[xa], ib = s_idx[xb];
-      const unsigned int i = min(ia, ib), j = max(ia, ib);
-      visit_pair<K, DPAD, WRITE>(i, j, c_grid[el], s_pt + (size_t)xa * DPAD,
-                                 s_pt + (size_t)xb * DPAD, key_mat, P, pts, dtype, row_cnt,
-                                 row_ptr, col, col_cap, symmetric, tl);
+      deliver<MODE>(keep, i, j, sk, tl);
     }
   }
-  flush_tally<WRITE>(tl, st, sbuf);
+  flush_tally<MODE>(tl, st, sbuf);
 }
 
 // Job offsets for the large cells: cell e has ceil(size / kTL) row tiles.
@@ -369,19 +416,19 @@ __global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restric
   }
 }
 
-template <typename K, int DPAD, bool WRITE>
+template <typename K, int DPAD, int MODE>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
-    const uint32_t* __restrict__ svals, const float* __restrict__ pf, const void* __restrict__ pts,
-    int dtype, const K* __restrict__ key_mat, const Plan* __restrict__ P, Status* st,
-    const LargeCell* __restrict__ large, unsigned int cap, const unsigned long long* job_off,
-    unsigned int* row_cnt, const long long* __restrict__ row_ptr, int* col, long long col_cap,
-    int symmetric) {
+    const uint32_t* __restrict__ svals, const float* __restrict__ pf, int dtype,
+    const K* __restrict__ key_mat, int m, const Inst* __restrict__ inst,
+    const InstPlan* __restrict__ iplan, Status* st, const LargeCell* __restrict__ large,
+    unsigned int cap, const unsigned long long* job_off, Sink sk) {
   __shared__ __align__(16) float sa[kTL * DPAD];
   __shared__ __align__(16) float sb[kTL * DPAD];
   __shared__ uint32_t ia[kTL], ib[kTL];
   __shared__ unsigned int sbuf[kPairThreads / 32];
   const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
   const unsigned long long J = L ? job_off[L] : 0;
+  const int lane = threadIdx.x & 31;
   Tally tl;
   for (unsigned long long job = blockIdx.x; job < J; job += gridDim.x) {
     long long el = 0, eh = (long long)L - 1;
@@ -390,6 +437,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
       if (job_off[mid] <= job) el = mid; else eh = mid - 1;
     }
     const LargeCell cell = large[el];
+    const Inst I = inst[cell.inst];
+    const InstPlan IP = iplan[cell.inst];
     const unsigned int s = cell.size;
     const unsigned int a0 = (unsigned int)(job - job_off[el]) * kTL;
     const unsigned int na = min((unsigned int)kTL, s - a0);
@@ -414,25 +463,88 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
         for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
       }
       __syncthreads();
-      for (unsigned int q = threadIdx.x; q < na * nb; q += blockDim.x) {
-        const unsigned int x = q / nb, y = q % nb;
-        if (a0 + x >= b0 + y) continue;
-        const unsigned int i = min(ia[x], ib[y]), j = max(ia[x], ib[y]);
-        visit_pair<K, DPAD, WRITE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD, key_mat,
-                                   P, pts, dtype, row_cnt, row_ptr, col, col_cap, symmetric, tl);
+      const unsigned int total = na * nb;
+      for (unsigned int qb = threadIdx.x & ~31u; qb < total; qb += blockDim.x) {
+        const unsigned int q = qb + lane;
+        bool keep = false;
+        unsigned int i = 0, j = 0;
+        if (q < total) {
+          const unsigned int x = q / nb, y = q % nb;
+          if (a0 + x < b0 + y) {
+            i = min(ia[x], ib[y]);
+            j = max(ia[x], ib[y]);
+            keep = decide_pair<K, DPAD, MODE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD,
+                                              key_mat, m, I, IP, dtype, tl);
+          }
+        }
+        deliver<MODE>(keep, i, j, sk, tl);
       }
     }
   }
-  flush_tally<WRITE>(tl, st, sbuf);
+  flush_tally<MODE>(tl, st, sbuf);
+}
+
+// Exact set of Sec. I: every pair (i < j) of one instance checked, in 128 x 128 tiles
+// (bi <= bj), with the same FP32 filter and FP64 recheck as the in-cell path.
+constexpr int kBT = 128;
+
+template <int DPAD, int MODE>
+__global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict__ pf, int dtype,
+                                                        const Inst* __restrict__ inst,
+                                                        const InstPlan* __restrict__ iplan,
+                                                        Status* st, Sink sk) {
+  __shared__ __align__(16) float sa[kBT * DPAD];
+  __shared__ __align__(16) float sb[kBT * DPAD];
+  __shared__ unsigned int sbuf[kPairThreads / 32];
+  const Inst I = inst[0];
+  const InstPlan IP = iplan[0];
+  const long long n = I.n;
+  const long long nt = (n + kBT - 1) / kBT;
+  const long long jobs = nt * (nt + 1) / 2;
+  Tally tl;
+  for (long long job = blockIdx.x; job < jobs; job += gridDim.x) {
+    long long bj = (long long)((sqrt(8.0 * (double)job + 1.0) - 1.0) * 0.5);
+    while (bj * (bj + 1) / 2 > job) --bj;
+    while ((bj + 1) * (bj + 2) / 2 <= job) ++bj;
+    const long long bi = job - bj * (bj + 1) / 2;
+    const long long i0 = bi * kBT, j0 = bj * kBT;
+    const int na = (int)min((long long)kBT, n - i0), nb = (int)min((long long)kBT, n - j0);
+    __syncthreads();
+    for (int x = threadIdx.x; x < 2 * kBT; x += blockDim.x) {
+      const bool first = x < kBT;
+      const int xx = first ? x : x - kBT;
+      const int cnt = first ? na : nb;
+      float* dst = (first ? sa : sb) + xx * DPAD;
+      if (xx < cnt) {
+        const float4* src =
+            reinterpret_cast<const float4*>(pf + (size_t)(I.p0 + (first ? i0 : j0) + xx) * DPAD);
+#pragma unroll
+        for (int v = 0; v < DPAD / 4; ++v) reinterpret_cast<float4*>(dst)[v] = __ldg(src + v);
+      }
+    }
+    __syncthreads();
+    const int y = threadIdx.x % kBT;
+    for (int x = threadIdx.x / kBT; x < na; x += kPairThreads / kBT) {
+      const long long li = i0 + x, lj = j0 + y;
+      const bool valid = y < nb && li < lj;
+      bool keep = false;
+      const unsigned int i = (unsigned int)(I.p0 + li), j = (unsigned int)(I.p0 + lj);
+      if (valid)
+        keep = decide_pair<uint32_t, DPAD, MODE>(i, j, 0, sa + x * DPAD, sb + y * DPAD, nullptr,
+                                                 1, I, IP, dtype, tl);
+      deliver<MODE>(keep, i, j, sk, tl);
+    }
+  }
+  flush_tally<MODE>(tl, st, sbuf);
 }
 
 // Row counts -> row pointers (exclusive scan, single pass with decoupled look-back); the
-// counts are reset to zero so that the WRITE pass can use them as fill cursors.
+// counts are reset to zero so that the scatter or WRITE pass can use them as fill cursors.
 constexpr int kScanItems = 16;
 constexpr int kScanTile = 256 * kScanItems;
 
-__global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, long long* row_ptr, int n,
-                                              unsigned long long* lookback,
+__global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, long long* row_ptr,
+                                              long long n, unsigned long long* lookback,
                                               unsigned int* tile_counter, Status* st,
                                               unsigned int tiles) {
   __shared__ unsigned long long sbuf[8];
@@ -494,43 +606,80 @@ __global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, long long* 
   }
 }
 
-__device__ __forceinline__ int bitonic32(int v, int lane) {
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int other = __shfl_xor_sync(0xffffffffu, v, j);
-      const bool up = (lane & k) == 0;
-      const bool lower = (lane & j) == 0;
-      v = (lower == up) ? min(v, other) : max(v, other);
+// Pair buffer -> columns in their rows (row order fixed later by the row sort).
+__global__ void __launch_bounds__(256) k_scatter(const unsigned long long* __restrict__ pairs,
+                                                 long long cap, const Status* st,
+                                                 unsigned int* row_cnt,
+                                                 const long long* __restrict__ row_ptr, int* col,
+                                                 long long col_cap, int symmetric,
+                                                 unsigned int* errors) {
+  const long long cnt = min((long long)st->emitted, cap);
+  bool overflow = false;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
+       k += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long p = pairs[k];
+    const unsigned int i = (unsigned int)(p >> 32), j = (unsigned int)p;
+    const long long pi = row_ptr[i] + atomicAdd(&row_cnt[i], 1u);
+    if (pi < col_cap) col[pi] = (int)j; else overflow = true;
+    if (symmetric) {
+      const long long pj = row_ptr[j] + atomicAdd(&row_cnt[j], 1u);
+      if (pj < col_cap) col[pj] = (int)i; else overflow = true;
     }
   }
-  return v;
+  if (overflow) atomicOr(errors, kErrColOverflow);
 }
 
-// One warp per row: rows of at most 32 entries are sorted in registers; longer rows are
-// queued for the block kernel.
-__global__ void __launch_bounds__(256) k_rowsort_warp(const long long* __restrict__ row_ptr,
-                                                      int* col, int n, unsigned int* long_rows,
-                                                      unsigned int* long_count) {
-  const int lane = threadIdx.x & 31;
-  const long long row = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+template <int L>
+__device__ __forceinline__ void bitonic_regs(int* v) {
+#pragma unroll
+  for (int k = 2; k <= L; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int x = 0; x < L; ++x) {
+        const int y = x ^ j;
+        if (y > x) {
+          const bool asc = (x & k) == 0;
+          if (asc ? v[x] > v[y] : v[x] < v[y]) {
+            const int t = v[x];
+            v[x] = v[y];
+            v[y] = t;
+          }
+        }
+      }
+}
+
+// One thread per row: rows of at most 16 entries are sorted in registers (bitonic network
+// with +infinity padding); longer rows are queued for the block kernel.  Rows that reach past
+// col_cap (only when an undersized buffer overflowed and the build will be re-run) are left
+// alone.
+__global__ void __launch_bounds__(256) k_rowsort_thread(const long long* __restrict__ row_ptr,
+                                                        int* col, long long n, long long col_cap,
+                                                        unsigned int* long_rows,
+                                                        unsigned int* long_count) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= n) return;
-  const long long b = row_ptr[row], e = row_ptr[row + 1], len = e - b;
-  if (len <= 1) return;
-  if (len <= 32) {
-    int v = lane < len ? col[b + lane] : INT_MAX;
-    v = bitonic32(v, lane);
-    if (lane < len) col[b + lane] = v;
-  } else if (lane == 0) {
+  const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
+  if (len <= 1 || b + len > col_cap) return;
+  if (len > 16) {
     long_rows[atomicAdd(long_count, 1u)] = (unsigned int)row;
+    return;
   }
+  int v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = q < len ? col[b + q] : INT_MAX;
+  if (len <= 4) bitonic_regs<4>(v);
+  else if (len <= 8) bitonic_regs<8>(v);
+  else bitonic_regs<16>(v);
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (q < len) col[b + q] = v[q];
 }
 
 constexpr int kRowSmem = 8192;
 
 __global__ void __launch_bounds__(256) k_rowsort_long(const long long* __restrict__ row_ptr,
-                                                      int* col,
+                                                      int* col, long long col_cap,
                                                       const unsigned int* __restrict__ long_rows,
                                                       const unsigned int* long_count) {
   __shared__ int buf[kRowSmem];
@@ -538,6 +687,7 @@ __global__ void __launch_bounds__(256) k_rowsort_long(const long long* __restric
   for (unsigned int k = blockIdx.x; k < cnt; k += gridDim.x) {
     const unsigned int row = long_rows[k];
     const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
+    if (b + len > col_cap) continue;  // uniform across the block: same row for all threads
     long long L = 1;
     while (L < len) L <<= 1;
     __syncthreads();
@@ -584,139 +734,113 @@ __global__ void __launch_bounds__(256) k_rowsort_long(const long long* __restric
   }
 }
 
-// Exact set of Sec. I: every pair (i < j) checked, in 128 x 128 tiles (bi <= bj), with the
-// same FP32 filter and FP64 recheck as the in-cell path.
-constexpr int kBT = 128;
-
-template <int DPAD, bool WRITE>
-__global__ void __launch_bounds__(kPairThreads) k_brute(
-    const float* __restrict__ pf, const void* __restrict__ pts, int dtype,
-    const Plan* __restrict__ P, Status* st, int n, unsigned int* row_cnt,
-    const long long* __restrict__ row_ptr, int* col, long long col_cap, int symmetric) {
-  __shared__ __align__(16) float sa[kBT * DPAD];
-  __shared__ __align__(16) float sb[kBT * DPAD];
-  __shared__ unsigned int sbuf[kPairThreads / 32];
-  const long long nt = ((long long)n + kBT - 1) / kBT;
-  const long long jobs = nt * (nt + 1) / 2;
-  Tally tl;
-  for (long long job = blockIdx.x; job < jobs; job += gridDim.x) {
-    long long bj = (long long)((sqrt(8.0 * (double)job + 1.0) - 1.0) * 0.5);
-    while (bj * (bj + 1) / 2 > job) --bj;
-    while ((bj + 1) * (bj + 2) / 2 <= job) ++bj;
-    const long long bi = job - bj * (bj + 1) / 2;
-    const long long i0 = bi * kBT, j0 = bj * kBT;
-    const int na = (int)min((long long)kBT, n - i0), nb = (int)min((long long)kBT, n - j0);
-    __syncthreads();
-    for (int x = threadIdx.x; x < 2 * kBT; x += blockDim.x) {
-      const bool first = x < kBT;
-      const int xx = first ? x : x - kBT;
-      const int cnt = first ? na : nb;
-      float* dst = (first ? sa : sb) + xx * DPAD;
-      if (xx < cnt) {
-        const float4* src = reinterpret_cast<const float4*>(pf + (size_t)((first ? i0 : j0) + xx) * DPAD);
-#pragma unroll
-        for (int v = 0; v < DPAD / 4; ++v) reinterpret_cast<float4*>(dst)[v] = __ldg(src + v);
-      }
-    }
-    __syncthreads();
-    const int y = threadIdx.x % kBT;
-    if (y < nb) {
-      for (int x = threadIdx.x / kBT; x < na; x += kPairThreads / kBT) {
-        const long long i = i0 + x, j = j0 + y;
-        if (i >= j) continue;
-        visit_pair<uint32_t, DPAD, WRITE>((unsigned int)i, (unsigned int)j, 0, sa + x * DPAD,
-                                          sb + y * DPAD, nullptr, P, pts, dtype, row_cnt,
-                                          row_ptr, col, col_cap, symmetric, tl);
-      }
-    }
-  }
-  flush_tally<WRITE>(tl, st, sbuf);
+Sink make_sink(const BuildArgs& a) {
+  Sink sk;
+  sk.row_cnt = a.row_cnt;
+  sk.row_ptr = a.row_ptr;
+  sk.col = a.col;
+  sk.col_cap = a.col_cap;
+  sk.pair_buf = a.pair_buf;
+  sk.pair_cap = a.pair_cap;
+  sk.emitted = &a.st->emitted;
+  sk.symmetric = a.symmetric;
+  return sk;
 }
 
-template <int DPAD>
-void brute_impl(const BuildArgs& a, bool write, cudaStream_t s) {
+template <int DPAD, int MODE>
+void brute_impl(const BuildArgs& a, cudaStream_t s) {
   const unsigned blocks = (unsigned)(8 * a.num_sms);
-  if (write)
-    k_brute<DPAD, true><<<blocks, kPairThreads, 0, s>>>(a.pf, a.pts, a.dtype, a.plan, a.st, a.n,
-                                                        a.row_cnt, a.row_ptr, a.col, a.col_cap,
-                                                        a.symmetric);
-  else
-    k_brute<DPAD, false><<<blocks, kPairThreads, 0, s>>>(a.pf, a.pts, a.dtype, a.plan, a.st, a.n,
-                                                         a.row_cnt, nullptr, nullptr, 0,
-                                                         a.symmetric);
+  k_brute<DPAD, MODE><<<blocks, kPairThreads, 0, s>>>(a.pf, a.dtype, a.inst, a.iplan, a.st,
+                                                      make_sink(a));
+}
+
+template <typename K, int DPAD, int MODE>
+void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
+  const long long N = a.n_total * a.m;
+  const unsigned blocks = (unsigned)((N + kSlice - 1) / kSlice);
+  const size_t smem = (size_t)kStage * DPAD * 4 + (size_t)kStage * 4 + (size_t)kKeyWin * sizeof(K) +
+                      (size_t)(kSlice + 1) * 8 + (size_t)kSlice * 4;
+  const K* sk = (const K*)a.keys[sorted_buf];
+  const uint32_t* sv = a.vals[sorted_buf];
+  cudaFuncSetAttribute(k_pairs_small<K, DPAD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  k_pairs_small<K, DPAD, MODE><<<blocks, kPairThreads, smem, s>>>(
+      sk, sv, N, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases, a.B * a.m,
+      a.st, make_sink(a), a.large, a.large_cap);
+  if (MODE != kWrite) k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
+  k_pairs_large<K, DPAD, MODE><<<(unsigned)(4 * a.num_sms), kPairThreads, 0, s>>>(
+      sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
+      a.large_job_off, make_sink(a));
 }
 
 template <typename K, int DPAD>
-void pairs_impl(const BuildArgs& a, int sorted_buf, bool write, cudaStream_t s) {
-  const long long N = (long long)a.n * a.m;
-  const unsigned blocks = (unsigned)((N + kSlice - 1) / kSlice);
-  const size_t smem = (size_t)kStage * DPAD * 4 + (size_t)kStage * 4 + (size_t)kKeyWin * sizeof(K) +
-                      (size_t)(kSlice + 1) * 8 + kSlice;
-  const K* sk = (const K*)a.keys[sorted_buf];
-  const uint32_t* sv = a.vals[sorted_buf];
-  unsigned int large_blocks = (unsigned)(4 * a.num_sms);
-  if (write) {
-    cudaFuncSetAttribute(k_pairs_small<K, DPAD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    k_pairs_small<K, DPAD, true><<<blocks, kPairThreads, smem, s>>>(
-        sk, sv, N, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.row_cnt, a.row_ptr,
-        a.col, a.col_cap, a.large, a.large_cap, a.symmetric);
-    k_pairs_large<K, DPAD, true><<<large_blocks, kPairThreads, 0, s>>>(
-        sv, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.large, a.large_cap,
-        a.large_job_off, a.row_cnt, a.row_ptr, a.col, a.col_cap, a.symmetric);
-  } else {
-    cudaFuncSetAttribute(k_pairs_small<K, DPAD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    k_pairs_small<K, DPAD, false><<<blocks, kPairThreads, smem, s>>>(
-        sk, sv, N, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.row_cnt, nullptr,
-        nullptr, 0, a.large, a.large_cap, a.symmetric);
-    k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
-    k_pairs_large<K, DPAD, false><<<large_blocks, kPairThreads, 0, s>>>(
-        sv, a.pf, a.pts, a.dtype, (const K*)a.key_mat, a.plan, a.st, a.large, a.large_cap,
-        a.large_job_off, a.row_cnt, nullptr, nullptr, 0, a.symmetric);
+int pairs_impl(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s) {
+  switch (mode) {
+    case kCount: pairs_mode<K, DPAD, kCount>(a, sorted_buf, s); return 3;
+    case kWrite: pairs_mode<K, DPAD, kWrite>(a, sorted_buf, s); return 2;
+    default: pairs_mode<K, DPAD, kEmit>(a, sorted_buf, s); return 3;
   }
 }
 
 }  // namespace
 
-int launch_pairs(const BuildArgs& a, int sorted_buf, bool write, cudaStream_t s) {
+int launch_pairs(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s) {
   if (a.key64) {
     switch (a.dpad) {
-      case 4: pairs_impl<unsigned long long, 4>(a, sorted_buf, write, s); break;
-      case 8: pairs_impl<unsigned long long, 8>(a, sorted_buf, write, s); break;
-      default: pairs_impl<unsigned long long, 16>(a, sorted_buf, write, s); break;
-    }
-  } else {
-    switch (a.dpad) {
-      case 4: pairs_impl<uint32_t, 4>(a, sorted_buf, write, s); break;
-      case 8: pairs_impl<uint32_t, 8>(a, sorted_buf, write, s); break;
-      default: pairs_impl<uint32_t, 16>(a, sorted_buf, write, s); break;
+      case 4: return pairs_impl<unsigned long long, 4>(a, sorted_buf, mode, s);
+      case 8: return pairs_impl<unsigned long long, 8>(a, sorted_buf, mode, s);
+      default: return pairs_impl<unsigned long long, 16>(a, sorted_buf, mode, s);
     }
   }
-  return write ? 2 : 3;
+  switch (a.dpad) {
+    case 4: return pairs_impl<uint32_t, 4>(a, sorted_buf, mode, s);
+    case 8: return pairs_impl<uint32_t, 8>(a, sorted_buf, mode, s);
+    default: return pairs_impl<uint32_t, 16>(a, sorted_buf, mode, s);
+  }
 }
 
-int launch_brute(const BuildArgs& a, bool write, cudaStream_t s) {
+int launch_brute(const BuildArgs& a, Mode mode, cudaStream_t s) {
   switch (a.dpad) {
-    case 4: brute_impl<4>(a, write, s); break;
-    case 8: brute_impl<8>(a, write, s); break;
-    default: brute_impl<16>(a, write, s); break;
+    case 4:
+      if (mode == kCount) brute_impl<4, kCount>(a, s);
+      else if (mode == kWrite) brute_impl<4, kWrite>(a, s);
+      else brute_impl<4, kEmit>(a, s);
+      break;
+    case 8:
+      if (mode == kCount) brute_impl<8, kCount>(a, s);
+      else if (mode == kWrite) brute_impl<8, kWrite>(a, s);
+      else brute_impl<8, kEmit>(a, s);
+      break;
+    default:
+      if (mode == kCount) brute_impl<16, kCount>(a, s);
+      else if (mode == kWrite) brute_impl<16, kWrite>(a, s);
+      else brute_impl<16, kEmit>(a, s);
+      break;
   }
   return 1;
 }
 
 void launch_scan(const BuildArgs& a, cudaStream_t s) {
-  const unsigned tiles = (unsigned)((a.n + kScanTile - 1) / kScanTile);
+  const unsigned tiles = (unsigned)((a.n_total + kScanTile - 1) / kScanTile);
   cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
-  k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.row_ptr, a.n, a.scan_lookback, &a.st->scan_tiles,
-                               a.st, tiles);
+  k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.row_ptr, a.n_total, a.scan_lookback,
+                               &a.st->scan_tiles, a.st, tiles);
+}
+
+int launch_scatter(const BuildArgs& a, cudaStream_t s) {
+  k_scatter<<<(unsigned)(8 * a.num_sms), 256, 0, s>>>(a.pair_buf, a.pair_cap, a.st, a.row_cnt,
+                                                      a.row_ptr, a.col, a.col_cap, a.symmetric,
+                                                      &a.st->errors);
+  return 1;
 }
 
 int launch_rowsort(const BuildArgs& a, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((a.n + 7) / 8);
+  const unsigned blocks = (unsigned)((a.n_total + 255) / 256);
   unsigned int* long_count = &a.st->long_rows;
-  k_rowsort_warp<<<blocks, 256, 0, s>>>(a.row_ptr, a.col, a.n, a.row_cnt, long_count);
-  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.row_ptr, a.col, a.row_cnt, long_count);
+  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.row_ptr, a.col, a.n_total, a.col_cap, a.row_cnt,
+                                          long_count);
+  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.row_ptr, a.col, a.col_cap, a.row_cnt,
+                                                           long_count);
   return 2;
 }
 

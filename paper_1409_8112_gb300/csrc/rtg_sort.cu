@@ -187,23 +187,38 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     st_volatile(lb, pack_lb(kFlagPrefix, epoch, tcount));
   } else {
     st_volatile(lb, pack_lb(kFlagAgg, epoch, tcount));
+    // Look back over a window of kWin predecessors at a time (independent loads), adding
+    // aggregates until an inclusive prefix is found.
+    constexpr int kWin = 8;
     long long p = (long long)tile - 1;
     unsigned int spins = 0;
+    const unsigned int ep_want = epoch & 0x3fffffffu;
     while (p >= 0) {
-      const unsigned long long w = ld_volatile(lookback + (size_t)p * kRadix + tid);
-      const unsigned long long flag = w >> 62;
-      const unsigned int ep = (unsigned int)(w >> 32) & 0x3fffffffu;
-      if (flag == 0 || ep != (epoch & 0x3fffffffu)) {
+      unsigned long long w[kWin];
+#pragma unroll
+      for (int q = 0; q < kWin; ++q)
+        w[q] = p - q >= 0 ? ld_volatile(lookback + (size_t)(p - q) * kRadix + tid) : 0ull;
+      int q = 0;
+      bool done = false;
+      for (; q < kWin && p - q >= 0; ++q) {
+        const unsigned long long flag = w[q] >> 62;
+        const unsigned int ep = (unsigned int)(w[q] >> 32) & 0x3fffffffu;
+        if (flag == 0 || ep != ep_want) break;
+        excl += (unsigned int)w[q];
+        if (flag == kFlagPrefix) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      p -= q;
+      if (q == 0 || (q < kWin && p >= 0)) {
         if (++spins > kSpinLimit) {
           atomicOr(errors, kErrTimeout);
           break;
         }
-        __nanosleep(32);
-        continue;
+        if (spins > 4) __nanosleep(32);
       }
-      excl += (unsigned int)w;
-      if (flag == kFlagPrefix) break;
-      --p;
     }
     st_volatile(lb, pack_lb(kFlagPrefix, epoch, excl + tcount));
   }
@@ -235,10 +250,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
 
 template <typename K>
 int sort_impl(const BuildArgs& a, cudaStream_t s) {
-  const long long N = (long long)a.n * a.m;
-  const int bits = a.sort_bits;
-  if (bits <= 0 || N <= 1) return 0;  // every key equal: already grouped
-  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const long long N = a.n_total * a.m;
+  const int passes = a.passes;
+  if (passes <= 0 || N <= 1) return 0;
   long long hb = (N + kSortThreads - 1) / kSortThreads;
   if (hb > 4LL * a.num_sms) hb = 4LL * a.num_sms;
   k_sort_hist<K><<<(unsigned)hb, kSortThreads, 0, s>>>((const K*)a.keys[0], N, passes, a.hist,

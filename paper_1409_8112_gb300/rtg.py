@@ -28,6 +28,7 @@ RTG_E_INTERNAL = 9
 RTG_FLAG_SHIFT_ONLY = 1
 RTG_FLAG_SYMMETRIC = 2
 RTG_FLAG_TIMING = 4
+RTG_FLAG_TWO_PASS = 8
 
 RTG_DTYPE_F64 = 0
 RTG_DTYPE_F32 = 1
@@ -35,7 +36,7 @@ RTG_DTYPE_F32 = 1
 RTG_MAX_DIM = 16
 RTG_MAX_GRIDS = 64
 
-PHASES = ("prep", "key", "sort", "count", "scan", "write", "rowsort", "total")
+PHASES = ("prep", "keys", "sort", "pairs", "scan", "scatter", "rowsort", "total")
 
 
 class rtg_config(ctypes.Structure):
@@ -51,7 +52,7 @@ class rtg_stats(ctypes.Structure):
                 ("large_cells", ctypes.c_int64), ("max_cell", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("key_bits", ctypes.c_int32),
                 ("sort_passes", ctypes.c_int32), ("launches", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("phase_us", ctypes.c_double * 8)]
+                ("attempts", ctypes.c_int32), ("phase_us", ctypes.c_double * 8)]
 
 
 class rtg_csr(ctypes.Structure):
@@ -59,6 +60,12 @@ class rtg_csr(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
                 ("symmetric", ctypes.c_int32), ("handle", ctypes.c_uint64),
                 ("stats", rtg_stats)]
+
+
+class rtg_instance(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int),
+                ("r", ctypes.c_double), ("cell_side", ctypes.c_double),
+                ("transforms", ctypes.c_void_p)]
 
 
 class RTGError(RuntimeError):
@@ -83,6 +90,10 @@ _SIGNATURES = {
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_uint32,
                                      ctypes.POINTER(rtg_csr)]),
+    "rtg_batch_all_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_instance),
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_uint32, ctypes.POINTER(rtg_csr),
+                                           ctypes.c_void_p]),
     "rtg_brute_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_uint32, ctypes.c_int,
@@ -156,6 +167,17 @@ def rtg_all_pairs(ctx, points_ptr: int, dtype: int, on_device: bool, n: int, d: 
     return out
 
 
+def rtg_batch_all_pairs(ctx, items, m: int, dtype: int, on_device: bool, flags: int = 0):
+    """items: sequence of rtg_instance; returns (block-diagonal csr, row_offsets)."""
+    arr = (rtg_instance * len(items))(*items)
+    offs = np.zeros(len(items) + 1, dtype=np.int64)
+    out = rtg_csr()
+    st = lib().rtg_batch_all_pairs(ctx, arr, len(items), m, dtype, 1 if on_device else 0, flags,
+                                   ctypes.byref(out), offs.ctypes.data)
+    _check(st, ctx)
+    return out, offs
+
+
 def rtg_brute_force(ctx, points_ptr: int, dtype: int, on_device: bool, n: int, d: int,
                     r: float, flags: int = 0, count_only: bool = False) -> rtg_csr:
     out = rtg_csr()
@@ -197,7 +219,7 @@ def stats_dict(s: rtg_stats, m: int) -> dict:
         "key_rechecks": int(s.key_rechecks), "dist_rechecks": int(s.dist_rechecks),
         "large_cells": int(s.large_cells), "max_cell": int(s.max_cell),
         "pairs": int(s.pairs), "key_bits": int(s.key_bits), "sort_passes": int(s.sort_passes),
-        "launches": int(s.launches),
+        "launches": int(s.launches), "attempts": int(s.attempts),
         "phase_us": {p: float(s.phase_us[i]) for i, p in enumerate(PHASES)},
     }
 
@@ -289,17 +311,40 @@ class Context:
             pass
 
     def all_pairs(self, points, r: float, transforms: np.ndarray, cell_side: float,
-                  symmetric: bool = False, timing: bool = False) -> Result:
+                  symmetric: bool = False, timing: bool = False, two_pass: bool = False) -> Result:
         ptr, code, on_dev, n, d, keep = _points_arg(points)
         T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
         if T.size % (d * d + d) != 0:
             raise ValueError("transforms must hold m * (d*d + d) values")
         m = T.size // (d * d + d)
-        flags = (RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0)
+        flags = ((RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0) |
+                 (RTG_FLAG_TWO_PASS if two_pass else 0))
         csr = rtg_all_pairs(self.handle, ptr, code, on_dev, n, d, float(r), T, m,
                             float(cell_side), flags)
         del keep
         return Result(self, csr, m)
+
+    def batch_all_pairs(self, instances, m: int, symmetric: bool = False, timing: bool = False,
+                        two_pass: bool = False):
+        """instances: list of (points, r, transforms, cell_side); points all numpy (host) or
+        all CUDA tensors, one dtype.  Returns (Result over the block-diagonal CSR, offsets)."""
+        items, keep, codes, devs = [], [], set(), set()
+        for pts, r, T, c in instances:
+            ptr, code, on_dev, n, d, kp = _points_arg(pts)
+            Tc = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+            if Tc.size != m * (d * d + d):
+                raise ValueError("each instance needs m * (d*d + d) transform values")
+            keep += [kp, Tc]
+            codes.add(code)
+            devs.add(on_dev)
+            items.append(rtg_instance(ptr, n, d, float(r), float(c), Tc.ctypes.data))
+        if len(codes) != 1 or len(devs) != 1:
+            raise ValueError("all instances need the same dtype and the same location")
+        flags = ((RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0) |
+                 (RTG_FLAG_TWO_PASS if two_pass else 0))
+        csr, offs = rtg_batch_all_pairs(self.handle, items, m, codes.pop(), devs.pop(), flags)
+        del keep
+        return Result(self, csr, m), offs
 
     def brute_force(self, points, r: float, symmetric: bool = False,
                     count_only: bool = False) -> Result:

@@ -237,3 +237,83 @@ def test_brute_force_count_config2_and_recall(ctx):
     T = gen.transforms(0, d, m, r)
     res = ctx.all_pairs(pts, r, T, r)
     assert 0.5 < res.nnz / cnt.nnz < 0.6
+
+
+def _check_block(rp, col, lo, hi, ref):
+    sub_rp = rp[lo:hi + 1] - rp[lo]
+    sub_col = col[rp[lo]:rp[hi]] - lo
+    assert np.array_equal(sub_rp, ref.row_ptr), "row pointers of an instance differ"
+    assert np.array_equal(sub_col, ref.col), "columns of an instance differ"
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_batch_matches_each_instance(ctx, dtype):
+    rng = np.random.default_rng(5)
+    inst = []
+    for b in range(14):
+        d = [2, 3, 6, 9][b % 4]
+        n = [0, 1, 2][b] if b < 3 else int(rng.integers(50, 4000))
+        pts = gen.points_uniform(100 + b, n, d, dtype)
+        r = gen.radius_for_degree(max(n, 2), d)
+        T = gen.transforms(200 + b, d, 4, 1.1 * r)
+        inst.append((pts, r, T, 1.1 * r))
+    res, offs = ctx.batch_all_pairs(inst, m=4)
+    rp, col = res.download()
+    total = 0
+    for b, (pts, r, T, c) in enumerate(inst):
+        ref = oracle.rtg(pts, r, T, c).csr
+        _check_block(rp, col, offs[b], offs[b + 1], ref)
+        total += ref.nnz
+    assert res.nnz == total
+    res.release()
+
+
+def test_batch_on_device_and_symmetric(ctx):
+    import torch
+    inst, host = [], []
+    for b in range(6):
+        n, d = 1500 + 300 * b, 3
+        pts = gen.points_uniform(300 + b, n, d)
+        r = gen.radius_for_degree(n, d)
+        T = gen.transforms(400 + b, d, 5, r)
+        inst.append((torch.from_numpy(pts).cuda(), r, T, r))
+        host.append((pts, r, T, r))
+    res, offs = ctx.batch_all_pairs(inst, m=5)
+    rp, col = res.download()
+    for b, (pts, r, T, c) in enumerate(host):
+        _check_block(rp, col, offs[b], offs[b + 1], oracle.rtg(pts, r, T, c).csr)
+    res.release()
+    res, offs = ctx.batch_all_pairs(inst, m=5, symmetric=True)
+    assert res.nnz == 2 * sum(oracle.rtg(p, r, T, c).csr.nnz for p, r, T, c in host)
+    res.release()
+
+
+def test_two_pass_mode_matches(ctx):
+    n, d, m = 30000, 6, 8
+    r = gen.radius_for_degree(n, d)
+    pts = gen.points_uniform(6, n, d)
+    T = gen.transforms(6, d, m, r)
+    a = ctx.all_pairs(pts, r, T, r, two_pass=True)
+    ra, ca = a.download()
+    ref = oracle.rtg(pts, r, T, r).csr
+    assert np.array_equal(ra, ref.row_ptr) and np.array_equal(ca, ref.col)
+
+
+def test_launch_assumptions_are_corrected():
+    # same shape, far more pairs the second time: the cached pair-buffer size is too small,
+    # the device reports it and the build is run again
+    ctx = rtg.Context(0)
+    n, d, m = 6000, 3, 4
+    r = 0.05
+    T = gen.transforms(7, d, m, r)
+    a = gen.points_uniform(7, n, d)
+    b = gen.points_mixture(7, n, d, k=2, sigma=0.01, dtype=np.float64)
+    ra = ctx.all_pairs(a, r, T, r)
+    rb = ctx.all_pairs(b, r, T, r)
+    assert rb.stats["attempts"] >= 2
+    got = rb.download()
+    ref = oracle.rtg(b, r, T, r).csr
+    assert np.array_equal(got[0], ref.row_ptr) and np.array_equal(got[1], ref.col)
+    ra.release()
+    rb.release()
+    ctx.close()

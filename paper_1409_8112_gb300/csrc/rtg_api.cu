@@ -62,6 +62,7 @@ struct rtg_ctx {
   DevBuf status, inst, iplan, gplan, bases, bbox, T64, pts, pf, key_mat, keys0, keys1, vals0,
       vals1, lookback, hist, digit_off, row_cnt, scan_lb, large, large_job, pair_buf;
   Status* h_status = nullptr;  // pinned
+  cudaMemPool_t pool = nullptr;  // output CSRs (stream ordered, kept cached)
   cudaEvent_t ev[8] = {};
   unsigned int epoch = 1;
   size_t ws_bytes = 0;
@@ -126,7 +127,7 @@ rtg_status alloc_out(rtg_ctx* c, size_t bytes, void** p) {
   if (c->budget && total_held(c) + bytes > c->budget)
     return fail(c, RTG_E_BUDGET, "CSR of " + std::to_string(bytes) +
                                      " bytes exceeds the memory budget");
-  RTG_CUDA(c, cudaMallocAsync(p, bytes, c->stream));
+  RTG_CUDA(c, cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream));
   c->out_bytes += bytes;
   return RTG_OK;
 }
@@ -203,7 +204,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
 
   // ---- instance table and packed transforms (host) ----
   c->h_inst.assign(B, Inst{});
-  long long p0 = 0, blk0 = 0, T0 = 0;
+  long long p0 = 0, blk0 = 0, pblk0 = 0, T0 = 0;
   int maxd = 1;
   for (int b = 0; b < B; ++b) {
     const rtg_instance& it = q.items[b];
@@ -216,8 +217,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     I.r = it.r;
     I.c = m > 0 ? it.cell_side : 1.0;
     I.blk0 = blk0;
+    I.pblk0 = pblk0;
     p0 += it.n;
     blk0 += (it.n + rtg::kPointBlock - 1) / rtg::kPointBlock;
+    pblk0 += (it.n + rtg::kPrepPoints - 1) / rtg::kPrepPoints;
     T0 += (long long)m * (it.d * it.d + it.d);
     maxd = std::max(maxd, it.d);
   }
@@ -289,6 +292,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.symmetric = sym;
   a.n_total = n_total;
   a.blocks = blk0;
+  a.pblocks = pblk0;
   a.inst = (const Inst*)c->inst.p;
   a.iplan = (InstPlan*)c->iplan.p;
   a.gplan = (GridPlan*)c->gplan.p;
@@ -581,6 +585,19 @@ rtg_status rtg_create(const rtg_config* cfg, rtg_ctx** out) {
     c->own_stream = true;
   }
   if ((e = cudaMallocHost(&c->h_status, sizeof(Status))) != cudaSuccess) return bail(e);
+  {
+    // a pool of its own for the output CSRs, so that freed blocks stay cached between builds
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    if ((e = cudaMemPoolCreate(&c->pool, &props)) != cudaSuccess) return bail(e);
+    uint64_t keep = ~0ull;
+    if ((e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep)) !=
+        cudaSuccess)
+      return bail(e);
+  }
   for (auto& ev : c->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e);
   rtg_status s = ensure(c, c->status, (sizeof(Status) + 255) & ~size_t(255), true);
@@ -606,6 +623,10 @@ void rtg_destroy(rtg_ctx* c) {
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->pool) {
+    for (auto& kv : c->live) (void)kv;  // outstanding CSRs are freed with the pool
+    cudaMemPoolDestroy(c->pool);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -32,7 +32,9 @@ constexpr int kMaxGrids = 64;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
-constexpr int kPointBlock = 128;  // points per block in the per-point kernels
+constexpr int kPointBlock = 128;   // points per block in the per-point kernels
+constexpr int kPrepThreads = 256;
+constexpr int kPrepPoints = 1024;  // points per block in the prep kernel
 
 // Bits of Status::errors.
 enum : uint32_t {
@@ -80,6 +82,7 @@ struct Inst {
   int n, d;
   double r, c;
   long long blk0;   // first block of this instance in the per-point kernels
+  long long pblk0;  // first block of this instance in the prep kernel
 };
 
 // Per-instance results of the plan.
@@ -147,6 +150,7 @@ struct BuildArgs {
   int symmetric;
   long long n_total;  // sum of n
   long long blocks;   // per-point kernel blocks (sum of ceil(n / kPointBlock))
+  long long pblocks;  // prep blocks (sum of ceil(n / kPrepPoints))
   const Inst* inst;   // device, B entries
   InstPlan* iplan;    // device, B entries
   GridPlan* gplan;    // device, B * m entries

@@ -28,15 +28,16 @@ __device__ __forceinline__ double load_coord(const void* pts, int dtype, long lo
                     : (double)__ldg((const float*)pts + i * d + l);
 }
 
-// Instance owning block `blk` of a per-point kernel (blk0 ascending): binary search by one
-// thread, broadcast through shared memory.
+// Instance owning block `blk` of a per-point kernel (first-block offsets ascending): binary
+// search by one thread, broadcast through shared memory.
+template <bool PREP>
 __device__ __forceinline__ int block_instance(const Inst* inst, int B, long long blk,
                                               int* s_b) {
   if (threadIdx.x == 0) {
     int lo = 0, hi = B - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (inst[mid].blk0 <= blk) lo = mid; else hi = mid - 1;
+      if ((PREP ? inst[mid].pblk0 : inst[mid].blk0) <= blk) lo = mid; else hi = mid - 1;
     }
     *s_b = lo;
   }
@@ -44,33 +45,37 @@ __device__ __forceinline__ int block_instance(const Inst* inst, int B, long long
   return *s_b;
 }
 
+// FP32 rows of the points and the per-instance bounding box; kPrepPoints points per block so
+// that each block adds one bound per axis.
 template <int DPAD>
-__global__ void __launch_bounds__(kPointBlock) k_prep(const Inst* __restrict__ inst, int B,
-                                                      int dtype, float* __restrict__ pf,
-                                                      unsigned long long* bbox, Status* st) {
+__global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ inst, int B,
+                                                       int dtype, float* __restrict__ pf,
+                                                       unsigned long long* bbox, Status* st) {
   __shared__ int s_b;
-  __shared__ double smn[kPointBlock / 32][DPAD], smx[kPointBlock / 32][DPAD];
-  const int b = block_instance(inst, B, blockIdx.x, &s_b);
+  __shared__ double smn[kPrepThreads / 32][DPAD], smx[kPrepThreads / 32][DPAD];
+  const int b = block_instance<true>(inst, B, blockIdx.x, &s_b);
   const Inst I = inst[b];
-  const long long i = (blockIdx.x - I.blk0) * (long long)kPointBlock + threadIdx.x;
   const int d = I.d;
   double mn[DPAD], mx[DPAD];
   bool bad = false;
-  float row[DPAD];
 #pragma unroll
   for (int l = 0; l < DPAD; ++l) {
     mn[l] = DBL_MAX;
     mx[l] = -DBL_MAX;
-    row[l] = 0.0f;
   }
-  if (i < I.n) {
+  const long long base = (blockIdx.x - I.pblk0) * (long long)kPrepPoints;
+  for (int q = 0; q < kPrepPoints / kPrepThreads; ++q) {
+    const long long i = base + q * kPrepThreads + threadIdx.x;
+    if (i >= I.n) break;
+    float row[DPAD];
 #pragma unroll
     for (int l = 0; l < DPAD; ++l) {
+      row[l] = 0.0f;
       if (l < d) {
         const double x = load_coord(I.pts, dtype, i, d, l);
         bad |= !isfinite(x);
-        mn[l] = x;
-        mx[l] = x;
+        mn[l] = fmin(mn[l], x);
+        mx[l] = fmax(mx[l], x);
         row[l] = __double2float_rn(x);
       }
     }
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(kPointBlock) k_prep(const Inst* __restrict__ i
   if (threadIdx.x < d) {
     const int l = threadIdx.x;
     double a = smn[0][l], c = smx[0][l];
-    for (int w = 1; w < kPointBlock / 32; ++w) {
+    for (int w = 1; w < kPrepThreads / 32; ++w) {
       a = fmin(a, smn[w][l]);
       c = fmax(c, smx[w][l]);
     }
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     K* __restrict__ comp, uint32_t* __restrict__ vals) {
   __shared__ int s_b;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int b = block_instance(inst, B, blockIdx.x, &s_b);
+  const int b = block_instance<false>(inst, B, blockIdx.x, &s_b);
   const Inst I = inst[b];
   const int d = I.d;
   // layout: qlo, ext, stride (m*d 8-byte each), base (m), R (m*d*DPAD floats), s, E (m*d)
@@ -390,14 +395,20 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
 
 template <int DPAD>
 void prep_impl(const BuildArgs& a, cudaStream_t s) {
-  k_prep<DPAD><<<(unsigned)a.blocks, kPointBlock, 0, s>>>(a.inst, a.B, a.dtype, a.pf, a.bbox, a.st);
+  k_prep<DPAD><<<(unsigned)a.pblocks, kPrepThreads, 0, s>>>(a.inst, a.B, a.dtype, a.pf, a.bbox,
+                                                             a.st);
 }
 
 template <typename K, int DPAD>
 void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
   const size_t smem = (size_t)a.m * maxd * (3 * 8 + (DPAD + 2) * 4) + (size_t)a.m * 8;
-  if (smem > 48 * 1024)
+  static size_t attr_smem[64] = {};  // largest size granted so far, per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || smem > attr_smem[dev])) {
     cudaFuncSetAttribute(k_keys<K, DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
+  }
   k_keys<K, DPAD><<<(unsigned)a.blocks, kPointBlock, smem, s>>>(
       a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.st, (K*)a.key_mat,
       (K*)a.keys[0], a.vals[0]);

@@ -30,7 +30,7 @@ namespace rtg {
 
 namespace {
 
-constexpr int kSlice = 1024;
+constexpr int kSlice = 512;
 constexpr int kSmax = 128;
 constexpr int kPairThreads = 256;
 constexpr int kStage = kSlice + kSmax;
@@ -117,21 +117,30 @@ struct Sink {
   int symmetric;
 };
 
-// Decide one candidate pair (i < j, global indices) of grid t of instance I.
+// Decide one candidate pair (i < j, global indices) of grid t of instance I; ki and kj are the
+// two points' key rows (shared or global memory).
 template <typename K, int DPAD, int MODE>
 __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int t, const float* pa,
-                                            const float* pb, const K* __restrict__ key_mat, int m,
+                                            const float* pb, const K* ki, const K* kj,
                                             const Inst& I, const InstPlan& IP, int dtype,
                                             Tally& tl) {
-  const K* ki = key_mat + (size_t)i * m;
-  const K* kj = key_mat + (size_t)j * m;
-  for (int u = 0; u < t; ++u)
-    if (__ldg(ki + u) == __ldg(kj + u)) return false;  // an earlier grid owns this pair
+  bool earlier = false;  // all loads issued before any test
+#pragma unroll 8
+  for (int u = 0; u < t; ++u) earlier |= ki[u] == kj[u];
+  if (earlier) return false;  // an earlier grid owns this pair
   if (MODE != kWrite) ++tl.owned;
   float sf = 0.0f;
 #pragma unroll
-  for (int l = 0; l < DPAD; ++l) {
-    const float e = pa[l] - pb[l];
+  for (int v = 0; v < DPAD / 4; ++v) {
+    const float4 x = reinterpret_cast<const float4*>(pa)[v];
+    const float4 y = reinterpret_cast<const float4*>(pb)[v];
+    float e = x.x - y.x;
+    sf = fmaf(e, e, sf);
+    e = x.y - y.y;
+    sf = fmaf(e, e, sf);
+    e = x.z - y.z;
+    sf = fmaf(e, e, sf);
+    e = x.w - y.w;
     sf = fmaf(e, e, sf);
   }
   bool keep;
@@ -188,18 +197,23 @@ __device__ __forceinline__ void deliver(bool keep, unsigned int i, unsigned int 
 
 template <int MODE>
 __device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigned int* sbuf) {
+  // sbuf: 4 block-wide counters, zeroed by the caller before its last barrier
+  unsigned int v[4] = {tl.owned, tl.rechecks, tl.near_r, tl.pairs};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (MODE != kWrite && (threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (v[q]) atomicAdd(&sbuf[q], v[q]);
+  }
   if (__syncthreads_or(tl.overflow) && threadIdx.x == 0)
     atomicOr(&st->errors, MODE == kEmit ? kErrPairOverflow : kErrColOverflow);
-  if (MODE == kWrite) return;
-  unsigned int tot;
-  block_excl_scan(tl.owned, &tot, sbuf);
-  if (threadIdx.x == 0 && tot) atomicAdd(&st->owned_candidates, (unsigned long long)tot);
-  block_excl_scan(tl.rechecks, &tot, sbuf);
-  if (threadIdx.x == 0 && tot) atomicAdd(&st->dist_rechecks, (unsigned long long)tot);
-  block_excl_scan(tl.near_r, &tot, sbuf);
-  if (threadIdx.x == 0 && tot) atomicAdd(&st->near_r, (unsigned long long)tot);
-  block_excl_scan(tl.pairs, &tot, sbuf);
-  if (threadIdx.x == 0 && tot) atomicAdd(&st->pairs, (unsigned long long)tot);
+  if (MODE == kWrite || threadIdx.x != 0) return;
+  if (sbuf[0]) atomicAdd(&st->owned_candidates, (unsigned long long)sbuf[0]);
+  if (sbuf[1]) atomicAdd(&st->dist_rechecks, (unsigned long long)sbuf[1]);
+  if (sbuf[2]) atomicAdd(&st->near_r, (unsigned long long)sbuf[2]);
+  if (sbuf[3]) atomicAdd(&st->pairs, (unsigned long long)sbuf[3]);
 }
 
 // (instance, grid) of a composite key: the last base <= key.
@@ -212,6 +226,9 @@ __device__ __forceinline__ int find_bt(unsigned long long key,
   }
   return lo;
 }
+
+// Shared-memory key rows are staged when a row (m keys) is at most this many bytes.
+constexpr int kMaxStagedRow = 64;
 
 template <typename K, int DPAD, int MODE>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
@@ -227,8 +244,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
   unsigned int* c_start = reinterpret_cast<unsigned int*>(s_key + kKeyWin);  // kSlice + 1
   unsigned int* c_cand = c_start + kSlice + 1;                               // kSlice + 1
   unsigned int* c_bt = c_cand + kSlice + 1;                                  // kSlice
+  K* s_rows = reinterpret_cast<K*>(c_bt + kSlice + (kSlice & 1));            // kStage * m (opt.)
+  const bool stage_rows = m * (int)sizeof(K) <= kMaxStagedRow;
   __shared__ unsigned int s_end, s_stage_lo, s_stage_hi, s_total;
   __shared__ unsigned int sbuf[kPairThreads / 32];
+  __shared__ unsigned int s_tally[4];
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned long long s_maxcell;
 
@@ -243,6 +263,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
     s_end = kUnknown;
     s_maxcell = 0;
   }
+  if (tid < 4) s_tally[tid] = 0;
   if (MODE != kWrite)
     for (int g = tid; g < kMaxGrids; g += kPairThreads) s_gcand[g] = 0;
   __syncthreads();
@@ -357,38 +378,61 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_small(
       float4* dst = reinterpret_cast<float4*>(s_pt + (size_t)x * DPAD);
 #pragma unroll
       for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+      if (stage_rows) {
+        const K* kr = key_mat + (size_t)idx * m;
+        for (int u = 0; u < m; ++u) s_rows[(size_t)x * m + u] = __ldg(kr + u);
+      }
     }
     __syncthreads();
-    const int lane = tid & 31;
-    for (unsigned int cb = tid & ~31u; cb < T; cb += kPairThreads) {
-      const unsigned int c = cb + lane;
+    // Each thread walks a contiguous run of `per` candidates, advancing (cell, a, b)
+    // incrementally; all lanes of a warp make the same number of steps so that EMIT can
+    // aggregate with ballots.
+    const unsigned int per = (T + kPairThreads - 1) / kPairThreads;
+    const unsigned int c0 = min(T, (unsigned int)tid * per), c1 = min(T, c0 + per);
+    int el = 0;
+    unsigned int a = 0, b = 1;
+    if (c0 < c1) {
+      int eh = (int)ncells - 1;
+      while (el < eh) {
+        const int mid = (el + eh + 1) >> 1;
+        if (c_cand[mid] <= c0) el = mid; else eh = mid - 1;
+      }
+      const unsigned int l = c0 - c_cand[el];
+      b = (unsigned int)((1.0f + sqrtf(8.0f * (float)l + 1.0f)) * 0.5f);
+      while (b * (b - 1) / 2 > l) --b;
+      while ((b + 1) * b / 2 <= l) ++b;
+      a = l - b * (b - 1) / 2;
+    }
+    for (unsigned int step = 0; step < per; ++step) {
+      const unsigned int c = c0 + step;
       bool keep = false;
       unsigned int i = 0, j = 0;
-      if (c < T) {
-        int el = 0, eh = (int)ncells - 1;
-        while (el < eh) {
-          const int mid = (el + eh + 1) >> 1;
-          if (c_cand[mid] <= c) el = mid; else eh = mid - 1;
+      if (c < c1) {
+        while (c >= c_cand[el + 1]) {  // next cell with candidates
+          ++el;
+          a = 0;
+          b = 1;
         }
-        const unsigned int l = c - c_cand[el];
-        unsigned int b = (unsigned int)((1.0f + sqrtf(8.0f * (float)l + 1.0f)) * 0.5f);
-        while (b * (b - 1) / 2 > l) --b;
-        while ((b + 1) * b / 2 <= l) ++b;
-        const unsigned int a = l - b * (b - 1) / 2;
         const unsigned int xa = c_start[el] + a - stage_lo, xb = c_start[el] + b - stage_lo;
         const unsigned int ia = s_idx[xa], ib = s_idx[xb];
         i = min(ia, ib);
         j = max(ia, ib);
         const unsigned int bt = c_bt[el];
         const int inst_b = (int)(bt / m);
+        const K* ka = stage_rows ? s_rows + (size_t)xa * m : key_mat + (size_t)ia * m;
+        const K* kb = stage_rows ? s_rows + (size_t)xb * m : key_mat + (size_t)ib * m;
         keep = decide_pair<K, DPAD, MODE>(i, j, (int)(bt % m), s_pt + (size_t)xa * DPAD,
-                                          s_pt + (size_t)xb * DPAD, key_mat, m, inst[inst_b],
+                                          s_pt + (size_t)xb * DPAD, ka, kb, inst[inst_b],
                                           iplan[inst_b], dtype, tl);
+        if (++a == b) {  // next pair of the cell in (b, a) order
+          a = 0;
+          ++b;
+        }
       }
       deliver<MODE>(keep, i, j, sk, tl);
     }
   }
-  flush_tally<MODE>(tl, st, sbuf);
+  flush_tally<MODE>(tl, st, s_tally);
 }
 
 // Job offsets for the large cells: cell e has ceil(size / kTL) row tiles.
@@ -425,7 +469,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
   __shared__ __align__(16) float sa[kTL * DPAD];
   __shared__ __align__(16) float sb[kTL * DPAD];
   __shared__ uint32_t ia[kTL], ib[kTL];
-  __shared__ unsigned int sbuf[kPairThreads / 32];
+  __shared__ unsigned int s_tally[4];
+  if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
   const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
   const unsigned long long J = L ? job_off[L] : 0;
   const int lane = threadIdx.x & 31;
@@ -474,14 +519,16 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
             i = min(ia[x], ib[y]);
             j = max(ia[x], ib[y]);
             keep = decide_pair<K, DPAD, MODE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD,
-                                              key_mat, m, I, IP, dtype, tl);
+                                              key_mat + (size_t)ia[x] * m,
+                                              key_mat + (size_t)ib[y] * m, I, IP, dtype, tl);
           }
         }
         deliver<MODE>(keep, i, j, sk, tl);
       }
     }
   }
-  flush_tally<MODE>(tl, st, sbuf);
+  __syncthreads();
+  flush_tally<MODE>(tl, st, s_tally);
 }
 
 // Exact set of Sec. I: every pair (i < j) of one instance checked, in 128 x 128 tiles
@@ -495,7 +542,8 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
                                                         Status* st, Sink sk) {
   __shared__ __align__(16) float sa[kBT * DPAD];
   __shared__ __align__(16) float sb[kBT * DPAD];
-  __shared__ unsigned int sbuf[kPairThreads / 32];
+  __shared__ unsigned int s_tally[4];
+  if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
   const Inst I = inst[0];
   const InstPlan IP = iplan[0];
   const long long n = I.n;
@@ -531,11 +579,12 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
       const unsigned int i = (unsigned int)(I.p0 + li), j = (unsigned int)(I.p0 + lj);
       if (valid)
         keep = decide_pair<uint32_t, DPAD, MODE>(i, j, 0, sa + x * DPAD, sb + y * DPAD, nullptr,
-                                                 1, I, IP, dtype, tl);
+                                                 nullptr, I, IP, dtype, tl);
       deliver<MODE>(keep, i, j, sk, tl);
     }
   }
-  flush_tally<MODE>(tl, st, sbuf);
+  __syncthreads();
+  flush_tally<MODE>(tl, st, s_tally);
 }
 
 // Row counts -> row pointers (exclusive scan, single pass with decoupled look-back); the
@@ -758,12 +807,20 @@ template <typename K, int DPAD, int MODE>
 void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   const long long N = a.n_total * a.m;
   const unsigned blocks = (unsigned)((N + kSlice - 1) / kSlice);
+  const bool stage_rows = a.m * (int)sizeof(K) <= kMaxStagedRow;
   const size_t smem = (size_t)kStage * DPAD * 4 + (size_t)kStage * 4 + (size_t)kKeyWin * sizeof(K) +
-                      (size_t)(kSlice + 1) * 8 + (size_t)kSlice * 4;
+                      (size_t)(kSlice + 1) * 8 + (size_t)(kSlice + (kSlice & 1)) * 4 +
+                      (stage_rows ? (size_t)kStage * a.m * sizeof(K) : 0);
   const K* sk = (const K*)a.keys[sorted_buf];
   const uint32_t* sv = a.vals[sorted_buf];
-  cudaFuncSetAttribute(k_pairs_small<K, DPAD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
+  static size_t attr_smem[64] = {};  // largest size granted so far, per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
+    cudaFuncSetAttribute(k_pairs_small<K, DPAD, MODE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
+  }
   k_pairs_small<K, DPAD, MODE><<<blocks, kPairThreads, smem, s>>>(
       sk, sv, N, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases, a.B * a.m,
       a.st, make_sink(a), a.large, a.large_cap);

@@ -26,11 +26,11 @@ template <typename K>
 struct SortTile;
 template <>
 struct SortTile<uint32_t> {
-  static constexpr int kItems = 16;
+  static constexpr int kItems = 8;
 };
 template <>
 struct SortTile<unsigned long long> {
-  static constexpr int kItems = 12;
+  static constexpr int kItems = 8;
 };
 
 template <typename K>
@@ -260,8 +260,13 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
   constexpr int kTile = tile_size<K>();
   const unsigned tiles = (unsigned)((N + kTile - 1) / kTile);
   const size_t smem = (size_t)kTile * (sizeof(K) + 4) + (size_t)kSortWarps * kRadix * 4;
-  if (smem > 48 * 1024)
+  static bool attr_set[64] = {};  // per instantiation and device; the size is fixed
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_set[dev])) {
     cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
     k_sort_pass<K><<<tiles, kSortThreads, smem, s>>>(

@@ -113,6 +113,19 @@ typedef struct {
   const double* transforms;  /* host, m*(d*d+d) doubles (R_t row-major, then s_t) */
 } rtg_instance;
 
+/* One roadmap build request for the server (rtg_submit). */
+typedef struct {
+  const void* points;        /* host, n x d row-major; copied by rtg_submit */
+  int dtype;                 /* RTG_DTYPE_F64 or RTG_DTYPE_F32 */
+  int64_t n;
+  int d;                     /* in [1, 16] */
+  double r;
+  double cell_side;
+  const double* transforms;  /* host, m*(d*d+d) doubles; copied by rtg_submit */
+  int m;                     /* in [1, 64] */
+  uint32_t flags;            /* RTG_FLAG_SYMMETRIC */
+} rtg_request;
+
 /* Create a context on cfg->device.  *out receives the context or NULL on failure. */
 rtg_status rtg_create(const rtg_config* cfg, rtg_ctx** out);
 
@@ -191,6 +204,30 @@ rtg_status rtg_brute_force(rtg_ctx* ctx, const void* points, int dtype, int poin
  * rtg_last_error(NULL). */
 rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int64_t n, int d, double r,
                                    void* stream, uint64_t* count);
+
+/* Serving: continuous batching of builds (Alg. 1 per request).  rtg_submit copies the
+ * request's points and transforms and returns at once with a ticket; a server owned by the
+ * context (started by the first submit) forms batches of waiting requests that share m,
+ * dtype and flags, runs them on several streams concurrently, and hands each request its own
+ * device CSR, bit-identical to what rtg_all_pairs returns for it alone.  Admission follows the
+ * context's mem_budget_bytes: a batch starts only when its estimated footprint fits next to
+ * the memory already held (results not yet released included); the oldest request goes first;
+ * a request that cannot fit even alone fails with RTG_E_BUDGET.  Thread safe: submit, poll and
+ * wait may be called from any thread.  The number of concurrent lanes is 2 (environment
+ * variable RTG_SERVE_LANES, 1 to 8).
+ * The result's stats describe the batch it ran in, except phase_us[0] (microseconds queued)
+ * and phase_us[7] (microseconds from submit to completion).
+ * Errors of rtg_submit: as rtg_all_pairs for invalid requests. */
+rtg_status rtg_submit(rtg_ctx* ctx, const rtg_request* req, uint64_t* ticket);
+
+/* RTG_PENDING while the request runs; otherwise its final status, and on RTG_OK *out holds its
+ * CSR (free it with rtg_release).  A ticket is forgotten once a final status is returned;
+ * RTG_E_UNKNOWN_TICKET for tickets never issued or already taken. */
+rtg_status rtg_poll(rtg_ctx* ctx, uint64_t ticket, rtg_csr* out);
+
+/* As rtg_poll, but waits up to timeout_us microseconds (negative: no limit) for a final
+ * status; RTG_E_TIMEOUT if the request is still running then (the ticket stays valid). */
+rtg_status rtg_wait(rtg_ctx* ctx, uint64_t ticket, int64_t timeout_us, rtg_csr* out);
 
 /* Free the device memory of a CSR returned by this context and zero *csr. */
 rtg_status rtg_release(rtg_ctx* ctx, rtg_csr* csr);

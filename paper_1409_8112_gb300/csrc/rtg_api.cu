@@ -30,51 +30,17 @@ using rtg::Inst;
 using rtg::InstPlan;
 using rtg::Status;
 
+#include "rtg_host.h"
+
 namespace {
-
 thread_local std::string g_err;
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-};
-
-// Launch decisions remembered per shape (sum n, instances, grids, dtype, widest d, flags).
-using ShapeKey = std::tuple<long long, int, int, int, int, int, int>;
-struct ShapeGuess {
-  bool key64 = true;
-  int passes = rtg::kMaxPasses;
-  long long pair_cap = 0;
-};
-
 }  // namespace
 
 void rtg::set_last_error(const char* msg) { g_err = msg; }
 
-struct rtg_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  uint64_t budget = 0;
-  int num_sms = 0;
-  std::mutex mu;
-  std::string err;
-  DevBuf status, inst, iplan, gplan, bases, bbox, T64, pts, pf, key_mat, keys0, keys1, vals0,
-      vals1, lookback, hist, digit_off, row_cnt, scan_lb, large, large_job, pair_buf;
-  Status* h_status = nullptr;  // pinned
-  cudaMemPool_t pool = nullptr;  // output CSRs (stream ordered, kept cached)
-  cudaEvent_t ev[8] = {};
-  unsigned int epoch = 1;
-  size_t ws_bytes = 0;
-  size_t out_bytes = 0;
-  uint64_t next_handle = 1;
-  std::unordered_map<uint64_t, size_t> live;  // CSR handle -> bytes
-  std::map<ShapeKey, ShapeGuess> guesses;
-  std::vector<Inst> h_inst;
-  std::vector<double> h_T;
-};
+namespace rtghost {
 
-namespace {
+std::string& last_error_text() { return g_err; }
 
 rtg_status fail(rtg_ctx* ctx, rtg_status s, const std::string& msg) {
   if (ctx) ctx->err = msg; else g_err = msg;
@@ -119,17 +85,38 @@ void free_buf(rtg_ctx* c, DevBuf& b) {
   b = DevBuf();
 }
 
-rtg_status alloc_out(rtg_ctx* c, size_t bytes, void** p) {
+rtg_status alloc_out_on(rtg_ctx* c, cudaStream_t s, size_t bytes, void** p) {
   if (bytes == 0) {
     *p = nullptr;
     return RTG_OK;
   }
-  if (c->budget && total_held(c) + bytes > c->budget)
-    return fail(c, RTG_E_BUDGET, "CSR of " + std::to_string(bytes) +
-                                     " bytes exceeds the memory budget");
-  RTG_CUDA(c, cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream));
-  c->out_bytes += bytes;
+  {
+    std::lock_guard<std::mutex> lk(c->live_mu);
+    if (c->budget && total_held(c) + bytes > c->budget)
+      return fail(c, RTG_E_BUDGET, "CSR of " + std::to_string(bytes) +
+                                       " bytes exceeds the memory budget");
+    c->out_bytes += bytes;
+  }
+  const cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(c->live_mu);
+    c->out_bytes -= bytes;
+    return fail(c, e == cudaErrorMemoryAllocation ? RTG_E_NOMEM : RTG_E_CUDA,
+                std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
+  }
   return RTG_OK;
+}
+
+rtg_status alloc_out(rtg_ctx* c, size_t bytes, void** p) {
+  return alloc_out_on(c, c->stream, bytes, p);
+}
+
+// Register `bytes` (already counted in out_bytes) under a new CSR handle.
+uint64_t register_out(rtg_ctx* c, size_t bytes) {
+  std::lock_guard<std::mutex> lk(c->live_mu);
+  const uint64_t h = c->next_handle++;
+  c->live[h] = bytes;
+  return h;
 }
 
 rtg_status read_status(rtg_ctx* c) {
@@ -156,10 +143,13 @@ rtg_status check_errors(rtg_ctx* c, unsigned int mask) {
 void release_out(rtg_ctx* c, rtg_csr* csr) {
   if (csr->row_ptr) cudaFreeAsync(csr->row_ptr, c->stream);
   if (csr->col) cudaFreeAsync(csr->col, c->stream);
-  auto it = c->live.find(csr->handle);
-  if (it != c->live.end()) {
-    c->out_bytes -= it->second;
-    c->live.erase(it);
+  {
+    std::lock_guard<std::mutex> lk(c->live_mu);
+    auto it = c->live.find(csr->handle);
+    if (it != c->live.end()) {
+      c->out_bytes -= it->second;
+      c->live.erase(it);
+    }
   }
   std::memset(csr, 0, sizeof(*csr));
 }
@@ -182,16 +172,6 @@ rtg_status validate_transforms(const double* T, int d, int m) {
     if (!std::isfinite(T[x])) return fail(nullptr, RTG_E_INVALID, "non-finite transform entry");
   return RTG_OK;
 }
-
-struct Request {
-  const rtg_instance* items;
-  int count;
-  int m;  // 0: brute force (count must be 1)
-  int dtype;
-  int points_on_device;
-  uint32_t flags;
-  bool count_only;
-};
 
 // The whole build.  On success *out holds the block-diagonal CSR of the batch.
 rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
@@ -237,8 +217,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     RTG_CUDA(c, cudaMemsetAsync(rp, 0, sizeof(int64_t), st));
     RTG_CUDA(c, cudaStreamSynchronize(st));
     out->row_ptr = (int64_t*)rp;
-    out->handle = c->next_handle++;
-    c->live[out->handle] = sizeof(int64_t);
+    out->handle = register_out(c, sizeof(int64_t));
     return RTG_OK;
   }
   const int dpad = rtg::dpad_for(maxd);
@@ -378,8 +357,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     if ((s = alloc_out(c, sizeof(int64_t) * (n_total + 1), &rp)) != RTG_OK) return s;
     out->row_ptr = (int64_t*)rp;
     out->col = nullptr;
-    out->handle = c->next_handle++;
-    c->live[out->handle] = sizeof(int64_t) * (n_total + 1);
+    out->handle = register_out(c, sizeof(int64_t) * (n_total + 1));
     a.row_ptr = (long long*)rp;
 
     // pair buffer for EMIT; COUNT then WRITE when asked, when only counting, or when the buffer
@@ -410,7 +388,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         return s;
       }
       out->col = (int32_t*)cp;
-      c->live[out->handle] += sizeof(int32_t) * (size_t)ccap;
+      {
+        std::lock_guard<std::mutex> lk(c->live_mu);
+        c->live[out->handle] += sizeof(int32_t) * (size_t)ccap;
+      }
       a.col = (int*)cp;
       a.col_cap = ccap;
       launches += rtg::launch_scatter(a, st);
@@ -441,7 +422,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
           return s;
         }
         out->col = (int32_t*)cp;
-        c->live[out->handle] += sizeof(int32_t) * (size_t)nnz;
+        {
+          std::lock_guard<std::mutex> lk(c->live_mu);
+          c->live[out->handle] += sizeof(int32_t) * (size_t)nnz;
+        }
         a.col = (int*)cp;
         a.col_cap = nnz;
         launches += pairs(rtg::kWrite);
@@ -522,7 +506,80 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   return fail(c, RTG_E_INTERNAL, "launch assumptions did not converge");
 }
 
-}  // namespace
+
+rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) {
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0)
+    return fail(nullptr, RTG_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  if (device < 0 || device >= ndev) return fail(nullptr, RTG_E_INVALID, "device ordinal out of range");
+  rtg_ctx* c = new rtg_ctx();
+  c->device = device;
+  c->budget = budget;
+  auto bail = [&](cudaError_t err) {
+    std::string msg = std::string("context setup: ") + cudaGetErrorString(err);
+    destroy_ctx(c);
+    return fail(nullptr, RTG_E_CUDA, msg);
+  };
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess) return bail(e);
+  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)) !=
+      cudaSuccess)
+    return bail(e);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(e);
+    c->own_stream = true;
+  }
+  if ((e = cudaMallocHost(&c->h_status, sizeof(Status))) != cudaSuccess) return bail(e);
+  {
+    // a pool of its own for the output CSRs, so that freed blocks stay cached between builds
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    if ((e = cudaMemPoolCreate(&c->pool, &props)) != cudaSuccess) return bail(e);
+    uint64_t keep = ~0ull;
+    if ((e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep)) !=
+        cudaSuccess)
+      return bail(e);
+  }
+  for (auto& ev : c->ev)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e);
+  rtg_status s = ensure(c, c->status, (sizeof(Status) + 255) & ~size_t(255), true);
+  if (s != RTG_OK) {
+    std::string msg = c->err;
+    destroy_ctx(c);
+    return fail(nullptr, s, msg);
+  }
+  *out = c;
+  return RTG_OK;
+}
+
+void destroy_ctx(rtg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->status,    &c->inst,      &c->iplan,   &c->gplan,   &c->bases,
+                    &c->bbox,      &c->T64,       &c->pts,     &c->pf,      &c->key_mat,
+                    &c->keys0,     &c->keys1,     &c->vals0,   &c->vals1,   &c->lookback,
+                    &c->hist,      &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
+                    &c->large_job, &c->pair_buf};
+  for (DevBuf* b : bufs) free_buf(c, *b);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->pool) cudaMemPoolDestroy(c->pool);  // outstanding CSRs go with the pool
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace rtghost
+
+using namespace rtghost;
 
 extern "C" {
 
@@ -559,76 +616,13 @@ rtg_status rtg_create(const rtg_config* cfg, rtg_ctx** out) {
   *out = nullptr;
   rtg_config def = {0, 0, nullptr, 0};
   if (!cfg) cfg = &def;
-  int ndev = 0;
-  cudaError_t e = cudaGetDeviceCount(&ndev);
-  if (e != cudaSuccess || ndev == 0)
-    return fail(nullptr, RTG_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
-  if (cfg->device < 0 || cfg->device >= ndev)
-    return fail(nullptr, RTG_E_INVALID, "device ordinal out of range");
-  rtg_ctx* c = new rtg_ctx();
-  c->device = cfg->device;
-  c->budget = cfg->mem_budget_bytes;
-  auto bail = [&](cudaError_t err) {
-    std::string msg = std::string("context setup: ") + cudaGetErrorString(err);
-    rtg_destroy(c);
-    return fail(nullptr, RTG_E_CUDA, msg);
-  };
-  if ((e = cudaSetDevice(c->device)) != cudaSuccess) return bail(e);
-  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)) !=
-      cudaSuccess)
-    return bail(e);
-  if (cfg->stream) {
-    c->stream = (cudaStream_t)cfg->stream;
-  } else {
-    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
-      return bail(e);
-    c->own_stream = true;
-  }
-  if ((e = cudaMallocHost(&c->h_status, sizeof(Status))) != cudaSuccess) return bail(e);
-  {
-    // a pool of its own for the output CSRs, so that freed blocks stay cached between builds
-    cudaMemPoolProps props = {};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.handleTypes = cudaMemHandleTypeNone;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = c->device;
-    if ((e = cudaMemPoolCreate(&c->pool, &props)) != cudaSuccess) return bail(e);
-    uint64_t keep = ~0ull;
-    if ((e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep)) !=
-        cudaSuccess)
-      return bail(e);
-  }
-  for (auto& ev : c->ev)
-    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e);
-  rtg_status s = ensure(c, c->status, (sizeof(Status) + 255) & ~size_t(255), true);
-  if (s != RTG_OK) {
-    std::string msg = c->err;
-    rtg_destroy(c);
-    return fail(nullptr, s, msg);
-  }
-  *out = c;
-  return RTG_OK;
+  return create_ctx(cfg->device, cfg->mem_budget_bytes, cfg->stream, out);
 }
 
 void rtg_destroy(rtg_ctx* c) {
   if (!c) return;
-  cudaSetDevice(c->device);
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  DevBuf* bufs[] = {&c->status,    &c->inst,      &c->iplan,   &c->gplan,   &c->bases,
-                    &c->bbox,      &c->T64,       &c->pts,     &c->pf,      &c->key_mat,
-                    &c->keys0,     &c->keys1,     &c->vals0,   &c->vals1,   &c->lookback,
-                    &c->hist,      &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
-                    &c->large_job, &c->pair_buf};
-  for (DevBuf* b : bufs) free_buf(c, *b);
-  for (auto& ev : c->ev)
-    if (ev) cudaEventDestroy(ev);
-  if (c->h_status) cudaFreeHost(c->h_status);
-  if (c->pool) {
-    for (auto& kv : c->live) (void)kv;  // outstanding CSRs are freed with the pool
-    cudaMemPoolDestroy(c->pool);
-  }
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-  delete c;
+  stop_server(c);
+  destroy_ctx(c);
 }
 
 rtg_status rtg_release(rtg_ctx* c, rtg_csr* csr) {

@@ -68,6 +68,12 @@ class rtg_instance(ctypes.Structure):
                 ("transforms", ctypes.c_void_p)]
 
 
+class rtg_request(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("dtype", ctypes.c_int), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int), ("r", ctypes.c_double), ("cell_side", ctypes.c_double),
+                ("transforms", ctypes.c_void_p), ("m", ctypes.c_int), ("flags", ctypes.c_uint32)]
+
+
 class RTGError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{status_name(status)}: {message}")
@@ -101,6 +107,11 @@ _SIGNATURES = {
     "rtg_brute_count_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                                ctypes.POINTER(ctypes.c_uint64)]),
+    "rtg_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_request),
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "rtg_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(rtg_csr)]),
+    "rtg_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64,
+                                ctypes.POINTER(rtg_csr)]),
     "rtg_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr)]),
     "rtg_csr_download": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
                                         ctypes.c_void_p, ctypes.c_void_p]),
@@ -194,6 +205,37 @@ def rtg_brute_count_noalloc(points_ptr: int, dtype: int, n: int, d: int, r: floa
     _check(lib().rtg_brute_count_noalloc(points_ptr, dtype, n, d, r, stream or None,
                                          ctypes.byref(out)))
     return int(out.value)
+
+
+def rtg_submit(ctx, points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,
+               flags: int = 0) -> int:
+    p = np.ascontiguousarray(points)
+    code = RTG_DTYPE_F64 if p.dtype == np.float64 else RTG_DTYPE_F32
+    if p.dtype not in (np.float64, np.float32):
+        raise TypeError("points must be float64 or float32")
+    n, d = p.shape
+    T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
+    m = T.size // (d * d + d)
+    req = rtg_request(p.ctypes.data, code, n, d, float(r), float(cell_side), T.ctypes.data, m, flags)
+    t = ctypes.c_uint64(0)
+    _check(lib().rtg_submit(ctx, ctypes.byref(req), ctypes.byref(t)), ctx)
+    return int(t.value)
+
+
+def rtg_poll(ctx, ticket: int):
+    """None while pending, else the CSR (raises on a failed request)."""
+    out = rtg_csr()
+    st = lib().rtg_poll(ctx, ticket, ctypes.byref(out))
+    if st == RTG_PENDING:
+        return None
+    _check(st, ctx)
+    return out
+
+
+def rtg_wait(ctx, ticket: int, timeout_us: int = -1) -> rtg_csr:
+    out = rtg_csr()
+    _check(lib().rtg_wait(ctx, ticket, timeout_us, ctypes.byref(out)), ctx)
+    return out
 
 
 def rtg_release(ctx, csr: rtg_csr) -> None:
@@ -345,6 +387,18 @@ class Context:
         csr, offs = rtg_batch_all_pairs(self.handle, items, m, codes.pop(), devs.pop(), flags)
         del keep
         return Result(self, csr, m), offs
+
+    def submit(self, points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,
+               symmetric: bool = False) -> int:
+        return rtg_submit(self.handle, points, r, transforms, cell_side,
+                          RTG_FLAG_SYMMETRIC if symmetric else 0)
+
+    def poll(self, ticket: int, m: int = 0):
+        csr = rtg_poll(self.handle, ticket)
+        return None if csr is None else Result(self, csr, m)
+
+    def wait(self, ticket: int, timeout_us: int = -1, m: int = 0) -> Result:
+        return Result(self, rtg_wait(self.handle, ticket, timeout_us), m)
 
     def brute_force(self, points, r: float, symmetric: bool = False,
                     count_only: bool = False) -> Result:

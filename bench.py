@@ -289,6 +289,153 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_workload(count=512, seed0=1000):
+    """512 roadmaps: n log-uniform in [1e3, 2e5], d uniform in {3, 6, 9}, FP32 uniform
+    points, r for expected degree 2 ln n, m = 6, seed 1000 + i (transforms c = r)."""
+    from paper_1409_8112_gb300 import gen
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(np.floor(np.exp(rng.uniform(np.log(1e3), np.log(2e5)))))
+        d = int(rng.choice([3, 6, 9]))
+        pts = gen.points_uniform(seed0 + i, n, d, np.float32)
+        r = gen.radius_for_degree(n, d)
+        T = gen.transforms(seed0 + i, d, 6, r)
+        out.append((pts, r, T, r))
+    return out
+
+
+def run_batch(args):
+    """Batched form vs one build per roadmap, same 512 roadmaps, points resident on device."""
+    import torch
+    from paper_1409_8112_gb300 import rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    work = batch_workload()
+    dev = [(torch.from_numpy(p).cuda(), r, T, c) for p, r, T, c in work]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        res, offs = ctx.batch_all_pairs(dev, m=6)
+        res.release()
+    times, pairs = [], 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, offs = ctx.batch_all_pairs(dev, m=6, timing=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        pairs = res.nnz
+        st = res.stats
+        res.release()
+    # one build per roadmap
+    for p, r, T, c in dev[:8]:
+        ctx.all_pairs(p, r, T, c).release()
+    single_ms, single_pairs = [], 0
+    for k in range(max(1, args.steps // 5)):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tot = 0
+        for p, r, T, c in dev:
+            res = ctx.all_pairs(p, r, T, c)
+            tot += res.nnz
+            res.release()
+        e1.record(stream)
+        e1.synchronize()
+        single_ms.append(e0.elapsed_time(e1))
+        single_pairs = tot
+    assert single_pairs == pairs, (single_pairs, pairs)
+    ms = float(np.mean(times))
+    sms = float(np.mean(single_ms))
+    line = {
+        "metric": METRIC, "value": round(pairs / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "batch of 512 roadmaps, n log-uniform [1e3,2e5], d in {3,6,9}, "
+                               "fp32 uniform, r=2lnn-degree, m=6, seeds 1000+i",
+                   "points": int(sum(len(w[0]) for w in work)), "l2": "flushed between steps"},
+        "builds_per_s": round(512 / (ms / 1e3), 1), "pairs_per_step": pairs,
+        "one_build_per_roadmap": {"ms_per_512": round(sms, 3),
+                                  "pairs_per_s": round(single_pairs / (sms / 1e3), 1),
+                                  "builds_per_s": round(512 / (sms / 1e3), 1)},
+        "speedup_vs_one_build_per_roadmap": round(sms / ms, 3),
+        "phase_us": {k2: round(v, 1) for k2, v in st["phase_us"].items()},
+        "key_bits": st["key_bits"], "sort_passes": st["sort_passes"],
+        "gpu_launches": st["launches"] * args.steps,
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def serve_trace(count, rate, nmax, seed=7):
+    """Poisson arrivals; n log-uniform in [1e3, nmax]; d uniform in {2..12}; points from a
+    mixture of 8 Gaussians (sigma 0.05, means in [0.1,0.9]^d) clipped to [0,1]^d, FP32;
+    r for expected degree 2 ln n under uniform density; m = 8."""
+    from paper_1409_8112_gb300 import gen
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        n = int(np.floor(np.exp(rng.uniform(np.log(1e3), np.log(nmax)))))
+        d = int(rng.integers(2, 13))
+        pts = gen.points_mixture(seed * 100000 + i, n, d, k=8, sigma=0.05, dtype=np.float32)
+        r = gen.radius_for_degree(n, d)
+        T = gen.transforms(seed * 100000 + i, d, 8, r)
+        out.append((t, pts, r, T))
+    return out
+
+
+def run_serve(args):
+    import torch
+    from paper_1409_8112_gb300 import rtg
+    torch.cuda.set_device(0)
+    budget = 64 << 30
+    ctx = rtg.Context(0, mem_budget_bytes=budget)
+    trace = serve_trace(args.requests, args.rate, args.nmax)
+    # warm the lanes with a few requests outside the measurement
+    for t0, pts, r, T in trace[:4]:
+        res = ctx.wait(ctx.submit(pts, r, T, r), m=8)
+        res.release()
+    start = time.perf_counter()
+    tickets = []
+    for t0, pts, r, T in trace:
+        now = time.perf_counter() - start
+        if t0 > now:
+            time.sleep(t0 - now)
+        tickets.append(ctx.submit(pts, r, T, r))
+    lat, pairs, rejected = [], 0, 0
+    for tk in tickets:
+        try:
+            res = ctx.wait(tk, m=8)
+        except rtg.RTGError as e:
+            if e.status == rtg.RTG_E_BUDGET:
+                rejected += 1
+                continue
+            raise
+        lat.append(res.stats["phase_us"]["total"] / 1e3)
+        pairs += res.nnz
+        res.release()
+    makespan = time.perf_counter() - start
+    line = {
+        "metric": METRIC, "value": round(pairs / makespan, 1), "unit": "pairs/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson {args.rate}/s, {args.requests} requests, n "
+                               f"log-uniform [1e3,{args.nmax}], d in 2..12, 8-Gaussian mixture "
+                               "sigma 0.05 fp32, r=2lnn-degree (uniform), m=8, budget 64 GiB"},
+        "served": len(lat), "rejected_budget": rejected,
+        "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat else None,
+        "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat else None,
+        "builds_per_s": round(len(lat) / makespan, 2), "makespan_s": round(makespan, 3),
+        "pairs": pairs,
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,11 +444,21 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="build", choices=["build", "batch", "serve"],
+                    help="build: the headline single-roadmap workload; batch: 512 roadmaps "
+                         "batched vs one by one; serve: a Poisson request trace")
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--nmax", type=int, default=500000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

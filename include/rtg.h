@@ -56,6 +56,8 @@ typedef enum {
 #define RTG_FLAG_TIMING 4u     /* rtg_all_pairs: fill rtg_stats.phase_us (adds events) */
 #define RTG_FLAG_TWO_PASS 8u   /* enumerate twice (count, then write in place) instead of
                                   holding a pair buffer: less memory, more time */
+#define RTG_FLAG_TC_FP16 16u   /* rtg_brute_force: distances from FP16 tensor-core tiles */
+#define RTG_FLAG_TC_BF16 32u   /* rtg_brute_force: distances from BF16 tensor-core tiles */
 
 /* Point coordinate types. */
 #define RTG_DTYPE_F64 0
@@ -91,6 +93,9 @@ typedef struct {
   int32_t attempts;      /* 1, or more when a launch assumption had to be corrected */
   double phase_us[8];    /* with RTG_FLAG_TIMING: prep+plan, keys, sort, pairs, scan,
                             scatter (or write), rowsort, total (microseconds, device events) */
+  double max_abs_err_d2; /* tensor-core brute force: max |tile d^2 - FP64 d^2| over the pairs
+                            the tiles did not reject */
+  double band;           /* tensor-core brute force: half-width of the FP64 band around r^2 */
 } rtg_stats;
 
 typedef struct {
@@ -179,7 +184,13 @@ rtg_status rtg_batch_all_pairs(rtg_ctx* ctx, const rtg_instance* items, int coun
  * the arithmetic contract above) by checking all n(n-1)/2 pairs on the device in tiles; the
  * recall denominator for Alg. 1 and an exact reference.  Same argument conventions and
  * errors as rtg_all_pairs (no transforms).  With count_only != 0 only out->nnz and
- * out->stats.pairs are set (no device memory is returned beyond the row pointers). */
+ * out->stats.pairs are set (no device memory is returned beyond the row pointers).
+ * With RTG_FLAG_TC_FP16 or RTG_FLAG_TC_BF16 the distances come from tensor-core tiles
+ * (|x|^2 + |y|^2 - 2 x.y, x.y as hi.hi + hi.lo + lo.hi of a half-precision split of the
+ * centred coordinates, FP32 accumulation); a pair is rejected on the tile only when its d^2
+ * exceeds r^2 + band, band = max(1e-3 r^2, proven error bound), and every other pair is
+ * decided with the FP64 sequence, so the set is unchanged.  stats.band and
+ * stats.max_abs_err_d2 report the band and the largest observed tile error. */
 rtg_status rtg_brute_force(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
                            int64_t n, int d, double r, uint32_t flags, int count_only,
                            rtg_csr* out);

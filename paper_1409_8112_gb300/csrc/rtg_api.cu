@@ -369,8 +369,19 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if (c->budget && total_held(c) - c->pair_buf.cap + need + need / (sym ? 1 : 2) > c->budget)
         two_pass = true;
     }
+    const bool tc = m == 0 && (q.flags & (RTG_FLAG_TC_FP16 | RTG_FLAG_TC_BF16)) != 0;
+    if (tc) {
+      if ((s = ensure(c, c->tc_tiles, rtg::tc_tiles_bytes(n_total))) != RTG_OK) return s;
+      if ((s = ensure(c, c->tc_norms, (size_t)(n_total + 128) * 4)) != RTG_OK) return s;
+      if ((s = ensure(c, c->tc_plan, sizeof(rtg::TcPlan))) != RTG_OK) return s;
+    }
     auto pairs = [&](rtg::Mode mode) {
-      return m > 0 ? rtg::launch_pairs(a, sorted, mode, st) : rtg::launch_brute(a, mode, st);
+      if (m > 0) return rtg::launch_pairs(a, sorted, mode, st);
+      if (tc)
+        return rtg::launch_brute_tc(a, (q.flags & RTG_FLAG_TC_BF16) != 0, mode,
+                                    (unsigned char*)c->tc_tiles.p, (float*)c->tc_norms.p,
+                                    (rtg::TcPlan*)c->tc_plan.p, st);
+      return rtg::launch_brute(a, mode, st);
     };
     if (!two_pass) {
       if ((s = ensure(c, c->pair_buf, (size_t)g.pair_cap * 8)) != RTG_OK) return s;
@@ -474,12 +485,12 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     out->nnz = q.count_only ? (long long)h.pairs * (sym ? 2 : 1) : (long long)h.nnz;
     rtg_stats& S = out->stats;
     std::memset(&S, 0, sizeof(S));
-    long long tc = 0;
+    long long total_cand = 0;
     for (int t = 0; t < m && t < RTG_MAX_GRIDS; ++t) {
       S.candidates[t] = (int64_t)h.candidates[t];
-      tc += (long long)h.candidates[t];
+      total_cand += (long long)h.candidates[t];
     }
-    S.total_candidates = tc;
+    S.total_candidates = total_cand;
     S.owned_candidates = (int64_t)h.owned_candidates;
     S.near_wall = (int64_t)h.near_wall;
     S.near_r = (int64_t)h.near_r;
@@ -492,6 +503,12 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     S.sort_passes = m > 0 ? a.passes : 0;
     S.launches = launches;
     S.attempts = attempt + 1;
+    {
+      float e;
+      std::memcpy(&e, &h.tc_max_err_bits, 4);
+      S.max_abs_err_d2 = e;
+      S.band = h.tc_band;
+    }
     if (timing) {
       float ms;
       // prep+plan, keys, sort, pairs, scan, scatter/write, rowsort, total
@@ -567,7 +584,7 @@ void destroy_ctx(rtg_ctx* c) {
                     &c->bbox,      &c->T64,       &c->pts,     &c->pf,      &c->key_mat,
                     &c->keys0,     &c->keys1,     &c->vals0,   &c->vals1,   &c->lookback,
                     &c->hist,      &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
-                    &c->large_job, &c->pair_buf};
+                    &c->large_job, &c->pair_buf,  &c->tc_tiles, &c->tc_norms, &c->tc_plan};
   for (DevBuf* b : bufs) free_buf(c, *b);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);

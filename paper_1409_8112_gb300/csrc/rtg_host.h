@@ -55,7 +55,8 @@ struct rtg_ctx {
   std::mutex live_mu;  // output bookkeeping (live, out_bytes)
   std::string err;
   rtghost::DevBuf status, inst, iplan, gplan, bases, bbox, T64, pts, pf, key_mat, keys0, keys1,
-      vals0, vals1, lookback, hist, digit_off, row_cnt, scan_lb, large, large_job, pair_buf;
+      vals0, vals1, lookback, hist, digit_off, row_cnt, scan_lb, large, large_job, pair_buf,
+      tc_tiles, tc_norms, tc_plan;
   rtg::Status* h_status = nullptr;  // pinned
   cudaMemPool_t pool = nullptr;     // output CSRs (stream ordered, kept cached)
   cudaEvent_t ev[8] = {};

@@ -71,7 +71,15 @@ struct Status {
   unsigned long long max_cell;
   unsigned int sort_tiles[kMaxPasses];
   unsigned int long_rows;  // rows queued for the block row sort
-  unsigned int pad;
+  unsigned int tc_max_err_bits;  // tensor-core path: max |FP32 d^2 - FP64 d^2| (float bits)
+  double tc_band;                // tensor-core path: band used around r^2
+};
+
+// Tensor-core brute force: centre of the points, error bound and decision band.
+struct TcPlan {
+  double center[kMaxDim];
+  double band, bound;
+  float lo, hi;  // FP32 d^2 below hi goes to the FP64 check; lo bounds the band from below
 };
 
 // One roadmap of a batch (filled on the host).
@@ -194,6 +202,10 @@ int launch_scatter(const BuildArgs& a, cudaStream_t s);
 int launch_rowsort(const BuildArgs& a, cudaStream_t s);
 
 size_t sort_tiles_for(long long N, bool key64);
+size_t tc_tiles_bytes(long long n);
+// tensor-core brute force (instance 0 only); returns kernels launched
+int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* tiles, float* norms,
+                    TcPlan* tp, cudaStream_t s);
 
 // Text returned by rtg_last_error(NULL) on this thread.
 void set_last_error(const char* msg);

@@ -29,6 +29,8 @@ RTG_FLAG_SHIFT_ONLY = 1
 RTG_FLAG_SYMMETRIC = 2
 RTG_FLAG_TIMING = 4
 RTG_FLAG_TWO_PASS = 8
+RTG_FLAG_TC_FP16 = 16
+RTG_FLAG_TC_BF16 = 32
 
 RTG_DTYPE_F64 = 0
 RTG_DTYPE_F32 = 1
@@ -52,7 +54,8 @@ class rtg_stats(ctypes.Structure):
                 ("large_cells", ctypes.c_int64), ("max_cell", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("key_bits", ctypes.c_int32),
                 ("sort_passes", ctypes.c_int32), ("launches", ctypes.c_int32),
-                ("attempts", ctypes.c_int32), ("phase_us", ctypes.c_double * 8)]
+                ("attempts", ctypes.c_int32), ("phase_us", ctypes.c_double * 8),
+                ("max_abs_err_d2", ctypes.c_double), ("band", ctypes.c_double)]
 
 
 class rtg_csr(ctypes.Structure):
@@ -263,6 +266,7 @@ def stats_dict(s: rtg_stats, m: int) -> dict:
         "pairs": int(s.pairs), "key_bits": int(s.key_bits), "sort_passes": int(s.sort_passes),
         "launches": int(s.launches), "attempts": int(s.attempts),
         "phase_us": {p: float(s.phase_us[i]) for i, p in enumerate(PHASES)},
+        "max_abs_err_d2": float(s.max_abs_err_d2), "band": float(s.band),
     }
 
 
@@ -401,10 +405,18 @@ class Context:
         return Result(self, rtg_wait(self.handle, ticket, timeout_us), m)
 
     def brute_force(self, points, r: float, symmetric: bool = False,
-                    count_only: bool = False) -> Result:
-        """Exact set of Sec. I on the device (all pairs checked)."""
+                    count_only: bool = False, tensor: str | None = None,
+                    timing: bool = False) -> Result:
+        """Exact set of Sec. I on the device (all pairs checked); tensor = "fp16" or "bf16"
+        takes the distances from tensor-core tiles with an FP64 band check."""
         ptr, code, on_dev, n, d, keep = _points_arg(points)
-        flags = RTG_FLAG_SYMMETRIC if symmetric else 0
+        flags = (RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0)
+        if tensor == "fp16":
+            flags |= RTG_FLAG_TC_FP16
+        elif tensor == "bf16":
+            flags |= RTG_FLAG_TC_BF16
+        elif tensor is not None:
+            raise ValueError("tensor must be 'fp16', 'bf16' or None")
         csr = rtg_brute_force(self.handle, ptr, code, on_dev, n, d, float(r), flags, count_only)
         del keep
         return Result(self, csr, 0)

@@ -436,6 +436,68 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """Precision workload: n = 1e6 points of U[0,1]^6 stored FP32, r for degree 2 ln n, m = 8
+    (RTG build), and the exact all-pairs set of a 200,000-point sample (first 200k points of a
+    separate seeded draw, r for that n) on CUDA cores and on FP16 / BF16 tensor-core tiles."""
+    import torch
+    from paper_1409_8112_gb300 import gen, rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, reps):
+        out, ms = None, []
+        for k in range(reps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if k + 1 < reps:
+                out.release()
+        return out, float(np.median(ms))
+
+    n, d, m = 1000000, 6, 8
+    r = gen.radius_for_degree(n, d)
+    pts = torch.from_numpy(gen.points_uniform(0, n, d, np.float32)).cuda()
+    T = gen.transforms(0, d, m, r)
+    for _ in range(args.warmup):
+        ctx.all_pairs(pts, r, T, r).release()
+    build, build_ms = timed(lambda: ctx.all_pairs(pts, r, T, r, timing=True), args.steps)
+    bst = build.stats
+    nb = 200000
+    rb = gen.radius_for_degree(nb, d)
+    sample = torch.from_numpy(gen.points_uniform(1, nb, d, np.float32)).cuda()
+    out = {}
+    for name, tensor in (("cuda_cores_fp32", None), ("tensor_fp16", "fp16"),
+                         ("tensor_bf16", "bf16")):
+        ctx.brute_force(sample, rb, count_only=True, tensor=tensor).release()
+        res, ms = timed(lambda: ctx.brute_force(sample, rb, count_only=True, tensor=tensor),
+                        max(2, args.steps // 3))
+        st = res.stats
+        out[name] = {"ms": round(ms, 3), "pairs": res.nnz,
+                     "pair_tests_per_s": round(nb * (nb - 1) / 2 / (ms / 1e3), 1),
+                     "fp64_band_rechecks": st["dist_rechecks"],
+                     "band": st["band"], "max_abs_err_d2": st["max_abs_err_d2"]}
+        res.release()
+    line = {
+        "metric": METRIC, "value": round(build.nnz / (build_ms / 1e3), 1), "unit": "pairs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(build_ms, 3),
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "precision: n=1e6 U[0,1]^6 fp32, r=2lnn-degree, m=8; brute force "
+                               "on a 200k sample", "l2": "flushed between steps"},
+        "rtg_pairs": build.nnz, "rtg_phase_us": {k: round(v, 1) for k, v in bst["phase_us"].items()},
+        "rtg_key_bits": bst["key_bits"], "rtg_sort_passes": bst["sort_passes"],
+        "brute_force_200k": out, "r_sample": rb, "r2_sample": rb * rb,
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,7 +506,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="build", choices=["build", "batch", "serve"],
+    ap.add_argument("--workload", default="build",
+                    choices=["build", "batch", "serve", "precision"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -459,6 +522,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

@@ -129,7 +129,8 @@ rtg_status read_status(rtg_ctx* c) {
 rtg_status check_errors(rtg_ctx* c, unsigned int mask) {
   const unsigned int e = c->h_status->errors & mask;
   if (!e) return RTG_OK;
-  if (e & rtg::kErrNonFinite) return fail(c, RTG_E_INVALID, "non-finite point coordinate");
+  if (e & rtg::kErrNonFinite)
+    return fail(c, RTG_E_INVALID, "a point coordinate is not finite or exceeds the FP32 range");
   if (e & rtg::kErrKeyOverflow)
     return fail(c, RTG_E_KEY_OVERFLOW, "the cell index ranges need more than 64 key bits");
   if (e & rtg::kErrTimeout) return fail(c, RTG_E_TIMEOUT, "a bounded device wait ran out");
@@ -320,9 +321,15 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if ((s = ensure(c, c->keys1, (size_t)N * ksz)) != RTG_OK) return s;
       if ((s = ensure(c, c->vals0, (size_t)N * 4)) != RTG_OK) return s;
       if ((s = ensure(c, c->vals1, (size_t)N * 4)) != RTG_OK) return s;
+      // look-back words (8 bytes) need zeroed memory once; counts (4 bytes) are rewritten
       if ((s = ensure(c, c->lookback, rtg::sort_tiles_for(N, a.key64) * rtg::kRadix * 8, true)) !=
           RTG_OK)
         return s;
+      if (g.sort_mode < 0)
+        g.sort_mode = rtg::sort_tiles_for(N, a.key64) <= (size_t)(3 * c->num_sms)
+                          ? rtg::kSortLookback
+                          : rtg::kSortReduceScan;
+      a.sort_mode = g.sort_mode;
       if ((s = ensure(c, c->hist, rtg::kMaxPasses * rtg::kRadix * 4, true)) != RTG_OK) return s;
       if ((s = ensure(c, c->digit_off, rtg::kMaxPasses * rtg::kRadix * 4)) != RTG_OK) return s;
       const unsigned int large_cap = (unsigned int)(N / 129 + 1);
@@ -346,7 +353,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       launches += 1;
       if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
       sorted = rtg::launch_sort(a, st);
-      launches += (a.passes > 0 && N > 1) ? 1 + a.passes : 0;
+      launches += (a.passes > 0 && N > 1)
+                      ? 1 + (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
+                      : 0;
     } else if (timing) {
       RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
     }

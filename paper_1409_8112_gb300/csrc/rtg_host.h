@@ -28,6 +28,7 @@ struct ShapeGuess {
   bool key64 = true;
   int passes = rtg::kMaxPasses;
   long long pair_cap = 0;
+  int sort_mode = -1;  // rtg::SortMode; -1: not chosen yet
 };
 
 // One build: a batch of instances sharing m, dtype and the points' location.

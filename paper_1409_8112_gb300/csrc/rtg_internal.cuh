@@ -51,6 +51,9 @@ enum : uint32_t {
 // Enumeration modes.
 enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2 };
 
+// Radix pass strategies.
+enum SortMode : int { kSortLookback = 0, kSortReduceScan = 1 };
+
 // Device-side counters; zeroed at the start of every build.
 struct Status {
   unsigned int errors;
@@ -170,7 +173,7 @@ struct BuildArgs {
   void* key_mat;      // n_total x m keys
   void* keys[2];      // N composite keys, ping-pong
   uint32_t* vals[2];  // N global point indices, ping-pong
-  unsigned long long* lookback;  // sort look-back words (tiles * 256)
+  unsigned long long* lookback;  // sort: look-back words, or per-(digit, tile) counts (u32)
   unsigned int* hist;            // kMaxPasses * 256 digit counts
   unsigned int* digit_off;       // kMaxPasses * 256 exclusive digit offsets
   unsigned int* row_cnt;         // n_total
@@ -184,6 +187,7 @@ struct BuildArgs {
   int* col;
   long long col_cap;
   bool key64;
+  int sort_mode;       // SortMode
   int passes;          // radix passes launched
   unsigned int epoch;  // look-back epoch base for this build's sort passes
   int num_sms;

@@ -51,17 +51,21 @@ template <int DPAD>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ inst, int B,
                                                        int dtype, float* __restrict__ pf,
                                                        unsigned long long* bbox, Status* st) {
+  // The bounding box only has to contain every coordinate: it is kept in FP32, each value
+  // widened by one ulp (the FP32 row is the FP64 value rounded to nearest), so that no FP64
+  // arithmetic runs here.  Finiteness of FP64 input is tested on the exponent bits; values
+  // beyond the FP32 range count as not finite (the FP32 rows could not hold them).
   __shared__ int s_b;
-  __shared__ double smn[kPrepThreads / 32][DPAD], smx[kPrepThreads / 32][DPAD];
+  __shared__ float smn[kPrepThreads / 32][DPAD], smx[kPrepThreads / 32][DPAD];
   const int b = block_instance<true>(inst, B, blockIdx.x, &s_b);
   const Inst I = inst[b];
   const int d = I.d;
-  double mn[DPAD], mx[DPAD];
+  float mn[DPAD], mx[DPAD];
   bool bad = false;
 #pragma unroll
   for (int l = 0; l < DPAD; ++l) {
-    mn[l] = DBL_MAX;
-    mx[l] = -DBL_MAX;
+    mn[l] = FLT_MAX;
+    mx[l] = -FLT_MAX;
   }
   const long long base = (blockIdx.x - I.pblk0) * (long long)kPrepPoints;
   for (int q = 0; q < kPrepPoints / kPrepThreads; ++q) {
@@ -72,11 +76,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
     for (int l = 0; l < DPAD; ++l) {
       row[l] = 0.0f;
       if (l < d) {
-        const double x = load_coord(I.pts, dtype, i, d, l);
-        bad |= !isfinite(x);
-        mn[l] = fmin(mn[l], x);
-        mx[l] = fmax(mx[l], x);
-        row[l] = __double2float_rn(x);
+        float f;
+        if (dtype == 0) {
+          const double x = __ldg((const double*)I.pts + i * d + l);
+          bad |= ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+          f = __double2float_rn(x);
+          mn[l] = fminf(mn[l], nextafterf(f, -FLT_MAX));
+          mx[l] = fmaxf(mx[l], nextafterf(f, FLT_MAX));
+        } else {
+          f = __ldg((const float*)I.pts + i * d + l);
+          mn[l] = fminf(mn[l], f);
+          mx[l] = fmaxf(mx[l], f);
+        }
+        bad |= !isfinite(f);
+        row[l] = f;
       }
     }
     float4* dst = reinterpret_cast<float4*>(pf + (I.p0 + i) * DPAD);
@@ -87,10 +100,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int l = 0; l < DPAD; ++l) {
-    double a = mn[l], c = mx[l];
+    float a = mn[l], c = mx[l];
     for (int o = 16; o > 0; o >>= 1) {
-      a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-      c = fmax(c, __shfl_xor_sync(0xffffffffu, c, o));
+      a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+      c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, o));
     }
     if (lane == 0) {
       smn[warp][l] = a;
@@ -100,14 +113,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->errors, kErrNonFinite);
   if (threadIdx.x < d) {
     const int l = threadIdx.x;
-    double a = smn[0][l], c = smx[0][l];
+    float a = smn[0][l], c = smx[0][l];
     for (int w = 1; w < kPrepThreads / 32; ++w) {
-      a = fmin(a, smn[w][l]);
-      c = fmax(c, smx[w][l]);
+      a = fminf(a, smn[w][l]);
+      c = fmaxf(c, smx[w][l]);
     }
     if (a <= c) {
-      atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 0], enc_double(c));
-      atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 1], ~enc_double(a));
+      atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 0], enc_double((double)c));
+      atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 1], ~enc_double((double)a));
     }
   }
 }
@@ -349,6 +362,7 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
       p[4 * v + 3] = q.w;
     }
     const int tstride = d * d + d;
+    K* krow = key_mat + (size_t)g * m;
     for (int t = 0; t < m; ++t) {
       K key = 0;
       bool near = false;
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
         key += (K)off * (K)sstr[t * d + k];
       }
       key += (K)sbase[t];
-      key_mat[(size_t)g * m + t] = key;
+      krow[t] = key;
       const long long pos = I.p0 * m + (long long)t * I.n + i;
       comp[pos] = key;
       vals[pos] = (uint32_t)g;

@@ -698,7 +698,7 @@ __device__ __forceinline__ void bitonic_regs(int* v) {
       }
 }
 
-// One thread per row: rows of at most 16 entries are sorted in registers (bitonic network
+// One thread per row: rows of at most 32 entries are sorted in registers (bitonic network
 // with +infinity padding); longer rows are queued for the block kernel.  Rows that reach past
 // col_cap (only when an undersized buffer overflowed and the build will be re-run) are left
 // alone.
@@ -710,19 +710,29 @@ __global__ void __launch_bounds__(256) k_rowsort_thread(const long long* __restr
   if (row >= n) return;
   const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
   if (len <= 1 || b + len > col_cap) return;
-  if (len > 16) {
+  if (len > 32) {
     long_rows[atomicAdd(long_count, 1u)] = (unsigned int)row;
     return;
   }
-  int v[16];
+  if (len <= 16) {
+    int v[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = q < len ? col[b + q] : INT_MAX;
-  if (len <= 4) bitonic_regs<4>(v);
-  else if (len <= 8) bitonic_regs<8>(v);
-  else bitonic_regs<16>(v);
+    for (int q = 0; q < 16; ++q) v[q] = q < len ? col[b + q] : INT_MAX;
+    if (len <= 4) bitonic_regs<4>(v);
+    else if (len <= 8) bitonic_regs<8>(v);
+    else bitonic_regs<16>(v);
 #pragma unroll
-  for (int q = 0; q < 16; ++q)
-    if (q < len) col[b + q] = v[q];
+    for (int q = 0; q < 16; ++q)
+      if (q < len) col[b + q] = v[q];
+  } else {
+    int v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = q < len ? col[b + q] : INT_MAX;
+    bitonic_regs<32>(v);
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (q < len) col[b + q] = v[q];
+  }
 }
 
 constexpr int kRowSmem = 8192;

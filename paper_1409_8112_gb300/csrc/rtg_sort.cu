@@ -2,13 +2,13 @@
 // (Alg. 1 lines 4-7 of arXiv:1409.8112 associate each point with its cell; the sort makes
 // every cell a contiguous run).  Stable, 8-bit digits.
 //
-// Onesweep structure: one kernel counts the digits of every pass in a single read of the
-// keys; each pass is then one kernel in which a tile ranks its keys with warp-level
-// multisplit (match.any), obtains its global digit offsets by decoupled look-back over the
-// preceding tiles, reorders the tile in shared memory and writes each digit's run
-// contiguously.  Tiles take their index from an atomic counter, so every tile waits only on
-// tiles that are already running; each wait is bounded and reports kErrTimeout instead of
-// hanging.
+// One kernel counts the digits of every pass in a single read of the keys (global digit
+// offsets).  A pass is either one kernel with decoupled look-back (few tiles) or
+// reduce-then-scan: an upsweep counts the digits of every tile, a
+// scan turns the per-(digit, tile) counts into output offsets, and a downsweep ranks each
+// tile's keys with a warp-level multisplit (peer masks from one ballot per digit bit),
+// reorders the tile in shared memory and writes each digit's run contiguously.  No tile waits
+// on another, so a pass costs the same however many tiles run at once.
 #include <cuda_runtime.h>
 
 #include "rtg_internal.cuh"
@@ -19,8 +19,6 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull;
-constexpr unsigned int kSpinLimit = 1u << 22;
 
 template <typename K>
 struct SortTile;
@@ -38,6 +36,9 @@ __host__ __device__ constexpr int tile_size() {
   return kSortWarps * 32 * SortTile<K>::kItems;
 }
 
+constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull;
+constexpr unsigned int kSpinLimit = 1u << 22;
+
 __device__ __forceinline__ unsigned long long pack_lb(unsigned long long flag, unsigned int epoch,
                                                       unsigned int value) {
   return (flag << 62) | ((unsigned long long)(epoch & 0x3fffffffu) << 32) | value;
@@ -48,6 +49,19 @@ __device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long
 }
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Lanes of the warp whose digit equals this lane's (kRadixBits ballots; no match.any, which
+// is slow here).  `valid` lanes only; an invalid lane gets an arbitrary mask.
+__device__ __forceinline__ unsigned int peer_mask(unsigned int dg, bool valid) {
+  unsigned int peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const unsigned int m = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? m : ~m;
+  }
+  return peers;
 }
 
 // Exclusive scan of one value per thread over a 256-thread block; returns the block total
@@ -92,13 +106,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict_
     const long long x = base + lane;
     const bool valid = x < N;
     const K k = valid ? keys[x] : (K)0;
-    for (int p = 0; p < passes; ++p) {
-      const unsigned int dg = valid ? (unsigned int)(k >> (p * kRadixBits)) & (kRadix - 1)
-                                    : (unsigned int)(kRadix + lane);
-      const unsigned int peers = __match_any_sync(0xffffffffu, dg);
-      if (valid && (peers & ((1u << lane) - 1)) == 0)
-        atomicAdd(&sh[p * kRadix + dg], (unsigned int)__popc(peers));
-    }
+    if (valid)
+      for (int p = 0; p < passes; ++p)
+        atomicAdd(&sh[p * kRadix + ((unsigned int)(k >> (p * kRadixBits)) & (kRadix - 1))], 1u);
   }
   __syncthreads();
   for (int x = threadIdx.x; x < passes * kRadix; x += blockDim.x)
@@ -119,6 +129,143 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict_
   if (threadIdx.x == 0) *ticket = 0;
 }
 
+// Digit counts of every tile of this pass, stored digit-major: counts[digit * tiles + tile].
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const K* __restrict__ kin,
+                                                               long long N, int shift,
+                                                               unsigned int* counts,
+                                                               unsigned int tiles) {
+  constexpr int kTile = tile_size<K>();
+  __shared__ unsigned int sh[kRadix];
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kTile;
+#pragma unroll
+  for (int j = 0; j < SortTile<K>::kItems; ++j) {
+    const long long pos = base + j * kSortThreads + threadIdx.x;
+    if (pos < N) atomicAdd(&sh[(unsigned int)(kin[pos] >> shift) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  counts[(size_t)threadIdx.x * tiles + blockIdx.x] = sh[threadIdx.x];
+}
+
+// One block per digit: exclusive scan of its per-tile counts, offset by the digit's global
+// start, in place.
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned int* counts, unsigned int tiles,
+                                                    const unsigned int* __restrict__ digit_off) {
+  __shared__ unsigned int sbuf[32];
+  __shared__ unsigned int carry;
+  unsigned int* row = counts + (size_t)blockIdx.x * tiles;
+  if (threadIdx.x == 0) carry = digit_off[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (unsigned int b = 0; b < tiles; b += blockDim.x) {
+    const unsigned int t = b + threadIdx.x;
+    const unsigned int v = t < tiles ? row[t] : 0u;
+    unsigned int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sbuf[warp] = x;
+    __syncthreads();
+    unsigned int wpre = 0, tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) wpre += sbuf[w];
+      tot += sbuf[w];
+    }
+    if (t < tiles) row[t] = carry + wpre + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+    uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ offs,
+    unsigned int tiles) {
+  constexpr int kItems = SortTile<K>::kItems;
+  constexpr int kTile = tile_size<K>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  K* s_keys = reinterpret_cast<K*>(smem);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
+  unsigned int* s_whist = s_vals + kTile;  // kSortWarps * kRadix
+  __shared__ unsigned int s_tdig[kRadix];
+  __shared__ unsigned int s_gbase[kRadix];
+  __shared__ unsigned int sbuf[kSortWarps];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int x = tid; x < kSortWarps * kRadix; x += kSortThreads) s_whist[x] = 0;
+  s_gbase[tid] = offs[(size_t)tid * tiles + blockIdx.x];
+  __syncthreads();
+  const long long tile_base = (long long)blockIdx.x * kTile;
+  const long long wbase = tile_base + (long long)warp * 32 * kItems;
+
+  K key[kItems];
+  uint32_t val[kItems];
+  unsigned int rank[kItems];
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const long long pos = wbase + j * 32 + lane;
+    if (pos < N) {
+      key[j] = kin[pos];
+      val[j] = vin[pos];
+    } else {
+      key[j] = (K)0;
+      val[j] = 0;
+    }
+  }
+  unsigned int* wh = s_whist + warp * kRadix;
+  const unsigned int lt = (1u << lane) - 1;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const bool valid = wbase + j * 32 + lane < N;
+    const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
+    const unsigned int peers = peer_mask(dg, valid);
+    const unsigned int before = valid ? wh[dg] : 0u;
+    __syncwarp();
+    if (valid && (peers & lt) == 0) wh[dg] = before + (unsigned int)__popc(peers);
+    __syncwarp();
+    rank[j] = before + (unsigned int)__popc(peers & lt);
+  }
+  __syncthreads();
+  // thread tid owns digit tid: warp-exclusive offsets and this tile's count
+  unsigned int run = 0;
+  for (int w = 0; w < kSortWarps; ++w) {
+    const unsigned int c = s_whist[w * kRadix + tid];
+    s_whist[w * kRadix + tid] = run;
+    run += c;
+  }
+  unsigned int tot;
+  s_tdig[tid] = block_excl_scan_256(run, &tot, sbuf);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const bool valid = wbase + j * 32 + lane < N;
+    if (valid) {
+      const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
+      const unsigned int local = s_tdig[dg] + s_whist[warp * kRadix + dg] + rank[j];
+      s_keys[local] = key[j];
+      s_vals[local] = val[j];
+    }
+  }
+  __syncthreads();
+  const long long rem = N - tile_base;
+  const int tvalid = rem < kTile ? (int)rem : kTile;
+  for (int x = tid; x < tvalid; x += kSortThreads) {
+    const K k = s_keys[x];
+    const unsigned int dg = (unsigned int)(k >> shift) & (kRadix - 1);
+    const unsigned int dst = s_gbase[dg] + (unsigned int)x - s_tdig[dg];
+    kout[dst] = k;
+    vout[dst] = s_vals[x];
+  }
+}
+
+// Single-kernel pass with decoupled look-back (tiles take their index from an atomic
+// counter, so a tile waits only on tiles already running; each wait is bounded).  Cheaper
+// than reduce-then-scan while all tiles fit in about one wave.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
@@ -163,9 +310,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const bool valid = wbase + j * 32 + lane < N;
-    const unsigned int dg =
-        valid ? (unsigned int)(key[j] >> shift) & (kRadix - 1) : (unsigned int)(kRadix + lane);
-    const unsigned int peers = __match_any_sync(0xffffffffu, dg);
+    const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
+    const unsigned int peers = peer_mask(dg, valid);
     const unsigned int before = valid ? wh[dg] : 0u;
     __syncwarp();
     if (valid && (peers & lt) == 0) wh[dg] = before + (unsigned int)__popc(peers);
@@ -264,15 +410,35 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_set[dev])) {
-    cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sort_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   int cur = 0;
+  if (a.sort_mode == kSortLookback) {
+    static bool attr_lb[64] = {};
+    if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_lb[dev])) {
+      cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (dev >= 0 && dev < 64) attr_lb[dev] = true;
+    }
+    for (int p = 0; p < passes; ++p) {
+      k_sort_pass<K><<<tiles, kSortThreads, smem, s>>>(
+          (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N,
+          p * kRadixBits, a.digit_off + p * kRadix, a.lookback, &a.st->sort_tiles[p],
+          a.epoch + (unsigned)p, &a.st->errors);
+      cur = 1 - cur;
+    }
+    return cur;
+  }
+  unsigned int* counts = (unsigned int*)a.lookback;  // kRadix * tiles words
   for (int p = 0; p < passes; ++p) {
-    k_sort_pass<K><<<tiles, kSortThreads, smem, s>>>(
-        (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N,
-        p * kRadixBits, a.digit_off + p * kRadix, a.lookback, &a.st->sort_tiles[p],
-        a.epoch + (unsigned)p, &a.st->errors);
+    const int shift = p * kRadixBits;
+    k_sort_upsweep<K><<<tiles, kSortThreads, 0, s>>>((const K*)a.keys[cur], N, shift, counts,
+                                                     tiles);
+    k_sort_scan<<<kRadix, 1024, 0, s>>>(counts, tiles, a.digit_off + p * kRadix);
+    k_sort_downsweep<K><<<tiles, kSortThreads, smem, s>>>(
+        (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, shift,
+        counts, tiles);
     cur = 1 - cur;
   }
   return cur;

@@ -151,6 +151,29 @@ __device__ __noinline__ double exact_dist2(const void* pts, int dtype, long long
   return s;
 }
 
+// A pair the tile did not reject: decided with the FP64 reference sequence (only rejections
+// rely on the error bound); [lo, hi] is where the tile alone could not decide.
+__device__ __noinline__ void tc_candidate(float d2, long long gi, long long gj, const Inst& I,
+                                          const InstPlan& IP, int dtype, float lo_thr,
+                                          const TcSink& sk, bool emit, unsigned int& pairs,
+                                          unsigned int& rechecks, unsigned int& near_r,
+                                          float& max_err, bool& overflow) {
+  const double s = exact_dist2(I.pts, dtype, gi, gj, I.d);
+  max_err = fmaxf(max_err, (float)fabs((double)d2 - s));
+  if (d2 >= lo_thr) ++rechecks;
+  if (fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r)) ++near_r;
+  if (!(s <= IP.rr)) return;
+  ++pairs;
+  const unsigned int i = (unsigned int)(I.p0 + gi), j = (unsigned int)(I.p0 + gj);
+  if (emit) {
+    const unsigned long long slot = atomicAdd(sk.emitted, 1ull);
+    if ((long long)slot < sk.pair_cap) sk.pair_buf[slot] = ((unsigned long long)i << 32) | j;
+    else overflow = true;
+  }
+  atomicAdd(&sk.row_cnt[i], 1u);
+  if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
+}
+
 // Persistent: each CTA walks a contiguous range of tile pairs (bi <= bj) in bi-major order,
 // so the A tile is reloaded only when bi changes.
 template <bool BF16, bool EMIT>
@@ -267,7 +290,8 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: row `row` of the tile against its 128 columns
+    // epilogue: row `row` of the tile against its 128 columns.  The fast path only builds a
+    // mask of the columns the tile does not reject; those (rare) go to the exact check.
     const int row = warp * 32 + lane;
     const long long gi = bi * kTcRows + row;
     const float nrow = na[row];
@@ -275,41 +299,28 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
     for (int c = 0; c < 128; c += 32) {
       uint32_t r[32];
       tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+      const long long colbase = bj * kTcRows + c;
+      // columns q with gi < colbase + q < n
+      const long long qlo = gi - colbase + 1, qhi = n - colbase;
+      uint32_t valid = 0;
+      if (qlo < 32 && qhi > 0) {
+        const int a0 = qlo > 0 ? (int)qlo : 0, a1 = qhi < 32 ? (int)qhi : 32;
+        if (a1 > a0) valid = (a1 - a0 == 32 ? 0xffffffffu : ((1u << (a1 - a0)) - 1u)) << a0;
+      }
+      float d2v[32];
+      uint32_t hits = 0;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const long long gj = bj * kTcRows + c + q;
-        const float d2 = (nrow + nb[c + q]) - 2.0f * __uint_as_float(r[q]);
-        bool keep = false;
-        if (d2 <= hi_thr && gi < gj && gj < n) {
-          // not rejected by the tile: decided by the FP64 reference (only rejections rely on
-          // the bound); the band [lo, hi] is where the tile alone could not decide
-          const double s = exact_dist2(I.pts, dtype, gi, gj, I.d);
-          max_err = fmaxf(max_err, (float)fabs((double)d2 - s));
-          keep = s <= IP.rr;
-          if (d2 >= lo_thr) ++tl_rechecks;
-          if (fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r)) ++tl_near;
-        }
-        if (EMIT) {
-          const unsigned int mask = __ballot_sync(0xffffffffu, keep);
-          if (mask) {
-            const int leader = __ffs(mask) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(sk.emitted, (unsigned long long)__popc(mask));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (keep) {
-              const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1));
-              if ((long long)slot < sk.pair_cap)
-                sk.pair_buf[slot] = ((unsigned long long)(I.p0 + gi) << 32) | (I.p0 + gj);
-              else
-                overflow = true;
-            }
-          }
-        }
-        if (keep) {
-          ++tl_pairs;
-          atomicAdd(&sk.row_cnt[I.p0 + gi], 1u);
-          if (sk.symmetric) atomicAdd(&sk.row_cnt[I.p0 + gj], 1u);
-        }
+        d2v[q] = (nrow + nb[c + q]) - 2.0f * __uint_as_float(r[q]);
+        hits |= (d2v[q] <= hi_thr ? 1u : 0u) << q;
+      }
+      hits &= valid;
+      if (hits) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (hits & (1u << q))
+            tc_candidate(d2v[q], gi, colbase + q, I, IP, dtype, lo_thr, sk, EMIT, tl_pairs,
+                         tl_rechecks, tl_near, max_err, overflow);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

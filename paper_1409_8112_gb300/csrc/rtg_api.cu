@@ -332,7 +332,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       a.sort_mode = g.sort_mode;
       if ((s = ensure(c, c->hist, rtg::kMaxPasses * rtg::kRadix * 4, true)) != RTG_OK) return s;
       if ((s = ensure(c, c->digit_off, rtg::kMaxPasses * rtg::kRadix * 4)) != RTG_OK) return s;
-      const unsigned int large_cap = (unsigned int)(N / 129 + 1);
+      const unsigned int large_cap = (unsigned int)(N / (rtg::kSmallCell + 1) + 1);
       if ((s = ensure(c, c->large, (size_t)large_cap * sizeof(rtg::LargeCell))) != RTG_OK) return s;
       if ((s = ensure(c, c->large_job, ((size_t)large_cap + 1) * 8)) != RTG_OK) return s;
       a.key_mat = c->key_mat.p;

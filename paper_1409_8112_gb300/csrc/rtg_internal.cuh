@@ -48,6 +48,9 @@ enum : uint32_t {
   kErrPairOverflow = 128u   // pair buffer too small (host re-runs bigger)
 };
 
+// Cells with more points than this are enumerated by the tiled large-cell kernel.
+constexpr int kSmallCell = 32;
+
 // Enumeration modes.
 enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2 };
 

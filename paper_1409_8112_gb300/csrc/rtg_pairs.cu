@@ -1,11 +1,11 @@
 // In-cell pair enumeration and CSR assembly (Alg. 1 lines 8-9 and the dedupe of Sec. III-B
 // of arXiv:1409.8112), for a batch of instances.
 //
-// After the sort every (instance, grid, cell) is a run of equal keys.  A block owns the cells
-// whose first position lies in its slice of kSlice sorted positions: it finds them with
-// adjacent key comparisons, stages their points (FP32, padded rows) in shared memory and walks
-// all pairs (a < b) of every cell with at most kSmax points as one flat candidate range.  Cells
-// with more points go to the tiled large-cell kernel.
+// After the sort every (instance, grid, cell) is a run of equal keys.  A warp owns the cells
+// whose first position lies in its span of sorted positions: it finds them with adjacent key
+// comparisons (ballots), stages their points (FP32, padded rows) in a per-warp shared-memory
+// ring and tests every pair (a < b) of every cell with at most kSmallCell points.  Cells with
+// more points go to the tiled large-cell kernel.
 //
 // Dedupe without an auxiliary set: the distance test does not depend on the grid, so pair
 // {i, j} is reported by grid t iff it is within r and shares a cell in t.  The pair is
@@ -17,7 +17,8 @@
 // distance is outside [s_lo, s_hi], the proven error band around fl(r*r) (see the plan
 // kernel); otherwise the FP64 reference sequence decides.
 //
-// Modes: EMIT writes reported pairs to a pair buffer (one atomic per warp) and counts rows;
+// Modes: EMIT writes reported pairs to a pair buffer (buffered per warp, one reservation per
+// flush) and counts rows;
 // after the scan, scatter places them.  COUNT then WRITE enumerates twice and needs no pair
 // buffer (for outputs too large to hold twice).  Rows are sorted at the end.
 #include <cuda_runtime.h>
@@ -30,13 +31,12 @@ namespace rtg {
 
 namespace {
 
-constexpr int kSlice = 512;
-constexpr int kSmax = 128;
 constexpr int kPairThreads = 256;
-constexpr int kStage = kSlice + kSmax;
-constexpr int kKeyWin = kSlice + kSmax + 2;
-constexpr unsigned int kUnknown = 0xffffffffu;
-constexpr int kTL = 128;  // large-cell tile
+constexpr int kRing = 64;  // staged positions per warp: covers the 31 partners behind a chunk
+static_assert(kRing >= kSmallCell - 1 + 32 && (kRing & (kRing - 1)) == 0, "ring too small");
+constexpr int kWarpEmit = 128;             // EMIT: reported pairs buffered per warp
+constexpr int kWarpFlush = kWarpEmit - 32;  // written out once more than this many are held
+constexpr int kTL = 128;                   // large-cell tile
 constexpr unsigned int kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ double load_coord(const void* pts, int dtype, long long i, int d,
@@ -216,10 +216,10 @@ __device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigne
   if (sbuf[3]) atomicAdd(&st->pairs, (unsigned long long)sbuf[3]);
 }
 
-// (instance, grid) of a composite key: the last base <= key.
+// (instance, grid) of a composite key: the last base <= key, searched in [lo, hi].
 __device__ __forceinline__ int find_bt(unsigned long long key,
-                                       const unsigned long long* __restrict__ bases, int nbt) {
-  int lo = 0, hi = nbt - 1;
+                                       const unsigned long long* __restrict__ bases, int lo,
+                                       int hi) {
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (__ldg(bases + mid) <= key) lo = mid; else hi = mid - 1;
@@ -227,210 +227,309 @@ __device__ __forceinline__ int find_bt(unsigned long long key,
   return lo;
 }
 
-// Shared-memory key rows are staged when a row (m keys) is at most this many bytes.
+// Key rows are staged in shared memory when a row (m keys) is at most this many bytes.
+// Staged rows are m + 1 keys apart so that neighbouring rows fall in different banks.
 constexpr int kMaxStagedRow = 64;
 
+// Bytes of one warp's shared-memory region in k_pairs_warp.
+template <typename K, int DPAD>
+__host__ __device__ inline int warp_region_bytes(int m, bool stage_rows) {
+  const int b = kWarpEmit * 8 + kRing * DPAD * 4 + (stage_rows ? kRing * (m + 1) * (int)sizeof(K) : 0) +
+                kRing * 4 + 3 * 32 * 4;
+  return (b + 15) & ~15;
+}
+
+// End of the run of keys equal to `key` that is known to reach position `from`: galloping
+// search, then bisection (the run may be long).
+template <typename K>
+__device__ long long run_end(const K* __restrict__ skeys, long long N, long long from, K key) {
+  long long lo = from + 1, step = 64, hi = lo;
+  while (true) {  // find hi with skeys[hi] != key (or hi = N)
+    hi = lo + step;
+    if (hi >= N) {
+      hi = N;
+      break;
+    }
+    if (skeys[hi] != key) break;
+    lo = hi + 1;
+    step <<= 1;
+  }
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (skeys[mid] == key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Segment detection and in-cell enumeration for cells of at most kSmallCell points.
+//
+// Each warp owns the cells whose first sorted position lies in its span of positions and walks
+// the span in chunks of 32 positions, one per lane, with the next chunk's keys and indices
+// loaded one chunk ahead.  Cell heads are adjacent-key changes (warp ballot); a head is a large
+// cell when the key 32 positions on is still the same, and large cells are queued for
+// k_pairs_large and skipped.  Every position of a small cell is staged in the warp's ring of
+// kRing slots (FP32 row, index, the first t keys of its key row), so the partners of a position
+// (the earlier positions of its cell, at most 31 back) are always in the ring.  The pairs of a
+// chunk are (position, earlier position of its cell); a warp scan spreads them over the lanes
+// 32 at a time, so the work is balanced whatever the cell sizes.  Only warp-level
+// synchronisation is used.
 template <typename K, int DPAD, int MODE>
-__global__ void __launch_bounds__(kPairThreads) k_pairs_small(
-    const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N,
+__global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
+    const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N, long long span,
     const float* __restrict__ pf, int dtype, const K* __restrict__ key_mat, int m,
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const unsigned long long* __restrict__ bases, int nbt, Status* st, Sink sk,
-    LargeCell* large, unsigned int large_cap) {
+    LargeCell* large, unsigned int large_cap, int warp_bytes, int stage_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* s_pt = reinterpret_cast<float*>(smem);                          // kStage * DPAD
-  uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_pt + kStage * DPAD);    // kStage
-  K* s_key = reinterpret_cast<K*>(s_idx + kStage);                       // kKeyWin
-  unsigned int* c_start = reinterpret_cast<unsigned int*>(s_key + kKeyWin);  // kSlice + 1
-  unsigned int* c_cand = c_start + kSlice + 1;                               // kSlice + 1
-  unsigned int* c_bt = c_cand + kSlice + 1;                                  // kSlice
-  K* s_rows = reinterpret_cast<K*>(c_bt + kSlice + (kSlice & 1));            // kStage * m (opt.)
-  const bool stage_rows = m * (int)sizeof(K) <= kMaxStagedRow;
-  __shared__ unsigned int s_end, s_stage_lo, s_stage_hi, s_total;
-  __shared__ unsigned int sbuf[kPairThreads / 32];
-  __shared__ unsigned int s_tally[4];
   __shared__ unsigned long long s_gcand[kMaxGrids];
-  __shared__ unsigned long long s_maxcell;
-
-  const int tid = threadIdx.x;
-  const long long lo = (long long)blockIdx.x * kSlice;
-  const long long hi = min(lo + kSlice, N);
-  const long long win_end = min(hi + kSmax + 1, N);
-
-  for (long long x = lo - 1 + tid; x < win_end; x += kPairThreads)
-    if (x >= 0) s_key[x - lo + 1] = skeys[x];
-  if (tid == 0) {
-    s_end = kUnknown;
-    s_maxcell = 0;
-  }
-  if (tid < 4) s_tally[tid] = 0;
-  if (MODE != kWrite)
-    for (int g = tid; g < kMaxGrids; g += kPairThreads) s_gcand[g] = 0;
+  __shared__ unsigned int s_maxcell;
+  __shared__ unsigned int s_tally[4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned char* ws = smem + (size_t)wib * warp_bytes;
+  unsigned long long* w_emit = reinterpret_cast<unsigned long long*>(ws);
+  float* w_pt = reinterpret_cast<float*>(ws + kWarpEmit * 8);
+  K* w_rows = reinterpret_cast<K*>(w_pt + kRing * DPAD);
+  const int rstride = m + 1;
+  uint32_t* w_idx = reinterpret_cast<uint32_t*>(w_rows + (stage_rows ? kRing * rstride : 0));
+  int* w_excl = reinterpret_cast<int*>(w_idx + kRing);  // per lane: first pair of the lane
+  int* w_hrel = w_excl + 32;                             // per lane: cell head - chunk start
+  unsigned int* w_cell = reinterpret_cast<unsigned int*>(w_hrel + 32);  // (instance << 8) | grid
+  for (int g = threadIdx.x; g < kMaxGrids; g += blockDim.x) s_gcand[g] = 0;
+  if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_maxcell = 0;
   __syncthreads();
-  auto is_head = [&](long long x) -> bool {
-    return x == 0 || s_key[x - lo + 1] != s_key[x - lo];
-  };
-  for (long long x = hi + tid; x < win_end; x += kPairThreads)
-    if (is_head(x)) atomicMin(&s_end, (unsigned int)(x - lo));
-  constexpr int kPer = kSlice / kPairThreads;
-  unsigned int flags = 0, cnt = 0;
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const long long x = lo + tid * kPer + q;
-    if (x < hi && is_head(x)) {
-      flags |= 1u << q;
-      ++cnt;
+
+  const unsigned int full = 0xffffffffu;
+  const unsigned int lt = (1u << lane) - 1u;
+  const unsigned int le = lane == 31 ? full : ((2u << lane) - 1u);
+  const long long nspans = (N + span - 1) / span;
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  Tally tl;
+  unsigned long long cand_acc = 0;
+  int cand_g = -1;
+  unsigned int maxcell = 0;
+  unsigned int ecnt = 0;  // pairs in w_emit (warp-uniform)
+
+  for (long long sp = (long long)blockIdx.x * (blockDim.x >> 5) + wib; sp < nspans; sp += W) {
+    // Positions inside the span loop are offsets from P0 (int): the warp leaves the span once
+    // it passes its end, so every offset it keeps is below span + 32.
+    const long long P0 = sp * span;
+    const int len = (int)(min(P0 + span, N) - P0);  // owned heads lie in [0, len)
+    const int lim = (int)(min(P0 + span + 64, N) - P0);  // positions read lie in [0, lim)
+    // (instance, grid) range of every cell this span can own
+    int bt_lo = 0, bt_hi = nbt - 1;
+    {
+      const long long q = lane == 0 ? P0 : P0 + min(len + 32, lim) - 1;
+      int v = 0;
+      if (lane < 2) v = find_bt((unsigned long long)skeys[q], bases, 0, nbt - 1);
+      bt_lo = __shfl_sync(full, v, 0);
+      bt_hi = __shfl_sync(full, v, 1);
     }
-  }
-  unsigned int ncells;
-  unsigned int w = block_excl_scan(cnt, &ncells, sbuf);
-#pragma unroll
-  for (int q = 0; q < kPer; ++q)
-    if (flags & (1u << q)) c_start[w++] = (unsigned int)(tid * kPer + q);
-  if (tid == 0) {
-    const unsigned int end_rel =
-        s_end != kUnknown ? s_end : (win_end == N ? (unsigned int)(N - lo) : kUnknown);
-    c_start[ncells] = end_rel;
-  }
-  __syncthreads();
-  if (ncells == 0) return;
-  for (unsigned int e = tid; e < ncells; e += kPairThreads) {
-    const unsigned int st_rel = c_start[e], en = c_start[e + 1];
-    const K key = s_key[st_rel + 1];
-    const int bt = find_bt((unsigned long long)key, bases, nbt);
-    const int g = bt % m;
-    c_bt[e] = (unsigned int)bt;
-    unsigned long long size = en == kUnknown ? 0ull : (unsigned long long)(en - st_rel);
-    unsigned int cand = 0;
-    if (en == kUnknown || size > (unsigned long long)kSmax) {
-      if (MODE != kWrite) {
-        if (en == kUnknown) {
-          long long a = win_end, b = N;  // the run continues past the window
-          while (a < b) {
-            const long long mid = (a + b) >> 1;
-            if (skeys[mid] == key) a = mid + 1; else b = mid;
+    const K* kspan = skeys + P0;
+    const uint32_t* vspan = svals + P0;
+    int P = 0;
+    K key_prev = P0 > 0 ? skeys[P0 - 1] : (K)0;
+    int ch = -1;              // head of the cell holding position P - 1, -1 if not ours
+    unsigned int ccell = 0;   // its (instance << 8) | grid
+    K kc = lane < lim ? kspan[lane] : (K)0;
+    uint32_t vc = lane < lim ? vspan[lane] : 0u;
+    while (true) {
+      const int p = P + lane;
+      const bool valid = p < lim;
+      const int pn = P + 32 + lane;
+      const K kn = pn < lim ? kspan[pn] : (K)0;
+      const uint32_t vn = pn < lim ? vspan[pn] : 0u;
+      K kprev = __shfl_up_sync(full, kc, 1);
+      if (lane == 0) kprev = key_prev;
+      const bool head = valid && ((P0 == 0 && p == 0) || kc != kprev);
+      const unsigned int hmask = __ballot_sync(full, head);
+      if (hmask == 0 && ch < 0) {
+        // the whole chunk continues a cell that starts before this span: skip past it
+        if (P + 32 >= lim) break;
+        const K k31 = __shfl_sync(full, kc, 31);
+        long long e = 0;
+        if (lane == 0) e = run_end(skeys, N, P0 + P + 31, k31);
+        e = __shfl_sync(full, e, 0) - P0;
+        if (e >= len) break;
+        P = (int)e;
+        key_prev = k31;
+        kc = P + lane < lim ? kspan[P + lane] : (K)0;
+        vc = P + lane < lim ? vspan[P + lane] : 0u;
+        continue;
+      }
+      // head lanes: large test, (instance, grid), and a large cell's end (offset, clamped)
+      bool lg = false;
+      unsigned int cell = 0;
+      int lend = 0;
+      if (head && p < len) {
+        lg = pn < lim && kn == kc;  // lim reaches 32 past every owned head unless N does not
+        const int bt = find_bt((unsigned long long)kc, bases, bt_lo, bt_hi);
+        cell = ((unsigned int)(bt / m) << 8) | (unsigned int)(bt % m);
+        if (lg) {
+          const long long e = run_end(skeys, N, P0 + pn, kc);
+          lend = (int)min(e - P0, (long long)INT_MAX);
+          if (MODE != kWrite) {
+            const unsigned long long size = (unsigned long long)(e - (P0 + p));
+            const unsigned long long slot = atomicAdd(&st->large_cells, 1ull);
+            if (slot < large_cap) {
+              large[slot].start = (unsigned long long)(P0 + p);
+              large[slot].size = (unsigned int)size;
+              large[slot].grid = (unsigned short)(cell & 0xffu);
+              large[slot].inst = (unsigned short)(cell >> 8);
+            } else {
+              atomicOr(&st->errors, kErrLargeOverflow);
+            }
+            atomicAdd(&s_gcand[cell & 0xffu], size * (size - 1) / 2);
+            maxcell = max(maxcell, (unsigned int)min(size, 0xffffffffull));
           }
-          size = (unsigned long long)(a - (lo + st_rel));
         }
-        const unsigned long long slot = atomicAdd(&st->large_cells, 1ull);
-        if (slot < large_cap) {
-          large[slot].start = (unsigned long long)(lo + st_rel);
-          large[slot].size = (unsigned int)size;
-          large[slot].grid = (unsigned short)g;
-          large[slot].inst = (unsigned short)(bt / m);
-        } else {
-          atomicOr(&st->errors, kErrLargeOverflow);
+      }
+      const unsigned int hm = hmask & le;
+      const int hl = hm ? 31 - __clz(hm) : lane;
+      const bool lg_h = __shfl_sync(full, lg, hl);
+      const unsigned int cell_h = __shfl_sync(full, cell, hl);
+      const int h = hm ? P + hl : ch;
+      const bool big = hm ? lg_h : false;
+      const unsigned int mycell = hm ? cell_h : ccell;
+      const bool owned = valid && h >= 0 && h < len;
+      const bool active = owned && !big;
+      const int np = active ? p - h : 0;
+      // stage this position in the ring
+      if (active) {
+        const int slot = (int)((P0 + p) & (kRing - 1));
+        w_idx[slot] = vc;
+        const float4* src = reinterpret_cast<const float4*>(pf + (size_t)vc * DPAD);
+        float4* dst = reinterpret_cast<float4*>(w_pt + slot * DPAD);
+#pragma unroll
+        for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+        if (stage_rows) {
+          const int t = (int)(mycell & 0xffu);
+          const K* kr = key_mat + (size_t)vc * m;
+          for (int u = 0; u < t; ++u) w_rows[slot * rstride + u] = __ldg(kr + u);
         }
-        atomicAdd(&s_gcand[g], size * (size - 1) / 2);
-        atomicMax(&s_maxcell, size);
+        if (MODE != kWrite) {
+          const int g = (int)(mycell & 0xffu);
+          if (g != cand_g) {
+            if (cand_acc) atomicAdd(&s_gcand[cand_g], cand_acc);
+            cand_g = g;
+            cand_acc = 0;
+          }
+          cand_acc += (unsigned long long)np;
+          maxcell = max(maxcell, (unsigned int)np + 1u);
+        }
       }
-    } else {
-      cand = (unsigned int)(size * (size - 1) / 2);
-      if (MODE != kWrite) {
-        if (cand) atomicAdd(&s_gcand[g], (unsigned long long)cand);
-        atomicMax(&s_maxcell, size);
+      // pairs of this chunk, spread over the lanes
+      int incl = np;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
       }
+      const int total = __shfl_sync(full, incl, 31);
+      if (total > 0) {
+        w_excl[lane] = incl - np;
+        w_hrel[lane] = h - P;
+        w_cell[lane] = mycell;
+        __syncwarp();
+        const int pbase = (int)((P0 + P) & (kRing - 1));
+        for (int base = 0; base < total; base += 32) {
+          const int k = base + lane;
+          bool keep = false;
+          unsigned int i = 0, j = 0;
+          if (k < total) {
+            int o = 0;
+#pragma unroll
+            for (int st2 = 16; st2 > 0; st2 >>= 1)
+              if (w_excl[o + st2] <= k) o += st2;
+            const int sa = (pbase + o) & (kRing - 1);
+            const int sb = (pbase + w_hrel[o] + (k - w_excl[o])) & (kRing - 1);
+            const unsigned int ia = w_idx[sa], ib = w_idx[sb];
+            i = min(ia, ib);
+            j = max(ia, ib);
+            const unsigned int cl = w_cell[o];
+            const int t = (int)(cl & 0xffu), ib_ = (int)(cl >> 8);
+            const K* ka = stage_rows ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
+            const K* kb = stage_rows ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
+            keep = decide_pair<K, DPAD, MODE>(i, j, t, w_pt + sa * DPAD, w_pt + sb * DPAD, ka, kb,
+                                              inst[ib_], iplan[ib_], dtype, tl);
+          }
+          if (MODE == kEmit) {
+            const unsigned int mask = __ballot_sync(full, keep);
+            if (keep) {
+              w_emit[ecnt + __popc(mask & lt)] = ((unsigned long long)i << 32) | j;
+              atomicAdd(&sk.row_cnt[i], 1u);
+              if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
+            }
+            ecnt += (unsigned int)__popc(mask);
+            if (ecnt > (unsigned int)kWarpFlush) {
+              __syncwarp();
+              unsigned long long b0 = 0;
+              if (lane == 0) b0 = atomicAdd(sk.emitted, (unsigned long long)ecnt);
+              b0 = __shfl_sync(full, b0, 0);
+              for (unsigned int x = lane; x < ecnt; x += 32) {
+                if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = w_emit[x];
+                else tl.overflow = true;
+              }
+              ecnt = 0;
+              __syncwarp();
+            }
+          } else {
+            deliver<MODE>(keep, i, j, sk, tl);
+          }
+        }
+        __syncwarp();
+      }
+      // next chunk
+      const bool own31 = __shfl_sync(full, owned, 31);
+      const bool big31 = __shfl_sync(full, big, 31);
+      const int h31 = __shfl_sync(full, h, 31);
+      const unsigned int cell31 = __shfl_sync(full, mycell, 31);
+      const K k31 = __shfl_sync(full, kc, 31);
+      if (own31 && big31) {  // jump past the large cell (its head is in this chunk)
+        const int hl31 = __shfl_sync(full, hl, 31);
+        const int e = __shfl_sync(full, lend, hl31);
+        if (e >= len) break;
+        P = e;
+        key_prev = k31;
+        ch = -1;
+        kc = P + lane < lim ? kspan[P + lane] : (K)0;
+        vc = P + lane < lim ? vspan[P + lane] : 0u;
+        continue;
+      }
+      const int nxt = P + 32;
+      if (nxt >= lim) break;
+      if (nxt >= len) {
+        const K k0n = __shfl_sync(full, kn, 0);
+        if (!(own31 && k0n == k31)) break;  // no cell of this span continues
+      }
+      P = nxt;
+      key_prev = k31;
+      ch = own31 ? h31 : -1;
+      ccell = cell31;
+      kc = kn;
+      vc = vn;
     }
-    c_cand[e] = cand;
   }
-  __syncthreads();
-  {
-    unsigned int v[kPer], sum = 0;
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const unsigned int e = tid * kPer + q;
-      v[q] = e < ncells ? c_cand[e] : 0u;
-      sum += v[q];
+  if (MODE == kEmit && ecnt) {
+    __syncwarp();
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(sk.emitted, (unsigned long long)ecnt);
+    b0 = __shfl_sync(full, b0, 0);
+    for (unsigned int x = lane; x < ecnt; x += 32) {
+      if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = w_emit[x];
+      else tl.overflow = true;
     }
-    unsigned int total;
-    unsigned int run = block_excl_scan(sum, &total, sbuf);
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const unsigned int e = tid * kPer + q;
-      if (e < ncells) c_cand[e] = run;
-      run += v[q];
-    }
-    if (tid == 0) {
-      c_cand[ncells] = total;
-      s_total = total;
-      s_stage_lo = c_start[0];
-      const unsigned int last = ncells - 1;
-      const unsigned int en = c_start[ncells];
-      const bool last_small = en != kUnknown && en - c_start[last] <= (unsigned int)kSmax;
-      unsigned int shi = last_small ? en : c_start[last];
-      if (shi > s_stage_lo + kStage) shi = s_stage_lo + kStage;
-      s_stage_hi = shi;
-    }
+  }
+  if (MODE != kWrite) {
+    if (cand_acc) atomicAdd(&s_gcand[cand_g], cand_acc);
+    for (int o = 16; o > 0; o >>= 1) maxcell = max(maxcell, __shfl_xor_sync(full, maxcell, o));
+    if (lane == 0 && maxcell) atomicMax(&s_maxcell, maxcell);
   }
   __syncthreads();
   if (MODE != kWrite) {
-    if (tid < m && s_gcand[tid]) atomicAdd(&st->candidates[tid], s_gcand[tid]);
-    if (tid == 0 && s_maxcell) atomicMax(&st->max_cell, s_maxcell);
-  }
-  const unsigned int T = s_total;
-  Tally tl;
-  if (T > 0) {
-    const unsigned int stage_lo = s_stage_lo, nstage = s_stage_hi - s_stage_lo;
-    for (unsigned int x = tid; x < nstage; x += kPairThreads) {
-      const uint32_t idx = svals[lo + stage_lo + x];
-      s_idx[x] = idx;
-      const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
-      float4* dst = reinterpret_cast<float4*>(s_pt + (size_t)x * DPAD);
-#pragma unroll
-      for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
-      if (stage_rows) {
-        const K* kr = key_mat + (size_t)idx * m;
-        for (int u = 0; u < m; ++u) s_rows[(size_t)x * m + u] = __ldg(kr + u);
-      }
-    }
-    __syncthreads();
-    // Each thread walks a contiguous run of `per` candidates, advancing (cell, a, b)
-    // incrementally; all lanes of a warp make the same number of steps so that EMIT can
-    // aggregate with ballots.
-    const unsigned int per = (T + kPairThreads - 1) / kPairThreads;
-    const unsigned int c0 = min(T, (unsigned int)tid * per), c1 = min(T, c0 + per);
-    int el = 0;
-    unsigned int a = 0, b = 1;
-    if (c0 < c1) {
-      int eh = (int)ncells - 1;
-      while (el < eh) {
-        const int mid = (el + eh + 1) >> 1;
-        if (c_cand[mid] <= c0) el = mid; else eh = mid - 1;
-      }
-      const unsigned int l = c0 - c_cand[el];
-      b = (unsigned int)((1.0f + sqrtf(8.0f * (float)l + 1.0f)) * 0.5f);
-      while (b * (b - 1) / 2 > l) --b;
-      while ((b + 1) * b / 2 <= l) ++b;
-      a = l - b * (b - 1) / 2;
-    }
-    for (unsigned int step = 0; step < per; ++step) {
-      const unsigned int c = c0 + step;
-      bool keep = false;
-      unsigned int i = 0, j = 0;
-      if (c < c1) {
-        while (c >= c_cand[el + 1]) {  // next cell with candidates
-          ++el;
-          a = 0;
-          b = 1;
-        }
-        const unsigned int xa = c_start[el] + a - stage_lo, xb = c_start[el] + b - stage_lo;
-        const unsigned int ia = s_idx[xa], ib = s_idx[xb];
-        i = min(ia, ib);
-        j = max(ia, ib);
-        const unsigned int bt = c_bt[el];
-        const int inst_b = (int)(bt / m);
-        const K* ka = stage_rows ? s_rows + (size_t)xa * m : key_mat + (size_t)ia * m;
-        const K* kb = stage_rows ? s_rows + (size_t)xb * m : key_mat + (size_t)ib * m;
-        keep = decide_pair<K, DPAD, MODE>(i, j, (int)(bt % m), s_pt + (size_t)xa * DPAD,
-                                          s_pt + (size_t)xb * DPAD, ka, kb, inst[inst_b],
-                                          iplan[inst_b], dtype, tl);
-        if (++a == b) {  // next pair of the cell in (b, a) order
-          a = 0;
-          ++b;
-        }
-      }
-      deliver<MODE>(keep, i, j, sk, tl);
-    }
+    if (threadIdx.x < m && s_gcand[threadIdx.x])
+      atomicAdd(&st->candidates[threadIdx.x], s_gcand[threadIdx.x]);
+    if (threadIdx.x == 0 && s_maxcell) atomicMax(&st->max_cell, (unsigned long long)s_maxcell);
   }
   flush_tally<MODE>(tl, st, s_tally);
 }
@@ -816,24 +915,32 @@ void brute_impl(const BuildArgs& a, cudaStream_t s) {
 template <typename K, int DPAD, int MODE>
 void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   const long long N = a.n_total * a.m;
-  const unsigned blocks = (unsigned)((N + kSlice - 1) / kSlice);
+  constexpr int kWarps = kPairThreads / 32;
   const bool stage_rows = a.m * (int)sizeof(K) <= kMaxStagedRow;
-  const size_t smem = (size_t)kStage * DPAD * 4 + (size_t)kStage * 4 + (size_t)kKeyWin * sizeof(K) +
-                      (size_t)(kSlice + 1) * 8 + (size_t)(kSlice + (kSlice & 1)) * 4 +
-                      (stage_rows ? (size_t)kStage * a.m * sizeof(K) : 0);
+  const int wbytes = warp_region_bytes<K, DPAD>(a.m, stage_rows);
+  const size_t smem = (size_t)wbytes * kWarps;
+  // spans of a multiple of 32 positions, about two per resident warp, 64..1024 positions
+  const long long resident = 4LL * a.num_sms * kWarps;
+  long long span = (N + 2 * resident - 1) / (2 * resident);
+  span = (span + 31) / 32 * 32;
+  span = span < 64 ? 64 : (span > 1024 ? 1024 : span);
+  const long long nspans = (N + span - 1) / span;
+  long long blocks = (nspans + kWarps - 1) / kWarps;
+  if (blocks > 4LL * a.num_sms) blocks = 4LL * a.num_sms;
+  if (blocks < 1) blocks = 1;
   const K* sk = (const K*)a.keys[sorted_buf];
   const uint32_t* sv = a.vals[sorted_buf];
   static size_t attr_smem[64] = {};  // largest size granted so far, per device
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
-    cudaFuncSetAttribute(k_pairs_small<K, DPAD, MODE>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
   }
-  k_pairs_small<K, DPAD, MODE><<<blocks, kPairThreads, smem, s>>>(
-      sk, sv, N, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases, a.B * a.m,
-      a.st, make_sink(a), a.large, a.large_cap);
+  k_pairs_warp<K, DPAD, MODE><<<(unsigned)blocks, kPairThreads, smem, s>>>(
+      sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
+      a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes, stage_rows ? 1 : 0);
   if (MODE != kWrite) k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
   k_pairs_large<K, DPAD, MODE><<<(unsigned)(4 * a.num_sms), kPairThreads, 0, s>>>(
       sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,

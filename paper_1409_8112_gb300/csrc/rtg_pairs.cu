@@ -46,7 +46,7 @@ __device__ __forceinline__ double load_coord(const void* pts, int dtype, long lo
 }
 
 // FP64 reference squared distance (fixed order, fused multiply-add, original coordinates).
-__device__ __noinline__ double exact_dist2(const void* pts, int dtype, long long i, long long j,
+__device__ __forceinline__ double exact_dist2(const void* pts, int dtype, long long i, long long j,
                                            int d) {
   double s = 0.0;
   for (int l = 0; l < d; ++l) {
@@ -99,10 +99,10 @@ __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long lo
   return wpre + x - v;
 }
 
-// Per-thread tallies.
+// Per-thread tallies (the rare events, near-r pairs and buffer overflow, go straight to the
+// status).
 struct Tally {
-  unsigned int owned = 0, rechecks = 0, near_r = 0, pairs = 0;
-  bool overflow = false;
+  unsigned int owned = 0, rechecks = 0, pairs = 0;
 };
 
 // Where the pairs go.
@@ -114,16 +114,25 @@ struct Sink {
   unsigned long long* pair_buf;
   long long pair_cap;
   unsigned long long* emitted;
+  unsigned int* errors;
+  unsigned long long* near_r;
   int symmetric;
 };
 
+// FP32 band of an instance as (lo, hi): FP32 decides below lo and above hi.  With the filter
+// off every candidate falls inside.
+__device__ __forceinline__ float2 band_of(const InstPlan& IP) {
+  return IP.filter_on ? make_float2(IP.s_lo, IP.s_hi) : make_float2(-1.0f, __int_as_float(0x7f800000));
+}
+
 // Decide one candidate pair (i < j, global indices) of grid t of instance I; ki and kj are the
-// two points' key rows (shared or global memory).
+// two points' key rows (shared or global memory); band is band_of(IP).
 template <typename K, int DPAD, int MODE>
 __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int t, const float* pa,
                                             const float* pb, const K* ki, const K* kj,
-                                            const Inst& I, const InstPlan& IP, int dtype,
-                                            Tally& tl) {
+                                            const Inst* __restrict__ Ip,
+                                            const InstPlan* __restrict__ IPp, float2 band,
+                                            int dtype, Tally& tl, unsigned long long* near_r) {
   bool earlier = false;  // all loads issued before any test
 #pragma unroll 8
   for (int u = 0; u < t; ++u) earlier |= ki[u] == kj[u];
@@ -144,16 +153,17 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
     sf = fmaf(e, e, sf);
   }
   bool keep;
-  if (IP.filter_on && sf < IP.s_lo) {
+  if (sf < band.x) {
     keep = true;
-  } else if (IP.filter_on && sf > IP.s_hi) {
+  } else if (sf > band.y) {
     keep = false;
   } else {
+    const Inst& I = *Ip;
     const double s = exact_dist2(I.pts, dtype, (long long)i - I.p0, (long long)j - I.p0, I.d);
-    keep = s <= IP.rr;
+    keep = s <= IPp->rr;
     if (MODE != kWrite) {
       ++tl.rechecks;
-      if (fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r)) ++tl.near_r;
+      if (fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r)) atomicAdd(near_r, 1ull);
     }
   }
   if (keep && MODE != kWrite) ++tl.pairs;
@@ -174,7 +184,7 @@ __device__ __forceinline__ void deliver(bool keep, unsigned int i, unsigned int 
     if (keep) {
       const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1));
       if ((long long)slot < sk.pair_cap) sk.pair_buf[slot] = ((unsigned long long)i << 32) | j;
-      else tl.overflow = true;
+      else atomicOr(sk.errors, kErrPairOverflow);
       atomicAdd(&sk.row_cnt[i], 1u);
       if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
     }
@@ -186,10 +196,10 @@ __device__ __forceinline__ void deliver(bool keep, unsigned int i, unsigned int 
   } else {
     if (keep) {
       const long long pi = sk.row_ptr[i] + atomicAdd(&sk.row_cnt[i], 1u);
-      if (pi < sk.col_cap) sk.col[pi] = (int)j; else tl.overflow = true;
+      if (pi < sk.col_cap) sk.col[pi] = (int)j; else atomicOr(sk.errors, kErrColOverflow);
       if (sk.symmetric) {
         const long long pj = sk.row_ptr[j] + atomicAdd(&sk.row_cnt[j], 1u);
-        if (pj < sk.col_cap) sk.col[pj] = (int)i; else tl.overflow = true;
+        if (pj < sk.col_cap) sk.col[pj] = (int)i; else atomicOr(sk.errors, kErrColOverflow);
       }
     }
   }
@@ -197,23 +207,21 @@ __device__ __forceinline__ void deliver(bool keep, unsigned int i, unsigned int 
 
 template <int MODE>
 __device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigned int* sbuf) {
-  // sbuf: 4 block-wide counters, zeroed by the caller before its last barrier
-  unsigned int v[4] = {tl.owned, tl.rechecks, tl.near_r, tl.pairs};
+  // sbuf: 3 block-wide counters, zeroed by the caller before its last barrier
+  unsigned int v[3] = {tl.owned, tl.rechecks, tl.pairs};
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 3; ++q)
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
   if (MODE != kWrite && (threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 3; ++q)
       if (v[q]) atomicAdd(&sbuf[q], v[q]);
   }
-  if (__syncthreads_or(tl.overflow) && threadIdx.x == 0)
-    atomicOr(&st->errors, MODE == kEmit ? kErrPairOverflow : kErrColOverflow);
+  __syncthreads();
   if (MODE == kWrite || threadIdx.x != 0) return;
   if (sbuf[0]) atomicAdd(&st->owned_candidates, (unsigned long long)sbuf[0]);
   if (sbuf[1]) atomicAdd(&st->dist_rechecks, (unsigned long long)sbuf[1]);
-  if (sbuf[2]) atomicAdd(&st->near_r, (unsigned long long)sbuf[2]);
-  if (sbuf[3]) atomicAdd(&st->pairs, (unsigned long long)sbuf[3]);
+  if (sbuf[2]) atomicAdd(&st->pairs, (unsigned long long)sbuf[2]);
 }
 
 // (instance, grid) of a composite key: the last base <= key, searched in [lo, hi].
@@ -273,13 +281,16 @@ __device__ long long run_end(const K* __restrict__ skeys, long long N, long long
 // chunk are (position, earlier position of its cell); a warp scan spreads them over the lanes
 // 32 at a time, so the work is balanced whatever the cell sizes.  Only warp-level
 // synchronisation is used.
-template <typename K, int DPAD, int MODE>
-__global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
+#ifndef RTG_PAIRS_MIN_BLOCKS
+#define RTG_PAIRS_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
+#endif
+template <typename K, int DPAD, int MODE, bool STAGE>
+__global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_warp(
     const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N, long long span,
     const float* __restrict__ pf, int dtype, const K* __restrict__ key_mat, int m,
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const unsigned long long* __restrict__ bases, int nbt, Status* st, Sink sk,
-    LargeCell* large, unsigned int large_cap, int warp_bytes, int stage_rows) {
+    LargeCell* large, unsigned int large_cap, int warp_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned int s_maxcell;
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
   float* w_pt = reinterpret_cast<float*>(ws + kWarpEmit * 8);
   K* w_rows = reinterpret_cast<K*>(w_pt + kRing * DPAD);
   const int rstride = m + 1;
-  uint32_t* w_idx = reinterpret_cast<uint32_t*>(w_rows + (stage_rows ? kRing * rstride : 0));
+  uint32_t* w_idx = reinterpret_cast<uint32_t*>(w_rows + (STAGE ? kRing * rstride : 0));
   int* w_excl = reinterpret_cast<int*>(w_idx + kRing);  // per lane: first pair of the lane
   int* w_hrel = w_excl + 32;                             // per lane: cell head - chunk start
   unsigned int* w_cell = reinterpret_cast<unsigned int*>(w_hrel + 32);  // (instance << 8) | grid
@@ -303,14 +314,14 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
   const unsigned int lt = (1u << lane) - 1u;
   const unsigned int le = lane == 31 ? full : ((2u << lane) - 1u);
   const long long nspans = (N + span - 1) / span;
-  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
   Tally tl;
-  unsigned long long cand_acc = 0;
+  unsigned int cand_acc = 0;  // at most 31 per position of the span
   int cand_g = -1;
   unsigned int maxcell = 0;
   unsigned int ecnt = 0;  // pairs in w_emit (warp-uniform)
 
-  for (long long sp = (long long)blockIdx.x * (blockDim.x >> 5) + wib; sp < nspans; sp += W) {
+  // one span per warp
+  if (const long long sp = (long long)blockIdx.x * (blockDim.x >> 5) + wib; sp < nspans) {
     // Positions inside the span loop are offsets from P0 (int): the warp leaves the span once
     // it passes its end, so every offset it keeps is below span + 32.
     const long long P0 = sp * span;
@@ -325,6 +336,10 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
       bt_lo = __shfl_sync(full, v, 0);
       bt_hi = __shfl_sync(full, v, 1);
     }
+    // one instance in the span (the usual case): its FP32 band stays in registers
+    const int inst_lo = bt_lo / m;
+    const bool one_inst = inst_lo == bt_hi / m;
+    const float2 span_band = band_of(iplan[inst_lo]);
     const K* kspan = skeys + P0;
     const uint32_t* vspan = svals + P0;
     int P = 0;
@@ -364,7 +379,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
       if (head && p < len) {
         lg = pn < lim && kn == kc;  // lim reaches 32 past every owned head unless N does not
         const int bt = find_bt((unsigned long long)kc, bases, bt_lo, bt_hi);
-        cell = ((unsigned int)(bt / m) << 8) | (unsigned int)(bt % m);
+        const int bi = one_inst ? inst_lo : bt / m;
+        cell = ((unsigned int)bi << 8) | (unsigned int)(bt - bi * m);
         if (lg) {
           const long long e = run_end(skeys, N, P0 + pn, kc);
           lend = (int)min(e - P0, (long long)INT_MAX);
@@ -402,7 +418,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
         float4* dst = reinterpret_cast<float4*>(w_pt + slot * DPAD);
 #pragma unroll
         for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
-        if (stage_rows) {
+        if (STAGE) {
           const int t = (int)(mycell & 0xffu);
           const K* kr = key_mat + (size_t)vc * m;
           for (int u = 0; u < t; ++u) w_rows[slot * rstride + u] = __ldg(kr + u);
@@ -410,11 +426,11 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
         if (MODE != kWrite) {
           const int g = (int)(mycell & 0xffu);
           if (g != cand_g) {
-            if (cand_acc) atomicAdd(&s_gcand[cand_g], cand_acc);
+            if (cand_acc) atomicAdd(&s_gcand[cand_g], (unsigned long long)cand_acc);
             cand_g = g;
             cand_acc = 0;
           }
-          cand_acc += (unsigned long long)np;
+          cand_acc += (unsigned int)np;
           maxcell = max(maxcell, (unsigned int)np + 1u);
         }
       }
@@ -448,10 +464,11 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
             j = max(ia, ib);
             const unsigned int cl = w_cell[o];
             const int t = (int)(cl & 0xffu), ib_ = (int)(cl >> 8);
-            const K* ka = stage_rows ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
-            const K* kb = stage_rows ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
+            const K* ka = STAGE ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
+            const K* kb = STAGE ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
+            const float2 band = one_inst ? span_band : band_of(iplan[ib_]);
             keep = decide_pair<K, DPAD, MODE>(i, j, t, w_pt + sa * DPAD, w_pt + sb * DPAD, ka, kb,
-                                              inst[ib_], iplan[ib_], dtype, tl);
+                                              inst + ib_, iplan + ib_, band, dtype, tl, sk.near_r);
           }
           if (MODE == kEmit) {
             const unsigned int mask = __ballot_sync(full, keep);
@@ -468,7 +485,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
               b0 = __shfl_sync(full, b0, 0);
               for (unsigned int x = lane; x < ecnt; x += 32) {
                 if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = w_emit[x];
-                else tl.overflow = true;
+                else atomicOr(sk.errors, kErrPairOverflow);
               }
               ecnt = 0;
               __syncwarp();
@@ -517,11 +534,11 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_pairs_warp(
     b0 = __shfl_sync(full, b0, 0);
     for (unsigned int x = lane; x < ecnt; x += 32) {
       if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = w_emit[x];
-      else tl.overflow = true;
+      else atomicOr(sk.errors, kErrPairOverflow);
     }
   }
   if (MODE != kWrite) {
-    if (cand_acc) atomicAdd(&s_gcand[cand_g], cand_acc);
+    if (cand_acc) atomicAdd(&s_gcand[cand_g], (unsigned long long)cand_acc);
     for (int o = 16; o > 0; o >>= 1) maxcell = max(maxcell, __shfl_xor_sync(full, maxcell, o));
     if (lane == 0 && maxcell) atomicMax(&s_maxcell, maxcell);
   }
@@ -581,8 +598,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
       if (job_off[mid] <= job) el = mid; else eh = mid - 1;
     }
     const LargeCell cell = large[el];
-    const Inst I = inst[cell.inst];
-    const InstPlan IP = iplan[cell.inst];
+    const float2 band = band_of(iplan[cell.inst]);
     const unsigned int s = cell.size;
     const unsigned int a0 = (unsigned int)(job - job_off[el]) * kTL;
     const unsigned int na = min((unsigned int)kTL, s - a0);
@@ -619,7 +635,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
             j = max(ia[x], ib[y]);
             keep = decide_pair<K, DPAD, MODE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD,
                                               key_mat + (size_t)ia[x] * m,
-                                              key_mat + (size_t)ib[y] * m, I, IP, dtype, tl);
+                                              key_mat + (size_t)ib[y] * m, inst + cell.inst,
+                                              iplan + cell.inst, band, dtype, tl, sk.near_r);
           }
         }
         deliver<MODE>(keep, i, j, sk, tl);
@@ -644,7 +661,7 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
   __shared__ unsigned int s_tally[4];
   if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
   const Inst I = inst[0];
-  const InstPlan IP = iplan[0];
+  const float2 band = band_of(iplan[0]);
   const long long n = I.n;
   const long long nt = (n + kBT - 1) / kBT;
   const long long jobs = nt * (nt + 1) / 2;
@@ -678,7 +695,7 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
       const unsigned int i = (unsigned int)(I.p0 + li), j = (unsigned int)(I.p0 + lj);
       if (valid)
         keep = decide_pair<uint32_t, DPAD, MODE>(i, j, 0, sa + x * DPAD, sb + y * DPAD, nullptr,
-                                                 nullptr, I, IP, dtype, tl);
+                                                 nullptr, inst, iplan, band, dtype, tl, sk.near_r);
       deliver<MODE>(keep, i, j, sk, tl);
     }
   }
@@ -901,6 +918,8 @@ Sink make_sink(const BuildArgs& a) {
   sk.pair_buf = a.pair_buf;
   sk.pair_cap = a.pair_cap;
   sk.emitted = &a.st->emitted;
+  sk.errors = &a.st->errors;
+  sk.near_r = &a.st->near_r;
   sk.symmetric = a.symmetric;
   return sk;
 }
@@ -925,22 +944,23 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   span = (span + 31) / 32 * 32;
   span = span < 64 ? 64 : (span > 1024 ? 1024 : span);
   const long long nspans = (N + span - 1) / span;
-  long long blocks = (nspans + kWarps - 1) / kWarps;
-  if (blocks > 4LL * a.num_sms) blocks = 4LL * a.num_sms;
-  if (blocks < 1) blocks = 1;
+  const long long blocks = (nspans + kWarps - 1) / kWarps;  // one span per warp
   const K* sk = (const K*)a.keys[sorted_buf];
   const uint32_t* sv = a.vals[sorted_buf];
   static size_t attr_smem[64] = {};  // largest size granted so far, per device
   int dev = 0;
   cudaGetDevice(&dev);
+  auto kern = stage_rows ? k_pairs_warp<K, DPAD, MODE, true> : k_pairs_warp<K, DPAD, MODE, false>;
   if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
-    cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
   }
-  k_pairs_warp<K, DPAD, MODE><<<(unsigned)blocks, kPairThreads, smem, s>>>(
+  kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(
       sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
-      a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes, stage_rows ? 1 : 0);
+      a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes);
   if (MODE != kWrite) k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
   k_pairs_large<K, DPAD, MODE><<<(unsigned)(4 * a.num_sms), kPairThreads, 0, s>>>(
       sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,

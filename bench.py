@@ -6,7 +6,7 @@ random rotations + shifts, cell side c = r, seed 0.  One step = one complete bui
 grids keyed, grouped, enumerated, deduplicated and assembled into the device CSR.
 
   value : unique reported pairs per second of device time, points resident in HBM, L2
-          flushed (512 MB write) between steps
+          flushed between steps (512 MB write, then a 256 MB read)
   e2e   : the same metric through the C ABI with host buffers: points copied in from pinned
           host memory and the CSR copied back inside the timed region
   --impl reference : the CPU oracle (test infrastructure) timed on the host cores on the
@@ -30,10 +30,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "reported r-NN pairs/s and roadmap builds/s at recall R; p50/p99 build latency"
+L2_FLUSH_BYTES = 512 << 20
+L2_CLEAN_BYTES = 256 << 20
+L2_NOTE = ("flushed between steps: 512 MB write, then a 256 MB read so that no dirty line of "
+           "the flush buffer is written back inside the timed region")
+
+
+class L2Flush:
+    """Evicts the inputs from the 129 MB L2 before each timed step: a 512 MB write, then a
+    256 MB read, so that the L2 holds only clean lines of an unrelated buffer."""
+
+    def __init__(self):
+        import torch
+        self.buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        self.clean = torch.zeros(L2_CLEAN_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def __call__(self, k: int = 0):
+        self.buf.fill_(k & 0xff)
+        self.sink = self.clean.sum()
+
+
 WORKLOAD = {"workload": "rtg_all_pairs n=100000 d=6 fp64 uniform[0,1]^6 r=2lnn-degree m=8 c=r seed0",
             "n": 100000, "d": 6, "m": 8, "points": "uniform [0,1]^6, fp64", "cell_side": "r",
-            "seed": 0, "l2": "flushed between steps (512 MB write)"}
-L2_FLUSH_BYTES = 512 << 20
+            "seed": 0, "l2": L2_NOTE}
+
 
 
 def workload():
@@ -142,7 +162,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = rtg.Context(local, stream=stream.cuda_stream)
     dev_pts = torch.from_numpy(pts).cuda()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush()
 
     # recall against the exact set (device brute force), outside the timed region
     exact = ctx.brute_force(dev_pts, r, count_only=True)
@@ -160,7 +180,7 @@ def run_ours(args):
     step_ms, phases, pairs, launches = [], [], None, None
     t_wall = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(k & 0xff)
+        flush(k)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -192,7 +212,7 @@ def run_ours(args):
     host_pts = _t.from_numpy(pts).pin_memory()
     e2e_ms = []
     for k in range(max(3, args.steps // 2) + 1):
-        flush.fill_(k & 0xff)
+        flush(k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = ctx.all_pairs(host_pts, r, T, r)
@@ -314,13 +334,13 @@ def run_batch(args):
     ctx = rtg.Context(0, stream=stream.cuda_stream)
     work = batch_workload()
     dev = [(torch.from_numpy(p).cuda(), r, T, c) for p, r, T, c in work]
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush()
     for _ in range(args.warmup):
         res, offs = ctx.batch_all_pairs(dev, m=6)
         res.release()
     times, pairs = [], 0
     for k in range(args.steps):
-        flush.fill_(k & 0xff)
+        flush(k)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         res, offs = ctx.batch_all_pairs(dev, m=6, timing=True)
@@ -335,7 +355,7 @@ def run_batch(args):
         ctx.all_pairs(p, r, T, c).release()
     single_ms, single_pairs = [], 0
     for k in range(max(1, args.steps // 5)):
-        flush.fill_(k & 0xff)
+        flush(k)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         tot = 0
@@ -357,7 +377,7 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": "batch of 512 roadmaps, n log-uniform [1e3,2e5], d in {3,6,9}, "
                                "fp32 uniform, r=2lnn-degree, m=6, seeds 1000+i",
-                   "points": int(sum(len(w[0]) for w in work)), "l2": "flushed between steps"},
+                   "points": int(sum(len(w[0]) for w in work)), "l2": L2_NOTE},
         "builds_per_s": round(512 / (ms / 1e3), 1), "pairs_per_step": pairs,
         "one_build_per_roadmap": {"ms_per_512": round(sms, 3),
                                   "pairs_per_s": round(single_pairs / (sms / 1e3), 1),
@@ -445,12 +465,12 @@ def run_precision(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     ctx = rtg.Context(0, stream=stream.cuda_stream)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush()
 
     def timed(fn, reps):
         out, ms = None, []
         for k in range(reps):
-            flush.fill_(k & 0xff)
+            flush(k)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             out = fn()
@@ -489,7 +509,7 @@ def run_precision(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(build_ms, 3),
         "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "precision: n=1e6 U[0,1]^6 fp32, r=2lnn-degree, m=8; brute force "
-                               "on a 200k sample", "l2": "flushed between steps"},
+                               "on a 200k sample", "l2": L2_NOTE},
         "rtg_pairs": build.nnz, "rtg_phase_us": {k: round(v, 1) for k, v in bst["phase_us"].items()},
         "rtg_key_bits": bst["key_bits"], "rtg_sort_passes": bst["sort_passes"],
         "brute_force_200k": out, "r_sample": rb, "r2_sample": rb * rb,

@@ -34,6 +34,9 @@ using rtg::Status;
 
 namespace {
 thread_local std::string g_err;
+// Sorts of fewer elements take the default variant: a measurement would cost more than the
+// best variant could save.
+constexpr long long kTuneMinElements = 1LL << 17;
 }  // namespace
 
 void rtg::set_last_error(const char* msg) { g_err = msg; }
@@ -291,10 +294,14 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   ShapeGuess g = known ? git->second : ShapeGuess{};
   const bool two_pass_flag = (q.flags & RTG_FLAG_TWO_PASS) != 0;
 
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  bool tuned_now = false;
+  for (int attempt = 0; attempt < 5; ++attempt) {
     int launches = 0;
     a.key64 = g.key64;
-    a.passes = g.passes;
+    a.passes = rtg::sort_passes_for(g.key_bits, g.sort.bits);
+    a.sort_bits = g.sort.bits;
+    a.sort_items = g.sort.items;
+    a.sort_mode = g.sort.mode;
     if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[0], st));
     RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
     RTG_CUDA(c, cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st));
@@ -308,10 +315,30 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if ((s = check_errors(c, rtg::kErrNonFinite | rtg::kErrKeyOverflow)) != RTG_OK) return s;
       const int bits = (int)c->h_status->sort_bits;
       g.key64 = bits > 32;
-      g.passes = (bits + rtg::kRadixBits - 1) / rtg::kRadixBits;
+      g.key_bits = bits;
       a.key64 = g.key64;
-      a.passes = g.passes;
     }
+    bool tune_now = false;
+    if (m > 0 && !g.sorted_cfg) {
+      // sort variant: the autotuner's table, else measure now (large sorts), else the default
+      const auto it = c->sort_tune.find(SortKey(N, g.key_bits));
+      if (c->sort_forced) {
+        g.sort = c->sort_force;
+        g.sorted_cfg = true;
+      } else if (it != c->sort_tune.end()) {
+        g.sort = it->second.cfg;
+        g.sorted_cfg = true;
+      } else if (c->autotune && N >= kTuneMinElements) {
+        tune_now = true;
+      } else {
+        g.sort = sort_default(N, c->num_sms);
+        g.sorted_cfg = true;
+      }
+    }
+    a.passes = rtg::sort_passes_for(g.key_bits, g.sort.bits);
+    a.sort_bits = g.sort.bits;
+    a.sort_items = g.sort.items;
+    a.sort_mode = g.sort.mode;
     if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[1], st));
     int sorted = 0;
     if (m > 0) {
@@ -321,17 +348,12 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if ((s = ensure(c, c->keys1, (size_t)N * ksz)) != RTG_OK) return s;
       if ((s = ensure(c, c->vals0, (size_t)N * 4)) != RTG_OK) return s;
       if ((s = ensure(c, c->vals1, (size_t)N * 4)) != RTG_OK) return s;
-      // look-back words (8 bytes) need zeroed memory once; counts (4 bytes) are rewritten
-      if ((s = ensure(c, c->lookback, rtg::sort_tiles_for(N, a.key64) * rtg::kRadix * 8, true)) !=
-          RTG_OK)
-        return s;
-      if (g.sort_mode < 0)
-        g.sort_mode = rtg::sort_tiles_for(N, a.key64) <= (size_t)(3 * c->num_sms)
-                          ? rtg::kSortLookback
-                          : rtg::kSortReduceScan;
-      a.sort_mode = g.sort_mode;
-      if ((s = ensure(c, c->hist, rtg::kMaxPasses * rtg::kRadix * 4, true)) != RTG_OK) return s;
-      if ((s = ensure(c, c->digit_off, rtg::kMaxPasses * rtg::kRadix * 4)) != RTG_OK) return s;
+      // look-back words (8 bytes, epoch tagged) need zeroed memory once; counts (4 bytes) are
+      // rewritten by every pass
+      const size_t scratch = tune_now ? sort_scratch_bytes_max(N) : sort_scratch_bytes(N, g.sort);
+      if ((s = ensure(c, c->lookback, scratch, true)) != RTG_OK) return s;
+      if ((s = ensure(c, c->hist, rtg::kSortCountWords * 4, true)) != RTG_OK) return s;
+      if ((s = ensure(c, c->digit_off, rtg::kSortCountWords * 4)) != RTG_OK) return s;
       const unsigned int large_cap = (unsigned int)(N / (rtg::kSmallCell + 1) + 1);
       if ((s = ensure(c, c->large, (size_t)large_cap * sizeof(rtg::LargeCell))) != RTG_OK) return s;
       if ((s = ensure(c, c->large_job, ((size_t)large_cap + 1) * 8)) != RTG_OK) return s;
@@ -346,6 +368,15 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       a.large = (rtg::LargeCell*)c->large.p;
       a.large_cap = large_cap;
       a.large_job_off = (unsigned long long*)c->large_job.p;
+      if (tune_now) {
+        // measure every sort variant on this build's keys, then run the build from the start
+        rtg::SortConfig best;
+        if ((s = tune_sort(c, a, N, g.key_bits, &best)) != RTG_OK) return s;
+        g.sort = best;
+        g.sorted_cfg = true;
+        tuned_now = true;
+        continue;
+      }
       a.epoch = c->epoch;
       c->epoch += rtg::kMaxPasses;
       if ((c->epoch & 0x3fffffffu) < rtg::kMaxPasses) c->epoch = 1;
@@ -470,7 +501,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       release_out(c, out);
       if (h.errors & rtg::kErrKeyBits) {
         g.key64 = h.sort_bits > 32;
-        g.passes = (int)((h.sort_bits + rtg::kRadixBits - 1) / rtg::kRadixBits);
+        g.key_bits = (int)h.sort_bits;
       }
       if (h.errors & rtg::kErrPairOverflow)
         g.pair_cap = (long long)((double)h.emitted * 1.05) + 4096;
@@ -483,7 +514,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     // remember the launch decisions for the next build of this shape
     if (m > 0) {
       g.key64 = h.sort_bits > 32;
-      g.passes = (int)((h.sort_bits + rtg::kRadixBits - 1) / rtg::kRadixBits);
+      g.key_bits = (int)h.sort_bits;
     }
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
@@ -510,8 +541,16 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     S.pairs = (int64_t)h.pairs;
     S.key_bits = (int32_t)h.sort_bits;
     S.sort_passes = m > 0 ? a.passes : 0;
+    S.sort_digit_bits = m > 0 ? a.sort_bits : 0;
+    S.sort_tile_keys = m > 0 ? 256 * a.sort_items : 0;
+    S.sort_lookback = m > 0 && a.sort_mode == rtg::kSortLookback ? 1 : 0;
+    {
+      const auto it = c->sort_tune.find(SortKey(N, g.key_bits));
+      S.sort_tuned = m > 0 && it != c->sort_tune.end() && it->second.cfg.bits == g.sort.bits &&
+                     it->second.cfg.items == g.sort.items && it->second.cfg.mode == g.sort.mode;
+    }
     S.launches = launches;
-    S.attempts = attempt + 1;
+    S.attempts = attempt + 1 - (tuned_now ? 1 : 0);
     {
       float e;
       std::memcpy(&e, &h.tc_max_err_bits, 4);
@@ -552,6 +591,14 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
   if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)) !=
       cudaSuccess)
     return bail(e);
+  {
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, c->device)) != cudaSuccess) return bail(e);
+    c->device_name = std::string(prop.name) + " sm_" + std::to_string(prop.major) +
+                     std::to_string(prop.minor) + " " + std::to_string(prop.multiProcessorCount) +
+                     "SM";
+  }
+  tune_load(c);
   if (stream) {
     c->stream = (cudaStream_t)stream;
   } else {

@@ -29,9 +29,14 @@ namespace rtg {
 
 constexpr int kMaxDim = 16;
 constexpr int kMaxGrids = 64;
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-constexpr int kMaxPasses = 8;
+constexpr int kMaxPasses = 8;  // radix passes of the narrowest digit (8 bits) over a 64-bit key
+// Digit widths and tile sizes the radix sort is compiled for.
+constexpr int kSortBitsChoices[] = {8, 11};
+constexpr int kSortItemsChoices[] = {8, 12, 16};
+constexpr int kSortCountWords = 6 * 2048;  // passes * digits, largest over the digit widths
+__host__ __device__ inline int sort_passes_for(int key_bits, int radix_bits) {
+  return key_bits <= 0 ? 0 : (key_bits + radix_bits - 1) / radix_bits;
+}
 constexpr int kPointBlock = 128;   // points per block in the per-point kernels
 constexpr int kPrepThreads = 256;
 constexpr int kPrepPoints = 1024;  // points per block in the prep kernel
@@ -56,6 +61,13 @@ enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2 };
 
 // Radix pass strategies.
 enum SortMode : int { kSortLookback = 0, kSortReduceScan = 1 };
+
+// One compiled variant of the sort and its pass strategy.
+struct SortConfig {
+  int bits = 8;   // digit width: 8 or 11
+  int items = 8;  // keys per thread: 8, 12 or 16 (tiles of 256 * items keys)
+  int mode = kSortReduceScan;
+};
 
 // Device-side counters; zeroed at the start of every build.
 struct Status {
@@ -177,8 +189,8 @@ struct BuildArgs {
   void* keys[2];      // N composite keys, ping-pong
   uint32_t* vals[2];  // N global point indices, ping-pong
   unsigned long long* lookback;  // sort: look-back words, or per-(digit, tile) counts (u32)
-  unsigned int* hist;            // kMaxPasses * 256 digit counts
-  unsigned int* digit_off;       // kMaxPasses * 256 exclusive digit offsets
+  unsigned int* hist;            // passes * digits counts (kSortCountWords)
+  unsigned int* digit_off;       // passes * digits exclusive digit offsets
   unsigned int* row_cnt;         // n_total
   unsigned long long* scan_lookback;
   LargeCell* large;
@@ -191,6 +203,8 @@ struct BuildArgs {
   long long col_cap;
   bool key64;
   int sort_mode;       // SortMode
+  int sort_bits;       // digit width
+  int sort_items;      // keys per thread in a tile
   int passes;          // radix passes launched
   unsigned int epoch;  // look-back epoch base for this build's sort passes
   int num_sms;
@@ -208,7 +222,7 @@ void launch_scan(const BuildArgs& a, cudaStream_t s);
 int launch_scatter(const BuildArgs& a, cudaStream_t s);
 int launch_rowsort(const BuildArgs& a, cudaStream_t s);
 
-size_t sort_tiles_for(long long N, bool key64);
+size_t sort_tiles_for(long long N, int items);
 size_t tc_tiles_bytes(long long n);
 // tensor-core brute force (instance 0 only); returns kernels launched
 int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* tiles, float* norms,

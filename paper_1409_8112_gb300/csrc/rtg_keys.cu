@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst
 __global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ inst, int B, int m,
                                                       GridPlan* gplan,
                                                       unsigned long long* bases, Status* st,
-                                                      int passes, int key64) {
+                                                      int passes, int radix_bits, int key64) {
   __shared__ unsigned long long sbuf[32];
   __shared__ unsigned long long carry;
   __shared__ int overflow;
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ i
     const unsigned int bits = total <= 1 ? 0u : 64u - (unsigned)__clzll((long long)(total - 1));
     st->sort_bits = bits;
     if (overflow) atomicOr(&st->errors, kErrKeyOverflow);
-    const int need = (int)((bits + kRadixBits - 1) / kRadixBits);
-    if (need > passes || (!key64 && bits > 32)) atomicOr(&st->errors, kErrKeyBits);
+    if (sort_passes_for((int)bits, radix_bits) > passes || (!key64 && bits > 32))
+      atomicOr(&st->errors, kErrKeyBits);
   }
 }
 
@@ -444,7 +444,7 @@ void launch_plan(const BuildArgs& a, cudaStream_t s) {
                                                               a.bbox, a.iplan, a.gplan);
   if (a.m > 0)
     k_plan_ranges<<<1, 1024, 0, s>>>(a.inst, a.B, a.m, a.gplan, a.bases, a.st, a.passes,
-                                     a.key64 ? 1 : 0);
+                                     a.sort_bits, a.key64 ? 1 : 0);
 }
 
 void launch_keys(const BuildArgs& a, cudaStream_t s) {

@@ -1,14 +1,21 @@
 // LSD radix sort of (key, point index) pairs: groups the points of every grid by cell
 // (Alg. 1 lines 4-7 of arXiv:1409.8112 associate each point with its cell; the sort makes
-// every cell a contiguous run).  Stable, 8-bit digits.
+// every cell a contiguous run).  Stable.
+//
+// Compile-time variants: digit width BITS (8 or 11 bits per pass, so a key of b bits takes
+// ceil(b / BITS) passes) and ITEMS keys per thread (tiles of 256 * ITEMS keys).  The
+// autotuner in the host code picks one variant and one pass strategy per shape.
 //
 // One kernel counts the digits of every pass in a single read of the keys (global digit
-// offsets).  A pass is either one kernel with decoupled look-back (few tiles) or
-// reduce-then-scan: an upsweep counts the digits of every tile, a
-// scan turns the per-(digit, tile) counts into output offsets, and a downsweep ranks each
-// tile's keys with a warp-level multisplit (peer masks from one ballot per digit bit),
-// reorders the tile in shared memory and writes each digit's run contiguously.  No tile waits
-// on another, so a pass costs the same however many tiles run at once.
+// offsets).  A pass is then either
+//   * look-back: one kernel; tiles take their index from an atomic counter, publish their
+//     digit counts and find their offsets by decoupled look-back over earlier tiles (bounded
+//     waits), or
+//   * reduce-then-scan: an upsweep counts the digits of every tile, a scan turns the
+//     per-(digit, tile) counts into output offsets, and a downsweep places the keys.
+// Both rank each tile's keys with a warp-level multisplit (peer masks from one ballot per
+// digit bit, per-warp 16-bit digit counters), reorder the tile in shared memory and write each
+// digit's run contiguously.
 #include <cuda_runtime.h>
 
 #include "rtg_internal.cuh"
@@ -20,21 +27,21 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 
-template <typename K>
-struct SortTile;
-template <>
-struct SortTile<uint32_t> {
-  static constexpr int kItems = 8;
-};
-template <>
-struct SortTile<unsigned long long> {
-  static constexpr int kItems = 8;
+template <int BITS>
+struct Digits {
+  static constexpr int kCount = 1 << BITS;
+  static constexpr int kPerThread = kCount / kSortThreads;
+  static_assert(kCount % kSortThreads == 0, "digit count must be a multiple of the block");
 };
 
-template <typename K>
-__host__ __device__ constexpr int tile_size() {
-  return kSortWarps * 32 * SortTile<K>::kItems;
-}
+template <typename K, int BITS, int ITEMS>
+struct SortShape {
+  static constexpr int kTile = kSortThreads * ITEMS;
+  static constexpr int kDigits = 1 << BITS;
+  // keys, values, tile digit starts, global digit starts, per-warp 16-bit counters
+  static constexpr size_t kSmem = (size_t)kTile * (sizeof(K) + 4) + (size_t)kDigits * 8 +
+                                  (size_t)kSortWarps * kDigits * 2;
+};
 
 constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull;
 constexpr unsigned int kSpinLimit = 1u << 22;
@@ -43,7 +50,6 @@ __device__ __forceinline__ unsigned long long pack_lb(unsigned long long flag, u
                                                       unsigned int value) {
   return (flag << 62) | ((unsigned long long)(epoch & 0x3fffffffu) << 32) | value;
 }
-
 __device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
   *reinterpret_cast<volatile unsigned long long*>(p) = v;
 }
@@ -51,12 +57,13 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-// Lanes of the warp whose digit equals this lane's (kRadixBits ballots; no match.any, which
-// is slow here).  `valid` lanes only; an invalid lane gets an arbitrary mask.
+// Lanes of the warp whose digit equals this lane's (BITS ballots).  `valid` lanes only; an
+// invalid lane gets an arbitrary mask.
+template <int BITS>
 __device__ __forceinline__ unsigned int peer_mask(unsigned int dg, bool valid) {
   unsigned int peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) {
+  for (int b = 0; b < BITS; ++b) {
     const bool bit = (dg >> b) & 1u;
     const unsigned int m = __ballot_sync(0xffffffffu, bit);
     peers &= bit ? m : ~m;
@@ -87,31 +94,46 @@ __device__ __forceinline__ unsigned int block_excl_scan_256(unsigned int v, unsi
   return wpre + x - v;
 }
 
-template <typename K>
+// Adds one to the digit counter of every valid lane; a warp whose lanes share one digit
+// (the high digits of neighbouring keys) makes a single add.
+__device__ __forceinline__ void count_digit(unsigned int* sh, unsigned int dg, bool valid,
+                                            unsigned int vmask) {
+  const unsigned int d0 = __shfl_sync(0xffffffffu, dg, 0);
+  if (__all_sync(0xffffffffu, !valid || dg == d0)) {
+    if ((threadIdx.x & 31) == 0 && vmask) atomicAdd(&sh[d0], (unsigned int)__popc(vmask));
+  } else if (valid) {
+    atomicAdd(&sh[dg], 1u);
+  }
+}
+
+// Digit counts of every pass in one read; the last block turns them into exclusive digit
+// offsets (digit_off[p * D + digit]) and clears the counts for the next sort.
+template <typename K, int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict__ keys,
                                                             long long N, int passes,
                                                             unsigned int* hist,
                                                             unsigned int* digit_off,
                                                             unsigned int* ticket) {
-  __shared__ unsigned int sh[kMaxPasses * kRadix];
+  constexpr int D = Digits<BITS>::kCount, PT = Digits<BITS>::kPerThread;
+  extern __shared__ unsigned int sh[];  // passes * D
   __shared__ unsigned int sbuf[kSortWarps];
   __shared__ bool last;
-  for (int x = threadIdx.x; x < kMaxPasses * kRadix; x += blockDim.x) sh[x] = 0;
+  for (int x = threadIdx.x; x < passes * D; x += blockDim.x) sh[x] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const long long step = (long long)gridDim.x * blockDim.x;
-  // warp-uniform loop so that match.any sees the full warp
+  // warp-uniform loop so that the warp votes see every lane
   for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N;
        base += step) {
     const long long x = base + lane;
     const bool valid = x < N;
     const K k = valid ? keys[x] : (K)0;
-    if (valid)
-      for (int p = 0; p < passes; ++p)
-        atomicAdd(&sh[p * kRadix + ((unsigned int)(k >> (p * kRadixBits)) & (kRadix - 1))], 1u);
+    const unsigned int vmask = __ballot_sync(0xffffffffu, valid);
+    for (int p = 0; p < passes; ++p)
+      count_digit(sh + p * D, (unsigned int)(k >> (p * BITS)) & (D - 1), valid, vmask);
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < passes * kRadix; x += blockDim.x)
+  for (int x = threadIdx.x; x < passes * D; x += blockDim.x)
     if (sh[x]) atomicAdd(&hist[x], sh[x]);
   __threadfence();
   __syncthreads();
@@ -120,33 +142,46 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict_
   if (!last) return;
   __threadfence();
   for (int p = 0; p < passes; ++p) {
-    const unsigned int v = __ldcg(&hist[p * kRadix + threadIdx.x]);
+    unsigned int v[PT], sum = 0;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      v[q] = __ldcg(&hist[p * D + threadIdx.x * PT + q]);
+      sum += v[q];
+    }
     unsigned int tot;
-    const unsigned int e = block_excl_scan_256(v, &tot, sbuf);
-    digit_off[p * kRadix + threadIdx.x] = e;
-    hist[p * kRadix + threadIdx.x] = 0;  // ready for the next sort
+    unsigned int run = block_excl_scan_256(sum, &tot, sbuf);
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      digit_off[p * D + threadIdx.x * PT + q] = run;
+      run += v[q];
+      hist[p * D + threadIdx.x * PT + q] = 0;  // ready for the next sort
+    }
   }
   if (threadIdx.x == 0) *ticket = 0;
 }
 
 // Digit counts of every tile of this pass, stored digit-major: counts[digit * tiles + tile].
-template <typename K>
+template <typename K, int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const K* __restrict__ kin,
                                                                long long N, int shift,
                                                                unsigned int* counts,
                                                                unsigned int tiles) {
-  constexpr int kTile = tile_size<K>();
-  __shared__ unsigned int sh[kRadix];
-  sh[threadIdx.x] = 0;
+  constexpr int D = Digits<BITS>::kCount;
+  constexpr int kTile = kSortThreads * ITEMS;
+  __shared__ unsigned int sh[D];
+  for (int x = threadIdx.x; x < D; x += kSortThreads) sh[x] = 0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * kTile;
 #pragma unroll
-  for (int j = 0; j < SortTile<K>::kItems; ++j) {
+  for (int j = 0; j < ITEMS; ++j) {
     const long long pos = base + j * kSortThreads + threadIdx.x;
-    if (pos < N) atomicAdd(&sh[(unsigned int)(kin[pos] >> shift) & (kRadix - 1)], 1u);
+    const bool valid = pos < N;
+    const unsigned int dg = valid ? (unsigned int)(kin[pos] >> shift) & (D - 1) : 0u;
+    count_digit(sh, dg, valid, __ballot_sync(0xffffffffu, valid));
   }
   __syncthreads();
-  counts[(size_t)threadIdx.x * tiles + blockIdx.x] = sh[threadIdx.x];
+  for (int x = threadIdx.x; x < D; x += kSortThreads)
+    counts[(size_t)x * tiles + blockIdx.x] = sh[x];
 }
 
 // One block per digit: exclusive scan of its per-tile counts, offset by the digit's global
@@ -181,262 +216,251 @@ __global__ void __launch_bounds__(1024) k_sort_scan(unsigned int* counts, unsign
   }
 }
 
-template <typename K>
+// Shared work of the two pass kernels: load a tile, rank its keys (stable), reorder it in
+// shared memory.  Afterwards s_tdig[d] is the tile-local start of digit d and tcount[q] the
+// tile's count of digit tid * PT + q; the caller fills s_gbase and writes the tile out.
+template <typename K, int BITS, int ITEMS>
+struct TileRank {
+  static constexpr int D = Digits<BITS>::kCount, PT = Digits<BITS>::kPerThread;
+  static constexpr int kTile = kSortThreads * ITEMS;
+  K* s_keys;
+  uint32_t* s_vals;
+  unsigned int* s_tdig;     // D
+  unsigned int* s_gbase;    // D
+  unsigned short* s_whist;  // kSortWarps * D
+
+  __device__ explicit TileRank(unsigned char* smem) {
+    s_keys = reinterpret_cast<K*>(smem);
+    s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
+    s_tdig = s_vals + kTile;
+    s_gbase = s_tdig + D;
+    s_whist = reinterpret_cast<unsigned short*>(s_gbase + D);
+  }
+
+  __device__ void rank(const K* __restrict__ kin, const uint32_t* __restrict__ vin, long long N,
+                       long long tile_base, int shift, unsigned int (&tcount)[PT],
+                       unsigned int* sbuf) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned int* wz = reinterpret_cast<unsigned int*>(s_whist);
+    for (int x = tid; x < kSortWarps * D / 2; x += kSortThreads) wz[x] = 0;
+    __syncthreads();
+    const long long wbase = tile_base + (long long)warp * 32 * ITEMS;
+    K key[ITEMS];
+    uint32_t val[ITEMS];
+    unsigned int rk[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const long long pos = wbase + j * 32 + lane;
+      if (pos < N) {
+        key[j] = kin[pos];
+        val[j] = vin[pos];
+      } else {
+        key[j] = (K)0;
+        val[j] = 0;
+      }
+    }
+    unsigned short* wh = s_whist + warp * D;
+    const unsigned int lt = (1u << lane) - 1;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const bool valid = wbase + j * 32 + lane < N;
+      const unsigned int dg = (unsigned int)(key[j] >> shift) & (D - 1);
+      const unsigned int peers = peer_mask<BITS>(dg, valid);
+      const unsigned int before = valid ? wh[dg] : 0u;
+      __syncwarp();
+      if (valid && (peers & lt) == 0) wh[dg] = (unsigned short)(before + __popc(peers));
+      __syncwarp();
+      rk[j] = before + (unsigned int)__popc(peers & lt);
+    }
+    __syncthreads();
+    // thread tid owns digits tid * PT .. tid * PT + PT - 1: warp-exclusive offsets, tile counts
+    unsigned int sum = 0;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      const int d = tid * PT + q;
+      unsigned int run = 0;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const unsigned int c = s_whist[w * D + d];
+        s_whist[w * D + d] = (unsigned short)run;
+        run += c;
+      }
+      tcount[q] = run;
+      sum += run;
+    }
+    unsigned int tot;
+    unsigned int start = block_excl_scan_256(sum, &tot, sbuf);
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      s_tdig[tid * PT + q] = start;
+      start += tcount[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const bool valid = wbase + j * 32 + lane < N;
+      if (valid) {
+        const unsigned int dg = (unsigned int)(key[j] >> shift) & (D - 1);
+        const unsigned int local = s_tdig[dg] + s_whist[warp * D + dg] + rk[j];
+        s_keys[local] = key[j];
+        s_vals[local] = val[j];
+      }
+    }
+  }
+
+  // Writes the reordered tile (after a barrier that publishes s_gbase and the tile).
+  __device__ void write(K* __restrict__ kout, uint32_t* __restrict__ vout, long long N,
+                        long long tile_base, int shift) {
+    const long long rem = N - tile_base;
+    const int tvalid = rem < kTile ? (int)rem : kTile;
+    for (int x = threadIdx.x; x < tvalid; x += kSortThreads) {
+      const K k = s_keys[x];
+      const unsigned int dg = (unsigned int)(k >> shift) & (D - 1);
+      const unsigned int dst = s_gbase[dg] + (unsigned int)x - s_tdig[dg];
+      kout[dst] = k;
+      vout[dst] = s_vals[x];
+    }
+  }
+};
+
+template <typename K, int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ offs,
     unsigned int tiles) {
-  constexpr int kItems = SortTile<K>::kItems;
-  constexpr int kTile = tile_size<K>();
+  using TR = TileRank<K, BITS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  K* s_keys = reinterpret_cast<K*>(smem);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
-  unsigned int* s_whist = s_vals + kTile;  // kSortWarps * kRadix
-  __shared__ unsigned int s_tdig[kRadix];
-  __shared__ unsigned int s_gbase[kRadix];
   __shared__ unsigned int sbuf[kSortWarps];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int x = tid; x < kSortWarps * kRadix; x += kSortThreads) s_whist[x] = 0;
-  s_gbase[tid] = offs[(size_t)tid * tiles + blockIdx.x];
+  TR tr(smem);
+  for (int x = threadIdx.x; x < TR::D; x += kSortThreads)
+    tr.s_gbase[x] = offs[(size_t)x * tiles + blockIdx.x];
+  const long long tile_base = (long long)blockIdx.x * TR::kTile;
+  unsigned int tcount[TR::PT];
+  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf);
   __syncthreads();
-  const long long tile_base = (long long)blockIdx.x * kTile;
-  const long long wbase = tile_base + (long long)warp * 32 * kItems;
-
-  K key[kItems];
-  uint32_t val[kItems];
-  unsigned int rank[kItems];
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const long long pos = wbase + j * 32 + lane;
-    if (pos < N) {
-      key[j] = kin[pos];
-      val[j] = vin[pos];
-    } else {
-      key[j] = (K)0;
-      val[j] = 0;
-    }
-  }
-  unsigned int* wh = s_whist + warp * kRadix;
-  const unsigned int lt = (1u << lane) - 1;
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const bool valid = wbase + j * 32 + lane < N;
-    const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
-    const unsigned int peers = peer_mask(dg, valid);
-    const unsigned int before = valid ? wh[dg] : 0u;
-    __syncwarp();
-    if (valid && (peers & lt) == 0) wh[dg] = before + (unsigned int)__popc(peers);
-    __syncwarp();
-    rank[j] = before + (unsigned int)__popc(peers & lt);
-  }
-  __syncthreads();
-  // thread tid owns digit tid: warp-exclusive offsets and this tile's count
-  unsigned int run = 0;
-  for (int w = 0; w < kSortWarps; ++w) {
-    const unsigned int c = s_whist[w * kRadix + tid];
-    s_whist[w * kRadix + tid] = run;
-    run += c;
-  }
-  unsigned int tot;
-  s_tdig[tid] = block_excl_scan_256(run, &tot, sbuf);
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const bool valid = wbase + j * 32 + lane < N;
-    if (valid) {
-      const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
-      const unsigned int local = s_tdig[dg] + s_whist[warp * kRadix + dg] + rank[j];
-      s_keys[local] = key[j];
-      s_vals[local] = val[j];
-    }
-  }
-  __syncthreads();
-  const long long rem = N - tile_base;
-  const int tvalid = rem < kTile ? (int)rem : kTile;
-  for (int x = tid; x < tvalid; x += kSortThreads) {
-    const K k = s_keys[x];
-    const unsigned int dg = (unsigned int)(k >> shift) & (kRadix - 1);
-    const unsigned int dst = s_gbase[dg] + (unsigned int)x - s_tdig[dg];
-    kout[dst] = k;
-    vout[dst] = s_vals[x];
-  }
+  tr.write(kout, vout, N, tile_base, shift);
 }
 
 // Single-kernel pass with decoupled look-back (tiles take their index from an atomic
 // counter, so a tile waits only on tiles already running; each wait is bounded).  Cheaper
 // than reduce-then-scan while all tiles fit in about one wave.
-template <typename K>
+template <typename K, int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ digit_off,
     unsigned long long* lookback, unsigned int* tile_counter, unsigned int epoch,
     unsigned int* errors) {
-  constexpr int kItems = SortTile<K>::kItems;
-  constexpr int kTile = tile_size<K>();
+  using TR = TileRank<K, BITS, ITEMS>;
+  constexpr int D = TR::D, PT = TR::PT;
   extern __shared__ __align__(16) unsigned char smem[];
-  K* s_keys = reinterpret_cast<K*>(smem);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
-  unsigned int* s_whist = s_vals + kTile;  // kSortWarps * kRadix
-  __shared__ unsigned int s_tdig[kRadix];
-  __shared__ unsigned int s_gbase[kRadix];
   __shared__ unsigned int sbuf[kSortWarps];
   __shared__ unsigned int s_tile;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  TR tr(smem);
+  const int tid = threadIdx.x;
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-  for (int x = tid; x < kSortWarps * kRadix; x += kSortThreads) s_whist[x] = 0;
   __syncthreads();
   const unsigned int tile = s_tile;
-  const long long tile_base = (long long)tile * kTile;
-  const long long wbase = tile_base + (long long)warp * 32 * kItems;
-
-  K key[kItems];
-  uint32_t val[kItems];
-  unsigned int rank[kItems];
+  const long long tile_base = (long long)tile * TR::kTile;
+  unsigned int tcount[PT];
+  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf);
+  // publish this tile's counts, then look back digit by digit
+  unsigned long long* lb_tile = lookback + (size_t)tile * D;
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const long long pos = wbase + j * 32 + lane;
-    if (pos < N) {
-      key[j] = kin[pos];
-      val[j] = vin[pos];
-    } else {
-      key[j] = (K)0;
-      val[j] = 0;
-    }
-  }
-  unsigned int* wh = s_whist + warp * kRadix;
-  const unsigned int lt = (1u << lane) - 1;
+  for (int q = 0; q < PT; ++q)
+    st_volatile(lb_tile + tid * PT + q,
+                pack_lb(tile == 0 ? kFlagPrefix : kFlagAgg, epoch, tcount[q]));
+  const unsigned int ep_want = epoch & 0x3fffffffu;
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const bool valid = wbase + j * 32 + lane < N;
-    const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
-    const unsigned int peers = peer_mask(dg, valid);
-    const unsigned int before = valid ? wh[dg] : 0u;
-    __syncwarp();
-    if (valid && (peers & lt) == 0) wh[dg] = before + (unsigned int)__popc(peers);
-    __syncwarp();
-    rank[j] = before + (unsigned int)__popc(peers & lt);
-  }
-  __syncthreads();
-  // thread tid owns digit tid: warp-exclusive offsets and this tile's count
-  unsigned int run = 0;
-  for (int w = 0; w < kSortWarps; ++w) {
-    const unsigned int c = s_whist[w * kRadix + tid];
-    s_whist[w * kRadix + tid] = run;
-    run += c;
-  }
-  const unsigned int tcount = run;
-  unsigned long long* lb = lookback + (size_t)tile * kRadix + tid;
-  unsigned int excl = 0;
-  if (tile == 0) {
-    st_volatile(lb, pack_lb(kFlagPrefix, epoch, tcount));
-  } else {
-    st_volatile(lb, pack_lb(kFlagAgg, epoch, tcount));
-    // Look back over a window of kWin predecessors at a time (independent loads), adding
-    // aggregates until an inclusive prefix is found.
-    constexpr int kWin = 8;
-    long long p = (long long)tile - 1;
-    unsigned int spins = 0;
-    const unsigned int ep_want = epoch & 0x3fffffffu;
-    while (p >= 0) {
-      unsigned long long w[kWin];
+  for (int q = 0; q < PT; ++q) {
+    const int d = tid * PT + q;
+    unsigned int excl = 0;
+    if (tile > 0) {
+      // a window of kWin predecessors at a time (independent loads), adding aggregates until
+      // an inclusive prefix is found
+      constexpr int kWin = 8;
+      long long p = (long long)tile - 1;
+      unsigned int spins = 0;
+      while (p >= 0) {
+        unsigned long long w[kWin];
 #pragma unroll
-      for (int q = 0; q < kWin; ++q)
-        w[q] = p - q >= 0 ? ld_volatile(lookback + (size_t)(p - q) * kRadix + tid) : 0ull;
-      int q = 0;
-      bool done = false;
-      for (; q < kWin && p - q >= 0; ++q) {
-        const unsigned long long flag = w[q] >> 62;
-        const unsigned int ep = (unsigned int)(w[q] >> 32) & 0x3fffffffu;
-        if (flag == 0 || ep != ep_want) break;
-        excl += (unsigned int)w[q];
-        if (flag == kFlagPrefix) {
-          done = true;
-          break;
+        for (int u = 0; u < kWin; ++u)
+          w[u] = p - u >= 0 ? ld_volatile(lookback + (size_t)(p - u) * D + d) : 0ull;
+        int u = 0;
+        bool done = false;
+        for (; u < kWin && p - u >= 0; ++u) {
+          const unsigned long long flag = w[u] >> 62;
+          const unsigned int ep = (unsigned int)(w[u] >> 32) & 0x3fffffffu;
+          if (flag == 0 || ep != ep_want) break;
+          excl += (unsigned int)w[u];
+          if (flag == kFlagPrefix) {
+            done = true;
+            break;
+          }
+        }
+        if (done) break;
+        p -= u;
+        if (u == 0 || (u < kWin && p >= 0)) {
+          if (++spins > kSpinLimit) {
+            atomicOr(errors, kErrTimeout);
+            break;
+          }
+          if (spins > 4) __nanosleep(32);
         }
       }
-      if (done) break;
-      p -= q;
-      if (q == 0 || (q < kWin && p >= 0)) {
-        if (++spins > kSpinLimit) {
-          atomicOr(errors, kErrTimeout);
-          break;
-        }
-        if (spins > 4) __nanosleep(32);
-      }
+      st_volatile(lb_tile + d, pack_lb(kFlagPrefix, epoch, excl + tcount[q]));
     }
-    st_volatile(lb, pack_lb(kFlagPrefix, epoch, excl + tcount));
-  }
-  s_gbase[tid] = digit_off[tid] + excl;
-  unsigned int tot;
-  s_tdig[tid] = block_excl_scan_256(tcount, &tot, sbuf);
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const bool valid = wbase + j * 32 + lane < N;
-    if (valid) {
-      const unsigned int dg = (unsigned int)(key[j] >> shift) & (kRadix - 1);
-      const unsigned int local = s_tdig[dg] + s_whist[warp * kRadix + dg] + rank[j];
-      s_keys[local] = key[j];
-      s_vals[local] = val[j];
-    }
+    tr.s_gbase[d] = digit_off[d] + excl;
   }
   __syncthreads();
-  const long long rem = N - tile_base;
-  const int tvalid = rem < kTile ? (int)rem : kTile;
-  for (int x = tid; x < tvalid; x += kSortThreads) {
-    const K k = s_keys[x];
-    const unsigned int dg = (unsigned int)(k >> shift) & (kRadix - 1);
-    const unsigned int dst = s_gbase[dg] + (unsigned int)x - s_tdig[dg];
-    kout[dst] = k;
-    vout[dst] = s_vals[x];
-  }
+  tr.write(kout, vout, N, tile_base, shift);
 }
 
-template <typename K>
+// Sets a kernel's dynamic shared-memory limit once per device (static shared memory adds to
+// the dynamic part, so the limit is raised whatever the size).
+template <typename F>
+void set_smem_once(F* kern, size_t smem, bool* done /*64*/) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && done[dev]) return;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
+template <typename K, int BITS, int ITEMS>
 int sort_impl(const BuildArgs& a, cudaStream_t s) {
+  using SS = SortShape<K, BITS, ITEMS>;
+  constexpr int D = SS::kDigits;
   const long long N = a.n_total * a.m;
   const int passes = a.passes;
   if (passes <= 0 || N <= 1) return 0;
   long long hb = (N + kSortThreads - 1) / kSortThreads;
   if (hb > 4LL * a.num_sms) hb = 4LL * a.num_sms;
-  k_sort_hist<K><<<(unsigned)hb, kSortThreads, 0, s>>>((const K*)a.keys[0], N, passes, a.hist,
-                                                        a.digit_off, &a.st->hist_ticket);
-  constexpr int kTile = tile_size<K>();
-  const unsigned tiles = (unsigned)((N + kTile - 1) / kTile);
-  const size_t smem = (size_t)kTile * (sizeof(K) + 4) + (size_t)kSortWarps * kRadix * 4;
-  static bool attr_set[64] = {};  // per instantiation and device; the size is fixed
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_set[dev])) {
-    cudaFuncSetAttribute(k_sort_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    if (dev >= 0 && dev < 64) attr_set[dev] = true;
-  }
+  static bool hist_attr[64] = {};
+  set_smem_once(k_sort_hist<K, BITS>, (size_t)kSortCountWords * 4, hist_attr);
+  k_sort_hist<K, BITS><<<(unsigned)hb, kSortThreads, (size_t)passes * D * 4, s>>>(
+      (const K*)a.keys[0], N, passes, a.hist, a.digit_off, &a.st->hist_ticket);
+  const unsigned tiles = (unsigned)((N + SS::kTile - 1) / SS::kTile);
   int cur = 0;
   if (a.sort_mode == kSortLookback) {
-    static bool attr_lb[64] = {};
-    if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_lb[dev])) {
-      cudaFuncSetAttribute(k_sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (dev >= 0 && dev < 64) attr_lb[dev] = true;
-    }
+    static bool attr[64] = {};
+    set_smem_once(k_sort_pass<K, BITS, ITEMS>, SS::kSmem, attr);
     for (int p = 0; p < passes; ++p) {
-      k_sort_pass<K><<<tiles, kSortThreads, smem, s>>>(
-          (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N,
-          p * kRadixBits, a.digit_off + p * kRadix, a.lookback, &a.st->sort_tiles[p],
-          a.epoch + (unsigned)p, &a.st->errors);
+      k_sort_pass<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
+          (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, p * BITS,
+          a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.epoch + (unsigned)p,
+          &a.st->errors);
       cur = 1 - cur;
     }
     return cur;
   }
-  unsigned int* counts = (unsigned int*)a.lookback;  // kRadix * tiles words
+  static bool attr[64] = {};
+  set_smem_once(k_sort_downsweep<K, BITS, ITEMS>, SS::kSmem, attr);
+  unsigned int* counts = (unsigned int*)a.lookback;  // D * tiles words
   for (int p = 0; p < passes; ++p) {
-    const int shift = p * kRadixBits;
-    k_sort_upsweep<K><<<tiles, kSortThreads, 0, s>>>((const K*)a.keys[cur], N, shift, counts,
-                                                     tiles);
-    k_sort_scan<<<kRadix, 1024, 0, s>>>(counts, tiles, a.digit_off + p * kRadix);
-    k_sort_downsweep<K><<<tiles, kSortThreads, smem, s>>>(
+    const int shift = p * BITS;
+    k_sort_upsweep<K, BITS, ITEMS><<<tiles, kSortThreads, 0, s>>>((const K*)a.keys[cur], N, shift,
+                                                                  counts, tiles);
+    k_sort_scan<<<D, 1024, 0, s>>>(counts, tiles, a.digit_off + p * D);
+    k_sort_downsweep<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
         (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, shift,
         counts, tiles);
     cur = 1 - cur;
@@ -444,15 +468,29 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
   return cur;
 }
 
+template <typename K, int BITS>
+int sort_items(const BuildArgs& a, cudaStream_t s) {
+  switch (a.sort_items) {
+    case 12: return sort_impl<K, BITS, 12>(a, s);
+    case 16: return sort_impl<K, BITS, 16>(a, s);
+    default: return sort_impl<K, BITS, 8>(a, s);
+  }
+}
+
+template <typename K>
+int sort_width(const BuildArgs& a, cudaStream_t s) {
+  return a.sort_bits == 11 ? sort_items<K, 11>(a, s) : sort_items<K, 8>(a, s);
+}
+
 }  // namespace
 
-size_t sort_tiles_for(long long N, bool key64) {
-  const int t = key64 ? tile_size<unsigned long long>() : tile_size<uint32_t>();
+size_t sort_tiles_for(long long N, int items) {
+  const long long t = (long long)kSortThreads * items;
   return (size_t)((N + t - 1) / t);
 }
 
 int launch_sort(const BuildArgs& a, cudaStream_t s) {
-  return a.key64 ? sort_impl<unsigned long long>(a, s) : sort_impl<uint32_t>(a, s);
+  return a.key64 ? sort_width<unsigned long long>(a, s) : sort_width<uint32_t>(a, s);
 }
 
 }  // namespace rtg

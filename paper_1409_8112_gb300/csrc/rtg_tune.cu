@@ -1,0 +1,224 @@
+// Autotuner of the radix sort: digit width (8 or 11 bits per pass), tile size (256 x 8, 12
+// or 16 keys) and pass strategy (look-back or reduce-then-scan).  On the first build of a
+// shape whose sort is large enough to matter it times every variant twice on the build's own
+// keys and keeps the fastest, per (sorted elements, key bits), in the context and, when
+// RTG_TUNE_CACHE names a file, in a JSON cache shared by later contexts and processes.
+// The sort is stable in every variant, so the choice never changes a result.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rtg_host.h"
+
+namespace rtghost {
+
+namespace {
+
+constexpr int kTuneReps = 2;
+
+std::vector<rtg::SortConfig> candidates() {
+  std::vector<rtg::SortConfig> v;
+  for (int bits : rtg::kSortBitsChoices)
+    for (int items : rtg::kSortItemsChoices)
+      for (int mode : {rtg::kSortLookback, rtg::kSortReduceScan}) {
+        rtg::SortConfig c;
+        c.bits = bits;
+        c.items = items;
+        c.mode = mode;
+        v.push_back(c);
+      }
+  return v;
+}
+
+// Number after `"name": ` in a line of our own cache format (no nesting, no escapes).
+bool field(const std::string& line, const char* name, double* v) {
+  const std::string pat = std::string("\"") + name + "\":";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return false;
+  *v = std::strtod(line.c_str() + at + pat.size(), nullptr);
+  return true;
+}
+
+bool field_str(const std::string& line, const char* name, std::string* v) {
+  const std::string pat = std::string("\"") + name + "\": \"";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return false;
+  const size_t b = at + pat.size(), e = line.find('"', b);
+  if (e == std::string::npos) return false;
+  *v = line.substr(b, e - b);
+  return true;
+}
+
+bool valid_cfg(const rtg::SortConfig& c) {
+  const bool bits_ok = std::find(std::begin(rtg::kSortBitsChoices), std::end(rtg::kSortBitsChoices),
+                                 c.bits) != std::end(rtg::kSortBitsChoices);
+  const bool items_ok = std::find(std::begin(rtg::kSortItemsChoices),
+                                  std::end(rtg::kSortItemsChoices),
+                                  c.items) != std::end(rtg::kSortItemsChoices);
+  return bits_ok && items_ok && (c.mode == rtg::kSortLookback || c.mode == rtg::kSortReduceScan);
+}
+
+// Reads the cache file into `out` (entries of this device only).
+void read_cache(const std::string& path, const std::string& device,
+                std::map<SortKey, TuneEntry>* out) {
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char buf[512];
+  while (std::fgets(buf, sizeof buf, f)) {
+    const std::string line(buf);
+    std::string dev;
+    double el, kb, bits, items, mode, us;
+    if (!field_str(line, "device", &dev) || dev != device) continue;
+    if (!field(line, "elements", &el) || !field(line, "key_bits", &kb) ||
+        !field(line, "bits", &bits) || !field(line, "items", &items) ||
+        !field(line, "mode", &mode) || !field(line, "us", &us))
+      continue;
+    TuneEntry e;
+    e.cfg.bits = (int)bits;
+    e.cfg.items = (int)items;
+    e.cfg.mode = (int)mode;
+    e.us = us;
+    if (valid_cfg(e.cfg)) (*out)[SortKey((long long)el, (int)kb)] = e;
+  }
+  std::fclose(f);
+}
+
+// Merges the context's entries into the cache file (write to a temporary, then rename).
+void save_cache(rtg_ctx* c) {
+  if (c->tune_path.empty()) return;
+  std::map<SortKey, TuneEntry> all;
+  read_cache(c->tune_path, c->device_name, &all);
+  for (const auto& kv : c->sort_tune) all[kv.first] = kv.second;
+  // keep other devices' lines as they are
+  std::vector<std::string> other;
+  if (FILE* f = std::fopen(c->tune_path.c_str(), "r")) {
+    char buf[512];
+    while (std::fgets(buf, sizeof buf, f)) {
+      const std::string line(buf);
+      std::string dev;
+      if (field_str(line, "device", &dev) && dev != c->device_name) {
+        std::string l = line;
+        while (!l.empty() && (l.back() == '\n' || l.back() == ',')) l.pop_back();
+        other.push_back(l);
+      }
+    }
+    std::fclose(f);
+  }
+  const std::string tmp = c->tune_path + ".tmp" + std::to_string((long long)(uintptr_t)c);
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\"rtg_sort_tune\": 1, \"entries\": [\n");
+  std::vector<std::string> lines = other;
+  for (const auto& kv : all) {
+    char line[400];
+    std::snprintf(line, sizeof line,
+                  "{\"device\": \"%s\", \"elements\": %lld, \"key_bits\": %d, \"bits\": %d, "
+                  "\"items\": %d, \"mode\": %d, \"us\": %.2f}",
+                  c->device_name.c_str(), kv.first.first, kv.first.second, kv.second.cfg.bits,
+                  kv.second.cfg.items, kv.second.cfg.mode, kv.second.us);
+    lines.push_back(line);
+  }
+  for (size_t i = 0; i < lines.size(); ++i)
+    std::fprintf(f, "%s%s\n", lines[i].c_str(), i + 1 < lines.size() ? "," : "");
+  std::fprintf(f, "]}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), c->tune_path.c_str());
+}
+
+}  // namespace
+
+rtg::SortConfig sort_default(long long N, int num_sms) {
+  rtg::SortConfig c;
+  c.bits = 8;
+  c.items = 8;
+  c.mode = rtg::sort_tiles_for(N, 8) <= (size_t)(3 * num_sms) ? rtg::kSortLookback
+                                                               : rtg::kSortReduceScan;
+  return c;
+}
+
+size_t sort_scratch_bytes(long long N, const rtg::SortConfig& cfg) {
+  const size_t words = rtg::sort_tiles_for(N, cfg.items) * ((size_t)1 << cfg.bits);
+  return words * (cfg.mode == rtg::kSortLookback ? 8 : 4);
+}
+
+size_t sort_scratch_bytes_max(long long N) {
+  size_t m = 0;
+  for (const auto& c : candidates()) m = std::max(m, sort_scratch_bytes(N, c));
+  return m;
+}
+
+void tune_load(rtg_ctx* c) {
+  const char* p = std::getenv("RTG_TUNE_CACHE");
+  c->tune_path = p ? p : "";
+  const char* off = std::getenv("RTG_AUTOTUNE");
+  c->autotune = !(off && std::strcmp(off, "0") == 0);
+  c->sort_forced = false;
+  if (const char* v = std::getenv("RTG_SORT_VARIANT")) {
+    // "bits,items,mode": one variant for every sort of this context (no measurement)
+    rtg::SortConfig f;
+    if (std::sscanf(v, "%d,%d,%d", &f.bits, &f.items, &f.mode) == 3 && valid_cfg(f)) {
+      c->sort_forced = true;
+      c->sort_force = f;
+    }
+  }
+  if (!c->tune_path.empty()) read_cache(c->tune_path, c->device_name, &c->sort_tune);
+}
+
+rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
+                     rtg::SortConfig* out) {
+  const std::vector<rtg::SortConfig> cands = candidates();
+  const int trials = (int)cands.size() * kTuneReps;
+  std::vector<cudaEvent_t> ev(2 * (size_t)trials, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess)
+      return fail(c, RTG_E_CUDA, "tune: cudaEventCreate failed");
+  const cudaStream_t st = c->stream;
+  const rtg::BuildArgs base = a;
+  for (int t = 0; t < trials; ++t) {
+    const rtg::SortConfig& cfg = cands[(size_t)t % cands.size()];
+    rtg::BuildArgs b = base;
+    b.sort_bits = cfg.bits;
+    b.sort_items = cfg.items;
+    b.sort_mode = cfg.mode;
+    b.passes = rtg::sort_passes_for(key_bits, cfg.bits);
+    b.epoch = c->epoch;
+    c->epoch += rtg::kMaxPasses;
+    if ((c->epoch & 0x3fffffffu) < rtg::kMaxPasses) c->epoch = 1;
+    cudaMemsetAsync(&b.st->sort_tiles[0], 0, sizeof(b.st->sort_tiles), st);
+    rtg::launch_keys(b, st);  // the sort consumes its input buffers
+    cudaEventRecord(ev[2 * (size_t)t], st);
+    rtg::launch_sort(b, st);
+    cudaEventRecord(ev[2 * (size_t)t + 1], st);
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  std::vector<double> best(cands.size(), 1e30);
+  if (e == cudaSuccess) {
+    for (int t = 0; t < trials; ++t) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * (size_t)t], ev[2 * (size_t)t + 1]) == cudaSuccess) {
+        double& b = best[(size_t)t % cands.size()];
+        b = std::min(b, (double)ms * 1e3);
+      }
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess)
+    return fail(c, RTG_E_CUDA, std::string("tune: ") + cudaGetErrorString(e));
+  size_t k = 0;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (best[i] < best[k]) k = i;
+  *out = cands[k];
+  TuneEntry te;
+  te.cfg = cands[k];
+  te.us = best[k];
+  c->sort_tune[SortKey(N, key_bits)] = te;
+  save_cache(c);
+  return RTG_OK;
+}
+
+}  // namespace rtghost

@@ -54,7 +54,9 @@ class rtg_stats(ctypes.Structure):
                 ("large_cells", ctypes.c_int64), ("max_cell", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("key_bits", ctypes.c_int32),
                 ("sort_passes", ctypes.c_int32), ("launches", ctypes.c_int32),
-                ("attempts", ctypes.c_int32), ("phase_us", ctypes.c_double * 8),
+                ("attempts", ctypes.c_int32), ("sort_digit_bits", ctypes.c_int32),
+                ("sort_tile_keys", ctypes.c_int32), ("sort_lookback", ctypes.c_int32),
+                ("sort_tuned", ctypes.c_int32), ("phase_us", ctypes.c_double * 8),
                 ("max_abs_err_d2", ctypes.c_double), ("band", ctypes.c_double)]
 
 
@@ -265,6 +267,8 @@ def stats_dict(s: rtg_stats, m: int) -> dict:
         "large_cells": int(s.large_cells), "max_cell": int(s.max_cell),
         "pairs": int(s.pairs), "key_bits": int(s.key_bits), "sort_passes": int(s.sort_passes),
         "launches": int(s.launches), "attempts": int(s.attempts),
+        "sort": {"digit_bits": int(s.sort_digit_bits), "tile_keys": int(s.sort_tile_keys),
+                 "lookback": int(s.sort_lookback), "tuned": int(s.sort_tuned)},
         "phase_us": {p: float(s.phase_us[i]) for i, p in enumerate(PHASES)},
         "max_abs_err_d2": float(s.max_abs_err_d2), "band": float(s.band),
     }

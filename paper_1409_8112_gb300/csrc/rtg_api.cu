@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -37,6 +38,7 @@ thread_local std::string g_err;
 // Sorts of fewer elements take the default variant: a measurement would cost more than the
 // best variant could save.
 constexpr long long kTuneMinElements = 1LL << 17;
+constexpr size_t kMaxGraphs = 32;  // executable graphs kept per context (one per shape)
 }  // namespace
 
 void rtg::set_last_error(const char* msg) { g_err = msg; }
@@ -178,6 +180,75 @@ rtg_status validate_transforms(const double* T, int d, int m) {
 }
 
 // The whole build.  On success *out holds the block-diagonal CSR of the batch.
+// Bytes that decide whether a captured launch sequence can be replayed: every launch argument
+// except the output pointers (which the kernels read from the device slot), plus the timing
+// flag and the stream.
+std::vector<unsigned char> graph_signature(const rtg::BuildArgs& a, bool timing, cudaStream_t st) {
+  rtg::BuildArgs b = a;
+  b.row_ptr = nullptr;
+  b.col = nullptr;
+  b.col_cap = 0;
+  std::vector<unsigned char> sig(sizeof(b) + 2 + sizeof(st));
+  std::memcpy(sig.data(), &b, sizeof(b));
+  sig[sizeof(b)] = timing ? 1 : 0;
+  sig[sizeof(b) + 1] = 0x5a;
+  std::memcpy(sig.data() + sizeof(b) + 2, &st, sizeof(st));
+  return sig;
+}
+
+void drop_graph(rtg_ctx* c, const ShapeKey& key) {
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) return;
+  if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+  c->graphs.erase(it);
+}
+
+// The executable graph of this shape's launch sequence: replayed when the arguments match,
+// else captured again from `enqueue` (which returns its kernel count).  *exec stays null when
+// the sequence cannot be captured; the caller then launches directly.
+template <typename F>
+rtg_status graph_for(rtg_ctx* c, const ShapeKey& key, const rtg::BuildArgs& a, bool timing,
+                     F&& enqueue, cudaGraphExec_t* exec, int* launches) {
+  *exec = nullptr;
+  const std::vector<unsigned char> sig = graph_signature(a, timing, c->stream);
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end() && it->second.sig == sig) {
+    *exec = it->second.exec;
+    *launches = it->second.launches;
+    return RTG_OK;
+  }
+  drop_graph(c, key);
+  if (c->graphs.size() >= kMaxGraphs) drop_graph(c, c->graphs.begin()->first);
+  cudaGetLastError();
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return RTG_OK;
+  }
+  const int l = enqueue();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return RTG_OK;
+  }
+  cudaGraphExec_t ge = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ge, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return RTG_OK;
+  }
+  GraphEntry ent;
+  ent.exec = ge;
+  ent.sig = sig;
+  ent.launches = l;
+  c->graphs[key] = ent;
+  *exec = ge;
+  *launches = l;
+  return RTG_OK;
+}
+
 rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   cudaStream_t st = c->stream;
   const bool timing = (q.flags & RTG_FLAG_TIMING) != 0;
@@ -249,6 +320,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   if ((s = ensure(c, c->pf, (size_t)n_total * dpad * 4)) != RTG_OK) return s;
   if ((s = ensure(c, c->row_cnt, (size_t)n_total * 4)) != RTG_OK) return s;
   if ((s = ensure(c, c->scan_lb, ((size_t)n_total / 4096 + 2) * 8)) != RTG_OK) return s;
+  if ((s = ensure(c, c->out_slot, sizeof(rtg::OutSlot))) != RTG_OK) return s;
+  if ((s = ensure(c, c->sort_epoch, sizeof(unsigned int), true)) != RTG_OK) return s;
   if (!q.points_on_device) {
     if ((s = ensure(c, c->pts, (size_t)n_total * maxd * esz + 16 * (size_t)B)) != RTG_OK) return s;
     size_t off = 0;
@@ -286,6 +359,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.pf = (float*)c->pf.p;
   a.row_cnt = (unsigned int*)c->row_cnt.p;
   a.scan_lookback = (unsigned long long*)c->scan_lb.p;
+  a.out = (const rtg::OutSlot*)c->out_slot.p;
+  a.sort_epoch = (unsigned int*)c->sort_epoch.p;
   a.num_sms = c->num_sms;
 
   const ShapeKey key{n_total, B, m, q.dtype, maxd, sym, q.count_only ? 1 : 0};
@@ -297,30 +372,23 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   bool tuned_now = false;
   for (int attempt = 0; attempt < 5; ++attempt) {
     int launches = 0;
-    a.key64 = g.key64;
-    a.passes = rtg::sort_passes_for(g.key_bits, g.sort.bits);
-    a.sort_bits = g.sort.bits;
-    a.sort_items = g.sort.items;
-    a.sort_mode = g.sort.mode;
-    if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[0], st));
-    RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
-    RTG_CUDA(c, cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st));
-    RTG_CUDA(c, cudaMemsetAsync(a.row_cnt, 0, (size_t)n_total * 4, st));
-    rtg::launch_prep(a, st);
-    rtg::launch_plan(a, st);
-    launches += m > 0 ? 3 : 2;
     if (m > 0 && !known && attempt == 0) {
       // first build of this shape: read the key width back once
+      RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
+      RTG_CUDA(c, cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st));
+      a.passes = rtg::sort_passes_for(64, 8);
+      a.sort_bits = 8;
+      rtg::launch_prep(a, st);
+      rtg::launch_plan(a, st);
       if ((s = read_status(c)) != RTG_OK) return s;
       if ((s = check_errors(c, rtg::kErrNonFinite | rtg::kErrKeyOverflow)) != RTG_OK) return s;
-      const int bits = (int)c->h_status->sort_bits;
-      g.key64 = bits > 32;
-      g.key_bits = bits;
-      a.key64 = g.key64;
+      g.key_bits = (int)c->h_status->sort_bits;
+      g.key64 = g.key_bits > 32;
     }
     bool tune_now = false;
     if (m > 0 && !g.sorted_cfg) {
-      // sort variant: the autotuner's table, else measure now (large sorts), else the default
+      // sort variant: forced, else the autotuner's table, else measure now (large sorts), else
+      // the default
       const auto it = c->sort_tune.find(SortKey(N, g.key_bits));
       if (c->sort_forced) {
         g.sort = c->sort_force;
@@ -335,12 +403,11 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         g.sorted_cfg = true;
       }
     }
+    a.key64 = g.key64;
     a.passes = rtg::sort_passes_for(g.key_bits, g.sort.bits);
     a.sort_bits = g.sort.bits;
     a.sort_items = g.sort.items;
     a.sort_mode = g.sort.mode;
-    if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[1], st));
-    int sorted = 0;
     if (m > 0) {
       const size_t ksz = a.key64 ? 8 : 4;
       if ((s = ensure(c, c->key_mat, (size_t)N * ksz)) != RTG_OK) return s;
@@ -369,7 +436,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       a.large_cap = large_cap;
       a.large_job_off = (unsigned long long*)c->large_job.p;
       if (tune_now) {
-        // measure every sort variant on this build's keys, then run the build from the start
+        // measure every sort variant on this build's keys (the plan of the key-width read-back
+        // above is in place), then run the build from the start
         rtg::SortConfig best;
         if ((s = tune_sort(c, a, N, g.key_bits, &best)) != RTG_OK) return s;
         g.sort = best;
@@ -377,20 +445,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         tuned_now = true;
         continue;
       }
-      a.epoch = c->epoch;
-      c->epoch += rtg::kMaxPasses;
-      if ((c->epoch & 0x3fffffffu) < rtg::kMaxPasses) c->epoch = 1;
-      rtg::launch_keys(a, st);
-      launches += 1;
-      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
-      sorted = rtg::launch_sort(a, st);
-      launches += (a.passes > 0 && N > 1)
-                      ? 1 + (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
-                      : 0;
-    } else if (timing) {
-      RTG_CUDA(c, cudaEventRecord(c->ev[2], st));
     }
-    if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[3], st));
 
     // output row pointers
     void* rp = nullptr;
@@ -399,6 +454,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     out->col = nullptr;
     out->handle = register_out(c, sizeof(int64_t) * (n_total + 1));
     a.row_ptr = (long long*)rp;
+    a.col = nullptr;
+    a.col_cap = 0;
 
     // pair buffer for EMIT; COUNT then WRITE when asked, when only counting, or when the buffer
     // would not fit the budget
@@ -415,6 +472,40 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if ((s = ensure(c, c->tc_norms, (size_t)(n_total + 128) * 4)) != RTG_OK) return s;
       if ((s = ensure(c, c->tc_plan, sizeof(rtg::TcPlan))) != RTG_OK) return s;
     }
+    int sorted = 0;
+    // phase marks: recorded as real event records even inside a captured graph
+    auto mark = [&](int i) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(st, &cs);
+      if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(c->ev[i], st, cudaEventRecordExternal);
+      else
+        cudaEventRecord(c->ev[i], st);
+    };
+    // front of every build: counters, bounding boxes, plan, keys, sort (phases 0-3)
+    auto front = [&]() -> int {
+      int l = 0;
+      if (timing) mark(0);
+      cudaMemsetAsync(a.st, 0, sizeof(Status), st);
+      cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st);
+      cudaMemsetAsync(a.row_cnt, 0, (size_t)n_total * 4, st);
+      rtg::launch_prep(a, st);
+      rtg::launch_plan(a, st);
+      l += m > 0 ? 3 : 2;
+      if (timing) mark(1);
+      if (m > 0) {
+        rtg::launch_keys(a, st);
+        l += 1;
+        if (timing) mark(2);
+        sorted = rtg::launch_sort(a, st);
+        l += (a.passes > 0 && N > 1) ? 1 + (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
+                                     : 0;
+      } else if (timing) {
+        mark(2);
+      }
+      if (timing) mark(3);
+      return l;
+    };
     auto pairs = [&](rtg::Mode mode) {
       if (m > 0) return rtg::launch_pairs(a, sorted, mode, st);
       if (tc)
@@ -423,15 +514,17 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
                                     (rtg::TcPlan*)c->tc_plan.p, st);
       return rtg::launch_brute(a, mode, st);
     };
+    // the output pointers the scan, scatter and row sort read (pinned copy -> device slot)
+    auto set_slot = [&]() {
+      c->h_slot->row_ptr = a.row_ptr;
+      c->h_slot->col = a.col;
+      c->h_slot->col_cap = a.col_cap;
+      cudaMemcpyAsync(c->out_slot.p, c->h_slot, sizeof(rtg::OutSlot), cudaMemcpyHostToDevice, st);
+    };
     if (!two_pass) {
       if ((s = ensure(c, c->pair_buf, (size_t)g.pair_cap * 8)) != RTG_OK) return s;
       a.pair_buf = (unsigned long long*)c->pair_buf.p;
       a.pair_cap = g.pair_cap;
-      launches += pairs(rtg::kEmit);
-      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
-      rtg::launch_scan(a, st);
-      launches += 1;
-      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[5], st));
       const long long ccap = a.pair_cap * (sym ? 2 : 1);
       void* cp = nullptr;
       if ((s = alloc_out(c, sizeof(int32_t) * (size_t)ccap, &cp)) != RTG_OK) {
@@ -445,16 +538,55 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       }
       a.col = (int*)cp;
       a.col_cap = ccap;
-      launches += rtg::launch_scatter(a, st);
-      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
-      launches += rtg::launch_rowsort(a, st);
-      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
+      c->h_slot->row_ptr = a.row_ptr;
+      c->h_slot->col = a.col;
+      c->h_slot->col_cap = a.col_cap;
+      // the whole build as one fixed launch sequence, ending with the status copy-back
+      auto emit_build = [&]() -> int {
+        int l = 0;
+        cudaMemcpyAsync(c->out_slot.p, c->h_slot, sizeof(rtg::OutSlot), cudaMemcpyHostToDevice,
+                        st);
+        l += front();
+        l += pairs(rtg::kEmit);
+        if (timing) mark(4);
+        rtg::launch_scan(a, st);
+        l += 1;
+        if (timing) mark(5);
+        l += rtg::launch_scatter(a, st);
+        if (timing) mark(6);
+        l += rtg::launch_rowsort(a, st);
+        if (timing) mark(7);
+        cudaMemcpyAsync(c->h_status, c->status.p, sizeof(Status), cudaMemcpyDeviceToHost, st);
+        return l;
+      };
+      bool done = false;
+      if (m > 0 && known && attempt == 0 && c->use_graphs) {
+        cudaGraphExec_t exec = nullptr;
+        int gl = 0;
+        if ((s = graph_for(c, key, a, timing, emit_build, &exec, &gl)) != RTG_OK) {
+          release_out(c, out);
+          return s;
+        }
+        if (exec && cudaGraphLaunch(exec, st) == cudaSuccess) {
+          launches += gl;
+          done = true;
+        } else {
+          cudaGetLastError();
+          drop_graph(c, key);
+        }
+      }
+      if (!done) launches += emit_build();
       RTG_CUDA(c, cudaGetLastError());
-      if ((s = read_status(c)) != RTG_OK) {
-        release_out(c, out);
-        return s;
+      {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+          release_out(c, out);
+          return fail(c, RTG_E_CUDA, std::string("build: ") + cudaGetErrorString(e));
+        }
       }
     } else {
+      set_slot();
+      launches += front();
       launches += pairs(rtg::kCount);
       if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
       rtg::launch_scan(a, st);
@@ -479,6 +611,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         }
         a.col = (int*)cp;
         a.col_cap = nnz;
+        set_slot();
         launches += pairs(rtg::kWrite);
         if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
         launches += rtg::launch_rowsort(a, st);
@@ -562,7 +695,11 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       // prep+plan, keys, sort, pairs, scan, scatter/write, rowsort, total
       const int idx[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {0, 7}};
       for (int p = 0; p < 8; ++p) {
-        cudaEventElapsedTime(&ms, c->ev[idx[p][0]], c->ev[idx[p][1]]);
+        ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[idx[p][0]], c->ev[idx[p][1]]) != cudaSuccess) {
+          cudaGetLastError();
+          ms = 0.f;
+        }
         S.phase_us[p] = 1000.0 * ms;
       }
     }
@@ -607,6 +744,11 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
     c->own_stream = true;
   }
   if ((e = cudaMallocHost(&c->h_status, sizeof(Status))) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->h_slot, sizeof(rtg::OutSlot))) != cudaSuccess) return bail(e);
+  {
+    const char* g = std::getenv("RTG_GRAPHS");
+    c->use_graphs = !(g && std::strcmp(g, "0") == 0);
+  }
   {
     // a pool of its own for the output CSRs, so that freed blocks stay cached between builds
     cudaMemPoolProps props = {};
@@ -642,6 +784,10 @@ void destroy_ctx(rtg_ctx* c) {
                     &c->hist,      &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
                     &c->large_job, &c->pair_buf,  &c->tc_tiles, &c->tc_norms, &c->tc_plan};
   for (DevBuf* b : bufs) free_buf(c, *b);
+  while (!c->graphs.empty()) drop_graph(c, c->graphs.begin()->first);
+  free_buf(c, c->out_slot);
+  free_buf(c, c->sort_epoch);
+  if (c->h_slot) cudaFreeHost(c->h_slot);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->h_status) cudaFreeHost(c->h_status);

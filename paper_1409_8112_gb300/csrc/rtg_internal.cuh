@@ -167,6 +167,15 @@ __host__ __device__ inline double dec_double(unsigned long long e) {
 
 inline int dpad_for(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : 16); }
 
+// Output CSR of the running build, read by the kernels that write it (the host fills it
+// before those kernels run, so that one captured launch sequence serves every build).
+struct OutSlot {
+  long long* row_ptr;  // n_total + 1
+  int* col;
+  long long col_cap;
+  long long reserved;
+};
+
 // ---- launch arguments ----------------------------------------------------------------------
 struct BuildArgs {
   int B;              // instances
@@ -198,15 +207,16 @@ struct BuildArgs {
   unsigned long long* large_job_off;  // large_cap + 1
   unsigned long long* pair_buf;       // EMIT: (i << 32) | j
   long long pair_cap;
-  long long* row_ptr;  // n_total + 1
+  long long* row_ptr;  // n_total + 1 (as in *out; the two-pass write takes it directly)
   int* col;
   long long col_cap;
+  const OutSlot* out;  // device copy of the output pointers
   bool key64;
   int sort_mode;       // SortMode
   int sort_bits;       // digit width
   int sort_items;      // keys per thread in a tile
   int passes;          // radix passes launched
-  unsigned int epoch;  // look-back epoch base for this build's sort passes
+  unsigned int* sort_epoch;  // device counter: look-back epoch base, advanced by every sort
   int num_sms;
 };
 

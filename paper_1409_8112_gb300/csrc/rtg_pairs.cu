@@ -708,10 +708,11 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
 constexpr int kScanItems = 16;
 constexpr int kScanTile = 256 * kScanItems;
 
-__global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, long long* row_ptr,
+__global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, const OutSlot* out,
                                               long long n, unsigned long long* lookback,
                                               unsigned int* tile_counter, Status* st,
                                               unsigned int tiles) {
+  long long* row_ptr = out->row_ptr;
   __shared__ unsigned long long sbuf[8];
   __shared__ unsigned long long s_base;
   __shared__ unsigned int s_tile;
@@ -774,10 +775,11 @@ __global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, long long* 
 // Pair buffer -> columns in their rows (row order fixed later by the row sort).
 __global__ void __launch_bounds__(256) k_scatter(const unsigned long long* __restrict__ pairs,
                                                  long long cap, const Status* st,
-                                                 unsigned int* row_cnt,
-                                                 const long long* __restrict__ row_ptr, int* col,
-                                                 long long col_cap, int symmetric,
-                                                 unsigned int* errors) {
+                                                 unsigned int* row_cnt, const OutSlot* out,
+                                                 int symmetric, unsigned int* errors) {
+  const long long* __restrict__ row_ptr = out->row_ptr;
+  int* col = out->col;
+  const long long col_cap = out->col_cap;
   const long long cnt = min((long long)st->emitted, cap);
   bool overflow = false;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
@@ -818,10 +820,12 @@ __device__ __forceinline__ void bitonic_regs(int* v) {
 // with +infinity padding); longer rows are queued for the block kernel.  Rows that reach past
 // col_cap (only when an undersized buffer overflowed and the build will be re-run) are left
 // alone.
-__global__ void __launch_bounds__(256) k_rowsort_thread(const long long* __restrict__ row_ptr,
-                                                        int* col, long long n, long long col_cap,
+__global__ void __launch_bounds__(256) k_rowsort_thread(const OutSlot* out, long long n,
                                                         unsigned int* long_rows,
                                                         unsigned int* long_count) {
+  const long long* __restrict__ row_ptr = out->row_ptr;
+  int* col = out->col;
+  const long long col_cap = out->col_cap;
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= n) return;
   const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
@@ -853,10 +857,12 @@ __global__ void __launch_bounds__(256) k_rowsort_thread(const long long* __restr
 
 constexpr int kRowSmem = 8192;
 
-__global__ void __launch_bounds__(256) k_rowsort_long(const long long* __restrict__ row_ptr,
-                                                      int* col, long long col_cap,
+__global__ void __launch_bounds__(256) k_rowsort_long(const OutSlot* out,
                                                       const unsigned int* __restrict__ long_rows,
                                                       const unsigned int* long_count) {
+  const long long* __restrict__ row_ptr = out->row_ptr;
+  int* col = out->col;
+  const long long col_cap = out->col_cap;
   __shared__ int buf[kRowSmem];
   const unsigned int cnt = *long_count;
   for (unsigned int k = blockIdx.x; k < cnt; k += gridDim.x) {
@@ -1017,24 +1023,21 @@ int launch_brute(const BuildArgs& a, Mode mode, cudaStream_t s) {
 void launch_scan(const BuildArgs& a, cudaStream_t s) {
   const unsigned tiles = (unsigned)((a.n_total + kScanTile - 1) / kScanTile);
   cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
-  k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.row_ptr, a.n_total, a.scan_lookback,
+  k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.out, a.n_total, a.scan_lookback,
                                &a.st->scan_tiles, a.st, tiles);
 }
 
 int launch_scatter(const BuildArgs& a, cudaStream_t s) {
   k_scatter<<<(unsigned)(8 * a.num_sms), 256, 0, s>>>(a.pair_buf, a.pair_cap, a.st, a.row_cnt,
-                                                      a.row_ptr, a.col, a.col_cap, a.symmetric,
-                                                      &a.st->errors);
+                                                      a.out, a.symmetric, &a.st->errors);
   return 1;
 }
 
 int launch_rowsort(const BuildArgs& a, cudaStream_t s) {
   const unsigned blocks = (unsigned)((a.n_total + 255) / 256);
   unsigned int* long_count = &a.st->long_rows;
-  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.row_ptr, a.col, a.n_total, a.col_cap, a.row_cnt,
-                                          long_count);
-  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.row_ptr, a.col, a.col_cap, a.row_cnt,
-                                                           long_count);
+  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, long_count);
+  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.out, a.row_cnt, long_count);
   return 2;
 }
 

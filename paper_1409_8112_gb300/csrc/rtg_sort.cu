@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict_
                                                             long long N, int passes,
                                                             unsigned int* hist,
                                                             unsigned int* digit_off,
-                                                            unsigned int* ticket) {
+                                                            unsigned int* ticket,
+                                                            unsigned int* epoch) {
   constexpr int D = Digits<BITS>::kCount, PT = Digits<BITS>::kPerThread;
   extern __shared__ unsigned int sh[];  // passes * D
   __shared__ unsigned int sbuf[kSortWarps];
@@ -157,7 +158,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K* __restrict_
       hist[p * D + threadIdx.x * PT + q] = 0;  // ready for the next sort
     }
   }
-  if (threadIdx.x == 0) *ticket = 0;
+  if (threadIdx.x == 0) {
+    *ticket = 0;
+    // a fresh look-back epoch for this sort's passes (never 0: zeroed words are never valid)
+    unsigned int e = *epoch + kMaxPasses;
+    if ((e & 0x3fffffffu) < (unsigned int)kMaxPasses) e = 1;
+    *epoch = e;
+  }
 }
 
 // Digit counts of every tile of this pass, stored digit-major: counts[digit * tiles + tile].
@@ -347,8 +354,8 @@ template <typename K, int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ digit_off,
-    unsigned long long* lookback, unsigned int* tile_counter, unsigned int epoch,
-    unsigned int* errors) {
+    unsigned long long* lookback, unsigned int* tile_counter, const unsigned int* epoch_base,
+    int pass, unsigned int* errors) {
   using TR = TileRank<K, BITS, ITEMS>;
   constexpr int D = TR::D, PT = TR::PT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -359,6 +366,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
   __syncthreads();
   const unsigned int tile = s_tile;
+  const unsigned int epoch = *epoch_base + (unsigned int)pass;
   const long long tile_base = (long long)tile * TR::kTile;
   unsigned int tcount[PT];
   tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf);
@@ -437,7 +445,7 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
   static bool hist_attr[64] = {};
   set_smem_once(k_sort_hist<K, BITS>, (size_t)kSortCountWords * 4, hist_attr);
   k_sort_hist<K, BITS><<<(unsigned)hb, kSortThreads, (size_t)passes * D * 4, s>>>(
-      (const K*)a.keys[0], N, passes, a.hist, a.digit_off, &a.st->hist_ticket);
+      (const K*)a.keys[0], N, passes, a.hist, a.digit_off, &a.st->hist_ticket, a.sort_epoch);
   const unsigned tiles = (unsigned)((N + SS::kTile - 1) / SS::kTile);
   int cur = 0;
   if (a.sort_mode == kSortLookback) {
@@ -446,8 +454,7 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
     for (int p = 0; p < passes; ++p) {
       k_sort_pass<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
           (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, p * BITS,
-          a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.epoch + (unsigned)p,
-          &a.st->errors);
+          a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.sort_epoch, p, &a.st->errors);
       cur = 1 - cur;
     }
     return cur;

@@ -186,9 +186,6 @@ rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
     b.sort_items = cfg.items;
     b.sort_mode = cfg.mode;
     b.passes = rtg::sort_passes_for(key_bits, cfg.bits);
-    b.epoch = c->epoch;
-    c->epoch += rtg::kMaxPasses;
-    if ((c->epoch & 0x3fffffffu) < rtg::kMaxPasses) c->epoch = 1;
     cudaMemsetAsync(&b.st->sort_tiles[0], 0, sizeof(b.st->sort_tiles), st);
     rtg::launch_keys(b, st);  // the sort consumes its input buffers
     cudaEventRecord(ev[2 * (size_t)t], st);

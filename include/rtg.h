@@ -145,6 +145,12 @@ void rtg_destroy(rtg_ctx* ctx);
  * the next call on that context. */
 const char* rtg_last_error(const rtg_ctx* ctx);
 
+/* The CUDA stream (cudaStream_t) every device operation of ctx is ordered on: the one given
+ * in rtg_config, or the context's own.  Callers whose device inputs are produced on another
+ * stream make this stream wait for it (an event) instead of synchronising the host.  NULL for
+ * a NULL ctx. */
+void* rtg_get_stream(const rtg_ctx* ctx);
+
 /* Name of a status code. */
 const char* rtg_status_string(rtg_status s);
 

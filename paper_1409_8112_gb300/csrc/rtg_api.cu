@@ -79,6 +79,7 @@ rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
   }
   RTG_CUDA(c, cudaMalloc(&b.p, bytes));
   b.cap = bytes;
+  b.gen = ++c->alloc_gen;
   c->ws_bytes += bytes;
   if (zero) RTG_CUDA(c, cudaMemsetAsync(b.p, 0, bytes, c->stream));
   return RTG_OK;
@@ -334,11 +335,32 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       off += (bytes + 15) & ~size_t(15);
     }
   }
-  RTG_CUDA(c, cudaMemcpyAsync(c->inst.p, c->h_inst.data(), sizeof(Inst) * B,
-                              cudaMemcpyHostToDevice, st));
-  if (m > 0)
-    RTG_CUDA(c, cudaMemcpyAsync(c->T64.p, c->h_T.data(), sizeof(double) * (size_t)T0,
-                                cudaMemcpyHostToDevice, st));
+  {
+    // instance table and transforms: through pinned staging, and only when they changed
+    const size_t ib = sizeof(Inst) * B, tb = m > 0 ? sizeof(double) * (size_t)T0 : 0;
+    const size_t ib_al = (ib + 255) & ~size_t(255);
+    if (c->h_stage_cap < ib_al + tb) {
+      if (c->h_stage) cudaFreeHost(c->h_stage);
+      c->h_stage = nullptr;
+      c->h_stage_cap = 0;
+      RTG_CUDA(c, cudaMallocHost(&c->h_stage, ib_al + tb));
+      c->h_stage_cap = ib_al + tb;
+    }
+    auto upload = [&](DevBuf& dst, const void* src, size_t bytes, size_t off,
+                      Upload& last) -> rtg_status {
+      if (last.gen == dst.gen && last.bytes.size() == bytes &&
+          std::memcmp(last.bytes.data(), src, bytes) == 0)
+        return RTG_OK;
+      std::memcpy((char*)c->h_stage + off, src, bytes);
+      RTG_CUDA(c, cudaMemcpyAsync(dst.p, (char*)c->h_stage + off, bytes, cudaMemcpyHostToDevice,
+                                  st));
+      last.bytes.assign((const unsigned char*)src, (const unsigned char*)src + bytes);
+      last.gen = dst.gen;
+      return RTG_OK;
+    };
+    if ((s = upload(c->inst, c->h_inst.data(), ib, 0, c->up_inst)) != RTG_OK) return s;
+    if (m > 0 && (s = upload(c->T64, c->h_T.data(), tb, ib_al, c->up_T)) != RTG_OK) return s;
+  }
 
   BuildArgs a{};
   a.B = B;
@@ -791,6 +813,7 @@ void destroy_ctx(rtg_ctx* c) {
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->pool) cudaMemPoolDestroy(c->pool);  // outstanding CSRs go with the pool
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -819,6 +842,8 @@ const char* rtg_status_string(rtg_status s) {
 }
 
 const char* rtg_last_error(const rtg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+void* rtg_get_stream(const rtg_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 rtg_status rtg_transforms_generate(uint64_t seed, int d, int m, double cell_side, uint32_t flags,
                                    double* out) {

@@ -92,6 +92,7 @@ _SIGNATURES = {
     "rtg_create": (ctypes.c_int, [ctypes.POINTER(rtg_config), ctypes.POINTER(ctypes.c_void_p)]),
     "rtg_destroy": (None, [ctypes.c_void_p]),
     "rtg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "rtg_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
     "rtg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rtg_transforms_generate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_uint32,
@@ -290,7 +291,6 @@ def _points_arg(points):
         if not p.is_cuda:
             p = p.numpy()
             return p.ctypes.data, code, False, p.shape[0], p.shape[1], p
-        torch.cuda.current_stream(p.device).synchronize()
         return p.data_ptr(), code, True, p.shape[0], p.shape[1], p
     p = np.ascontiguousarray(points)
     if p.ndim != 2:
@@ -342,6 +342,16 @@ class Result:
 class Context:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: int | None = None):
         self.handle = rtg_create(device, mem_budget_bytes, stream)
+        self.stream = lib().rtg_get_stream(self.handle) or 0
+
+    def _after_producer(self, points):
+        """Orders the library's stream after torch's current stream when the points are a
+        CUDA tensor produced there (a device-side wait; the host does not block)."""
+        if hasattr(points, "is_cuda") and points.is_cuda:
+            import torch
+            cur = torch.cuda.current_stream(points.device)
+            if cur.cuda_stream != self.stream:
+                torch.cuda.ExternalStream(self.stream, device=points.device).wait_stream(cur)
 
     def close(self):
         if self.handle is not None:
@@ -363,6 +373,7 @@ class Context:
     def all_pairs(self, points, r: float, transforms: np.ndarray, cell_side: float,
                   symmetric: bool = False, timing: bool = False, two_pass: bool = False) -> Result:
         ptr, code, on_dev, n, d, keep = _points_arg(points)
+        self._after_producer(keep)
         T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
         if T.size % (d * d + d) != 0:
             raise ValueError("transforms must hold m * (d*d + d) values")
@@ -381,6 +392,7 @@ class Context:
         items, keep, codes, devs = [], [], set(), set()
         for pts, r, T, c in instances:
             ptr, code, on_dev, n, d, kp = _points_arg(pts)
+            self._after_producer(kp)
             Tc = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
             if Tc.size != m * (d * d + d):
                 raise ValueError("each instance needs m * (d*d + d) transform values")
@@ -414,6 +426,7 @@ class Context:
         """Exact set of Sec. I on the device (all pairs checked); tensor = "fp16" or "bf16"
         takes the distances from tensor-core tiles with an FP64 band check."""
         ptr, code, on_dev, n, d, keep = _points_arg(points)
+        self._after_producer(keep)
         flags = (RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0)
         if tensor == "fp16":
             flags |= RTG_FLAG_TC_FP16

@@ -72,6 +72,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(total_ms: float, ws: int, device="cuda") -> float:
+    """Duration of the timed region for the whole job: the slowest replica decides (an
+    all-reduce MAX over the ranks' own timings; the identity on one rank)."""
+    if ws == 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pairs_per_build: int, steps: int, ws: int, total_ms: float) -> float:
+    """Whole-job pairs/s: every rank builds `steps` roadmaps (replicas, weak scaling)."""
+    return pairs_per_build * steps * ws / (total_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
 
@@ -200,13 +217,9 @@ def run_ours(args):
         dist.barrier()
     wall_s = time.perf_counter() - t_wall
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), ws)
     ms_per_step = total_ms / args.steps
-    value = pairs * args.steps * ws / (total_ms / 1e3)
+    value = job_throughput(pairs, args.steps, ws, total_ms)
 
     # end to end through the C ABI with host buffers (pinned) and the CSR copied back
     import torch as _t

@@ -56,11 +56,21 @@ WORKLOAD = {"workload": "rtg_all_pairs n=100000 d=6 fp64 uniform[0,1]^6 r=2lnn-d
 
 
 
+def set_workload(n: int, dtype: str):
+    """The single-roadmap workload: n uniform points in [0,1]^6, m = 8, c = r for degree
+    2 ln n, seed 0; FP64 (the headline, n = 100,000) or FP32 (the 1,000,000-point case)."""
+    WORKLOAD["n"] = n
+    WORKLOAD["points"] = f"uniform [0,1]^6, {dtype}"
+    WORKLOAD["workload"] = (f"rtg_all_pairs n={n} d=6 {dtype} uniform[0,1]^6 r=2lnn-degree m=8 "
+                            "c=r seed0")
+    WORKLOAD["dtype"] = dtype
+
+
 def workload():
     from paper_1409_8112_gb300 import gen
     n, d, m = WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["m"]
     r = gen.radius_for_degree(n, d)
-    pts = gen.points_uniform(0, n, d)
+    pts = gen.points_uniform(0, n, d, np.float32 if WORKLOAD.get("dtype") == "fp32" else np.float64)
     T = gen.transforms(0, d, m, r)
     return pts, T, r
 
@@ -156,6 +166,18 @@ def measured_peaks():
 #   sort  : upfront histogram reads the N keys once; each pass reads and writes N (key, index)
 #   pairs : reads the N sorted (key, index) pairs, gathers each point's padded FP32 row and
 #           writes 8 bytes per reported pair
+# DRAM bytes (read + write) of each phase's kernels per build, from ncu
+# (profiles/dram_rtg_all_pairs_n100k_and_n1m.md; cold replays, one build).  Only for the two
+# profiled workloads; to be refreshed whenever those kernels change.
+NCU_TRAFFIC = {
+    (100000, "fp64"): {"prep": 4890880, "keys": 3645696, "sort": 30044416, "pairs": 13268224,
+                       "scan": 412160, "scatter": 4858112, "rowsort": 2653184},
+    (1000000, "fp32"): {"prep": 24097280, "keys": 65918976, "sort": 361427200,
+                        "pairs": 311729920, "scan": 4013568, "scatter": 90754560,
+                        "rowsort": 32083712},
+}
+
+
 def phase_bytes(n, d, m, key_bytes, passes, dpad, pairs):
     N = n * m
     return {
@@ -245,9 +267,12 @@ def run_ours(args):
     dom = max(pb, key=lambda p: mean_phase[p])
     peak, peak_kind = measured_peaks()
     achieved = pb[dom] / (mean_phase[dom] * 1e-6) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+    traffic = NCU_TRAFFIC.get((n, WORKLOAD.get("dtype", "fp64")), {}).get(dom)
+    kernels = {"sort": "k_sort_hist + one k_sort_pass per radix pass (autotuned variant)",
+               "pairs": "k_pairs_warp + k_large_setup + k_pairs_large"}[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "kernels": kernels, "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes": pb[dom], "launch_us": round(mean_phase[dom], 2)}
 
     line = {
@@ -550,9 +575,14 @@ def main():
     ap.add_argument("--requests", type=int, default=400)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--nmax", type=int, default=500000)
+    ap.add_argument("--n", type=int, default=100000,
+                    help="points of the single-roadmap workload (headline: 100000)")
+    ap.add_argument("--dtype", default="fp64", choices=["fp64", "fp32"],
+                    help="coordinate type of the single-roadmap workload (headline: fp64)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    set_workload(args.n, args.dtype)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

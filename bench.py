@@ -498,6 +498,69 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_table2(args):
+    """Shift-only RTG with the paper's Table II parameters (Sec. IV-A): d = 6, m = 20 grids,
+    c = 1.35 r, r from Eq. 2, n uniform points in [0,1]^6 (FP64, seed 0).  Reported pairs/s
+    at the recall Table II guarantees (>= 98%), beside the exact set on the same device
+    (brute force, CUDA cores and FP16 tensor-core tiles, recall 1) and the rotated
+    m = 8, c = r build of the headline workload (same points, its own radius)."""
+    import torch
+    from paper_1409_8112_gb300 import gen, rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = L2Flush()
+    n, d, m, ct = args.n, 6, 20, 1.35
+    r = gen.radius_fmt(n, d)
+    pts = torch.from_numpy(gen.points_uniform(0, n, d)).cuda()
+    T = gen.transforms(0, d, m, ct * r, flags=gen.SHIFT_ONLY)
+
+    def timed(fn, reps, warm):
+        for _ in range(warm):
+            fn().release()
+        ms, res = [], None
+        for k in range(reps):
+            flush(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if k + 1 < reps:
+                res.release()
+        return float(np.mean(ms)), res
+
+    ms, res = timed(lambda: ctx.all_pairs(pts, r, T, ct * r, timing=True), args.steps, args.warmup)
+    pairs, st = res.nnz, res.stats
+    res.release()
+    ex_ms, ex = timed(lambda: ctx.brute_force(pts, r, count_only=True), 3, 1)
+    exact = ex.nnz
+    ex.release()
+    tc_ms, tc = timed(lambda: ctx.brute_force(pts, r, count_only=True, tensor="fp16"), 3, 1)
+    assert tc.nnz == exact
+    tc.release()
+    line = {
+        "metric": METRIC, "value": round(pairs / (ms / 1e3), 1), "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"Table II shift-only RTG: n={n} uniform [0,1]^6 fp64, r from "
+                               f"Eq. 2 ({r:.6f}), m={m}, c={ct} r, seed 0", "l2": L2_NOTE},
+        "recall": round(pairs / exact, 5), "pairs_per_build": pairs, "exact_pairs": exact,
+        "phase_us": {k: round(v, 1) for k, v in st["phase_us"].items()},
+        "sort": dict(st["sort"], key_bits=st["key_bits"], passes=st["sort_passes"]),
+        "exact_set_same_device": {
+            "brute_force_cuda_cores_ms": round(ex_ms, 3),
+            "brute_force_tensor_fp16_ms": round(tc_ms, 3),
+            "pairs_per_s_cuda_cores": round(exact / (ex_ms / 1e3), 1),
+            "pairs_per_s_tensor_fp16": round(exact / (tc_ms / 1e3), 1)},
+        "speedup_vs_exact_tensor": round(tc_ms / ms, 2),
+        "gpu_launches": st["launches"] * args.steps,
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Precision workload: n = 1e6 points of U[0,1]^6 stored FP32, r for degree 2 ln n, m = 8
     (RTG build), and the exact all-pairs set of a 200,000-point sample (first 200k points of a
@@ -569,7 +632,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="build",
-                    choices=["build", "batch", "serve", "precision"],
+                    choices=["build", "batch", "serve", "precision", "table2"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -591,6 +654,8 @@ def main():
         run_serve(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "table2":
+        run_table2(args)
     else:
         run_ours(args)
 

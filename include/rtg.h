@@ -79,7 +79,8 @@ typedef struct {
 typedef struct {
   int64_t candidates[RTG_MAX_GRIDS]; /* grid t: sum over non-empty cells of C(size, 2) */
   int64_t total_candidates;          /* sum of the above */
-  int64_t owned_candidates;          /* candidates whose pair first shares a cell in grid t */
+  int64_t owned_candidates;          /* candidates not beyond r by the FP32 test whose pair
+                                        first shares a cell in their grid t */
   int64_t near_wall;     /* (point, grid) pairs with a coordinate within 1e-12 of a wall */
   int64_t near_r;        /* distinct co-located pairs with |dist - r| <= 1e-12 r */
   int64_t key_rechecks;  /* coordinates whose cell index was recomputed in FP64 */

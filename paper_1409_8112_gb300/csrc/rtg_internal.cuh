@@ -89,6 +89,7 @@ struct Status {
   unsigned long long max_cell;
   unsigned int sort_tiles[kMaxPasses];
   unsigned int long_rows;  // rows queued for the block row sort
+  unsigned int mid_rows;   // rows queued for the warp row sort
   unsigned int tc_max_err_bits;  // tensor-core path: max |FP32 d^2 - FP64 d^2| (float bits)
   double tc_band;                // tensor-core path: band used around r^2
 };

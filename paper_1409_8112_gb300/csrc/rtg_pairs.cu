@@ -10,8 +10,9 @@
 // Dedupe without an auxiliary set: the distance test does not depend on the grid, so pair
 // {i, j} is reported by grid t iff it is within r and shares a cell in t.  The pair is
 // therefore emitted only by the first grid that puts i and j in one cell; a candidate in
-// grid t is dropped when key_mat[i][t'] == key_mat[j][t'] for some t' < t.  The check runs
-// before the distance (the filtering use of the auxiliary structure in Sec. III-B).
+// grid t is dropped when key_mat[i][t'] == key_mat[j][t'] for some t' < t (the filtering use
+// of the auxiliary structure in Sec. III-B).  It runs after the FP32 distance has ruled out
+// the pairs that are certainly beyond r, so far pairs cost no key-row loads.
 //
 // Distance: FP32 on the staged rows; a pair is decided in FP32 only when the FP32 squared
 // distance is outside [s_lo, s_hi], the proven error band around fl(r*r) (see the plan
@@ -37,6 +38,9 @@ static_assert(kRing >= kSmallCell - 1 + 32 && (kRing & (kRing - 1)) == 0, "ring 
 constexpr int kWarpEmit = 128;             // EMIT: reported pairs buffered per warp
 constexpr int kWarpFlush = kWarpEmit - 32;  // written out once more than this many are held
 constexpr int kTL = 128;                   // large-cell tile
+constexpr int kMediumMax = 256;            // large cells up to this size: one warp per cell
+constexpr int kMediumWarps = 4;            // warps per block of the medium-cell kernel
+constexpr int kMediumKeyBytes = 8192;      // per warp: staged key rows of a medium cell
 constexpr unsigned int kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ double load_coord(const void* pts, int dtype, long long i, int d,
@@ -133,11 +137,6 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
                                             const Inst* __restrict__ Ip,
                                             const InstPlan* __restrict__ IPp, float2 band,
                                             int dtype, Tally& tl, unsigned long long* near_r) {
-  bool earlier = false;  // all loads issued before any test
-#pragma unroll 8
-  for (int u = 0; u < t; ++u) earlier |= ki[u] == kj[u];
-  if (earlier) return false;  // an earlier grid owns this pair
-  if (MODE != kWrite) ++tl.owned;
   float sf = 0.0f;
 #pragma unroll
   for (int v = 0; v < DPAD / 4; ++v) {
@@ -152,11 +151,21 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
     e = x.w - y.w;
     sf = fmaf(e, e, sf);
   }
+  if (sf > band.y) return false;  // beyond r for certain: no ownership test needed
+  // an earlier grid owns the pair if it co-locates it; grids in batches of four (the loads of
+  // a batch issued together), stopping at the first batch with a match: a close pair usually
+  // shares a cell in one of the first grids
+  for (int u0 = 0; u0 < t; u0 += 4) {
+    bool earlier = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (u0 + q < t) earlier |= ki[u0 + q] == kj[u0 + q];
+    if (earlier) return false;
+  }
+  if (MODE != kWrite) ++tl.owned;
   bool keep;
   if (sf < band.x) {
     keep = true;
-  } else if (sf > band.y) {
-    keep = false;
   } else {
     const Inst& I = *Ip;
     const double s = exact_dist2(I.pts, dtype, (long long)i - I.p0, (long long)j - I.p0, I.d);
@@ -205,6 +214,40 @@ __device__ __forceinline__ void deliver(bool keep, unsigned int i, unsigned int 
   }
 }
 
+// EMIT through a per-warp shared-memory buffer of kWarpEmit pairs: one reservation in the
+// pair buffer per flush instead of one per warp step.  Called by all 32 lanes together;
+// `ecnt` (the pairs held) is the same in every lane.
+__device__ __forceinline__ void warp_flush(unsigned long long* wbuf, unsigned int ecnt,
+                                           const Sink& sk) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  unsigned long long b0 = 0;
+  if (lane == 0) b0 = atomicAdd(sk.emitted, (unsigned long long)ecnt);
+  b0 = __shfl_sync(0xffffffffu, b0, 0);
+  for (unsigned int x = lane; x < ecnt; x += 32) {
+    if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = wbuf[x];
+    else atomicOr(sk.errors, kErrPairOverflow);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void warp_emit(bool keep, unsigned int i, unsigned int j,
+                                          unsigned long long* wbuf, unsigned int& ecnt,
+                                          const Sink& sk) {
+  const unsigned int mask = __ballot_sync(0xffffffffu, keep);
+  const int lane = threadIdx.x & 31;
+  if (keep) {
+    wbuf[ecnt + __popc(mask & ((1u << lane) - 1))] = ((unsigned long long)i << 32) | j;
+    atomicAdd(&sk.row_cnt[i], 1u);
+    if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
+  }
+  ecnt += (unsigned int)__popc(mask);
+  if (ecnt > (unsigned int)kWarpFlush) {
+    warp_flush(wbuf, ecnt, sk);
+    ecnt = 0;
+  }
+}
+
 template <int MODE>
 __device__ __forceinline__ void flush_tally(const Tally& tl, Status* st, unsigned int* sbuf) {
   // sbuf: 3 block-wide counters, zeroed by the caller before its last barrier
@@ -237,7 +280,7 @@ __device__ __forceinline__ int find_bt(unsigned long long key,
 
 // Key rows are staged in shared memory when a row (m keys) is at most this many bytes.
 // Staged rows are m + 1 keys apart so that neighbouring rows fall in different banks.
-constexpr int kMaxStagedRow = 64;
+constexpr int kMaxStagedRow = 128;
 
 // Bytes of one warp's shared-memory region in k_pairs_warp.
 template <typename K, int DPAD>
@@ -471,25 +514,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
                                               inst + ib_, iplan + ib_, band, dtype, tl, sk.near_r);
           }
           if (MODE == kEmit) {
-            const unsigned int mask = __ballot_sync(full, keep);
-            if (keep) {
-              w_emit[ecnt + __popc(mask & lt)] = ((unsigned long long)i << 32) | j;
-              atomicAdd(&sk.row_cnt[i], 1u);
-              if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
-            }
-            ecnt += (unsigned int)__popc(mask);
-            if (ecnt > (unsigned int)kWarpFlush) {
-              __syncwarp();
-              unsigned long long b0 = 0;
-              if (lane == 0) b0 = atomicAdd(sk.emitted, (unsigned long long)ecnt);
-              b0 = __shfl_sync(full, b0, 0);
-              for (unsigned int x = lane; x < ecnt; x += 32) {
-                if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = w_emit[x];
-                else atomicOr(sk.errors, kErrPairOverflow);
-              }
-              ecnt = 0;
-              __syncwarp();
-            }
+            warp_emit(keep, i, j, w_emit, ecnt, sk);
           } else {
             deliver<MODE>(keep, i, j, sk, tl);
           }
@@ -527,16 +552,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
       vc = vn;
     }
   }
-  if (MODE == kEmit && ecnt) {
-    __syncwarp();
-    unsigned long long b0 = 0;
-    if (lane == 0) b0 = atomicAdd(sk.emitted, (unsigned long long)ecnt);
-    b0 = __shfl_sync(full, b0, 0);
-    for (unsigned int x = lane; x < ecnt; x += 32) {
-      if ((long long)(b0 + x) < sk.pair_cap) sk.pair_buf[b0 + x] = w_emit[x];
-      else atomicOr(sk.errors, kErrPairOverflow);
-    }
-  }
+  if (MODE == kEmit && ecnt) warp_flush(w_emit, ecnt, sk);
   if (MODE != kWrite) {
     if (cand_acc) atomicAdd(&s_gcand[cand_g], (unsigned long long)cand_acc);
     for (int o = 16; o > 0; o >>= 1) maxcell = max(maxcell, __shfl_xor_sync(full, maxcell, o));
@@ -551,7 +567,9 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   flush_tally<MODE>(tl, st, s_tally);
 }
 
-// Job offsets for the large cells: cell e has ceil(size / kTL) row tiles.
+// Job offsets for the tiled kernel: a cell of more than kMediumMax points and T =
+// ceil(size / kTL) tiles has T (T + 1) / 2 tile pairs; smaller cells have none (the
+// medium-cell kernel takes them).
 __global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restrict__ large,
                                                       unsigned int cap, Status* st,
                                                       unsigned long long* job_off) {
@@ -562,7 +580,9 @@ __global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restric
   __syncthreads();
   for (unsigned long long base = 0; base < L; base += blockDim.x) {
     const unsigned long long e = base + threadIdx.x;
-    const unsigned long long v = e < L ? (large[e].size + kTL - 1) / kTL : 0;
+    const unsigned long long T =
+        e < L && large[e].size > (unsigned int)kMediumMax ? (large[e].size + kTL - 1) / kTL : 0;
+    const unsigned long long v = T * (T + 1) / 2;
     unsigned long long tot;
     const unsigned long long ex = block_excl_scan64(v, &tot, sbuf);
     if (e < L) job_off[e] = carry + ex;
@@ -576,6 +596,91 @@ __global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restric
   }
 }
 
+// Cells of kSmallCell + 1 .. kMediumMax points, one warp per cell: the warp stages the members
+// (FP32 rows, indices) in shared memory and walks the cell's s (s - 1) / 2 pairs 32 at a time,
+// pair k = b (b - 1) / 2 + a (a < b) advanced incrementally, so that every lane is busy
+// whatever the cell size.
+template <typename K, int DPAD, int MODE>
+__global__ void __launch_bounds__(kMediumWarps * 32) k_pairs_medium(
+    const uint32_t* __restrict__ svals, const float* __restrict__ pf, int dtype,
+    const K* __restrict__ key_mat, int m, const Inst* __restrict__ inst,
+    const InstPlan* __restrict__ iplan, Status* st, const LargeCell* __restrict__ large,
+    unsigned int cap, Sink sk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_emit[kMediumWarps][kWarpEmit];
+  __shared__ unsigned int s_tally[4];
+  if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* w_pt = reinterpret_cast<float*>(smem) + (size_t)wib * kMediumMax * DPAD;
+  uint32_t* w_idx = reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(smem) +
+                                                (size_t)kMediumWarps * kMediumMax * DPAD) +
+                    wib * kMediumMax;
+  K* w_keys = reinterpret_cast<K*>(reinterpret_cast<unsigned char*>(smem) +
+                                   (size_t)kMediumWarps * kMediumMax * (DPAD * 4 + 4) +
+                                   (size_t)wib * kMediumKeyBytes);
+  unsigned long long* w_emit = s_emit[wib];
+  unsigned int ecnt = 0;
+  Tally tl;
+  const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
+  const unsigned long long W = (unsigned long long)gridDim.x * kMediumWarps;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * kMediumWarps + wib; e < L; e += W) {
+    const LargeCell cell = large[e];
+    const unsigned int s = cell.size;
+    if (s > (unsigned int)kMediumMax) continue;  // warp-uniform
+    const int t = (int)cell.grid, kst = t + 1;  // staged keys per member (odd stride)
+    const bool kstage = (size_t)s * kst * sizeof(K) <= (size_t)kMediumKeyBytes;
+    for (unsigned int x = lane; x < s; x += 32) {
+      const uint32_t idx = svals[cell.start + x];
+      w_idx[x] = idx;
+      const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
+      float4* dst = reinterpret_cast<float4*>(w_pt + x * DPAD);
+#pragma unroll
+      for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+      if (kstage) {
+        const K* kr = key_mat + (size_t)idx * m;
+        for (int u = 0; u < t; ++u) w_keys[x * kst + u] = __ldg(kr + u);
+      }
+    }
+    __syncwarp();
+    const float2 band = band_of(iplan[cell.inst]);
+    const unsigned int P = s * (s - 1) / 2;
+    // pair `lane`: b from the triangular root, then a
+    unsigned int b = (unsigned int)((1.0f + sqrtf(8.0f * (float)lane + 1.0f)) * 0.5f);
+    while (b * (b - 1) / 2 > (unsigned int)lane) --b;
+    while ((b + 1) * b / 2 <= (unsigned int)lane) ++b;
+    unsigned int a = (unsigned int)lane - b * (b - 1) / 2;
+    for (unsigned int base = 0; base < P; base += 32) {
+      bool keep = false;
+      unsigned int i = 0, j = 0;
+      if (base + lane < P) {
+        const uint32_t ia = w_idx[a], ib = w_idx[b];
+        i = min(ia, ib);
+        j = max(ia, ib);
+        const K* ka = kstage ? w_keys + a * kst : key_mat + (size_t)ia * m;
+        const K* kb = kstage ? w_keys + b * kst : key_mat + (size_t)ib * m;
+        keep = decide_pair<K, DPAD, MODE>(i, j, t, w_pt + a * DPAD, w_pt + b * DPAD, ka, kb,
+                                          inst + cell.inst, iplan + cell.inst, band, dtype, tl,
+                                          sk.near_r);
+      }
+      if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
+      else deliver<MODE>(keep, i, j, sk, tl);
+      a += 32;  // next pair of this lane: 32 on
+      while (a >= b) {
+        a -= b;
+        ++b;
+      }
+    }
+    __syncwarp();
+  }
+  if (MODE == kEmit && ecnt) warp_flush(w_emit, ecnt, sk);
+  __syncthreads();
+  flush_tally<MODE>(tl, st, s_tally);
+}
+
+// Cells of more than kSmallCell points, as 128 x 128 tiles of member pairs: job = (cell, row
+// tile a, column tile b >= a), so every job is one tile pair however large the cell.  Each
+// thread keeps one column member (y) and walks the row members (x), which all lanes of a warp
+// read at the same address.
 template <typename K, int DPAD, int MODE>
 __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
     const uint32_t* __restrict__ svals, const float* __restrict__ pf, int dtype,
@@ -585,11 +690,13 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
   __shared__ __align__(16) float sa[kTL * DPAD];
   __shared__ __align__(16) float sb[kTL * DPAD];
   __shared__ uint32_t ia[kTL], ib[kTL];
+  __shared__ unsigned long long s_emit[kPairThreads / 32][kWarpEmit];
   __shared__ unsigned int s_tally[4];
   if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
   const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
   const unsigned long long J = L ? job_off[L] : 0;
-  const int lane = threadIdx.x & 31;
+  unsigned long long* w_emit = s_emit[threadIdx.x >> 5];
+  unsigned int ecnt = 0;
   Tally tl;
   for (unsigned long long job = blockIdx.x; job < J; job += gridDim.x) {
     long long el = 0, eh = (long long)L - 1;
@@ -600,49 +707,47 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
     const LargeCell cell = large[el];
     const float2 band = band_of(iplan[cell.inst]);
     const unsigned int s = cell.size;
-    const unsigned int a0 = (unsigned int)(job - job_off[el]) * kTL;
-    const unsigned int na = min((unsigned int)kTL, s - a0);
+    // tile pair (bi <= bj) of this cell
+    const long long k = (long long)(job - job_off[el]);
+    long long bj = (long long)((sqrt(8.0 * (double)k + 1.0) - 1.0) * 0.5);
+    while (bj * (bj + 1) / 2 > k) --bj;
+    while ((bj + 1) * (bj + 2) / 2 <= k) ++bj;
+    const long long bi = k - bj * (bj + 1) / 2;
+    const unsigned int a0 = (unsigned int)bi * kTL, b0 = (unsigned int)bj * kTL;
+    const unsigned int na = min((unsigned int)kTL, s - a0), nb = min((unsigned int)kTL, s - b0);
     __syncthreads();
-    for (unsigned int x = threadIdx.x; x < na; x += blockDim.x) {
-      const uint32_t idx = svals[cell.start + a0 + x];
-      ia[x] = idx;
-      const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
-      float4* dst = reinterpret_cast<float4*>(sa + x * DPAD);
-#pragma unroll
-      for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
-    }
-    for (unsigned int b0 = a0; b0 < s; b0 += kTL) {
-      const unsigned int nb = min((unsigned int)kTL, s - b0);
-      __syncthreads();
-      for (unsigned int x = threadIdx.x; x < nb; x += blockDim.x) {
-        const uint32_t idx = svals[cell.start + b0 + x];
-        ib[x] = idx;
+    for (unsigned int x = threadIdx.x; x < 2 * kTL; x += blockDim.x) {
+      const bool first = x < kTL;
+      const unsigned int xx = first ? x : x - kTL;
+      if (xx < (first ? na : nb)) {
+        const uint32_t idx = svals[cell.start + (first ? a0 : b0) + xx];
+        (first ? ia : ib)[xx] = idx;
         const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
-        float4* dst = reinterpret_cast<float4*>(sb + x * DPAD);
+        float4* dst = reinterpret_cast<float4*>((first ? sa : sb) + xx * DPAD);
 #pragma unroll
         for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
       }
-      __syncthreads();
-      const unsigned int total = na * nb;
-      for (unsigned int qb = threadIdx.x & ~31u; qb < total; qb += blockDim.x) {
-        const unsigned int q = qb + lane;
-        bool keep = false;
-        unsigned int i = 0, j = 0;
-        if (q < total) {
-          const unsigned int x = q / nb, y = q % nb;
-          if (a0 + x < b0 + y) {
-            i = min(ia[x], ib[y]);
-            j = max(ia[x], ib[y]);
-            keep = decide_pair<K, DPAD, MODE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD,
-                                              key_mat + (size_t)ia[x] * m,
-                                              key_mat + (size_t)ib[y] * m, inst + cell.inst,
-                                              iplan + cell.inst, band, dtype, tl, sk.near_r);
-          }
-        }
-        deliver<MODE>(keep, i, j, sk, tl);
+    }
+    __syncthreads();
+    const unsigned int y = threadIdx.x % kTL;
+    const uint32_t iy = y < nb ? ib[y] : 0u;
+    for (unsigned int x = threadIdx.x / kTL; x < na; x += kPairThreads / kTL) {
+      bool keep = false;
+      unsigned int i = 0, j = 0;
+      if (y < nb && a0 + x < b0 + y) {
+        const uint32_t ix = ia[x];
+        i = min(ix, iy);
+        j = max(ix, iy);
+        keep = decide_pair<K, DPAD, MODE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD,
+                                          key_mat + (size_t)ix * m, key_mat + (size_t)iy * m,
+                                          inst + cell.inst, iplan + cell.inst, band, dtype, tl,
+                                          sk.near_r);
       }
+      if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
+      else deliver<MODE>(keep, i, j, sk, tl);
     }
   }
+  if (MODE == kEmit && ecnt) warp_flush(w_emit, ecnt, sk);
   __syncthreads();
   flush_tally<MODE>(tl, st, s_tally);
 }
@@ -816,12 +921,16 @@ __device__ __forceinline__ void bitonic_regs(int* v) {
       }
 }
 
+constexpr int kWarpRowMax = 256;  // rows up to this length are sorted by one warp
+
 // One thread per row: rows of at most 32 entries are sorted in registers (bitonic network
-// with +infinity padding); longer rows are queued for the block kernel.  Rows that reach past
-// col_cap (only when an undersized buffer overflowed and the build will be re-run) are left
-// alone.
+// with +infinity padding).  Longer rows are queued in row_queue (n entries): rows of up to
+// kWarpRowMax entries from the front for the warp kernel, longer ones from the back for the
+// block kernel.  Rows that reach past col_cap (only when an undersized buffer overflowed and
+// the build will be re-run) are left alone.
 __global__ void __launch_bounds__(256) k_rowsort_thread(const OutSlot* out, long long n,
-                                                        unsigned int* long_rows,
+                                                        unsigned int* row_queue,
+                                                        unsigned int* mid_count,
                                                         unsigned int* long_count) {
   const long long* __restrict__ row_ptr = out->row_ptr;
   int* col = out->col;
@@ -830,8 +939,12 @@ __global__ void __launch_bounds__(256) k_rowsort_thread(const OutSlot* out, long
   if (row >= n) return;
   const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
   if (len <= 1 || b + len > col_cap) return;
+  if (len > kWarpRowMax) {
+    row_queue[n - 1 - atomicAdd(long_count, 1u)] = (unsigned int)row;
+    return;
+  }
   if (len > 32) {
-    long_rows[atomicAdd(long_count, 1u)] = (unsigned int)row;
+    row_queue[atomicAdd(mid_count, 1u)] = (unsigned int)row;
     return;
   }
   if (len <= 16) {
@@ -855,10 +968,77 @@ __global__ void __launch_bounds__(256) k_rowsort_thread(const OutSlot* out, long
   }
 }
 
+// One row of at most 32 V entries sorted by one warp: lane l holds entries l V .. l V + V - 1
+// in registers (+infinity padding); bitonic network, exchanges across lanes by shuffles.
+template <int V>
+__device__ __forceinline__ void warp_sort_row(int* a, int len) {
+  constexpr int L = 32 * V;
+  const int lane = threadIdx.x & 31;
+  int v[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    const int e = lane * V + q;
+    v[q] = e < len ? a[e] : INT_MAX;
+  }
+#pragma unroll
+  for (int k = 2; k <= L; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= V) {
+        const int lj = j / V;  // partner lane distance
+        const bool low = (lane & lj) == 0;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const int other = __shfl_xor_sync(0xffffffffu, v[q], lj);
+          const bool up = ((lane * V + q) & k) == 0;
+          v[q] = (up == low) ? min(v[q], other) : max(v[q], other);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const int p = q ^ j;
+          if (p > q) {
+            const bool up = ((lane * V + q) & k) == 0;
+            if (up ? v[q] > v[p] : v[q] < v[p]) {
+              const int t = v[q];
+              v[q] = v[p];
+              v[p] = t;
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    const int e = lane * V + q;
+    if (e < len) a[e] = v[q];
+  }
+}
+
+// One warp per queued row of 33 .. kWarpRowMax entries.
+__global__ void __launch_bounds__(256) k_rowsort_warp(const OutSlot* out,
+                                                      const unsigned int* __restrict__ row_queue,
+                                                      const unsigned int* mid_count) {
+  const long long* __restrict__ row_ptr = out->row_ptr;
+  int* col = out->col;
+  const unsigned int cnt = *mid_count;
+  const unsigned int warps = gridDim.x * (blockDim.x >> 5);
+  for (unsigned int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < cnt; k += warps) {
+    const unsigned int row = row_queue[k];
+    const long long b = row_ptr[row];
+    const int len = (int)(row_ptr[row + 1] - b);
+    if (len <= 64) warp_sort_row<2>(col + b, len);
+    else if (len <= 128) warp_sort_row<4>(col + b, len);
+    else warp_sort_row<8>(col + b, len);
+  }
+}
+
 constexpr int kRowSmem = 8192;
 
-__global__ void __launch_bounds__(256) k_rowsort_long(const OutSlot* out,
-                                                      const unsigned int* __restrict__ long_rows,
+// One block per queued row of more than kWarpRowMax entries.
+__global__ void __launch_bounds__(256) k_rowsort_long(const OutSlot* out, long long n,
+                                                      const unsigned int* __restrict__ row_queue,
                                                       const unsigned int* long_count) {
   const long long* __restrict__ row_ptr = out->row_ptr;
   int* col = out->col;
@@ -866,7 +1046,7 @@ __global__ void __launch_bounds__(256) k_rowsort_long(const OutSlot* out,
   __shared__ int buf[kRowSmem];
   const unsigned int cnt = *long_count;
   for (unsigned int k = blockIdx.x; k < cnt; k += gridDim.x) {
-    const unsigned int row = long_rows[k];
+    const unsigned int row = row_queue[n - 1 - k];
     const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
     if (b + len > col_cap) continue;  // uniform across the block: same row for all threads
     long long L = 1;
@@ -967,6 +1147,19 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(
       sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
       a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes);
+  {
+    const size_t msmem =
+        (size_t)kMediumWarps * kMediumMax * (DPAD * 4 + 4) + (size_t)kMediumWarps * kMediumKeyBytes;
+    static bool mattr[64] = {};
+    if (dev >= 0 && dev < 64 && !mattr[dev]) {
+      cudaFuncSetAttribute(k_pairs_medium<K, DPAD, MODE>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+      mattr[dev] = true;
+    }
+    k_pairs_medium<K, DPAD, MODE><<<(unsigned)(8 * a.num_sms), kMediumWarps * 32, msmem, s>>>(
+        sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
+        make_sink(a));
+  }
   if (MODE != kWrite) k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
   k_pairs_large<K, DPAD, MODE><<<(unsigned)(4 * a.num_sms), kPairThreads, 0, s>>>(
       sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
@@ -976,9 +1169,9 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
 template <typename K, int DPAD>
 int pairs_impl(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s) {
   switch (mode) {
-    case kCount: pairs_mode<K, DPAD, kCount>(a, sorted_buf, s); return 3;
-    case kWrite: pairs_mode<K, DPAD, kWrite>(a, sorted_buf, s); return 2;
-    default: pairs_mode<K, DPAD, kEmit>(a, sorted_buf, s); return 3;
+    case kCount: pairs_mode<K, DPAD, kCount>(a, sorted_buf, s); return 4;
+    case kWrite: pairs_mode<K, DPAD, kWrite>(a, sorted_buf, s); return 3;
+    default: pairs_mode<K, DPAD, kEmit>(a, sorted_buf, s); return 4;
   }
 }
 
@@ -1036,9 +1229,12 @@ int launch_scatter(const BuildArgs& a, cudaStream_t s) {
 int launch_rowsort(const BuildArgs& a, cudaStream_t s) {
   const unsigned blocks = (unsigned)((a.n_total + 255) / 256);
   unsigned int* long_count = &a.st->long_rows;
-  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, long_count);
-  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.out, a.row_cnt, long_count);
-  return 2;
+  unsigned int* mid_count = &a.st->mid_rows;
+  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, mid_count, long_count);
+  k_rowsort_warp<<<(unsigned)(4 * a.num_sms), 256, 0, s>>>(a.out, a.row_cnt, mid_count);
+  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.out, a.n_total, a.row_cnt,
+                                                           long_count);
+  return 3;
 }
 
 }  // namespace rtg

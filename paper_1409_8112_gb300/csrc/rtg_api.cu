@@ -272,6 +272,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     I.d = it.d;
     I.r = it.r;
     I.c = m > 0 ? it.cell_side : 1.0;
+    I.inv_c = 1.0 / I.c;
+    I.inv_cf = (float)I.inv_c;
     I.blk0 = blk0;
     I.pblk0 = pblk0;
     p0 += it.n;
@@ -400,8 +402,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       RTG_CUDA(c, cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st));
       a.passes = rtg::sort_passes_for(64, 8);
       a.sort_bits = 8;
-      rtg::launch_prep(a, st);
-      rtg::launch_plan(a, st);
+      rtg::launch_prep_plan(a, st);
       if ((s = read_status(c)) != RTG_OK) return s;
       if ((s = check_errors(c, rtg::kErrNonFinite | rtg::kErrKeyOverflow)) != RTG_OK) return s;
       g.key_bits = (int)c->h_status->sort_bits;
@@ -510,10 +511,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if (timing) mark(0);
       cudaMemsetAsync(a.st, 0, sizeof(Status), st);
       cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st);
-      cudaMemsetAsync(a.row_cnt, 0, (size_t)n_total * 4, st);
-      rtg::launch_prep(a, st);
-      rtg::launch_plan(a, st);
-      l += m > 0 ? 3 : 2;
+      l += rtg::launch_prep_plan(a, st);
       if (timing) mark(1);
       if (m > 0) {
         rtg::launch_keys(a, st);

@@ -74,6 +74,7 @@ struct Status {
   unsigned int errors;
   unsigned int sort_bits;  // bits of the composite key (set by the plan)
   unsigned int hist_ticket;
+  unsigned int prep_ticket;
   unsigned int scan_tiles;
   unsigned long long nnz;      // stored CSR entries (set by the scan)
   unsigned long long pairs;    // reported pairs
@@ -108,6 +109,8 @@ struct Inst {
   long long T0;     // first double of its m transforms in the packed transform array
   int n, d;
   double r, c;
+  double inv_c;   // fl64(1 / c), set by the host
+  float inv_cf;   // fl32(1 / c), set by the host
   long long blk0;   // first block of this instance in the per-point kernels
   long long pblk0;  // first block of this instance in the prep kernel
 };
@@ -221,8 +224,9 @@ struct BuildArgs {
   int num_sms;
 };
 
-void launch_prep(const BuildArgs& a, cudaStream_t s);
-void launch_plan(const BuildArgs& a, cudaStream_t s);
+// FP32 rows, zeroed row counters, bounding boxes and the plan (in the prep kernel's last block
+// for small batches); returns the kernels launched.
+int launch_prep_plan(const BuildArgs& a, cudaStream_t s);
 void launch_keys(const BuildArgs& a, cudaStream_t s);
 // returns the ping-pong buffer (0 or 1) that holds the sorted data
 int launch_sort(const BuildArgs& a, cudaStream_t s);

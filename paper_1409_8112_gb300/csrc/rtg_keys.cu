@@ -45,12 +45,33 @@ __device__ __forceinline__ int block_instance(const Inst* inst, int B, long long
   return *s_b;
 }
 
-// FP32 rows of the points and the per-instance bounding box; kPrepPoints points per block so
-// that each block adds one bound per axis.
+__device__ void plan_axis_item(long long idx, const Inst* __restrict__ inst, int m, int dtype,
+                               const double* __restrict__ T64, const unsigned long long* bbox,
+                               InstPlan* iplan, GridPlan* gplan);
+__device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, GridPlan* gplan,
+                                  unsigned long long* bases, Status* st, int passes,
+                                  int radix_bits, int key64);
+
+// Plan arguments for the prep kernel's last block (small batches plan there, saving two
+// launches on the build's critical path).
+struct PlanArgs {
+  int fuse;  // 1: the last block to finish runs the plan
+  int m;
+  const double* T64;
+  InstPlan* iplan;
+  GridPlan* gplan;
+  unsigned long long* bases;
+  int passes, radix_bits, key64;
+};
+
+// FP32 rows of the points, zeroed row counters and the per-instance bounding box;
+// kPrepPoints points per block so that each block adds one bound per axis.
 template <int DPAD>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ inst, int B,
                                                        int dtype, float* __restrict__ pf,
-                                                       unsigned long long* bbox, Status* st) {
+                                                       unsigned int* __restrict__ row_cnt,
+                                                       unsigned long long* bbox, Status* st,
+                                                       PlanArgs pa) {
   // The bounding box only has to contain every coordinate: it is kept in FP32, each value
   // widened by one ulp (the FP32 row is the FP64 value rounded to nearest), so that no FP64
   // arithmetic runs here.  Finiteness of FP64 input is tested on the exponent bits; values
@@ -96,6 +117,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
 #pragma unroll
     for (int v = 0; v < DPAD / 4; ++v)
       dst[v] = make_float4(row[4 * v], row[4 * v + 1], row[4 * v + 2], row[4 * v + 3]);
+    row_cnt[I.p0 + i] = 0u;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -123,31 +145,35 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
       atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 1], ~enc_double((double)a));
     }
   }
+  if (!pa.fuse) return;
+  // the last block to finish plans every (instance, grid, axis), then the key ranges
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->prep_ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const long long items = (long long)B * (pa.m > 0 ? pa.m : 1) * kMaxDim;
+  for (long long idx = threadIdx.x; idx < items; idx += blockDim.x)
+    plan_axis_item(idx, inst, pa.m, dtype, pa.T64, bbox, pa.iplan, pa.gplan);
+  if (pa.m == 0) return;
+  __syncthreads();
+  plan_ranges_block(inst, B, pa.m, pa.gplan, pa.bases, st, pa.passes, pa.radix_bits, pa.key64);
 }
 
-// Thread (b, t, k): key layout of axis k of grid t of instance b; thread (b, 0, 0) also sets
-// the instance's distance band.
-__global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst, int B, int m,
-                                                   int dtype, const double* __restrict__ T64,
-                                                   const unsigned long long* __restrict__ bbox,
-                                                   InstPlan* iplan, GridPlan* gplan) {
-  const int mm = m > 0 ? m : 1;
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * mm * kMaxDim) return;
-  const int b = (int)(idx / (mm * kMaxDim));
-  const int t = (int)(idx / kMaxDim % mm);
-  const int k = (int)(idx % kMaxDim);
-  const Inst I = inst[b];
+// Distance band of instance b (one thread).  The bounding box is read from L2 (it was built
+// by atomics).
+__device__ void plan_band(int b, const Inst& I, int dtype, const unsigned long long* bbox,
+                          InstPlan* iplan) {
   const int d = I.d;
   double M[kMaxDim];
-  for (int l = 0; l < kMaxDim; ++l) M[l] = 0.0;
-  double lo[kMaxDim], hi[kMaxDim];
   for (int l = 0; l < d; ++l) {
-    hi[l] = I.n > 0 ? dec_double(bbox[((size_t)b * kMaxDim + l) * 2 + 0]) : 0.0;
-    lo[l] = I.n > 0 ? dec_double(~bbox[((size_t)b * kMaxDim + l) * 2 + 1]) : 0.0;
-    M[l] = fmax(fabs(lo[l]), fabs(hi[l]));
+    const double hi = I.n > 0 ? dec_double(__ldcg(bbox + ((size_t)b * kMaxDim + l) * 2 + 0)) : 0.0;
+    const double lo = I.n > 0 ? dec_double(~__ldcg(bbox + ((size_t)b * kMaxDim + l) * 2 + 1)) : 0.0;
+    M[l] = fmax(fabs(lo), fabs(hi));
   }
-  if (t == 0 && k == 0) {
+  {
     // Distance band.  With S the exact squared distance and e_f the FP32 differences,
     // |fl32-chain(e_f) - S| <= 2|eta| sqrt(S) + |eta|^2 + d 2^-24 (sqrt(S) + |eta|)^2 where
     // eta_l bounds |e_f,l - e_l|: 2^-24 (|p_a,l| + |p_b,l|) from rounding FP64 input to FP32
@@ -175,10 +201,27 @@ __global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst
     ip.filter_on = on ? 1 : 0;
     ip.s_lo = on ? __double2float_rd(rr - Es) : 0.0f;
     ip.s_hi = on ? __double2float_ru(rr + Es) : 0.0f;
-    ip.inv_c = __double2float_rn(1.0 / I.c);
+    ip.inv_c = I.inv_cf;
     iplan[b] = ip;
   }
-  if (m == 0) return;
+}
+
+// Item (b, t, k): key layout of axis k of grid t of instance b (the bounding box is read from
+// L2).  Without grids (brute force) item (b, 0, 0) sets the instance's distance band; with
+// grids the key kernel sets it, off the critical path.
+__device__ void plan_axis_item(long long idx, const Inst* __restrict__ inst, int m, int dtype,
+                               const double* __restrict__ T64, const unsigned long long* bbox,
+                               InstPlan* iplan, GridPlan* gplan) {
+  const int mm = m > 0 ? m : 1;
+  const int b = (int)(idx / (mm * kMaxDim));
+  const int t = (int)(idx / kMaxDim % mm);
+  const int k = (int)(idx % kMaxDim);
+  const Inst I = inst[b];
+  if (m == 0) {
+    if (t == 0 && k == 0) plan_band(b, I, dtype, bbox, iplan);
+    return;
+  }
+  const int d = I.d;
   GridPlan& G = gplan[(size_t)b * m + t];
   if (k >= d) {
     for (int l = 0; l < kMaxDim; ++l) G.Rf[k * kMaxDim + l] = 0.0f;
@@ -188,26 +231,24 @@ __global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst
     G.ext[k] = 1;
     return;
   }
-  const double c = I.c;
   const double* R = T64 + I.T0 + (size_t)t * (d * d + d);
   const double* s = R + d * d;
   double ymin = s[k], ymax = s[k], A = fabs(s[k]);
-  for (int l = 0; l < kMaxDim; ++l) {
-    if (l < d) {
-      const double rkl = R[k * d + l];
-      const double a = rkl * lo[l], bb = rkl * hi[l];
-      ymin += fmin(a, bb);
-      ymax += fmax(a, bb);
-      A += fabs(rkl) * M[l];
-      G.Rf[k * kMaxDim + l] = __double2float_rn(rkl);
-    } else {
-      G.Rf[k * kMaxDim + l] = 0.0f;
-    }
+  for (int l = 0; l < d; ++l) {
+    const double hi = I.n > 0 ? dec_double(__ldcg(bbox + ((size_t)b * kMaxDim + l) * 2 + 0)) : 0.0;
+    const double lo = I.n > 0 ? dec_double(~__ldcg(bbox + ((size_t)b * kMaxDim + l) * 2 + 1)) : 0.0;
+    const double rkl = R[k * d + l];
+    const double a = rkl * lo, bb = rkl * hi;
+    ymin += fmin(a, bb);
+    ymax += fmax(a, bb);
+    A += fabs(rkl) * fmax(fabs(lo), fabs(hi));
+    G.Rf[k * kMaxDim + l] = __double2float_rn(rkl);
   }
+  for (int l = d; l < kMaxDim; ++l) G.Rf[k * kMaxDim + l] = 0.0f;
   G.sf[k] = __double2float_rn(s[k]);
   // Two cells of margin on each side absorb every rounding difference between these sums
-  // and the per-point fma chains (both are far below one cell).
-  const double qmin = floor(ymin / c) - 2.0, qmax = floor(ymax / c) + 2.0;
+  // and the per-point fma chains (both are far below one cell); 1/c comes from the host.
+  const double qmin = floor(ymin * I.inv_c) - 2.0, qmax = floor(ymax * I.inv_c) + 2.0;
   if (!(qmin > -4.0e18 && qmax < 4.0e18)) {
     G.qlo[k] = 0;
     G.ext[k] = ~0ull;  // flagged as overflow by the range pass
@@ -215,16 +256,25 @@ __global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst
     G.qlo[k] = (long long)qmin;
     G.ext[k] = (unsigned long long)((long long)qmax - (long long)qmin + 1);
   }
-  const double E = (double)(d + 6) * 0x1.0p-24 * A / c * (1.0 + 1e-6) + 3e-12 / c;
+  const double E = ((double)(d + 6) * 0x1.0p-24 * A + 3e-12) * I.inv_c * (1.0 + 1e-6);
   G.E[k] = __double2float_ru(E);
 }
 
+__global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst, int B, int m,
+                                                   int dtype, const double* __restrict__ T64,
+                                                   const unsigned long long* bbox,
+                                                   InstPlan* iplan, GridPlan* gplan) {
+  const int mm = m > 0 ? m : 1;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx < (long long)B * mm * kMaxDim) plan_axis_item(idx, inst, m, dtype, T64, bbox, iplan, gplan);
+}
+
 // One block: strides and key range of every (instance, grid), their exclusive prefix (the
-// composite key bases), and the width of the composite key.
-__global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ inst, int B, int m,
-                                                      GridPlan* gplan,
-                                                      unsigned long long* bases, Status* st,
-                                                      int passes, int radix_bits, int key64) {
+// composite key bases), and the width of the composite key.  Any block size that is a
+// multiple of 32, up to 1024.
+__device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, GridPlan* gplan,
+                                  unsigned long long* bases, Status* st, int passes,
+                                  int radix_bits, int key64) {
   __shared__ unsigned long long sbuf[32];
   __shared__ unsigned long long carry;
   __shared__ int overflow;
@@ -297,6 +347,13 @@ __global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ i
   }
 }
 
+__global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ inst, int B, int m,
+                                                      GridPlan* gplan,
+                                                      unsigned long long* bases, Status* st,
+                                                      int passes, int radix_bits, int key64) {
+  plan_ranges_block(inst, B, m, gplan, bases, st, passes, radix_bits, key64);
+}
+
 // FP64 reference cell index (the oracle's sequence) for point i, grid data Tt, axis k.
 __device__ __noinline__ long long exact_cell(const void* pts, int dtype, long long i, int d,
                                              const double* Tt, int k, double c, bool* near) {
@@ -313,9 +370,9 @@ __device__ __noinline__ long long exact_cell(const void* pts, int dtype, long lo
 template <typename K, int DPAD>
 __global__ void __launch_bounds__(kPointBlock) k_keys(
     const Inst* __restrict__ inst, int B, int m, int dtype, const float* __restrict__ pf,
-    const double* __restrict__ T64, const GridPlan* __restrict__ gplan,
-    const InstPlan* __restrict__ iplan, Status* st, K* __restrict__ key_mat,
-    K* __restrict__ comp, uint32_t* __restrict__ vals) {
+    const double* __restrict__ T64, const GridPlan* __restrict__ gplan, InstPlan* iplan,
+    const unsigned long long* bbox, Status* st, K* __restrict__ key_mat, K* __restrict__ comp,
+    uint32_t* __restrict__ vals) {
   __shared__ int s_b;
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = block_instance<false>(inst, B, blockIdx.x, &s_b);
@@ -344,7 +401,8 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     sR[x] = Gb[t].Rf[k * kMaxDim + l];
   }
   __syncthreads();
-  const float inv_c = iplan[b].inv_c;
+  const float inv_c = I.inv_cf;
+  if (threadIdx.x == 0 && blockIdx.x == I.blk0) plan_band(b, I, dtype, bbox, iplan);
   const double c = I.c;
   const long long i = (blockIdx.x - I.blk0) * (long long)kPointBlock + threadIdx.x;
   unsigned int near_cnt = 0, rechecks = 0;
@@ -407,10 +465,27 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
   if (range_err) atomicOr(&st->errors, kErrKeyRange);
 }
 
+// Batches up to this many (instance, grid, axis) items plan in the prep kernel's last block.
+constexpr long long kFusedPlanItems = 4096;
+
+bool plan_fused(const BuildArgs& a) {
+  return (long long)a.B * (a.m > 0 ? a.m : 1) * kMaxDim <= kFusedPlanItems;
+}
+
 template <int DPAD>
 void prep_impl(const BuildArgs& a, cudaStream_t s) {
-  k_prep<DPAD><<<(unsigned)a.pblocks, kPrepThreads, 0, s>>>(a.inst, a.B, a.dtype, a.pf, a.bbox,
-                                                             a.st);
+  PlanArgs pa;
+  pa.fuse = plan_fused(a) ? 1 : 0;
+  pa.m = a.m;
+  pa.T64 = a.T64;
+  pa.iplan = a.iplan;
+  pa.gplan = a.gplan;
+  pa.bases = a.bases;
+  pa.passes = a.passes;
+  pa.radix_bits = a.sort_bits;
+  pa.key64 = a.key64 ? 1 : 0;
+  k_prep<DPAD><<<(unsigned)a.pblocks, kPrepThreads, 0, s>>>(a.inst, a.B, a.dtype, a.pf,
+                                                             a.row_cnt, a.bbox, a.st, pa);
 }
 
 template <typename K, int DPAD>
@@ -424,27 +499,26 @@ void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
     if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
   }
   k_keys<K, DPAD><<<(unsigned)a.blocks, kPointBlock, smem, s>>>(
-      a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.st, (K*)a.key_mat,
+      a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st, (K*)a.key_mat,
       (K*)a.keys[0], a.vals[0]);
 }
 
 }  // namespace
 
-void launch_prep(const BuildArgs& a, cudaStream_t s) {
+int launch_prep_plan(const BuildArgs& a, cudaStream_t s) {
   switch (a.dpad) {
     case 4: prep_impl<4>(a, s); break;
     case 8: prep_impl<8>(a, s); break;
     default: prep_impl<16>(a, s); break;
   }
-}
-
-void launch_plan(const BuildArgs& a, cudaStream_t s) {
+  if (plan_fused(a)) return 1;
   const long long threads = (long long)a.B * (a.m > 0 ? a.m : 1) * kMaxDim;
   k_plan_axes<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a.inst, a.B, a.m, a.dtype, a.T64,
                                                               a.bbox, a.iplan, a.gplan);
   if (a.m > 0)
     k_plan_ranges<<<1, 1024, 0, s>>>(a.inst, a.B, a.m, a.gplan, a.bases, a.st, a.passes,
                                      a.sort_bits, a.key64 ? 1 : 0);
+  return a.m > 0 ? 3 : 2;
 }
 
 void launch_keys(const BuildArgs& a, cudaStream_t s) {

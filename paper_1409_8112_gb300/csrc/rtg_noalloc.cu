@@ -96,6 +96,8 @@ extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int
   I.d = d;
   I.r = r;
   I.c = 1.0;
+  I.inv_c = 1.0;
+  I.inv_cf = 1.0f;
   // the counters and the bounding box must start at zero; the instance record is copied in;
   // every other region is fully rewritten (plan, point rows) or only incremented and never
   // read (row counts)
@@ -103,8 +105,7 @@ extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int
       cudaMemsetAsync(a.bbox, 0, kBoxBytes, s) != cudaSuccess ||
       cudaMemcpyAsync((void*)a.inst, &I, sizeof(I), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(RTG_E_CUDA, "scratch set-up failed");
-  rtg::launch_prep(a, s);
-  rtg::launch_plan(a, s);
+  rtg::launch_prep_plan(a, s);
   rtg::launch_brute(a, rtg::kCount, s);
   rtg::Status h;
   std::memset(&h, 0, sizeof(h));

@@ -39,7 +39,7 @@ __host__ __device__ inline int sort_passes_for(int key_bits, int radix_bits) {
 }
 constexpr int kPointBlock = 128;   // points per block in the per-point kernels
 constexpr int kPrepThreads = 256;
-constexpr int kPrepPoints = 1024;  // points per block in the prep kernel
+constexpr int kPrepPoints = 256;   // points per block in the prep kernel
 
 // Bits of Status::errors.
 enum : uint32_t {

@@ -561,6 +561,47 @@ def run_table2(args):
     print(json.dumps(line), flush=True)
 
 
+def run_query(args):
+    """Multiple r-NN queries (Sec. II): the headline workload built once with every pair stored
+    twice (symmetric CSR), then the neighbour lists of a random 10% of the points (host index
+    list, repeats allowed) read back as a CSR, per step."""
+    import torch
+    from paper_1409_8112_gb300 import rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = L2Flush()
+    pts, T, r = workload()
+    n = len(pts)
+    dev = torch.from_numpy(pts).cuda()
+    g = ctx.all_pairs(dev, r, T, r, symmetric=True)
+    q = np.random.default_rng(3).integers(0, n, n // 10).astype(np.int32)
+    for _ in range(args.warmup):
+        ctx.query_neighbors(g, q).release()
+    ms, nnz = [], 0
+    for k in range(args.steps):
+        flush(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.query_neighbors(g, q)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        nnz = res.nnz
+        res.release()
+    t = float(np.mean(ms))
+    line = {"metric": METRIC, "value": round(nnz / (t / 1e3), 1), "unit": "neighbours/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t, 4),
+            "higher_is_better": True, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": f"multiple r-NN queries: {len(q)} random indices into the "
+                                   f"symmetric CSR of {WORKLOAD['workload']}", "l2": L2_NOTE},
+            "queries": len(q), "neighbours_per_step": nnz,
+            "queries_per_s": round(len(q) / (t / 1e3), 1), "graph_nnz": g.nnz}
+    g.release()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Precision workload: n = 1e6 points of U[0,1]^6 stored FP32, r for degree 2 ln n, m = 8
     (RTG build), and the exact all-pairs set of a 200,000-point sample (first 200k points of a
@@ -632,7 +673,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="build",
-                    choices=["build", "batch", "serve", "precision", "table2"],
+                    choices=["build", "batch", "serve", "precision", "table2", "query"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -656,6 +697,8 @@ def main():
         run_precision(args)
     elif args.workload == "table2":
         run_table2(args)
+    elif args.workload == "query":
+        run_query(args)
     else:
         run_ours(args)
 

@@ -252,6 +252,18 @@ rtg_status rtg_poll(rtg_ctx* ctx, uint64_t ticket, rtg_csr* out);
  * status; RTG_E_TIMEOUT if the request is still running then (the ticket stays valid). */
 rtg_status rtg_wait(rtg_ctx* ctx, uint64_t ticket, int64_t timeout_us, rtg_csr* out);
 
+/* Multiple r-nearest-neighbour queries (Sec. II): the neighbours of a subset of the points,
+ * read from a stored pair set that holds every pair twice (Sec. III-B).
+ *   graph   : a symmetric CSR returned by this context (RTG_FLAG_SYMMETRIC), not released
+ *   queries : nq point indices in [0, graph->n), host or device (queries_on_device);
+ *             repeats allowed
+ *   out     : library-owned device CSR with nq rows; row k is the neighbour list of
+ *             queries[k], ascending (out->symmetric = 0).  Free with rtg_release.
+ * Synchronous.  Errors: RTG_E_INVALID (graph not symmetric, nq out of range, an index
+ * outside the graph), RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA. */
+rtg_status rtg_query_neighbors(rtg_ctx* ctx, const rtg_csr* graph, const int32_t* queries,
+                               int64_t nq, int queries_on_device, rtg_csr* out);
+
 /* Free the device memory of a CSR returned by this context and zero *csr. */
 rtg_status rtg_release(rtg_ctx* ctx, rtg_csr* csr);
 

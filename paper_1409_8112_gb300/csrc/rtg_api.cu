@@ -63,7 +63,7 @@ rtg_status fail(rtg_ctx* ctx, rtg_status s, const std::string& msg) {
 size_t total_held(const rtg_ctx* c) { return c->ws_bytes + c->out_bytes; }
 
 // Grow a workspace buffer to at least `bytes` (contents are not kept).
-rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
+rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
   if (b.cap >= bytes) return RTG_OK;
@@ -806,6 +806,7 @@ void destroy_ctx(rtg_ctx* c) {
   for (DevBuf* b : bufs) free_buf(c, *b);
   while (!c->graphs.empty()) drop_graph(c, c->graphs.begin()->first);
   free_buf(c, c->out_slot);
+  free_buf(c, c->q_idx);
   free_buf(c, c->sort_epoch);
   if (c->h_slot) cudaFreeHost(c->h_slot);
   for (auto& ev : c->ev)
@@ -873,6 +874,20 @@ rtg_status rtg_release(rtg_ctx* c, rtg_csr* csr) {
   cudaSetDevice(c->device);
   release_out(c, csr);
   return RTG_OK;
+}
+
+rtg_status rtg_query_neighbors(rtg_ctx* c, const rtg_csr* graph, const int32_t* queries,
+                               int64_t nq, int queries_on_device, rtg_csr* out) {
+  if (!c || !graph || !out) return fail(c, RTG_E_INVALID, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (!graph->symmetric)
+    return fail(c, RTG_E_INVALID, "neighbour queries need a symmetric CSR (RTG_FLAG_SYMMETRIC)");
+  if (nq < 0 || nq >= (int64_t(1) << 31) || (nq > 0 && !queries))
+    return fail(c, RTG_E_INVALID, "queries: count out of range or NULL");
+  if (graph->n > 0 && !graph->row_ptr) return fail(c, RTG_E_INVALID, "graph has no row pointers");
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return query_neighbors(c, graph, queries, nq, queries_on_device, out);
 }
 
 rtg_status rtg_csr_download(rtg_ctx* c, const rtg_csr* csr, int64_t* row_ptr, int32_t* col) {

@@ -50,7 +50,8 @@ enum : uint32_t {
   kErrKeyBits = 16u,        // key wider than the launch assumed (host re-runs)
   kErrKeyRange = 32u,       // a cell index fell outside the planned range (internal)
   kErrLargeOverflow = 64u,  // large-cell list full (internal)
-  kErrPairOverflow = 128u   // pair buffer too small (host re-runs bigger)
+  kErrPairOverflow = 128u,  // pair buffer too small (host re-runs bigger)
+  kErrQueryRange = 256u     // a neighbour query names a point outside the graph
 };
 
 // Cells with more points than this are enumerated by the tiled large-cell kernel.

@@ -93,6 +93,9 @@ _SIGNATURES = {
     "rtg_destroy": (None, [ctypes.c_void_p]),
     "rtg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "rtg_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "rtg_query_neighbors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.POINTER(rtg_csr)]),
     "rtg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rtg_transforms_generate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_uint32,
@@ -419,6 +422,25 @@ class Context:
 
     def wait(self, ticket: int, timeout_us: int = -1, m: int = 0) -> Result:
         return Result(self, rtg_wait(self.handle, ticket, timeout_us), m)
+
+    def query_neighbors(self, graph: "Result", queries) -> "Result":
+        """Multiple r-NN queries (Sec. II): row k of the result is the neighbour list of
+        queries[k], read from `graph` (a symmetric result of this context).  queries: int32
+        numpy array or CUDA tensor."""
+        if hasattr(queries, "is_cuda") and queries.is_cuda:
+            import torch
+            q = queries.to(torch.int32).contiguous()
+            self._after_producer(q)
+            ptr, on_dev, nq, keep = q.data_ptr(), 1, q.numel(), q
+        else:
+            q = np.ascontiguousarray(queries, dtype=np.int32).reshape(-1)
+            ptr, on_dev, nq, keep = (q.ctypes.data if q.size else None), 0, q.size, q
+        out = rtg_csr()
+        st = lib().rtg_query_neighbors(self.handle, ctypes.byref(graph.csr), ptr, nq, on_dev,
+                                       ctypes.byref(out))
+        del keep
+        _check(st, self.handle)
+        return Result(self, out, 0)
 
     def brute_force(self, points, r: float, symmetric: bool = False,
                     count_only: bool = False, tensor: str | None = None,

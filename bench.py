@@ -561,6 +561,66 @@ def run_table2(args):
     print(json.dumps(line), flush=True)
 
 
+def run_params(args):
+    """Grid parameters for a target recall (Sec. III-A): rtg_tune_params picks (c, m) for 98%
+    recall on n uniform points in [0,1]^6 (FP64, seed 0, r from Eq. 2), shift-only and rotated;
+    each choice is then built and timed like the headline, beside Table II's shift-only
+    setting (m = 20, c = 1.35 r)."""
+    import torch
+    from paper_1409_8112_gb300 import gen, rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = L2Flush()
+    n, d, target = args.n, 6, 0.98
+    r = gen.radius_fmt(n, d)
+    pts = torch.from_numpy(gen.points_uniform(0, n, d)).cuda()
+    exact = ctx.brute_force(pts, r, count_only=True)
+    n_exact = exact.nnz
+    exact.release()
+
+    def timed(T, c):
+        for _ in range(args.warmup):
+            ctx.all_pairs(pts, r, T, c).release()
+        ms, pairs = [], 0
+        for k in range(args.steps):
+            flush(k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = ctx.all_pairs(pts, r, T, c)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            pairs = res.nnz
+            res.release()
+        t = float(np.mean(ms))
+        return {"ms_per_build": round(t, 4), "recall_full": round(pairs / n_exact, 5),
+                "pairs_per_s": round(pairs / (t / 1e3), 1)}
+
+    out = {}
+    for name, shift in (("shift_only", True), ("rotated", False)):
+        t0 = time.perf_counter()
+        ch = ctx.tune_params(pts, r, target, seed=0, shift_only=shift)
+        tune_s = time.perf_counter() - t0
+        flags = gen.SHIFT_ONLY if shift else 0
+        T = gen.transforms(0, d, ch["m"], ch["cell_side"], flags)
+        out[name] = dict({"m": ch["m"], "c_over_r": ch["c_factor"],
+                          "recall_sample": round(ch["recall"], 5), "tuning_s": round(tune_s, 3)},
+                         **timed(T, ch["cell_side"]))
+    T2 = gen.transforms(0, d, 20, 1.35 * r, gen.SHIFT_ONLY)
+    out["table2_shift_only_m20_c1.35"] = timed(T2, 1.35 * r)
+    best = min(("shift_only", "rotated"), key=lambda k: out[k]["ms_per_build"])
+    line = {"metric": METRIC, "value": out[best]["pairs_per_s"], "unit": "pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out[best]["ms_per_build"], "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"tuned grids for recall >= {target}: n={n} uniform [0,1]^6 "
+                                   f"fp64, r from Eq. 2 ({r:.6f}), seed 0", "l2": L2_NOTE},
+            "exact_pairs": n_exact, "choices": out, "best": best}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_query(args):
     """Multiple r-NN queries (Sec. II): the headline workload built once with every pair stored
     twice (symmetric CSR), then the neighbour lists of a random 10% of the points (host index
@@ -673,7 +733,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="build",
-                    choices=["build", "batch", "serve", "precision", "table2", "query"],
+                    choices=["build", "batch", "serve", "precision", "table2", "query",
+                             "params"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -699,6 +760,8 @@ def main():
         run_table2(args)
     elif args.workload == "query":
         run_query(args)
+    elif args.workload == "params":
+        run_params(args)
     else:
         run_ours(args)
 

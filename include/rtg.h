@@ -264,6 +264,29 @@ rtg_status rtg_wait(rtg_ctx* ctx, uint64_t ticket, int64_t timeout_us, rtg_csr* 
 rtg_status rtg_query_neighbors(rtg_ctx* ctx, const rtg_csr* graph, const int32_t* queries,
                                int64_t nq, int queries_on_device, rtg_csr* out);
 
+/* Grid parameters chosen by rtg_tune_params. */
+typedef struct {
+  int m;                /* number of grids */
+  double cell_side;     /* c = c_factor * r */
+  double c_factor;      /* c / r */
+  double recall;        /* measured on the sample (reported pairs / exact pairs) */
+  double build_us;      /* device time of a full-size build with (m, c) */
+  int64_t sample_n;     /* points in the recall sample (a prefix of the input) */
+  int64_t sample_exact; /* exact pairs of the sample */
+  int candidates;       /* count-only builds measured */
+} rtg_param_choice;
+
+/* Choose c and m for a target recall (the parameter tuning of Sec. III-A): for each c/r in
+ * {1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.75, 2.0}, the smallest m <= 64 whose grids report at least
+ * target_recall of the exact pairs of a prefix sample (at most 32768 points), then the
+ * (c, m) with the least full-size build time.  The grids are the first m of
+ * rtg_transforms_generate(seed, d, 64, c, flags & RTG_FLAG_SHIFT_ONLY), which equal
+ * rtg_transforms_generate(seed, d, m, c, ...).  Builds on ctx; synchronous.  Errors as
+ * rtg_all_pairs, and RTG_E_INVALID when no setting reaches the target. */
+rtg_status rtg_tune_params(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
+                           int64_t n, int d, double r, double target_recall, uint64_t seed,
+                           uint32_t flags, rtg_param_choice* out);
+
 /* Free the device memory of a CSR returned by this context and zero *csr. */
 rtg_status rtg_release(rtg_ctx* ctx, rtg_csr* csr);
 

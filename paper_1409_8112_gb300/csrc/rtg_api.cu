@@ -876,6 +876,21 @@ rtg_status rtg_release(rtg_ctx* c, rtg_csr* csr) {
   return RTG_OK;
 }
 
+rtg_status rtg_tune_params(rtg_ctx* c, const void* points, int dtype, int points_on_device,
+                           int64_t n, int d, double r, double target_recall, uint64_t seed,
+                           uint32_t flags, rtg_param_choice* out) {
+  if (!c || !out) return fail(c, RTG_E_INVALID, "NULL context or output");
+  std::memset(out, 0, sizeof(*out));
+  rtg_status s = validate_common(dtype, n, d, r, r, points);
+  if (s != RTG_OK) return fail(c, s, g_err);
+  if (!(target_recall > 0.0 && target_recall <= 1.0))
+    return fail(c, RTG_E_INVALID, "target_recall must be in (0, 1]");
+  if (n < 2) return fail(c, RTG_E_INVALID, "n must be at least 2");
+  std::lock_guard<std::mutex> lk(c->mu);
+  RTG_CUDA(c, cudaSetDevice(c->device));
+  return tune_params(c, points, dtype, points_on_device, n, d, r, target_recall, seed, flags, out);
+}
+
 rtg_status rtg_query_neighbors(rtg_ctx* c, const rtg_csr* graph, const int32_t* queries,
                                int64_t nq, int queries_on_device, rtg_csr* out) {
   if (!c || !graph || !out) return fail(c, RTG_E_INVALID, "NULL argument");

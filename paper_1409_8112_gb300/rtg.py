@@ -67,6 +67,13 @@ class rtg_csr(ctypes.Structure):
                 ("stats", rtg_stats)]
 
 
+class rtg_param_choice(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("cell_side", ctypes.c_double), ("c_factor", ctypes.c_double),
+                ("recall", ctypes.c_double), ("build_us", ctypes.c_double),
+                ("sample_n", ctypes.c_int64), ("sample_exact", ctypes.c_int64),
+                ("candidates", ctypes.c_int)]
+
+
 class rtg_instance(ctypes.Structure):
     _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int),
                 ("r", ctypes.c_double), ("cell_side", ctypes.c_double),
@@ -93,6 +100,10 @@ _SIGNATURES = {
     "rtg_destroy": (None, [ctypes.c_void_p]),
     "rtg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "rtg_get_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "rtg_tune_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.POINTER(rtg_param_choice)]),
     "rtg_query_neighbors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                            ctypes.POINTER(rtg_csr)]),
@@ -422,6 +433,21 @@ class Context:
 
     def wait(self, ticket: int, timeout_us: int = -1, m: int = 0) -> Result:
         return Result(self, rtg_wait(self.handle, ticket, timeout_us), m)
+
+    def tune_params(self, points, r: float, target_recall: float, seed: int = 0,
+                    shift_only: bool = False) -> dict:
+        """c and m for a target recall (Sec. III-A): the fastest measured (c, m) whose grids
+        report at least target_recall of a prefix sample's exact pairs.  The grids are
+        gen.transforms(seed, d, m, c, flags) with the same shift-only flag."""
+        ptr, code, on_dev, n, d, keep = _points_arg(points)
+        self._after_producer(keep)
+        out = rtg_param_choice()
+        st = lib().rtg_tune_params(self.handle, ptr, code, on_dev, n, d, float(r),
+                                   float(target_recall), int(seed),
+                                   RTG_FLAG_SHIFT_ONLY if shift_only else 0, ctypes.byref(out))
+        del keep
+        _check(st, self.handle)
+        return {f: getattr(out, f) for f, _ in rtg_param_choice._fields_}
 
     def query_neighbors(self, graph: "Result", queries) -> "Result":
         """Multiple r-NN queries (Sec. II): row k of the result is the neighbour list of

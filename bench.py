@@ -621,6 +621,60 @@ def run_params(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bitset(args):
+    """Bit-matrix dedupe (Sec. III-B's flattened bit array) against the first-grid rule on the
+    batched form: 512 small roadmaps, n log-uniform in [1e3, 16384], d in {3, 6, 9}, FP32
+    uniform, r for degree 2 ln n, m = 6 and m = 20; same output, both timed warm."""
+    import torch
+    from paper_1409_8112_gb300 import gen, rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = L2Flush()
+    rng = np.random.default_rng(11)
+    ns = gen.log_uniform_int(rng, 1000, 16384, 512)
+    ds = rng.choice([3, 6, 9], 512)
+    out = {}
+    for m in (6, 20):
+        work = []
+        for i, (n, d) in enumerate(zip(ns, ds)):
+            r = gen.radius_for_degree(int(n), int(d))
+            p = torch.from_numpy(gen.points_uniform(2000 + i, int(n), int(d), np.float32)).cuda()
+            work.append((p, r, gen.transforms(2000 + i, int(d), m, r), r))
+        res = {}
+        for name, bits in (("first_grid", False), ("bitset", True)):
+            for _ in range(args.warmup):
+                ctx.batch_all_pairs(work, m=m, bitset=bits)[0].release()
+            ms, pairs = [], 0
+            for k in range(args.steps):
+                flush(k)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r_, _ = ctx.batch_all_pairs(work, m=m, bitset=bits)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                pairs = r_.nnz
+                r_.release()
+            t = float(np.mean(ms))
+            res[name] = {"ms_per_batch": round(t, 3), "pairs": pairs,
+                         "pairs_per_s": round(pairs / (t / 1e3), 1)}
+        assert res["bitset"]["pairs"] == res["first_grid"]["pairs"]
+        res["bitset_speedup"] = round(res["first_grid"]["ms_per_batch"] /
+                                      res["bitset"]["ms_per_batch"], 3)
+        out[f"m{m}"] = res
+    line = {"metric": METRIC, "value": out["m6"]["bitset"]["pairs_per_s"], "unit": "pairs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["m6"]["bitset"]["ms_per_batch"], "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch of 512 small roadmaps, n log-uniform [1e3,16384], d in "
+                                   "{3,6,9}, fp32 uniform, r=2lnn-degree, m=6 and m=20",
+                       "points": int(ns.sum()), "l2": L2_NOTE},
+            "results": out}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_query(args):
     """Multiple r-NN queries (Sec. II): the headline workload built once with every pair stored
     twice (symmetric CSR), then the neighbour lists of a random 10% of the points (host index
@@ -734,7 +788,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="build",
                     choices=["build", "batch", "serve", "precision", "table2", "query",
-                             "params"],
+                             "params", "bitset"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -762,6 +816,8 @@ def main():
         run_query(args)
     elif args.workload == "params":
         run_params(args)
+    elif args.workload == "bitset":
+        run_bitset(args)
     else:
         run_ours(args)
 

@@ -58,6 +58,9 @@ typedef enum {
                                   holding a pair buffer: less memory, more time */
 #define RTG_FLAG_TC_FP16 16u   /* rtg_brute_force: distances from FP16 tensor-core tiles */
 #define RTG_FLAG_TC_BF16 32u   /* rtg_brute_force: distances from BF16 tensor-core tiles */
+#define RTG_FLAG_BITSET 64u    /* small instances (n <= 16384 each): dedupe through an n x n
+                                  bit matrix per instance (the flattened bit array of
+                                  Sec. III-B) instead of the first-grid rule; same output */
 
 /* Point coordinate types. */
 #define RTG_DTYPE_F64 0

@@ -260,7 +260,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
 
   // ---- instance table and packed transforms (host) ----
   c->h_inst.assign(B, Inst{});
-  long long p0 = 0, blk0 = 0, pblk0 = 0, T0 = 0;
+  long long p0 = 0, blk0 = 0, pblk0 = 0, T0 = 0, bits_words = 0;
+  const bool bitset = (q.flags & RTG_FLAG_BITSET) != 0 && m > 0;
   int maxd = 1;
   for (int b = 0; b < B; ++b) {
     const rtg_instance& it = q.items[b];
@@ -276,6 +277,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     I.inv_cf = (float)I.inv_c;
     I.blk0 = blk0;
     I.pblk0 = pblk0;
+    I.bits_w = (int)((it.n + 31) / 32);
+    I.bits_off = bits_words;
+    bits_words += it.n * (long long)I.bits_w;
     p0 += it.n;
     blk0 += (it.n + rtg::kPointBlock - 1) / rtg::kPointBlock;
     pblk0 += (it.n + rtg::kPrepPoints - 1) / rtg::kPrepPoints;
@@ -289,6 +293,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     return fail(c, RTG_E_INVALID, "total points times grids must be below 2^31");
   if (m > 0 && B * (long long)m > 65535)
     return fail(c, RTG_E_INVALID, "instances times grids must be at most 65535");
+  if (bitset)
+    for (int b = 0; b < B; ++b)
+      if (q.items[b].n > rtg::kBitsetMaxN)
+        return fail(c, RTG_E_INVALID, "RTG_FLAG_BITSET takes instances of at most 16384 points");
   if (n_total == 0) {
     void* rp = nullptr;
     if ((s = alloc_out(c, sizeof(int64_t), &rp)) != RTG_OK) return s;
@@ -324,6 +332,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   if ((s = ensure(c, c->row_cnt, (size_t)n_total * 4)) != RTG_OK) return s;
   if ((s = ensure(c, c->scan_lb, ((size_t)n_total / 4096 + 2) * 8)) != RTG_OK) return s;
   if ((s = ensure(c, c->out_slot, sizeof(rtg::OutSlot))) != RTG_OK) return s;
+  if (bitset && (s = ensure(c, c->bits, (size_t)bits_words * 4)) != RTG_OK) return s;
   if ((s = ensure(c, c->sort_epoch, sizeof(unsigned int), true)) != RTG_OK) return s;
   if (!q.points_on_device) {
     if ((s = ensure(c, c->pts, (size_t)n_total * maxd * esz + 16 * (size_t)B)) != RTG_OK) return s;
@@ -384,6 +393,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.row_cnt = (unsigned int*)c->row_cnt.p;
   a.scan_lookback = (unsigned long long*)c->scan_lb.p;
   a.out = (const rtg::OutSlot*)c->out_slot.p;
+  a.bits = bitset ? (unsigned int*)c->bits.p : nullptr;
   a.sort_epoch = (unsigned int*)c->sort_epoch.p;
   a.num_sms = c->num_sms;
 
@@ -483,7 +493,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     // pair buffer for EMIT; COUNT then WRITE when asked, when only counting, or when the buffer
     // would not fit the budget
     if (g.pair_cap <= 0) g.pair_cap = std::max<long long>(4096, n_total * 16);
-    bool two_pass = two_pass_flag || q.count_only;
+    bool two_pass = two_pass_flag || q.count_only || bitset;
     if (!two_pass) {
       const size_t need = (size_t)g.pair_cap * 8;
       if (c->budget && total_held(c) - c->pair_buf.cap + need + need / (sym ? 1 : 2) > c->budget)
@@ -604,6 +614,51 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
           return fail(c, RTG_E_CUDA, std::string("build: ") + cudaGetErrorString(e));
         }
       }
+    } else if (bitset) {
+      // bit-matrix dedupe (Sec. III-B): every reported candidate sets its bit; rows come out
+      // of the matrices already sorted
+      RTG_CUDA(c, cudaMemsetAsync(a.bits, 0, (size_t)bits_words * 4, st));
+      set_slot();
+      launches += front();
+      launches += pairs(rtg::kBits);
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[4], st));
+      launches += rtg::launch_bits_count(a, st);
+      rtg::launch_scan(a, st);
+      launches += 1;
+      if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[5], st));
+      RTG_CUDA(c, cudaGetLastError());
+      if ((s = read_status(c)) != RTG_OK) {
+        release_out(c, out);
+        return s;
+      }
+      const long long nnz = (long long)c->h_status->nnz;
+      if (!(c->h_status->errors & rtg::kErrKeyBits) && !q.count_only && nnz > 0) {
+        void* cp = nullptr;
+        if ((s = alloc_out(c, sizeof(int32_t) * (size_t)nnz, &cp)) != RTG_OK) {
+          release_out(c, out);
+          return s;
+        }
+        out->col = (int32_t*)cp;
+        {
+          std::lock_guard<std::mutex> lk(c->live_mu);
+          c->live[out->handle] += sizeof(int32_t) * (size_t)nnz;
+        }
+        a.col = (int*)cp;
+        a.col_cap = nnz;
+        set_slot();
+        launches += rtg::launch_bits_write(a, st);
+      }
+      if (timing) {
+        RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
+        RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
+      }
+      RTG_CUDA(c, cudaGetLastError());
+      if ((s = read_status(c)) != RTG_OK) {
+        release_out(c, out);
+        return s;
+      }
+      c->h_status->pairs = c->h_status->nnz / (sym ? 2 : 1);
+      c->h_status->owned_candidates = 0;
     } else {
       set_slot();
       launches += front();
@@ -807,6 +862,7 @@ void destroy_ctx(rtg_ctx* c) {
   while (!c->graphs.empty()) drop_graph(c, c->graphs.begin()->first);
   free_buf(c, c->out_slot);
   free_buf(c, c->q_idx);
+  free_buf(c, c->bits);
   free_buf(c, c->sort_epoch);
   if (c->h_slot) cudaFreeHost(c->h_slot);
   for (auto& ev : c->ev)

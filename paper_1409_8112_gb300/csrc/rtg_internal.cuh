@@ -58,7 +58,12 @@ enum : uint32_t {
 constexpr int kSmallCell = 32;
 
 // Enumeration modes.
-enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2 };
+// kBits: every reported candidate sets its bit in the instance's bit matrix (no ownership
+// test; the matrix makes the union).
+enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2, kBits = 3 };
+
+// Largest instance the bit-matrix dedupe takes (n x ceil(n/32) words: 32 MB at this n).
+constexpr int kBitsetMaxN = 16384;
 
 // Radix pass strategies.
 enum SortMode : int { kSortLookback = 0, kSortReduceScan = 1 };
@@ -114,6 +119,8 @@ struct Inst {
   float inv_cf;   // fl32(1 / c), set by the host
   long long blk0;   // first block of this instance in the per-point kernels
   long long pblk0;  // first block of this instance in the prep kernel
+  long long bits_off;  // bit-matrix dedupe: first word of this instance's matrix
+  int bits_w;          // words per matrix row (ceil(n / 32))
 };
 
 // Per-instance results of the plan.
@@ -216,6 +223,7 @@ struct BuildArgs {
   int* col;
   long long col_cap;
   const OutSlot* out;  // device copy of the output pointers
+  unsigned int* bits;  // bit-matrix dedupe: the instances' matrices
   bool key64;
   int sort_mode;       // SortMode
   int sort_bits;       // digit width
@@ -236,6 +244,9 @@ int launch_pairs(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s);
 int launch_brute(const BuildArgs& a, Mode mode, cudaStream_t s);
 void launch_scan(const BuildArgs& a, cudaStream_t s);
 int launch_scatter(const BuildArgs& a, cudaStream_t s);
+// Bit-matrix dedupe: row counts from the matrices, then (after the scan) the columns.
+int launch_bits_count(const BuildArgs& a, cudaStream_t s);
+int launch_bits_write(const BuildArgs& a, cudaStream_t s);
 int launch_rowsort(const BuildArgs& a, cudaStream_t s);
 
 size_t sort_tiles_for(long long N, int items);

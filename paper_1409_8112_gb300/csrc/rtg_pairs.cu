@@ -120,8 +120,19 @@ struct Sink {
   unsigned long long* emitted;
   unsigned int* errors;
   unsigned long long* near_r;
+  unsigned int* bits;
   int symmetric;
 };
+
+// Bit-matrix dedupe: set bit (i, j) (and (j, i) for symmetric output) of the instance's matrix.
+__device__ __forceinline__ void deliver_bits(bool keep, unsigned int i, unsigned int j,
+                                             const Inst* __restrict__ Ip, const Sink& sk) {
+  if (!keep) return;
+  const Inst& I = *Ip;
+  const long long li = (long long)i - I.p0, lj = (long long)j - I.p0;
+  atomicOr(&sk.bits[I.bits_off + li * I.bits_w + (lj >> 5)], 1u << (lj & 31));
+  if (sk.symmetric) atomicOr(&sk.bits[I.bits_off + lj * I.bits_w + (li >> 5)], 1u << (li & 31));
+}
 
 // FP32 band of an instance as (lo, hi): FP32 decides below lo and above hi.  With the filter
 // off every candidate falls inside.
@@ -155,14 +166,16 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
   // an earlier grid owns the pair if it co-locates it; grids in batches of four (the loads of
   // a batch issued together), stopping at the first batch with a match: a close pair usually
   // shares a cell in one of the first grids
-  for (int u0 = 0; u0 < t; u0 += 4) {
-    bool earlier = false;
+  if (MODE != kBits) {
+    for (int u0 = 0; u0 < t; u0 += 4) {
+      bool earlier = false;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (u0 + q < t) earlier |= ki[u0 + q] == kj[u0 + q];
-    if (earlier) return false;
+      for (int q = 0; q < 4; ++q)
+        if (u0 + q < t) earlier |= ki[u0 + q] == kj[u0 + q];
+      if (earlier) return false;
+    }
   }
-  if (MODE != kWrite) ++tl.owned;
+  if (MODE != kWrite && MODE != kBits) ++tl.owned;
   bool keep;
   if (sf < band.x) {
     keep = true;
@@ -172,7 +185,8 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
     keep = s <= IPp->rr;
     if (MODE != kWrite) {
       ++tl.rechecks;
-      if (fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r)) atomicAdd(near_r, 1ull);
+      if (MODE != kBits && fabs(__dsub_rn(__dsqrt_rn(s), I.r)) <= __dmul_rn(1e-12, I.r))
+        atomicAdd(near_r, 1ull);
     }
   }
   if (keep && MODE != kWrite) ++tl.pairs;
@@ -495,6 +509,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
           const int k = base + lane;
           bool keep = false;
           unsigned int i = 0, j = 0;
+          int pinst = 0;
           if (k < total) {
             int o = 0;
 #pragma unroll
@@ -507,13 +522,16 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
             j = max(ia, ib);
             const unsigned int cl = w_cell[o];
             const int t = (int)(cl & 0xffu), ib_ = (int)(cl >> 8);
+            pinst = ib_;
             const K* ka = STAGE ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
             const K* kb = STAGE ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
             const float2 band = one_inst ? span_band : band_of(iplan[ib_]);
             keep = decide_pair<K, DPAD, MODE>(i, j, t, w_pt + sa * DPAD, w_pt + sb * DPAD, ka, kb,
                                               inst + ib_, iplan + ib_, band, dtype, tl, sk.near_r);
           }
-          if (MODE == kEmit) {
+          if (MODE == kBits) {
+            deliver_bits(keep, i, j, inst + pinst, sk);
+          } else if (MODE == kEmit) {
             warp_emit(keep, i, j, w_emit, ecnt, sk);
           } else {
             deliver<MODE>(keep, i, j, sk, tl);
@@ -662,7 +680,8 @@ __global__ void __launch_bounds__(kMediumWarps * 32) k_pairs_medium(
                                           inst + cell.inst, iplan + cell.inst, band, dtype, tl,
                                           sk.near_r);
       }
-      if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
+      if (MODE == kBits) deliver_bits(keep, i, j, inst + cell.inst, sk);
+      else if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
       else deliver<MODE>(keep, i, j, sk, tl);
       a += 32;  // next pair of this lane: 32 on
       while (a >= b) {
@@ -743,7 +762,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
                                           inst + cell.inst, iplan + cell.inst, band, dtype, tl,
                                           sk.near_r);
       }
-      if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
+      if (MODE == kBits) deliver_bits(keep, i, j, inst + cell.inst, sk);
+      else if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
       else deliver<MODE>(keep, i, j, sk, tl);
     }
   }
@@ -1106,6 +1126,7 @@ Sink make_sink(const BuildArgs& a) {
   sk.emitted = &a.st->emitted;
   sk.errors = &a.st->errors;
   sk.near_r = &a.st->near_r;
+  sk.bits = a.bits;
   sk.symmetric = a.symmetric;
   return sk;
 }
@@ -1171,6 +1192,7 @@ int pairs_impl(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s) {
   switch (mode) {
     case kCount: pairs_mode<K, DPAD, kCount>(a, sorted_buf, s); return 4;
     case kWrite: pairs_mode<K, DPAD, kWrite>(a, sorted_buf, s); return 3;
+    case kBits: pairs_mode<K, DPAD, kBits>(a, sorted_buf, s); return 4;
     default: pairs_mode<K, DPAD, kEmit>(a, sorted_buf, s); return 4;
   }
 }
@@ -1218,6 +1240,87 @@ void launch_scan(const BuildArgs& a, cudaStream_t s) {
   cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
   k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.out, a.n_total, a.scan_lookback,
                                &a.st->scan_tiles, a.st, tiles);
+}
+
+namespace {
+
+// Instance of a global point index (the last instance whose first point is at most i).
+__device__ __forceinline__ int instance_of(const Inst* __restrict__ inst, int B, long long i) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].p0 <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One warp per row: the row's count is the population of its matrix row.
+__global__ void __launch_bounds__(256) k_bits_count(const Inst* __restrict__ inst, int B,
+                                                    const unsigned int* __restrict__ bits,
+                                                    unsigned int* row_cnt, long long n_total) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n_total;
+       i += warps) {
+    const Inst& I = inst[instance_of(inst, B, i)];
+    const unsigned int* row = bits + I.bits_off + (i - I.p0) * I.bits_w;
+    unsigned int c = 0;
+    for (int w = lane; w < I.bits_w; w += 32) c += (unsigned int)__popc(row[w]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) row_cnt[i] = c;
+  }
+}
+
+// One warp per row: set bits become the row's columns, in ascending order (32 words at a
+// time, a warp scan placing each word's bits).
+__global__ void __launch_bounds__(256) k_bits_write(const Inst* __restrict__ inst, int B,
+                                                    const unsigned int* __restrict__ bits,
+                                                    const OutSlot* out, long long n_total) {
+  const long long* __restrict__ row_ptr = out->row_ptr;
+  int* col = out->col;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n_total;
+       i += warps) {
+    const Inst& I = inst[instance_of(inst, B, i)];
+    const unsigned int* row = bits + I.bits_off + (i - I.p0) * I.bits_w;
+    long long pos = row_ptr[i];
+    for (int w0 = 0; w0 < I.bits_w; w0 += 32) {
+      const int w = w0 + lane;
+      unsigned int word = w < I.bits_w ? row[w] : 0u;
+      const unsigned int c = (unsigned int)__popc(word);
+      unsigned int incl = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      long long p = pos + (incl - c);
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        col[p++] = (int)(I.p0 + (long long)w * 32 + b);
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+unsigned bits_blocks(const BuildArgs& a) {
+  long long blocks = (a.n_total + 7) / 8;
+  if (blocks > 16LL * a.num_sms) blocks = 16LL * a.num_sms;
+  return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+
+int launch_bits_count(const BuildArgs& a, cudaStream_t s) {
+  k_bits_count<<<bits_blocks(a), 256, 0, s>>>(a.inst, a.B, a.bits, a.row_cnt, a.n_total);
+  return 1;
+}
+
+int launch_bits_write(const BuildArgs& a, cudaStream_t s) {
+  k_bits_write<<<bits_blocks(a), 256, 0, s>>>(a.inst, a.B, a.bits, a.out, a.n_total);
+  return 1;
 }
 
 int launch_scatter(const BuildArgs& a, cudaStream_t s) {

@@ -31,6 +31,7 @@ RTG_FLAG_TIMING = 4
 RTG_FLAG_TWO_PASS = 8
 RTG_FLAG_TC_FP16 = 16
 RTG_FLAG_TC_BF16 = 32
+RTG_FLAG_BITSET = 64
 
 RTG_DTYPE_F64 = 0
 RTG_DTYPE_F32 = 1
@@ -385,7 +386,8 @@ class Context:
             pass
 
     def all_pairs(self, points, r: float, transforms: np.ndarray, cell_side: float,
-                  symmetric: bool = False, timing: bool = False, two_pass: bool = False) -> Result:
+                  symmetric: bool = False, timing: bool = False, two_pass: bool = False,
+                  bitset: bool = False) -> Result:
         ptr, code, on_dev, n, d, keep = _points_arg(points)
         self._after_producer(keep)
         T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
@@ -393,14 +395,14 @@ class Context:
             raise ValueError("transforms must hold m * (d*d + d) values")
         m = T.size // (d * d + d)
         flags = ((RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0) |
-                 (RTG_FLAG_TWO_PASS if two_pass else 0))
+                 (RTG_FLAG_TWO_PASS if two_pass else 0) | (RTG_FLAG_BITSET if bitset else 0))
         csr = rtg_all_pairs(self.handle, ptr, code, on_dev, n, d, float(r), T, m,
                             float(cell_side), flags)
         del keep
         return Result(self, csr, m)
 
     def batch_all_pairs(self, instances, m: int, symmetric: bool = False, timing: bool = False,
-                        two_pass: bool = False):
+                        two_pass: bool = False, bitset: bool = False):
         """instances: list of (points, r, transforms, cell_side); points all numpy (host) or
         all CUDA tensors, one dtype.  Returns (Result over the block-diagonal CSR, offsets)."""
         items, keep, codes, devs = [], [], set(), set()
@@ -417,7 +419,7 @@ class Context:
         if len(codes) != 1 or len(devs) != 1:
             raise ValueError("all instances need the same dtype and the same location")
         flags = ((RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0) |
-                 (RTG_FLAG_TWO_PASS if two_pass else 0))
+                 (RTG_FLAG_TWO_PASS if two_pass else 0) | (RTG_FLAG_BITSET if bitset else 0))
         csr, offs = rtg_batch_all_pairs(self.handle, items, m, codes.pop(), devs.pop(), flags)
         del keep
         return Result(self, csr, m), offs

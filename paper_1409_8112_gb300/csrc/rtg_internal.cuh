@@ -31,7 +31,7 @@ constexpr int kMaxDim = 16;
 constexpr int kMaxGrids = 64;
 constexpr int kMaxPasses = 8;  // radix passes of the narrowest digit (8 bits) over a 64-bit key
 // Digit widths and tile sizes the radix sort is compiled for.
-constexpr int kSortBitsChoices[] = {8, 11};
+constexpr int kSortBitsChoices[] = {8, 10, 11};
 constexpr int kSortItemsChoices[] = {8, 12, 16};
 constexpr int kSortCountWords = 6 * 2048;  // passes * digits, largest over the digit widths
 __host__ __device__ inline int sort_passes_for(int key_bits, int radix_bits) {
@@ -70,7 +70,7 @@ enum SortMode : int { kSortLookback = 0, kSortReduceScan = 1 };
 
 // One compiled variant of the sort and its pass strategy.
 struct SortConfig {
-  int bits = 8;   // digit width: 8 or 11
+  int bits = 8;   // digit width: 8, 10 or 11
   int items = 8;  // keys per thread: 8, 12 or 16 (tiles of 256 * items keys)
   int mode = kSortReduceScan;
 };

@@ -2,7 +2,7 @@
 // (Alg. 1 lines 4-7 of arXiv:1409.8112 associate each point with its cell; the sort makes
 // every cell a contiguous run).  Stable.
 //
-// Compile-time variants: digit width BITS (8 or 11 bits per pass, so a key of b bits takes
+// Compile-time variants: digit width BITS (8, 10 or 11 bits per pass, so a key of b bits takes
 // ceil(b / BITS) passes) and ITEMS keys per thread (tiles of 256 * ITEMS keys).  The
 // autotuner in the host code picks one variant and one pass strategy per shape.
 //
@@ -486,7 +486,11 @@ int sort_items(const BuildArgs& a, cudaStream_t s) {
 
 template <typename K>
 int sort_width(const BuildArgs& a, cudaStream_t s) {
-  return a.sort_bits == 11 ? sort_items<K, 11>(a, s) : sort_items<K, 8>(a, s);
+  switch (a.sort_bits) {
+    case 10: return sort_items<K, 10>(a, s);
+    case 11: return sort_items<K, 11>(a, s);
+    default: return sort_items<K, 8>(a, s);
+  }
 }
 
 }  // namespace

@@ -1,4 +1,4 @@
-// Autotuner of the radix sort: digit width (8 or 11 bits per pass), tile size (256 x 8, 12
+// Autotuner of the radix sort: digit width (8, 10 or 11 bits per pass), tile size (256 x 8, 12
 // or 16 keys) and pass strategy (look-back or reduce-then-scan).  On the first build of a
 // shape whose sort is large enough to matter it times every variant twice on the build's own
 // keys and keeps the fastest, per (sorted elements, key bits), in the context and, when

@@ -12,7 +12,8 @@ from paper_1409_8112_gb300 import gen, rtg
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(bits, items, mode) for bits in (8, 11) for items in (8, 12, 16) for mode in (0, 1)]
+VARIANTS = [(bits, items, mode) for bits in (8, 10, 11) for items in (8, 12, 16)
+            for mode in (0, 1)]
 
 
 def _context(env):

@@ -43,6 +43,9 @@ struct SortShape {
                                   (size_t)kSortWarps * kDigits * 2;
 };
 
+#ifndef RTG_SORT_WIN
+#define RTG_SORT_WIN 4  // look-back window: predecessors read per round
+#endif
 constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull;
 constexpr unsigned int kSpinLimit = 1u << 22;
 
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     if (tile > 0) {
       // a window of kWin predecessors at a time (independent loads), adding aggregates until
       // an inclusive prefix is found
-      constexpr int kWin = 8;
+      constexpr int kWin = RTG_SORT_WIN;
       long long p = (long long)tile - 1;
       unsigned int spins = 0;
       while (p >= 0) {

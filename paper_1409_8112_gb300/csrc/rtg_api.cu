@@ -528,7 +528,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         l += 1;
         if (timing) mark(2);
         sorted = rtg::launch_sort(a, st);
-        l += (a.passes > 0 && N > 1) ? 1 + (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
+        l += (a.passes > 0 && N > 1) ? (rtg::hist_in_keys(a) ? 0 : 1) +
+                                           (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
                                      : 0;
       } else if (timing) {
         mark(2);

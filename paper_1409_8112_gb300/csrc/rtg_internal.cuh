@@ -233,6 +233,73 @@ struct BuildArgs {
   int num_sms;
 };
 
+// With 8-bit digits the key kernel also counts the digits of every radix pass (the sort then
+// needs no histogram kernel).
+inline bool hist_in_keys(const BuildArgs& a) { return a.sort_bits == 8 && a.passes > 0; }
+
+// Radix digit counting shared by the key and histogram kernels (256 digits per pass).  Adds one
+// per valid lane; a warp whose lanes share one digit (the high digits of neighbouring keys)
+// makes a single add.  Called by all 32 lanes.
+__device__ __forceinline__ void count_digit256(unsigned int* sh, unsigned int dg, bool valid,
+                                               unsigned int vmask) {
+  const unsigned int d0 = __shfl_sync(0xffffffffu, dg, 0);
+  if (__all_sync(0xffffffffu, !valid || dg == d0)) {
+    if ((threadIdx.x & 31) == 0 && vmask) atomicAdd(&sh[d0], (unsigned int)__popc(vmask));
+  } else if (valid) {
+    atomicAdd(&sh[dg], 1u);
+  }
+}
+
+// End of a digit count: the block adds its counts to the global ones; the last block to finish
+// turns them into exclusive digit offsets (digit_off[p * 256 + digit]), clears the counts for
+// the next sort and advances the look-back epoch.  Any block size that is a multiple of 32 and
+// divides 256.
+__device__ __forceinline__ void finish_digit_count256(const unsigned int* sh, int passes,
+                                                      unsigned int* hist, unsigned int* digit_off,
+                                                      unsigned int* ticket, unsigned int* epoch) {
+  __shared__ unsigned int s_w[32];
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int x = tid; x < passes * 256; x += nt)
+    if (sh[x]) atomicAdd(&hist[x], sh[x]);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int per = 256 / nt, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int p = 0; p < passes; ++p) {
+    unsigned int v[8], sum = 0;
+    for (int q = 0; q < per; ++q) {
+      v[q] = __ldcg(&hist[p * 256 + tid * per + q]);
+      sum += v[q];
+    }
+    unsigned int x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    unsigned int run = x - sum;
+    for (int w = 0; w < warp; ++w) run += s_w[w];
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+      digit_off[p * 256 + tid * per + q] = run;
+      run += v[q];
+      hist[p * 256 + tid * per + q] = 0;  // ready for the next sort
+    }
+    (void)nw;
+  }
+  if (tid == 0) {
+    *ticket = 0;
+    unsigned int e = *epoch + kMaxPasses;  // a fresh look-back epoch, never 0
+    if ((e & 0x3fffffffu) < (unsigned int)kMaxPasses) e = 1;
+    *epoch = e;
+  }
+}
+
 // FP32 rows, zeroed row counters, bounding boxes and the plan (in the prep kernel's last block
 // for small batches); returns the kernels launched.
 int launch_prep_plan(const BuildArgs& a, cudaStream_t s);

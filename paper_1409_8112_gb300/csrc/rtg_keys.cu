@@ -372,8 +372,11 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     const Inst* __restrict__ inst, int B, int m, int dtype, const float* __restrict__ pf,
     const double* __restrict__ T64, const GridPlan* __restrict__ gplan, InstPlan* iplan,
     const unsigned long long* bbox, Status* st, K* __restrict__ key_mat, K* __restrict__ comp,
-    uint32_t* __restrict__ vals) {
+    uint32_t* __restrict__ vals, int hist_passes, unsigned int* hist, unsigned int* digit_off,
+    unsigned int* sort_epoch) {
   __shared__ int s_b;
+  __shared__ unsigned int s_hist[kMaxPasses * 256];  // 8-bit digit counts of every pass
+  for (int x = threadIdx.x; x < hist_passes * 256; x += blockDim.x) s_hist[x] = 0;
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = block_instance<false>(inst, B, blockIdx.x, &s_b);
   const Inst I = inst[b];
@@ -407,13 +410,15 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
   const long long i = (blockIdx.x - I.blk0) * (long long)kPointBlock + threadIdx.x;
   unsigned int near_cnt = 0, rechecks = 0;
   bool range_err = false;
-  if (i < I.n) {
-    const long long g = I.p0 + i;
+  const bool valid = i < I.n;
+  const unsigned int vmask = __ballot_sync(0xffffffffu, valid);
+  {
+    const long long g = I.p0 + (valid ? i : 0);
     float p[DPAD];
     const float4* src = reinterpret_cast<const float4*>(pf + g * DPAD);
 #pragma unroll
     for (int v = 0; v < DPAD / 4; ++v) {
-      const float4 q = src[v];
+      const float4 q = valid ? src[v] : make_float4(0.f, 0.f, 0.f, 0.f);
       p[4 * v] = q.x;
       p[4 * v + 1] = q.y;
       p[4 * v + 2] = q.z;
@@ -421,10 +426,10 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     }
     const int tstride = d * d + d;
     K* krow = key_mat + (size_t)g * m;
-    for (int t = 0; t < m; ++t) {
+    for (int t = 0; t < m; ++t) {  // every lane takes every grid (warp votes below)
       K key = 0;
       bool near = false;
-      for (int k = 0; k < d; ++k) {
+      for (int k = 0; k < d && valid; ++k) {
         const float* Rk = sR + (t * d + k) * DPAD;
         float y = ss[t * d + k];
 #pragma unroll
@@ -447,11 +452,15 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
         key += (K)off * (K)sstr[t * d + k];
       }
       key += (K)sbase[t];
-      krow[t] = key;
-      const long long pos = I.p0 * m + (long long)t * I.n + i;
-      comp[pos] = key;
-      vals[pos] = (uint32_t)g;
-      near_cnt += near ? 1u : 0u;
+      if (valid) {
+        krow[t] = key;
+        const long long pos = I.p0 * m + (long long)t * I.n + i;
+        comp[pos] = key;
+        vals[pos] = (uint32_t)g;
+        near_cnt += near ? 1u : 0u;
+      }
+      for (int q = 0; q < hist_passes; ++q)
+        count_digit256(s_hist + q * 256, (unsigned int)(key >> (8 * q)) & 255u, valid, vmask);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -463,6 +472,10 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     if (rechecks) atomicAdd(&st->key_rechecks, (unsigned long long)rechecks);
   }
   if (range_err) atomicOr(&st->errors, kErrKeyRange);
+  if (hist_passes > 0) {
+    __syncthreads();
+    finish_digit_count256(s_hist, hist_passes, hist, digit_off, &st->hist_ticket, sort_epoch);
+  }
 }
 
 // Batches up to this many (instance, grid, axis) items plan in the prep kernel's last block.
@@ -500,7 +513,8 @@ void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
   }
   k_keys<K, DPAD><<<(unsigned)a.blocks, kPointBlock, smem, s>>>(
       a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st, (K*)a.key_mat,
-      (K*)a.keys[0], a.vals[0]);
+      (K*)a.keys[0], a.vals[0], hist_in_keys(a) ? a.passes : 0, a.hist, a.digit_off,
+      a.sort_epoch);
 }
 
 }  // namespace

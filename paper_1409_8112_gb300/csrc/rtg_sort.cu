@@ -445,10 +445,12 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
   if (passes <= 0 || N <= 1) return 0;
   long long hb = (N + kSortThreads - 1) / kSortThreads;
   if (hb > 4LL * a.num_sms) hb = 4LL * a.num_sms;
-  static bool hist_attr[64] = {};
-  set_smem_once(k_sort_hist<K, BITS>, (size_t)kSortCountWords * 4, hist_attr);
-  k_sort_hist<K, BITS><<<(unsigned)hb, kSortThreads, (size_t)passes * D * 4, s>>>(
-      (const K*)a.keys[0], N, passes, a.hist, a.digit_off, &a.st->hist_ticket, a.sort_epoch);
+  if (!hist_in_keys(a)) {  // else the key kernel has counted the digits
+    static bool hist_attr[64] = {};
+    set_smem_once(k_sort_hist<K, BITS>, (size_t)kSortCountWords * 4, hist_attr);
+    k_sort_hist<K, BITS><<<(unsigned)hb, kSortThreads, (size_t)passes * D * 4, s>>>(
+        (const K*)a.keys[0], N, passes, a.hist, a.digit_off, &a.st->hist_ticket, a.sort_epoch);
+  }
   const unsigned tiles = (unsigned)((N + SS::kTile - 1) / SS::kTile);
   int cur = 0;
   if (a.sort_mode == kSortLookback) {

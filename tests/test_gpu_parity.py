@@ -317,3 +317,17 @@ def test_launch_assumptions_are_corrected():
     ra.release()
     rb.release()
     ctx.close()
+
+
+@pytest.mark.parametrize("flags,ct", [(0, 1.1), (0, 1.6), (gen.SHIFT_ONLY, 1.35)])
+def test_cells_wider_than_r_use_parity_signatures(ctx, flags, ct):
+    # c well above r: the earlier-grid test of the medium and large cells runs on cell-parity
+    # signatures; clustered points make many such cells
+    n, d, m = 12000, 4, 12
+    pts = np.concatenate([gen.points_uniform(81, n // 2, d),
+                          gen.points_mixture(82, n - n // 2, d, k=3, sigma=0.03,
+                                             dtype=np.float64)])
+    r = gen.radius_for_degree(n, d)
+    T = gen.transforms(83, d, m, ct * r, flags=flags)
+    st, ref = run_and_compare(ctx, pts, r, T, ct * r)
+    assert st["large_cells"] > 0

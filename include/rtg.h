@@ -175,9 +175,9 @@ rtg_status rtg_transforms_generate(uint64_t seed, int d, int m, double cell_side
  *   cell_side  grid cell side c (> 0, finite); the paper takes c = c~ r with c~ > 1
  *   flags      RTG_FLAG_SYMMETRIC, RTG_FLAG_TIMING
  *   out        receives a library-owned device CSR; free it with rtg_release
- * Errors: RTG_E_INVALID (n < 0 or n >= 2^31, d outside [1,16], m outside [1,64], r or c not
- * positive and finite, a non-finite coordinate or transform entry, a coordinate beyond the
- * FP32 range), RTG_E_KEY_OVERFLOW,
+ * Errors: RTG_E_INVALID (n < 0 or n >= 2^31, n * m >= 2^31, d outside [1,16], m outside
+ * [1,64], r or c not positive and finite, a non-finite coordinate or transform entry, a
+ * coordinate beyond the FP32 range), RTG_E_KEY_OVERFLOW,
  * RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT.  n in {0, 1} gives an empty CSR. */
 rtg_status rtg_all_pairs(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
                          int64_t n, int d, double r, const double* transforms, int m,

@@ -143,6 +143,8 @@ rtg_status check_errors(rtg_ctx* c, unsigned int mask) {
   if (e & rtg::kErrKeyRange)
     return fail(c, RTG_E_INTERNAL, "a cell index fell outside the planned key range");
   if (e & rtg::kErrLargeOverflow) return fail(c, RTG_E_INTERNAL, "large-cell list overflow");
+  if (e & rtg::kErrSortRange)
+    return fail(c, RTG_E_INTERNAL, "a sort tile or offset fell outside the keys");
   if (e & rtg::kErrColOverflow) return fail(c, RTG_E_INTERNAL, "column buffer overflow");
   return fail(c, RTG_E_INTERNAL, "device error flags " + std::to_string(e));
 }

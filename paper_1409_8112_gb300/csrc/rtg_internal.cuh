@@ -51,7 +51,8 @@ enum : uint32_t {
   kErrKeyRange = 32u,       // a cell index fell outside the planned range (internal)
   kErrLargeOverflow = 64u,  // large-cell list full (internal)
   kErrPairOverflow = 128u,  // pair buffer too small (host re-runs bigger)
-  kErrQueryRange = 256u     // a neighbour query names a point outside the graph
+  kErrQueryRange = 256u,    // a neighbour query names a point outside the graph
+  kErrSortRange = 512u      // a sort tile or offset fell outside the keys (internal)
 };
 
 // Cells with more points than this are enumerated by the tiled large-cell kernel.

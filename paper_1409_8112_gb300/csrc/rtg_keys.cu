@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
   const int b = block_instance<false>(inst, B, blockIdx.x, &s_b);
   const Inst I = inst[b];
   const int d = I.d;
-  // layout: qlo, ext, stride (m*d 8-byte each), base (m), R (m*d*DPAD floats), s, E (m*d)
+  // layout: qlo, ext, stride (m*d 8-byte each), base (m), R (m*d*DPAD floats), s, E (m*d),
+  // then the block's key rows (kPointBlock rows of m keys, m + 1 apart), written out together
   long long* sqlo = reinterpret_cast<long long*>(smem);
   unsigned long long* sext = reinterpret_cast<unsigned long long*>(sqlo + m * d);
   unsigned long long* sstr = sext + m * d;
@@ -389,6 +390,7 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
   float* sR = reinterpret_cast<float*>(sbase + m);
   float* ss = sR + m * d * DPAD;
   float* sE = ss + m * d;
+  K* s_krow = reinterpret_cast<K*>(sE + m * d);
   const GridPlan* Gb = gplan + (size_t)b * m;
   for (int x = threadIdx.x; x < m * d; x += blockDim.x) {
     const int t = x / d, k = x % d;
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
       p[4 * v + 3] = q.w;
     }
     const int tstride = d * d + d;
-    K* krow = key_mat + (size_t)g * m;
+    K* krow = s_krow + threadIdx.x * (m + 1);
     for (int t = 0; t < m; ++t) {  // every lane takes every grid (warp votes below)
       K key = 0;
       bool near = false;
@@ -436,10 +438,13 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
         for (int l = 0; l < DPAD; ++l) y = fmaf(Rk[l], p[l], y);
         const float u = y * inv_c;
         const float E = sE[t * d + k];
-        const float flo = floorf(__fsub_rd(u, E)), fhi = floorf(__fadd_ru(u, E));
+        // the FP32 index is certain when [u - E, u + E] holds no cell wall: both ends (rounded
+        // outwards) lie in [floor(u), floor(u) + 1).  |u| >= 2^23 always fails (u is then an
+        // integer and u - E < u), so floor(u) is exact in 32-bit integers here.
+        const float f = floorf(u);
         long long q;
-        if (flo == fhi) {
-          q = (long long)flo;
+        if (__fsub_rd(u, E) >= f && __fadd_ru(u, E) < f + 1.0f) {
+          q = (long long)(int)f;
         } else {
           q = exact_cell(I.pts, dtype, i, d, T64 + I.T0 + (size_t)t * tstride, k, c, &near);
           ++rechecks;
@@ -472,8 +477,17 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     if (rechecks) atomicAdd(&st->key_rechecks, (unsigned long long)rechecks);
   }
   if (range_err) atomicOr(&st->errors, kErrKeyRange);
+  __syncthreads();
+  {  // the block's key rows are one contiguous stretch of key_mat: coalesced copy-out
+    const long long i0 = (blockIdx.x - I.blk0) * (long long)kPointBlock;
+    const unsigned int words = (unsigned int)max(0LL, min((long long)kPointBlock, I.n - i0)) * m;
+    K* dst = key_mat + (size_t)(I.p0 + i0) * m;
+    for (unsigned int w = threadIdx.x; w < words; w += kPointBlock) {
+      const unsigned int row = w / (unsigned int)m;
+      dst[w] = s_krow[row * (m + 1) + (w - row * m)];
+    }
+  }
   if (hist_passes > 0) {
-    __syncthreads();
     finish_digit_count256(s_hist, hist_passes, hist, digit_off, &st->hist_ticket, sort_epoch);
   }
 }
@@ -503,11 +517,14 @@ void prep_impl(const BuildArgs& a, cudaStream_t s) {
 
 template <typename K, int DPAD>
 void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
-  const size_t smem = (size_t)a.m * maxd * (3 * 8 + (DPAD + 2) * 4) + (size_t)a.m * 8;
+  const size_t smem = (size_t)a.m * maxd * (3 * 8 + (DPAD + 2) * 4) + (size_t)a.m * 8 +
+                      (size_t)kPointBlock * (a.m + 1) * sizeof(K);
+  // the 48 KB default covers static and dynamic shared memory together (the digit counts
+  // are static), so the limit is raised to every new largest size, not only above 48 KB
   static size_t attr_smem[64] = {};  // largest size granted so far, per device
   int dev = 0;
   cudaGetDevice(&dev);
-  if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || smem > attr_smem[dev])) {
+  if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
     cudaFuncSetAttribute(k_keys<K, DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
   }

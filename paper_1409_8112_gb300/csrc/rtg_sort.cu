@@ -317,18 +317,26 @@ struct TileRank {
     }
   }
 
-  // Writes the reordered tile (after a barrier that publishes s_gbase and the tile).
+  // Writes the reordered tile (after a barrier that publishes s_gbase and the tile).  Offsets
+  // outside [0, N) (digit counts that do not belong to these keys) are dropped and flagged.
   __device__ void write(K* __restrict__ kout, uint32_t* __restrict__ vout, long long N,
-                        long long tile_base, int shift) {
+                        long long tile_base, int shift, unsigned int* errors) {
     const long long rem = N - tile_base;
     const int tvalid = rem < kTile ? (int)rem : kTile;
+    const unsigned int nu = (unsigned int)N;  // the host keeps N below 2^31
+    bool bad = false;
     for (int x = threadIdx.x; x < tvalid; x += kSortThreads) {
       const K k = s_keys[x];
       const unsigned int dg = (unsigned int)(k >> shift) & (D - 1);
       const unsigned int dst = s_gbase[dg] + (unsigned int)x - s_tdig[dg];
-      kout[dst] = k;
-      vout[dst] = s_vals[x];
+      if (dst < nu) {
+        kout[dst] = k;
+        vout[dst] = s_vals[x];
+      } else {
+        bad = true;
+      }
     }
+    if (bad) atomicOr(errors, kErrSortRange);
   }
 };
 
@@ -336,7 +344,7 @@ template <typename K, int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ offs,
-    unsigned int tiles) {
+    unsigned int tiles, unsigned int* errors) {
   using TR = TileRank<K, BITS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned int sbuf[kSortWarps];
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
   unsigned int tcount[TR::PT];
   tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf);
   __syncthreads();
-  tr.write(kout, vout, N, tile_base, shift);
+  tr.write(kout, vout, N, tile_base, shift, errors);
 }
 
 // Single-kernel pass with decoupled look-back (tiles take their index from an atomic
@@ -369,6 +377,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
   __syncthreads();
   const unsigned int tile = s_tile;
+  // one index per launched tile (the counter starts at zero); anything else is flagged
+  if ((long long)tile * TR::kTile >= N) {
+    if (tid == 0) atomicOr(errors, kErrSortRange);
+    return;
+  }
   const unsigned int epoch = *epoch_base + (unsigned int)pass;
   const long long tile_base = (long long)tile * TR::kTile;
   unsigned int tcount[PT];
@@ -422,7 +435,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     tr.s_gbase[d] = digit_off[d] + excl;
   }
   __syncthreads();
-  tr.write(kout, vout, N, tile_base, shift);
+  tr.write(kout, vout, N, tile_base, shift, errors);
 }
 
 // Sets a kernel's dynamic shared-memory limit once per device (static shared memory adds to
@@ -474,7 +487,7 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
     k_sort_scan<<<D, 1024, 0, s>>>(counts, tiles, a.digit_off + p * D);
     k_sort_downsweep<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
         (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, shift,
-        counts, tiles);
+        counts, tiles, &a.st->errors);
     cur = 1 - cur;
   }
   return cur;

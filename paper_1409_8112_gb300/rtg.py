@@ -264,8 +264,9 @@ def rtg_release(ctx, csr: rtg_csr) -> None:
 
 
 def rtg_csr_download(ctx, csr: rtg_csr):
-    row_ptr = np.zeros(csr.n + 1, dtype=np.int64)
-    col = np.zeros(max(csr.nnz, 0), dtype=np.int32)
+    # every element is written by the copy (fresh zeroed pages would fault during it)
+    row_ptr = np.empty(csr.n + 1, dtype=np.int64)
+    col = np.empty(max(csr.nnz, 0), dtype=np.int32)
     _check(lib().rtg_csr_download(ctx, ctypes.byref(csr), row_ptr.ctypes.data,
                                   col.ctypes.data if csr.nnz > 0 else None), ctx)
     return row_ptr, col

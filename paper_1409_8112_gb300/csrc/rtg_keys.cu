@@ -367,6 +367,25 @@ __device__ __noinline__ long long exact_cell(const void* pts, int dtype, long lo
   return (long long)floor(u);
 }
 
+// One (grid, axis) row of the key computation, 16-byte aligned in shared memory so that a
+// thread reads it with a few vector loads: the FP32 rotation row, the FP32 shift and error
+// bound, and the axis's cell range and key stride.
+template <int DPAD>
+struct __align__(16) AxisRow {
+  float R[DPAD];
+  float s, E;
+  float pad0, pad1;
+  long long qlo;
+  unsigned long long ext;
+  unsigned long long stride;
+  unsigned long long pad2;
+};
+
+template <int DPAD>
+constexpr size_t axis_row_bytes() {
+  return sizeof(AxisRow<DPAD>);
+}
+
 template <typename K, int DPAD>
 __global__ void __launch_bounds__(kPointBlock) k_keys(
     const Inst* __restrict__ inst, int B, int m, int dtype, const float* __restrict__ pf,
@@ -381,30 +400,24 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
   const int b = block_instance<false>(inst, B, blockIdx.x, &s_b);
   const Inst I = inst[b];
   const int d = I.d;
-  // layout: qlo, ext, stride (m*d 8-byte each), base (m), R (m*d*DPAD floats), s, E (m*d),
-  // then the block's key rows (kPointBlock rows of m keys, m + 1 apart), written out together
-  long long* sqlo = reinterpret_cast<long long*>(smem);
-  unsigned long long* sext = reinterpret_cast<unsigned long long*>(sqlo + m * d);
-  unsigned long long* sstr = sext + m * d;
-  unsigned long long* sbase = sstr + m * d;
-  float* sR = reinterpret_cast<float*>(sbase + m);
-  float* ss = sR + m * d * DPAD;
-  float* sE = ss + m * d;
-  K* s_krow = reinterpret_cast<K*>(sE + m * d);
+  // layout: the m*d axis rows (grid-major), the m grid bases, then the block's key rows
+  // (kPointBlock rows of m keys, m + 1 apart), written out together at the end
+  AxisRow<DPAD>* rows = reinterpret_cast<AxisRow<DPAD>*>(smem);
+  unsigned long long* sbase = reinterpret_cast<unsigned long long*>(rows + m * d);
+  K* s_krow = reinterpret_cast<K*>(sbase + m);
   const GridPlan* Gb = gplan + (size_t)b * m;
   for (int x = threadIdx.x; x < m * d; x += blockDim.x) {
-    const int t = x / d, k = x % d;
-    sqlo[x] = Gb[t].qlo[k];
-    sext[x] = Gb[t].ext[k];
-    sstr[x] = Gb[t].stride[k];
-    ss[x] = Gb[t].sf[k];
-    sE[x] = Gb[t].E[k];
+    const int t = x / d, k = x - t * d;
+    AxisRow<DPAD>& A = rows[x];
+#pragma unroll
+    for (int l = 0; l < DPAD; ++l) A.R[l] = Gb[t].Rf[k * kMaxDim + l];
+    A.s = Gb[t].sf[k];
+    A.E = Gb[t].E[k];
+    A.qlo = Gb[t].qlo[k];
+    A.ext = Gb[t].ext[k];
+    A.stride = Gb[t].stride[k];
   }
   for (int t = threadIdx.x; t < m; t += blockDim.x) sbase[t] = Gb[t].base;
-  for (int x = threadIdx.x; x < m * d * DPAD; x += blockDim.x) {
-    const int t = x / (d * DPAD), rem = x % (d * DPAD), k = rem / DPAD, l = rem % DPAD;
-    sR[x] = Gb[t].Rf[k * kMaxDim + l];
-  }
   __syncthreads();
   const float inv_c = I.inv_cf;
   if (threadIdx.x == 0 && blockIdx.x == I.blk0) plan_band(b, I, dtype, bbox, iplan);
@@ -428,44 +441,56 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     }
     const int tstride = d * d + d;
     K* krow = s_krow + threadIdx.x * (m + 1);
+    const long long pos0 = I.p0 * m + i;
     for (int t = 0; t < m; ++t) {  // every lane takes every grid (warp votes below)
-      K key = 0;
+      K key = (K)sbase[t];
       bool near = false;
-      for (int k = 0; k < d && valid; ++k) {
-        const float* Rk = sR + (t * d + k) * DPAD;
-        float y = ss[t * d + k];
+      const AxisRow<DPAD>* A = rows + t * d;
+      for (int k = 0; k < d && valid; ++k, ++A) {
+        const float2 se = *reinterpret_cast<const float2*>(&A->s);
+        float y = se.x;
 #pragma unroll
-        for (int l = 0; l < DPAD; ++l) y = fmaf(Rk[l], p[l], y);
+        for (int v = 0; v < DPAD / 4; ++v) {
+          const float4 r = reinterpret_cast<const float4*>(A->R)[v];
+          y = fmaf(r.x, p[4 * v], y);
+          y = fmaf(r.y, p[4 * v + 1], y);
+          y = fmaf(r.z, p[4 * v + 2], y);
+          y = fmaf(r.w, p[4 * v + 3], y);
+        }
         const float u = y * inv_c;
-        const float E = sE[t * d + k];
         // the FP32 index is certain when [u - E, u + E] holds no cell wall: both ends (rounded
         // outwards) lie in [floor(u), floor(u) + 1).  |u| >= 2^23 always fails (u is then an
         // integer and u - E < u), so floor(u) is exact in 32-bit integers here.
         const float f = floorf(u);
         long long q;
-        if (__fsub_rd(u, E) >= f && __fadd_ru(u, E) < f + 1.0f) {
+        if (__fsub_rd(u, se.y) >= f && __fadd_ru(u, se.y) < f + 1.0f) {
           q = (long long)(int)f;
         } else {
           q = exact_cell(I.pts, dtype, i, d, T64 + I.T0 + (size_t)t * tstride, k, c, &near);
           ++rechecks;
         }
-        long long off = q - sqlo[t * d + k];
-        if ((unsigned long long)off >= sext[t * d + k]) {
+        const longlong2 qe = *reinterpret_cast<const longlong2*>(&A->qlo);
+        long long off = q - qe.x;
+        if ((unsigned long long)off >= (unsigned long long)qe.y) {
           range_err = true;
           off = 0;
         }
-        key += (K)off * (K)sstr[t * d + k];
+        key += (K)off * (K)A->stride;
       }
-      key += (K)sbase[t];
       if (valid) {
         krow[t] = key;
-        const long long pos = I.p0 * m + (long long)t * I.n + i;
+        const long long pos = pos0 + (long long)t * I.n;
         comp[pos] = key;
         vals[pos] = (uint32_t)g;
         near_cnt += near ? 1u : 0u;
       }
-      for (int q = 0; q < hist_passes; ++q)
-        count_digit256(s_hist + q * 256, (unsigned int)(key >> (8 * q)) & 255u, valid, vmask);
+      // digit counts: the low digits of neighbouring points differ, so only the top digit
+      // (mostly the grid's base) tries the one-add-per-warp path
+      for (int q = 0; q + 1 < hist_passes; ++q)
+        if (valid) atomicAdd(&s_hist[q * 256 + ((unsigned int)(key >> (8 * q)) & 255u)], 1u);
+      if (hist_passes > 0)
+        count_digit256(s_hist + (hist_passes - 1) * 256,
+                       (unsigned int)(key >> (8 * (hist_passes - 1))) & 255u, valid, vmask);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -517,7 +542,7 @@ void prep_impl(const BuildArgs& a, cudaStream_t s) {
 
 template <typename K, int DPAD>
 void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
-  const size_t smem = (size_t)a.m * maxd * (3 * 8 + (DPAD + 2) * 4) + (size_t)a.m * 8 +
+  const size_t smem = (size_t)a.m * maxd * axis_row_bytes<DPAD>() + (size_t)a.m * 8 +
                       (size_t)kPointBlock * (a.m + 1) * sizeof(K);
   // the 48 KB default covers static and dynamic shared memory together (the digit counts
   // are static), so the limit is raised to every new largest size, not only above 48 KB

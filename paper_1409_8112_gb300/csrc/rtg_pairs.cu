@@ -1145,9 +1145,12 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   const bool stage_rows = a.m * (int)sizeof(K) <= kMaxStagedRow;
   const int wbytes = warp_region_bytes<K, DPAD>(a.m, stage_rows);
   const size_t smem = (size_t)wbytes * kWarps;
-  // spans of a multiple of 32 positions, about two per resident warp, 64..1024 positions
+  // spans of a multiple of 32 positions (64..1024): the fewest whole waves of resident warps
+  // whose spans stay within 1024 positions, so that no partial wave of long spans trails
   const long long resident = 4LL * a.num_sms * kWarps;
-  long long span = (N + 2 * resident - 1) / (2 * resident);
+  long long waves = (N + 1024 * resident - 1) / (1024 * resident);
+  if (waves < 1) waves = 1;
+  long long span = (N + waves * resident - 1) / (waves * resident);
   span = (span + 31) / 32 * 32;
   span = span < 64 ? 64 : (span > 1024 ? 1024 : span);
   const long long nspans = (N + span - 1) / span;

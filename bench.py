@@ -163,27 +163,38 @@ def measured_peaks():
 
 
 # Algorithmic bytes per build for each timed phase (lower-bound model):
-#   sort  : upfront histogram reads the N keys once; each pass reads and writes N (key, index)
+#   sort  : each pass reads and writes the N (key, index) pairs; with digits wider than 8 bits
+#           a histogram kernel first reads the N keys once (8-bit digits are counted by the key
+#           kernel as it writes the keys)
 #   pairs : reads the N sorted (key, index) pairs, gathers each point's padded FP32 row and
 #           writes 8 bytes per reported pair
 # DRAM bytes (read + write) of each phase's kernels per build, from ncu
-# (profiles/dram_rtg_all_pairs_n100k_and_n1m.md; cold replays, one build).  Only for the two
-# profiled workloads; to be refreshed whenever those kernels change.
+# (profiles/dram_rtg_all_pairs_n100k_and_n1m.md; cold replays, one build), for the two
+# profiled workloads and, for the sort, the variant the profiled run used
+# (digit bits, keys per tile, look-back).  None where the kernels changed after the capture.
 NCU_TRAFFIC = {
-    (100000, "fp64"): {"prep": 4890880, "keys": 3645696, "sort": 30044416, "pairs": 13268224,
-                       "scan": 412160, "scatter": 4858112, "rowsort": 2653184},
-    (1000000, "fp32"): {"prep": 24097280, "keys": 65918976, "sort": 361427200,
-                        "pairs": 311729920, "scan": 4013568, "scatter": 90754560,
-                        "rowsort": 32083712},
+    (100000, "fp64"): {"prep": 4870656, "keys": None, "sort": {(8, 3072, 1): 26580224},
+                       "pairs": 13299200, "scan": 412160, "scatter": 4857600, "rowsort": 2714368},
+    (1000000, "fp32"): {"prep": 24076032, "keys": None, "sort": {(8, 3072, 0): 454930432},
+                        "pairs": 311938560, "scan": 4014080, "scatter": 90723072,
+                        "rowsort": 32142592},
 }
 
 
-def phase_bytes(n, d, m, key_bytes, passes, dpad, pairs):
+def phase_bytes(n, d, m, key_bytes, passes, dpad, pairs, digit_bits=8):
     N = n * m
+    hist_read = N * key_bytes if digit_bits != 8 else 0
     return {
-        "sort": N * key_bytes + passes * 2 * N * (key_bytes + 4),
+        "sort": hist_read + passes * 2 * N * (key_bytes + 4),
         "pairs": N * (key_bytes + 4) + N * dpad * 4 + 8 * pairs,
     }
+
+
+def ncu_traffic(n, dtype, phase, sort_cfg):
+    t = NCU_TRAFFIC.get((n, dtype), {}).get(phase)
+    if phase == "sort" and isinstance(t, dict):
+        t = t.get((sort_cfg.get("digit_bits"), sort_cfg.get("tile_keys"), sort_cfg.get("lookback")))
+    return t
 
 
 def run_ours(args):
@@ -198,7 +209,9 @@ def run_ours(args):
     pts, T, r = workload()
     n, d = pts.shape
     m = T.shape[0]
-    stream = torch.cuda.current_stream()
+    # torch and the library share one stream: inputs made by torch need no cross-stream wait
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = rtg.Context(local, stream=stream.cuda_stream)
     dev_pts = torch.from_numpy(pts).cuda()
     flush = L2Flush()
@@ -208,37 +221,50 @@ def run_ours(args):
     exact_pairs = exact.nnz
     exact.release()
 
-    for _ in range(args.warmup):
-        res = ctx.all_pairs(dev_pts, r, T, r, timing=True)
-        res.release()
+    for k in range(args.warmup):
+        for timing in (False, True):  # both launch plans (with and without phase events)
+            res = ctx.all_pairs(dev_pts, r, T, r, timing=timing)
+            res.release()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms, phases, pairs, launches = [], [], None, None
+
+    def steps(timing):
+        out_ms, out_ph, info = [], [], {}
+        for k in range(args.steps):
+            flush(k)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = ctx.all_pairs(dev_pts, r, T, r, timing=timing)
+            e1.record(stream)
+            e1.synchronize()
+            out_ms.append(e0.elapsed_time(e1))
+            st = res.stats
+            if timing:
+                out_ph.append(st["phase_us"])
+            info = {"pairs": res.nnz, "launches": st["launches"], "key_bits": st["key_bits"],
+                    "passes": st["sort_passes"], "sort": st["sort"]}
+            res.release()
+        return out_ms, out_ph, info
+
+    # timed region: whole builds, no instrumentation
     t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush(k)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = ctx.all_pairs(dev_pts, r, T, r, timing=True)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        st = res.stats
-        phases.append(st["phase_us"])
-        pairs, launches = res.nnz, st["launches"]
-        key_bytes = 8 if st["key_bits"] > 32 else 4
-        passes = st["sort_passes"]
-        sort_cfg = dict(st["sort"], key_bits=st["key_bits"], passes=passes)
-        res.release()
+    step_ms, _, info = steps(False)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     wall_s = time.perf_counter() - t_wall
+    # the same steps again with phase events (they cost about 30 us a build), for the roofline
+    _, phases, _ = steps(True)
+    torch.cuda.synchronize()
     clk = clocks.stop()
+    pairs, launches = info["pairs"], info["launches"]
+    key_bytes = 8 if info["key_bits"] > 32 else 4
+    passes = info["passes"]
+    sort_cfg = dict(info["sort"], key_bits=info["key_bits"], passes=passes)
     total_ms = max_over_ranks(float(np.sum(step_ms)), ws)
     ms_per_step = total_ms / args.steps
     value = job_throughput(pairs, args.steps, ws, total_ms)
@@ -265,13 +291,15 @@ def run_ours(args):
 
     # roofline of the dominant phase (per-phase device events over the timed region)
     mean_phase = {p: float(np.mean([ph[p] for ph in phases])) for p in phases[0]}
-    pb = phase_bytes(n, d, m, key_bytes, passes, 8 if d <= 8 else 16, pairs)
+    dpad = 4 if d <= 4 else (8 if d <= 8 else 16)
+    pb = phase_bytes(n, d, m, key_bytes, passes, dpad, pairs, sort_cfg.get("digit_bits", 8))
     dom = max(pb, key=lambda p: mean_phase[p])
     peak, peak_kind = measured_peaks()
     achieved = pb[dom] / (mean_phase[dom] * 1e-6) / 1e9
-    traffic = NCU_TRAFFIC.get((n, WORKLOAD.get("dtype", "fp64")), {}).get(dom)
-    kernels = {"sort": "k_sort_hist + one k_sort_pass per radix pass (autotuned variant)",
-               "pairs": "k_pairs_warp + k_large_setup + k_pairs_large"}[dom]
+    traffic = ncu_traffic(n, WORKLOAD.get("dtype", "fp64"), dom, sort_cfg)
+    kernels = {"sort": "one k_sort_pass per radix pass (look-back) or upsweep, scan and "
+                       "downsweep per pass (autotuned variant); k_sort_hist for digits over 8 bits",
+               "pairs": "k_pairs_warp + k_pairs_medium + k_large_setup + k_pairs_large"}[dom]
     roofline = {"bound": "hbm", "kernel": dom, "kernels": kernels, "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -289,6 +317,9 @@ def run_ours(args):
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
         "wall_s_timed_region": round(wall_s, 3),
         "phase_us": {p: round(v, 2) for p, v in mean_phase.items()},
+        "phase_note": "device phases from CUDA events on the library's stream, in a second pass of "
+                      "the same steps (phase events add about 30 us a build, so the timed steps "
+                      "run without them)",
         "sort": sort_cfg,
         "roofline": roofline,
         "e2e": {"value": round(e2e_value, 1), "unit": "pairs/s", "h2d_bytes_per_step": h2d,

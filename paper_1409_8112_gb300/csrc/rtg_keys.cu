@@ -442,16 +442,18 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     const int tstride = d * d + d;
     K* krow = s_krow + threadIdx.x * (m + 1);
     const long long pos0 = I.p0 * m + i;
+    const int dv = valid ? d : 0;
     for (int t = 0; t < m; ++t) {  // every lane takes every grid (warp votes below)
       K key = (K)sbase[t];
       bool near = false;
       const AxisRow<DPAD>* A = rows + t * d;
-      for (int k = 0; k < d && valid; ++k, ++A) {
-        const float2 se = *reinterpret_cast<const float2*>(&A->s);
+      unsigned int redo = 0;  // axes whose FP32 index is not certain
+      for (int k = 0; k < dv; ++k) {
+        const float2 se = *reinterpret_cast<const float2*>(&A[k].s);
         float y = se.x;
 #pragma unroll
         for (int v = 0; v < DPAD / 4; ++v) {
-          const float4 r = reinterpret_cast<const float4*>(A->R)[v];
+          const float4 r = reinterpret_cast<const float4*>(A[k].R)[v];
           y = fmaf(r.x, p[4 * v], y);
           y = fmaf(r.y, p[4 * v + 1], y);
           y = fmaf(r.z, p[4 * v + 2], y);
@@ -462,20 +464,27 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
         // outwards) lie in [floor(u), floor(u) + 1).  |u| >= 2^23 always fails (u is then an
         // integer and u - E < u), so floor(u) is exact in 32-bit integers here.
         const float f = floorf(u);
-        long long q;
-        if (__fsub_rd(u, se.y) >= f && __fadd_ru(u, se.y) < f + 1.0f) {
-          q = (long long)(int)f;
-        } else {
-          q = exact_cell(I.pts, dtype, i, d, T64 + I.T0 + (size_t)t * tstride, k, c, &near);
-          ++rechecks;
-        }
-        const longlong2 qe = *reinterpret_cast<const longlong2*>(&A->qlo);
-        long long off = q - qe.x;
-        if ((unsigned long long)off >= (unsigned long long)qe.y) {
+        const bool certain = __fsub_rd(u, se.y) >= f && __fadd_ru(u, se.y) < f + 1.0f;
+        const longlong2 qe = *reinterpret_cast<const longlong2*>(&A[k].qlo);
+        long long off = (long long)(int)f - qe.x;
+        const bool out = (unsigned long long)off >= (unsigned long long)qe.y;
+        if (!certain) redo |= 1u << k;
+        if (certain && out) range_err = true;
+        if (!certain || out) off = 0;
+        key += (K)off * (K)A[k].stride;
+      }
+      while (redo) {  // rare: the FP64 reference sequence decides these axes
+        const int k = __ffs(redo) - 1;
+        redo &= redo - 1;
+        const long long q =
+            exact_cell(I.pts, dtype, i, d, T64 + I.T0 + (size_t)t * tstride, k, c, &near);
+        ++rechecks;
+        long long off = q - A[k].qlo;
+        if ((unsigned long long)off >= A[k].ext) {
           range_err = true;
           off = 0;
         }
-        key += (K)off * (K)A->stride;
+        key += (K)off * (K)A[k].stride;
       }
       if (valid) {
         krow[t] = key;

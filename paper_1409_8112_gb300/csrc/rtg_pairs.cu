@@ -1037,29 +1037,15 @@ __device__ __forceinline__ void warp_sort_row(int* a, int len) {
 }
 
 // One warp per queued row of 33 .. kWarpRowMax entries.
-__global__ void __launch_bounds__(256) k_rowsort_warp(const OutSlot* out,
-                                                      const unsigned int* __restrict__ row_queue,
-                                                      const unsigned int* mid_count) {
-  const long long* __restrict__ row_ptr = out->row_ptr;
-  int* col = out->col;
-  const unsigned int cnt = *mid_count;
-  const unsigned int warps = gridDim.x * (blockDim.x >> 5);
-  for (unsigned int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < cnt; k += warps) {
-    const unsigned int row = row_queue[k];
-    const long long b = row_ptr[row];
-    const int len = (int)(row_ptr[row + 1] - b);
-    if (len <= 64) warp_sort_row<2>(col + b, len);
-    else if (len <= 128) warp_sort_row<4>(col + b, len);
-    else warp_sort_row<8>(col + b, len);
-  }
-}
-
 constexpr int kRowSmem = 8192;
 
-// One block per queued row of more than kWarpRowMax entries.
-__global__ void __launch_bounds__(256) k_rowsort_long(const OutSlot* out, long long n,
-                                                      const unsigned int* __restrict__ row_queue,
-                                                      const unsigned int* long_count) {
+// The queued rows: first one block per row of more than kWarpRowMax entries (bitonic sort in
+// shared memory, or in place when the row is longer than the buffer), then one warp per row of
+// kSmallCell + 1 .. kWarpRowMax entries (register sort).
+__global__ void __launch_bounds__(256) k_rowsort_queued(const OutSlot* out, long long n,
+                                                        const unsigned int* __restrict__ row_queue,
+                                                        const unsigned int* long_count,
+                                                        const unsigned int* mid_count) {
   const long long* __restrict__ row_ptr = out->row_ptr;
   int* col = out->col;
   const long long col_cap = out->col_cap;
@@ -1112,6 +1098,18 @@ __global__ void __launch_bounds__(256) k_rowsort_long(const OutSlot* out, long l
         }
       }
     }
+  }
+  // rows of kSmallCell + 1 .. kWarpRowMax entries, one warp each
+  const unsigned int mcnt = *mid_count;
+  const unsigned int warps = gridDim.x * (blockDim.x >> 5);
+  for (unsigned int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < mcnt;
+       k += warps) {
+    const unsigned int row = row_queue[k];
+    const long long b = row_ptr[row];
+    const int len = (int)(row_ptr[row + 1] - b);
+    if (len <= 64) warp_sort_row<2>(col + b, len);
+    else if (len <= 128) warp_sort_row<4>(col + b, len);
+    else warp_sort_row<8>(col + b, len);
   }
 }
 
@@ -1174,13 +1172,22 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   {
     const size_t msmem =
         (size_t)kMediumWarps * kMediumMax * (DPAD * 4 + 4) + (size_t)kMediumWarps * kMediumKeyBytes;
+    // one wave of resident blocks (the kernel loops over the cells): a build without medium
+    // cells pays for a single wave of blocks that find nothing to do
     static bool mattr[64] = {};
+    static int mocc[64] = {};
     if (dev >= 0 && dev < 64 && !mattr[dev]) {
       cudaFuncSetAttribute(k_pairs_medium<K, DPAD, MODE>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_medium<K, DPAD, MODE>,
+                                                        kMediumWarps * 32, msmem) != cudaSuccess)
+        occ = 0;
+      mocc[dev] = occ;
       mattr[dev] = true;
     }
-    k_pairs_medium<K, DPAD, MODE><<<(unsigned)(8 * a.num_sms), kMediumWarps * 32, msmem, s>>>(
+    const int mper = (dev >= 0 && dev < 64 && mocc[dev] > 0) ? mocc[dev] : 2;
+    k_pairs_medium<K, DPAD, MODE><<<(unsigned)(mper * a.num_sms), kMediumWarps * 32, msmem, s>>>(
         sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
         make_sink(a));
   }
@@ -1337,10 +1344,9 @@ int launch_rowsort(const BuildArgs& a, cudaStream_t s) {
   unsigned int* long_count = &a.st->long_rows;
   unsigned int* mid_count = &a.st->mid_rows;
   k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, mid_count, long_count);
-  k_rowsort_warp<<<(unsigned)(4 * a.num_sms), 256, 0, s>>>(a.out, a.row_cnt, mid_count);
-  k_rowsort_long<<<(unsigned)(2 * a.num_sms), 256, 0, s>>>(a.out, a.n_total, a.row_cnt,
-                                                           long_count);
-  return 3;
+  k_rowsort_queued<<<(unsigned)(4 * a.num_sms), 256, 0, s>>>(a.out, a.n_total, a.row_cnt,
+                                                              long_count, mid_count);
+  return 2;
 }
 
 }  // namespace rtg

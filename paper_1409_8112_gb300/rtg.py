@@ -367,7 +367,11 @@ class Context:
             import torch
             cur = torch.cuda.current_stream(points.device)
             if cur.cuda_stream != self.stream:
-                torch.cuda.ExternalStream(self.stream, device=points.device).wait_stream(cur)
+                ext = getattr(self, "_ext_stream", None)
+                if ext is None or ext.device != points.device:
+                    ext = torch.cuda.ExternalStream(self.stream, device=points.device)
+                    self._ext_stream = ext
+                ext.wait_stream(cur)
 
     def close(self):
         if self.handle is not None:

@@ -830,6 +830,8 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
 
 // Row counts -> row pointers (exclusive scan, single pass with decoupled look-back); the
 // counts are reset to zero so that the scatter or WRITE pass can use them as fill cursors.
+// Each thread holds 16 consecutive counts (vector loads and stores); the first warp of a tile
+// looks back over 32 predecessor tiles at a time, one per lane.
 constexpr int kScanItems = 16;
 constexpr int kScanTile = 256 * kScanItems;
 
@@ -845,55 +847,101 @@ __global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, const OutSl
   __syncthreads();
   const unsigned int tile = s_tile;
   const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+  // 16 whole counts, and both arrays 16-byte aligned (always, for device allocations)
+  const bool whole = base + kScanItems <= n &&
+                     ((reinterpret_cast<uintptr_t>(row_cnt) | reinterpret_cast<uintptr_t>(row_ptr)) &
+                      15u) == 0;
   unsigned int v[kScanItems];
+  if (whole) {
+    const uint4* src = reinterpret_cast<const uint4*>(row_cnt + base);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) {
+      const uint4 x = src[q];
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] = base + q < n ? row_cnt[base + q] : 0u;
+  }
   unsigned long long sum = 0;
 #pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    v[q] = base + q < n ? row_cnt[base + q] : 0u;
-    sum += v[q];
-  }
+  for (int q = 0; q < kScanItems; ++q) sum += v[q];
   unsigned long long total;
   const unsigned long long ex = block_excl_scan64(sum, &total, sbuf);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     const unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kMask = (1ull << 62) - 1;
+    const unsigned int full = 0xffffffffu;
+    const int lane = threadIdx.x;
     unsigned long long excl = 0;
     if (tile == 0) {
-      *reinterpret_cast<volatile unsigned long long*>(lookback) = kPre | total;
+      if (lane == 0) *reinterpret_cast<volatile unsigned long long*>(lookback) = kPre | total;
     } else {
-      *reinterpret_cast<volatile unsigned long long*>(lookback + tile) = kAgg | total;
-      long long p = (long long)tile - 1;
+      if (lane == 0)
+        *reinterpret_cast<volatile unsigned long long*>(lookback + tile) = kAgg | total;
+      long long p = (long long)tile - 1;  // nearest predecessor of the window (lane 0)
       unsigned int spins = 0;
-      while (p >= 0) {
-        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(lookback + p);
-        if ((w >> 62) == 0) {
+      while (true) {
+        const long long q = p - lane;
+        // before tile 0 there is nothing: read as an inclusive prefix of zero
+        const unsigned long long w =
+            q >= 0 ? *reinterpret_cast<const volatile unsigned long long*>(lookback + q) : kPre;
+        const unsigned int flag = (unsigned int)(w >> 62);
+        const unsigned int pre = __ballot_sync(full, flag == 2);
+        const unsigned int upto = pre ? (((pre & (0u - pre)) - 1u) << 1 | 1u) : full;
+        if (__ballot_sync(full, flag == 0) & upto) {  // a tile that matters has not published
           if (++spins > kSpinLimit) {
-            atomicOr(&st->errors, kErrTimeout);
+            if (lane == 0) atomicOr(&st->errors, kErrTimeout);
             break;
           }
           __nanosleep(32);
           continue;
         }
-        excl += w & kMask;
-        if ((w >> 62) == 2) break;
-        --p;
+        unsigned long long add = ((upto >> lane) & 1u) ? (w & kMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(full, add, o);
+        excl += add;
+        if (pre) break;
+        p -= 32;
       }
-      *reinterpret_cast<volatile unsigned long long*>(lookback + tile) = kPre | (excl + total);
+      if (lane == 0)
+        *reinterpret_cast<volatile unsigned long long*>(lookback + tile) = kPre | (excl + total);
     }
-    s_base = excl;
-    if (tile == tiles - 1) {
-      row_ptr[n] = (long long)(excl + total);
-      st->nnz = excl + total;
+    if (lane == 0) {
+      s_base = excl;
+      if (tile == tiles - 1) {
+        row_ptr[n] = (long long)(excl + total);
+        st->nnz = excl + total;
+      }
     }
   }
   __syncthreads();
   unsigned long long run = s_base + ex;
+  if (whole) {
+    longlong2* dst = reinterpret_cast<longlong2*>(row_ptr + base);
 #pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    if (base + q < n) {
-      row_ptr[base + q] = (long long)run;
-      row_cnt[base + q] = 0u;
+    for (int q = 0; q < kScanItems / 2; ++q) {
+      longlong2 x;
+      x.x = (long long)run;
+      run += v[2 * q];
+      x.y = (long long)run;
+      run += v[2 * q + 1];
+      dst[q] = x;
     }
-    run += v[q];
+    uint4* z = reinterpret_cast<uint4*>(row_cnt + base);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) z[q] = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+      if (base + q < n) {
+        row_ptr[base + q] = (long long)run;
+        row_cnt[base + q] = 0u;
+      }
+      run += v[q];
+    }
   }
 }
 
@@ -907,15 +955,51 @@ __global__ void __launch_bounds__(256) k_scatter(const unsigned long long* __res
   const long long col_cap = out->col_cap;
   const long long cnt = min((long long)st->emitted, cap);
   bool overflow = false;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
-       k += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long p = pairs[k];
-    const unsigned int i = (unsigned int)(p >> 32), j = (unsigned int)p;
-    const long long pi = row_ptr[i] + atomicAdd(&row_cnt[i], 1u);
-    if (pi < col_cap) col[pi] = (int)j; else overflow = true;
+  // four independent pairs per thread and step: their row-pointer loads and cursor atomics
+  // are in flight together
+  constexpr int U = 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k0 < cnt;
+       k0 += U * stride) {
+    unsigned long long pr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long k = k0 + u * stride;
+      pr[u] = k < cnt ? pairs[k] : ~0ull;
+    }
+    long long base[U];
+    unsigned int slot[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pr[u] != ~0ull) {
+        const unsigned int i = (unsigned int)(pr[u] >> 32);
+        base[u] = row_ptr[i];
+        slot[u] = atomicAdd(&row_cnt[i], 1u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pr[u] != ~0ull) {
+        const long long pi = base[u] + slot[u];
+        if (pi < col_cap) col[pi] = (int)(unsigned int)pr[u]; else overflow = true;
+      }
+    }
     if (symmetric) {
-      const long long pj = row_ptr[j] + atomicAdd(&row_cnt[j], 1u);
-      if (pj < col_cap) col[pj] = (int)i; else overflow = true;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (pr[u] != ~0ull) {
+          const unsigned int j = (unsigned int)pr[u];
+          base[u] = row_ptr[j];
+          slot[u] = atomicAdd(&row_cnt[j], 1u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (pr[u] != ~0ull) {
+          const long long pj = base[u] + slot[u];
+          if (pj < col_cap) col[pj] = (int)(pr[u] >> 32); else overflow = true;
+        }
+      }
     }
   }
   if (overflow) atomicOr(errors, kErrColOverflow);

@@ -267,6 +267,34 @@ rtg_status rtg_wait(rtg_ctx* ctx, uint64_t ticket, int64_t timeout_us, rtg_csr* 
 rtg_status rtg_query_neighbors(rtg_ctx* ctx, const rtg_csr* graph, const int32_t* queries,
                                int64_t nq, int queries_on_device, rtg_csr* out);
 
+/* r-NN queries of new points from the stored grids (Sec. V: keep all m grids; for a query,
+ * examine the m cells that contain it).  An index holds, on the device, what a build of
+ * Alg. 1 makes for one point set: the m grids' sorted cell keys with their point indices,
+ * the per-point key rows, the FP32 rows, a copy of the points and the plan (error bounds,
+ * key ranges, distance band).  It is charged to the context's budget until destroyed. */
+typedef struct rtg_index rtg_index;
+
+/* Builds the index of points (arguments as rtg_all_pairs; n may be 0).  *out receives a
+ * handle owned by the caller, valid for this context until rtg_index_destroy.  Synchronous.
+ * Errors as rtg_all_pairs. */
+rtg_status rtg_index_create(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
+                            int64_t n, int d, double r, const double* transforms, int m,
+                            double cell_side, rtg_index** out);
+
+/* Answers nq queries: queries is nq x d row-major in the index's dtype, a device pointer if
+ * queries_on_device, else a host pointer (copied in).  Row k of out lists, ascending, every
+ * indexed point j that shares a cell with query k in at least one grid and lies within r of
+ * it: squared distance on the original coordinates <= fl(r * r), the same FP64 sequence and
+ * the same FP32 filter with FP64 recheck as the build.  out is a library-owned device CSR
+ * with nq rows (out->symmetric = 0); free it with rtg_release.  Synchronous.
+ * Errors: RTG_E_INVALID (NULL arguments, nq < 0 or nq >= 2^31, a query coordinate not finite
+ * or beyond the FP32 range), RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT. */
+rtg_status rtg_index_query(rtg_ctx* ctx, const rtg_index* index, const void* queries,
+                           int queries_on_device, int64_t nq, rtg_csr* out);
+
+/* Frees the index's device memory (stream ordered) and the handle.  NULL is ignored. */
+void rtg_index_destroy(rtg_ctx* ctx, rtg_index* index);
+
 /* Grid parameters chosen by rtg_tune_params. */
 typedef struct {
   int m;                /* number of grids */

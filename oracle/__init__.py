@@ -89,8 +89,10 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.oracle_exact_grid.argtypes = [vp, i32, i64, i32, dbl, csrp]
     lib.oracle_cells.argtypes = [vp, i32, i64, i32, vp, i32, dbl, vp, vp]
     lib.oracle_rtg.argtypes = [vp, i32, i64, i32, dbl, vp, i32, dbl, csrp, vp, vp]
+    lib.oracle_rtg_query.argtypes = [vp, i32, i64, i32, dbl, vp, i32, dbl, vp, i64, csrp]
     lib.oracle_free.argtypes = [csrp]
-    for f in (lib.oracle_brute, lib.oracle_exact_grid, lib.oracle_cells, lib.oracle_rtg):
+    for f in (lib.oracle_brute, lib.oracle_exact_grid, lib.oracle_cells, lib.oracle_rtg,
+              lib.oracle_rtg_query):
         f.restype = ctypes.c_int
     lib.oracle_mutant.restype = ctypes.c_int
     _libs[mutant] = lib
@@ -143,7 +145,8 @@ def exact_grid(points: np.ndarray, r: float, mutant: int = 0) -> CSR:
 
 
 def cells(points: np.ndarray, transforms: np.ndarray, cell_side: float, mutant: int = 0):
-    """Alg. 1 lines 4-7 for each grid: (m, n, d) int64 cell coordinates, near-wall counts."""
+    """The point-to-cell step of Alg. 1 for each grid: (m, n, d) int64 cell coordinates and
+    near-wall counts."""
     lib = _lib(mutant)
     p, dt = _points(points)
     n, d = p.shape
@@ -184,6 +187,29 @@ def rtg(points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,
         raise ValueError("oracle_rtg: invalid arguments")
     stats = [{f: int(getattr(st[t], f)) for f, _ in _GridStats._fields_} for t in range(m)]
     return RTGResult(_take(lib, c), stats, int(near_r.value))
+
+
+def rtg_query(points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,
+              queries: np.ndarray, mutant: int = 0) -> CSR:
+    """r-NN queries of new points from the m stored grids (the single-query use of the grids,
+    Sec. V): row k lists the points of P within r of query k that share a cell with it in
+    some grid, ascending."""
+    lib = _lib(mutant)
+    p, dt = _points(points)
+    x, dq = _points(queries)
+    n, d = p.shape
+    if x.ndim != 2 or x.shape[1] != d or dq != dt:
+        raise ValueError("queries must be nq x d with the points' dtype")
+    T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
+    if T.size % (d * d + d) != 0:
+        raise ValueError("transforms must hold m * (d*d + d) values")
+    m = T.size // (d * d + d)
+    c = _CSR()
+    rc = lib.oracle_rtg_query(p.ctypes.data, dt, n, d, float(r), T.ctypes.data, m,
+                              float(cell_side), x.ctypes.data, x.shape[0], ctypes.byref(c))
+    if rc != 0:
+        raise ValueError("oracle_rtg_query: invalid arguments")
+    return _take(lib, c)
 
 
 def recall(rtg_csr: CSR, exact: CSR) -> float:

@@ -10,8 +10,10 @@
 //                        Euclidean distance at most r, by checking all n(n-1)/2 pairs.
 //   oracle_exact_grid  - the same set through a fixed uniform grid of side r, scanning
 //                        same and adjacent cells (the Lenhof-Smid idea recalled in Sec. II-B).
-//   oracle_cells       - Alg. 1 lines 4-7 for each grid: the cell u each point lies in, for
-//                        the rotated + shifted grids of Sec. III ("second algorithm").
+//   oracle_cells       - the point-to-cell step of Alg. 1 for each grid: the cell u each
+//                        point lies in, for the rotated + shifted grids of Sec. III ("second
+//                        algorithm").
+//   oracle_rtg_query   - r-NN queries of new points from the m stored grids (Sec. V).
 //   oracle_rtg         - Alg. 1 in full (Sec. III): for each of the m grids, associate points
 //                        to cells, go over all pairs inside each non-empty cell, report those
 //                        at distance at most r; duplicates across grids are removed with the
@@ -113,7 +115,7 @@ bool within(double s, double rr) {
   return s <= rr;
 }
 
-// Alg. 1 lines 4-7 for grid t: the rotated coordinate y = R p + s and the cell index
+// Alg. 1 (point-to-cell step) for grid t: the rotated coordinate y = R p + s and the cell index
 // q_k = floor(y_k / c).  Writes q (d entries); returns true if the point lies within
 // 1e-12 of a cell wall of this grid.
 bool cell_of(const double* p, const double* R, const double* s, int d, double c, int64_t* q) {
@@ -231,8 +233,8 @@ int oracle_exact_grid(const void* pts, int dtype, int64_t n, int d, double r, or
   return 0;
 }
 
-// Alg. 1 lines 4-7 for every grid: q_out[(t*n + i)*d + k] is the cell coordinate of point i
-// on axis k in grid t.  near_wall_out (optional, m entries) counts near-wall points.
+// The point-to-cell step of Alg. 1 for every grid: q_out[(t*n + i)*d + k] is the cell
+// coordinate of point i on axis k in grid t.  near_wall_out (optional, m entries) counts near-wall points.
 int oracle_cells(const void* pts, int dtype, int64_t n, int d, const double* T, int m, double c,
                  int64_t* q_out, int64_t* near_wall_out) {
   if (n < 0 || d < 1 || d > 16 || m < 1 || !(c > 0) || !T || !q_out) return -1;
@@ -267,14 +269,14 @@ int oracle_rtg(const void* pts, int dtype, int64_t n, int d, double r, const dou
   for (int t = 0; t < grids; ++t) {
     const double* R = T + (size_t)t * stride;
     const double* s = R + d * d;
-    // lines 3-7: U and the association of points to cells
+    // Alg. 1: the set U of non-empty cells and the association of points to cells
     std::map<std::vector<int64_t>, std::vector<uint32_t>> U;
     int64_t near_wall = 0;
     for (int64_t i = 0; i < n; ++i) {
       near_wall += cell_of(&p[(size_t)i * d], R, s, d, c, q.data()) ? 1 : 0;
       U[q].push_back((uint32_t)i);
     }
-    // lines 8-9: all pairs inside each non-empty cell, reported if at distance <= r
+    // Alg. 1: all pairs inside each non-empty cell, reported if at distance <= r
     int64_t candidates = 0, multi = 0, maxc = 0, reported = 0;
     for (const auto& cell : U) {
       const auto& A = cell.second;
@@ -307,6 +309,41 @@ int oracle_rtg(const void* pts, int dtype, int64_t n, int d, double r, const dou
     }
   }
   if (near_r_out) *near_r_out = near_r;
+  to_csr(sets, out);
+  return 0;
+}
+
+// An r-NN query of a point x that need not belong to P, answered from the m stored grids
+// (the single-query use of the grids in the conclusion, Sec. V): the answer is every point p
+// of P with dist2(x, p) <= fl(r*r) that shares a cell with x in at least one grid, the cells
+// being those of the point-to-cell step of Alg. 1 for x and for p alike.  Row k of out lists
+// the answers to query k, ascending.
+int oracle_rtg_query(const void* pts, int dtype, int64_t n, int d, double r, const double* T,
+                     int m, double c, const void* queries, int64_t nq, oracle_csr* out) {
+  if (n < 0 || nq < 0 || d < 1 || d > 16 || m < 1 || !(c > 0) || !(r > 0) || !T || !out)
+    return -1;
+  std::vector<double> p = widen(pts, dtype, n, d);
+  std::vector<double> x = widen(queries, dtype, nq, d);
+  const double rr = r * r;
+  const int stride = d * d + d;
+  std::vector<std::unordered_set<uint32_t>> sets((size_t)nq);
+  std::vector<int64_t> q(d);
+  for (int t = 0; t < m; ++t) {
+    const double* R = T + (size_t)t * stride;
+    const double* s = R + d * d;
+    std::map<std::vector<int64_t>, std::vector<uint32_t>> U;
+    for (int64_t i = 0; i < n; ++i) {
+      cell_of(&p[(size_t)i * d], R, s, d, c, q.data());
+      U[q].push_back((uint32_t)i);
+    }
+    for (int64_t k = 0; k < nq; ++k) {
+      cell_of(&x[(size_t)k * d], R, s, d, c, q.data());
+      const auto it = U.find(q);
+      if (it == U.end()) continue;
+      for (uint32_t j : it->second)
+        if (within(dist2(&x[(size_t)k * d], &p[(size_t)j * d], d), rr)) sets[(size_t)k].insert(j);
+    }
+  }
   to_csr(sets, out);
   return 0;
 }

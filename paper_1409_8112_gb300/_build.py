@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "librtg.so")
 
 CU_SOURCES = ["rtg_api.cu", "rtg_keys.cu", "rtg_sort.cu", "rtg_pairs.cu", "rtg_serve.cu",
               "rtg_tc.cu", "rtg_noalloc.cu", "rtg_tune.cu", "rtg_query.cu",
-              "rtg_params.cu"]
+              "rtg_params.cu", "rtg_index.cu"]
 C_SOURCES = [os.path.join("gen", "rtg_gen.c")]
 HEADERS = ["rtg_internal.cuh", "rtg_host.h", os.path.join("gen", "rtg_gen.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,7 +1,7 @@
 /* Seeded synthetic inputs for randomly transformed grids (RTG).
  *
  * This module only draws random numbers and lays them out: point sets, the m random
- * rotations + shifts of Sec. III (Alg. 1 line 2 and the rotated variant), the radius
+ * rotations + shifts of Sec. III (Alg. 1 (grid set-up) and the rotated variant), the radius
  * for a target expected degree, and request traces.  It holds none of the method's
  * arithmetic (no cell keys, no distances, no dedupe), so both the CPU oracle's tests
  * and the GPU library may draw their inputs from it.

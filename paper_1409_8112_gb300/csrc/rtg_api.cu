@@ -730,6 +730,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
     c->guesses[key] = g;
+    c->last_sorted = sorted;
 
     out->n = n_total;
     out->symmetric = sym;
@@ -962,6 +963,40 @@ rtg_status rtg_query_neighbors(rtg_ctx* c, const rtg_csr* graph, const int32_t* 
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
   return query_neighbors(c, graph, queries, nq, queries_on_device, out);
+}
+
+rtg_status rtg_index_create(rtg_ctx* c, const void* points, int dtype, int points_on_device,
+                            int64_t n, int d, double r, const double* transforms, int m,
+                            double cell_side, rtg_index** out) {
+  if (!c || !out) return fail(c, RTG_E_INVALID, "NULL context or output");
+  *out = nullptr;
+  rtg_status s = validate_common(dtype, n, d, r, cell_side, points);
+  if (s == RTG_OK && (m < 1 || m > RTG_MAX_GRIDS))
+    s = fail(nullptr, RTG_E_INVALID, "m must be in [1, 64]");
+  if (s == RTG_OK) s = validate_transforms(transforms, d, m);
+  if (s != RTG_OK) return fail(c, s, g_err);
+  std::lock_guard<std::mutex> lk(c->mu);
+  RTG_CUDA(c, cudaSetDevice(c->device));
+  rtg_instance it{points, n, d, r, cell_side, transforms};
+  return index_create(c, it, m, dtype, points_on_device, out);
+}
+
+rtg_status rtg_index_query(rtg_ctx* c, const rtg_index* index, const void* queries,
+                           int queries_on_device, int64_t nq, rtg_csr* out) {
+  if (!c || !index || !out) return fail(c, RTG_E_INVALID, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (nq < 0 || nq >= (int64_t(1) << 31) || (nq > 0 && !queries))
+    return fail(c, RTG_E_INVALID, "queries: count out of range or NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  RTG_CUDA(c, cudaSetDevice(c->device));
+  return index_query(c, index, queries, queries_on_device, nq, out);
+}
+
+void rtg_index_destroy(rtg_ctx* c, rtg_index* index) {
+  if (!c || !index) return;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  index_destroy(c, index);
 }
 
 rtg_status rtg_csr_download(rtg_ctx* c, const rtg_csr* csr, int64_t* row_ptr, int32_t* col) {

@@ -7,12 +7,12 @@
 //   plan    : per (instance, grid, axis) the cell-index range (mixed-radix key layout) and the
 //             FP32 error bound of the cell index; per instance the distance-filter band;
 //             composite key bases so that every (instance, grid) owns a disjoint key range
-//   keys    : y = R p + s and q = floor(y / c) per point and grid (Alg. 1 lines 4-7), packed
-//             into base(instance, grid) + mixed-radix cell key
+//   keys    : y = R p + s and q = floor(y / c) per point and grid (the point-to-cell step of
+//             Alg. 1), packed into base(instance, grid) + mixed-radix cell key
 //   sort    : LSD radix sort (onesweep) of the composite keys with global point indices
-//   pairs   : per cell, all pairs (Alg. 1 lines 8-9); a pair is owned by the first grid that
-//             puts both points in one cell (dedupe of Sec. III-B without an auxiliary set);
-//             owned pairs at distance <= r are emitted to a pair buffer with row counts
+//   pairs   : per cell, all pairs (the in-cell reporting of Alg. 1); a pair is owned by the
+//             first grid that puts both points in one cell (dedupe of Sec. III-B without an
+//             auxiliary set); owned pairs at distance <= r are emitted to a pair buffer with row counts
 //             (EMIT), or counted and later written in place (COUNT then WRITE)
 //   scan    : row counts -> CSR row pointers
 //   scatter : pair buffer -> columns in their rows

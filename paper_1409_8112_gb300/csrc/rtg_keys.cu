@@ -1,5 +1,6 @@
-// Point preparation, per-build plan and the transform+key kernel (Alg. 1 lines 4-7 of
-// arXiv:1409.8112, for the rotated + shifted grids of Sec. III), for a batch of instances.
+// Point preparation, per-build plan and the transform+key kernel (the point-to-cell step of
+// Alg. 1 of arXiv:1409.8112, for the rotated + shifted grids of Sec. III), for a batch of
+// instances.
 //
 // The cell index of a point in grid t is q_k = floor(y_k / c) with y = R_t p + s_t, where the
 // reference value is the FP64 fma chain acc = s_k; acc = fma(R[k][l], p_l, acc) followed by an

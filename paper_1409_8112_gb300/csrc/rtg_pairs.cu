@@ -1,5 +1,5 @@
-// In-cell pair enumeration and CSR assembly (Alg. 1 lines 8-9 and the dedupe of Sec. III-B
-// of arXiv:1409.8112), for a batch of instances.
+// In-cell pair enumeration and CSR assembly (the in-cell pair reporting of Alg. 1 and the
+// dedupe of Sec. III-B of arXiv:1409.8112), for a batch of instances.
 //
 // After the sort every (instance, grid, cell) is a run of equal keys.  A warp owns the cells
 // whose first position lies in its span of sorted positions: it finds them with adjacent key

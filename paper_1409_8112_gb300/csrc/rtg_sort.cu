@@ -1,6 +1,6 @@
 // LSD radix sort of (key, point index) pairs: groups the points of every grid by cell
-// (Alg. 1 lines 4-7 of arXiv:1409.8112 associate each point with its cell; the sort makes
-// every cell a contiguous run).  Stable.
+// (Alg. 1 of arXiv:1409.8112 associates each point with its cell; the sort makes every cell
+// a contiguous run).  Stable.
 //
 // Compile-time variants: digit width BITS (8, 10 or 11 bits per pass, so a key of b bits takes
 // ceil(b / BITS) passes) and ITEMS keys per thread (tiles of 256 * ITEMS keys).  The

@@ -108,6 +108,13 @@ _SIGNATURES = {
     "rtg_query_neighbors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                            ctypes.POINTER(rtg_csr)]),
+    "rtg_index_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    "rtg_index_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_int64, ctypes.POINTER(rtg_csr)]),
+    "rtg_index_destroy": (None, [ctypes.c_void_p, ctypes.c_void_p]),
     "rtg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rtg_transforms_generate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_uint32,
@@ -355,6 +362,43 @@ class Result:
             pass
 
 
+class Index:
+    """Device index of one point set's m grids (``Context.index``); ``query`` answers r-NN
+    queries of new points.  ``close()`` frees it (also on garbage collection)."""
+
+    def __init__(self, ctx: "Context", handle: int, d: int, dtype_code: int):
+        self._ctx = ctx
+        self.handle = handle
+        self.d = d
+        self.dtype_code = dtype_code
+
+    def query(self, queries) -> "Result":
+        """Row k of the result lists, ascending, the indexed points within r of queries[k]
+        that share a cell with it in some grid.  queries: (nq, d) array of the index's dtype,
+        numpy or CUDA tensor."""
+        ptr, code, on_dev, nq, d, keep = _points_arg(queries)
+        if nq > 0 and (d != self.d or code != self.dtype_code):
+            raise ValueError("queries must be (nq, d) with the indexed points' d and dtype")
+        self._ctx._after_producer(keep)
+        out = rtg_csr()
+        st = lib().rtg_index_query(self._ctx.handle, self.handle, ptr if nq > 0 else None,
+                                   on_dev, nq, ctypes.byref(out))
+        del keep
+        _check(st, self._ctx.handle)
+        return Result(self._ctx, out, 0)
+
+    def close(self):
+        if self.handle and self._ctx.handle is not None:
+            lib().rtg_index_destroy(self._ctx.handle, self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: int | None = None):
         self.handle = rtg_create(device, mem_budget_bytes, stream)
@@ -474,6 +518,22 @@ class Context:
         del keep
         _check(st, self.handle)
         return Result(self, out, 0)
+
+    def index(self, points, r: float, transforms: np.ndarray, cell_side: float) -> "Index":
+        """The m grids of `points` kept on the device for r-NN queries of new points (Sec. V).
+        points: (n, d) float64/float32 numpy array or CUDA tensor."""
+        ptr, code, on_dev, n, d, keep = _points_arg(points)
+        self._after_producer(keep)
+        T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
+        if T.size % (d * d + d) != 0:
+            raise ValueError("transforms must hold m * (d*d + d) values")
+        m = T.size // (d * d + d)
+        h = ctypes.c_void_p()
+        st = lib().rtg_index_create(self.handle, ptr, code, on_dev, n, d, float(r),
+                                    T.ctypes.data, m, float(cell_side), ctypes.byref(h))
+        del keep
+        _check(st, self.handle)
+        return Index(self, h.value, d, code)
 
     def brute_force(self, points, r: float, symmetric: bool = False,
                     count_only: bool = False, tensor: str | None = None,

@@ -162,6 +162,56 @@ def pin_candidate_counts(mutant=0):
         assert res.stats[t]["nonempty_cells"] == len({tuple(x) for x in q[t]})
 
 
+def pin_queries(mutant=0):
+    """Queries of new points from the stored grids (Sec. V).  (1) With one cell larger than the
+    whole point set the answer to a query is every point within r (numpy distances; pairs
+    within 1e-9 r of r are left out of the comparison).  (2) Querying the points themselves
+    gives each point plus its RTG neighbours, the symmetric form of Alg. 1's pair set.
+    (3) Queries far outside the grids' occupied cells get no answer.  (4) Answers lie within
+    r and a prefix of the grids answers a subset."""
+    d, n = 3, 400
+    pts = gen.points_uniform(21, n, d)
+    r = gen.radius_for_degree(n, d, 10.0)
+    qs = np.concatenate([gen.points_uniform(22, 60, d), pts[:20]])
+    c = 8.0 * np.sqrt(d)
+    T = gen.transforms(4, d, 2, c)
+    T[:, d * d:] = c / 2
+    res = oracle.rtg_query(pts, r, T, c, qs, mutant=mutant)
+    assert res.n == len(qs)
+    dist = np.sqrt(((qs[:, None, :] - pts[None, :, :]) ** 2).sum(-1))
+    for k in range(len(qs)):
+        got = set(map(int, res.col[res.row_ptr[k]:res.row_ptr[k + 1]]))
+        sure = np.abs(dist[k] - r) > 1e-9 * r
+        want = set(np.nonzero((dist[k] <= r) & sure)[0].tolist())
+        assert {j for j in got if sure[j]} == want, k
+    # (2) the points as queries
+    m = 4
+    T = gen.transforms(5, d, m, r)
+    full = oracle.rtg(pts, r, T, r, mutant=mutant)
+    nb = [{i} for i in range(n)]
+    for (i, j) in _pairset(full.csr):
+        nb[i].add(j)
+        nb[j].add(i)
+    res = oracle.rtg_query(pts, r, T, r, pts, mutant=mutant)
+    for i in range(n):
+        row = res.col[res.row_ptr[i]:res.row_ptr[i + 1]]
+        assert np.all(np.diff(row) > 0)
+        assert set(map(int, row)) == nb[i], i
+    # (3) far away
+    far = oracle.rtg_query(pts, r, T, r, qs + 100.0, mutant=mutant)
+    assert far.nnz == 0
+    # (4) within r, and prefix-monotone in the grids
+    prev = None
+    for t in range(1, m + 1):
+        cur = oracle.rtg_query(pts, r, T[:t], r, qs, mutant=mutant)
+        rows = np.repeat(np.arange(len(qs)), np.diff(cur.row_ptr))
+        assert np.all(dist[rows, cur.col] <= r * (1 + 1e-12))
+        pairs = set(zip(rows.tolist(), cur.col.tolist()))
+        if prev is not None:
+            assert prev <= pairs
+        prev = pairs
+
+
 ALL_PINS = [pin_worked_2d, pin_worked_boundary, pin_exact_grid_equals_brute,
             pin_single_cell_equals_brute, pin_invariants, pin_shift_probability,
-            pin_table2_recall, pin_candidate_counts]
+            pin_table2_recall, pin_candidate_counts, pin_queries]

@@ -103,6 +103,17 @@ def test_grid_counts(ctx, m):
     run_and_compare(ctx, pts, r, T, r)
 
 
+def test_many_grids_high_dimension(ctx):
+    # 64 grids of 16-dimensional rows: the key kernel's table of axis rows is too large to stage
+    # the key rows in shared memory as well, so they go straight to global memory
+    n, d, m = 3000, 16, 64
+    r = gen.radius_for_degree(n, d, 10.0)
+    pts = gen.points_uniform(7, n, d)
+    T = gen.transforms(8, d, m, 1.2 * r)
+    st, ref = run_and_compare(ctx, pts, r, T, 1.2 * r)
+    assert ref.csr.nnz > 0
+
+
 def test_shift_only_table2_parameters(ctx):
     n, d, m, ct = 12800, 3, 20, 1.15
     r = gen.radius_fmt(n, d)

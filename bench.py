@@ -749,6 +749,64 @@ def run_query(args):
     print(json.dumps(line), flush=True)
 
 
+def run_points_query(args):
+    """r-NN queries of new points from the stored grids (Sec. V): an index of the headline
+    workload's m = 8 grids built once, then 100,000 new points uniform in [0,1]^6 (seed 9,
+    host FP64) queried per step, their answers read back as a CSR; with the oracle's time on
+    a 2,000-query sample of the same queries beside it."""
+    import torch
+    from paper_1409_8112_gb300 import rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = L2Flush()
+    pts, T, r = workload()
+    d = pts.shape[1]
+    dev = torch.from_numpy(pts).cuda()
+    t0 = time.perf_counter()
+    ix = ctx.index(dev, r, T, r)
+    build_s = time.perf_counter() - t0
+    qs = np.random.default_rng(9).random((100000, d)).astype(pts.dtype)
+    qdev = torch.from_numpy(qs).cuda()
+    for _ in range(args.warmup):
+        ix.query(qdev).release()
+    ms, nnz = [], 0
+    for k in range(args.steps):
+        flush(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ix.query(qdev)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        nnz = res.nnz
+        res.release()
+    t = float(np.mean(ms))
+    line = {"metric": METRIC, "value": round(len(qs) / (t / 1e3), 1), "unit": "queries/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t, 4),
+            "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"r-NN queries of {len(qs)} new points uniform in [0,1]^6 "
+                                   f"(seed 9) against the stored grids of {WORKLOAD['workload']}",
+                       "l2": L2_NOTE},
+            "answers_per_step": nnz, "answers_per_s": round(nnz / (t / 1e3), 1),
+            "index_build_s": round(build_s, 4)}
+    if not args.no_cpu_baseline:
+        import oracle
+        sample = qs[:2000]
+        t0 = time.perf_counter()
+        oracle.rtg_query(pts, r, T, r, sample)
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(len(sample) / cpu_s, 1), "unit": "queries/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"{len(sample)} of the same queries against the same "
+                                          f"points and grids, {cpu_s:.2f} s (grids rebuilt "
+                                          f"per call)"}
+    ix.close()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Precision workload: n = 1e6 points of U[0,1]^6 stored FP32, r for degree 2 ln n, m = 8
     (RTG build), and the exact all-pairs set of a 200,000-point sample (first 200k points of a
@@ -821,7 +879,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="build",
                     choices=["build", "batch", "serve", "precision", "table2", "query",
-                             "params", "bitset"],
+                             "points_query", "params", "bitset"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -847,6 +905,8 @@ def main():
         run_table2(args)
     elif args.workload == "query":
         run_query(args)
+    elif args.workload == "points_query":
+        run_points_query(args)
     elif args.workload == "params":
         run_params(args)
     elif args.workload == "bitset":

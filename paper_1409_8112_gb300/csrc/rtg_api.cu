@@ -443,6 +443,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     a.sort_bits = g.sort.bits;
     a.sort_items = g.sort.items;
     a.sort_mode = g.sort.mode;
+    // pair enumeration: one static span per warp for light cells (fewest span set-ups); more,
+    // smaller spans claimed dynamically when the shape's cells held many candidates, so that
+    // warps with heavy spans do not trail
+    a.spans_per_warp = g.cand_per_pos < 0.0f ? 2 : (g.cand_per_pos >= 3.0f ? 4 : 1);
     if (m > 0) {
       const size_t ksz = a.key64 ? 8 : 4;
       if ((s = ensure(c, c->key_mat, (size_t)N * ksz)) != RTG_OK) return s;
@@ -729,6 +733,11 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     }
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
+    {
+      double cand = 0.0;
+      for (int t = 0; t < m && t < RTG_MAX_GRIDS; ++t) cand += (double)h.candidates[t];
+      g.cand_per_pos = N > 0 ? (float)(cand / (double)N) : 0.0f;
+    }
     c->guesses[key] = g;
     c->last_sorted = sorted;
 

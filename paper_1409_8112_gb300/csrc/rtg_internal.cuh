@@ -96,6 +96,7 @@ struct Status {
   unsigned long long large_jobs;
   unsigned long long max_cell;
   unsigned int sort_tiles[kMaxPasses];
+  unsigned int span_next[2];  // pair enumeration: next unclaimed span (count/emit, write)
   unsigned int long_rows;  // rows queued for the block row sort
   unsigned int mid_rows;   // rows queued for the warp row sort
   unsigned int tc_max_err_bits;  // tensor-core path: max |FP32 d^2 - FP64 d^2| (float bits)
@@ -191,6 +192,7 @@ struct OutSlot {
 
 // ---- launch arguments ----------------------------------------------------------------------
 struct BuildArgs {
+  int spans_per_warp;  // pair enumeration: spans per resident warp (1: static, one each)
   int B;              // instances
   int m;              // grids per instance (0: brute force)
   int dtype;          // 0 FP64, 1 FP32 (common to the batch)

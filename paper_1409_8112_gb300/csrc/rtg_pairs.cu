@@ -24,6 +24,7 @@
 // buffer (for outputs too large to hold twice).  Rows are sorted at the end.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "rtg_internal.cuh"
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
     const float* __restrict__ pf, int dtype, const K* __restrict__ key_mat, int m,
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const unsigned long long* __restrict__ bases, int nbt, Status* st, Sink sk,
-    LargeCell* large, unsigned int large_cap, int warp_bytes) {
+    LargeCell* large, unsigned int large_cap, int warp_bytes, unsigned int* span_next) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned int s_maxcell;
@@ -377,8 +378,11 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   unsigned int maxcell = 0;
   unsigned int ecnt = 0;  // pairs in w_emit (warp-uniform)
 
-  // one span per warp
-  if (const long long sp = (long long)blockIdx.x * (blockDim.x >> 5) + wib; sp < nspans) {
+  // the first span of a warp is its own; when there are more spans than warps the rest are
+  // claimed one at a time from a counter, so that a warp whose spans held few pairs takes
+  // more of them (cell sizes, and so the work per span, vary)
+  const long long launched = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long sp = (long long)blockIdx.x * (blockDim.x >> 5) + wib; sp < nspans;) {
     // Positions inside the span loop are offsets from P0 (int): the warp leaves the span once
     // it passes its end, so every offset it keeps is below span + 32.
     const long long P0 = sp * span;
@@ -569,6 +573,10 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
       kc = kn;
       vc = vn;
     }
+    if (nspans <= launched) break;
+    long long nx = 0;
+    if (lane == 0) nx = launched + atomicAdd(span_next, 1u);
+    sp = __shfl_sync(full, nx, 0);
   }
   if (MODE == kEmit && ecnt) warp_flush(w_emit, ecnt, sk);
   if (MODE != kWrite) {
@@ -1227,16 +1235,17 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   const bool stage_rows = a.m * (int)sizeof(K) <= kMaxStagedRow;
   const int wbytes = warp_region_bytes<K, DPAD>(a.m, stage_rows);
   const size_t smem = (size_t)wbytes * kWarps;
-  // spans of a multiple of 32 positions (64..1024): the fewest whole waves of resident warps
-  // whose spans stay within 1024 positions, so that no partial wave of long spans trails
+  // spans of a multiple of 32 positions (64..1024), about a.spans_per_warp of them per
+  // resident warp (more when spans would pass 1024 positions), for one wave of warps
   const long long resident = 4LL * a.num_sms * kWarps;
-  long long waves = (N + 1024 * resident - 1) / (1024 * resident);
-  if (waves < 1) waves = 1;
-  long long span = (N + waves * resident - 1) / (waves * resident);
+  long long W = a.spans_per_warp > 0 ? a.spans_per_warp : 1;
+  W = std::max(W, (N + 1024 * resident - 1) / (1024 * resident));  // spans of at most 1024
+  long long span = (N + W * resident - 1) / (W * resident);
   span = (span + 31) / 32 * 32;
   span = span < 64 ? 64 : (span > 1024 ? 1024 : span);
   const long long nspans = (N + span - 1) / span;
-  const long long blocks = (nspans + kWarps - 1) / kWarps;  // one span per warp
+  long long blocks = (nspans + kWarps - 1) / kWarps;
+  if (blocks > 4LL * a.num_sms) blocks = 4LL * a.num_sms;
   const K* sk = (const K*)a.keys[sorted_buf];
   const uint32_t* sv = a.vals[sorted_buf];
   static size_t attr_smem[64] = {};  // largest size granted so far, per device
@@ -1252,7 +1261,8 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   }
   kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(
       sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
-      a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes);
+      a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes,
+      &a.st->span_next[MODE == kWrite ? 1 : 0]);
   {
     const size_t msmem =
         (size_t)kMediumWarps * kMediumMax * (DPAD * 4 + 4) + (size_t)kMediumWarps * kMediumKeyBytes;

@@ -235,6 +235,7 @@ __device__ void plan_axis_item(long long idx, const Inst* __restrict__ inst, int
   const double* R = T64 + I.T0 + (size_t)t * (d * d + d);
   const double* s = R + d * d;
   double ymin = s[k], ymax = s[k], A = fabs(s[k]);
+#pragma unroll 3  // the loads of a few axes in flight together
   for (int l = 0; l < d; ++l) {
     const double hi = I.n > 0 ? dec_double(__ldcg(bbox + ((size_t)b * kMaxDim + l) * 2 + 0)) : 0.0;
     const double lo = I.n > 0 ? dec_double(~__ldcg(bbox + ((size_t)b * kMaxDim + l) * 2 + 1)) : 0.0;

@@ -270,10 +270,21 @@ def rtg_release(ctx, csr: rtg_csr) -> None:
     _check(lib().rtg_release(ctx, ctypes.byref(csr)), ctx)
 
 
-def rtg_csr_download(ctx, csr: rtg_csr):
-    # every element is written by the copy (fresh zeroed pages would fault during it)
-    row_ptr = np.empty(csr.n + 1, dtype=np.int64)
-    col = np.empty(max(csr.nnz, 0), dtype=np.int32)
+def rtg_csr_download(ctx, csr: rtg_csr, out=None):
+    """Copies the CSR to host arrays: new ones, or out = (row_ptr, col), contiguous int64 and
+    int32 arrays of at least n + 1 and nnz entries (pinned ones make the copy a direct DMA);
+    returns views of the copied length."""
+    if out is None:
+        # every element is written by the copy (fresh zeroed pages would fault during it)
+        row_ptr = np.empty(csr.n + 1, dtype=np.int64)
+        col = np.empty(max(csr.nnz, 0), dtype=np.int32)
+    else:
+        row_ptr, col = out
+        if (row_ptr.dtype != np.int64 or col.dtype != np.int32 or
+                not row_ptr.flags.c_contiguous or not col.flags.c_contiguous or
+                row_ptr.size < csr.n + 1 or col.size < max(csr.nnz, 0)):
+            raise ValueError("out must be contiguous int64 / int32 arrays of n + 1 / nnz entries")
+        row_ptr, col = row_ptr[:csr.n + 1], col[:max(csr.nnz, 0)]
     _check(lib().rtg_csr_download(ctx, ctypes.byref(csr), row_ptr.ctypes.data,
                                   col.ctypes.data if csr.nnz > 0 else None), ctx)
     return row_ptr, col
@@ -347,8 +358,10 @@ class Result:
     def stats(self) -> dict:
         return stats_dict(self.csr.stats, self.m)
 
-    def download(self):
-        return rtg_csr_download(self._ctx.handle, self.csr)
+    def download(self, out=None):
+        """(row_ptr, col) on the host; out = (row_ptr, col) arrays to fill (see
+        rtg_csr_download)."""
+        return rtg_csr_download(self._ctx.handle, self.csr, out)
 
     def release(self):
         if self.csr.handle:

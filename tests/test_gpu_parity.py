@@ -114,6 +114,22 @@ def test_many_grids_high_dimension(ctx):
     assert ref.csr.nnz > 0
 
 
+def test_download_into_caller_arrays(ctx):
+    import torch
+    pts = gen.points_uniform(12, 4000, 3)
+    r = gen.radius_for_degree(4000, 3, 10.0)
+    T = gen.transforms(13, 3, 4, r)
+    res = ctx.all_pairs(pts, r, T, r)
+    rp, col = res.download()
+    bufs = (torch.empty(5000, dtype=torch.int64).pin_memory().numpy(),
+            torch.empty(res.nnz + 100, dtype=torch.int32).pin_memory().numpy())
+    rp2, col2 = res.download(bufs)
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+    with pytest.raises(ValueError):
+        res.download((np.empty(10, dtype=np.int64), np.empty(res.nnz, dtype=np.int32)))
+    res.release()
+
+
 def test_shift_only_table2_parameters(ctx):
     n, d, m, ct = 12800, 3, 20, 1.15
     r = gen.radius_fmt(n, d)

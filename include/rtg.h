@@ -270,8 +270,8 @@ rtg_status rtg_query_neighbors(rtg_ctx* ctx, const rtg_csr* graph, const int32_t
 /* r-NN queries of new points from the stored grids (Sec. V: keep all m grids; for a query,
  * examine the m cells that contain it).  An index holds, on the device, what a build of
  * Alg. 1 makes for one point set: the m grids' sorted cell keys with their point indices,
- * the per-point key rows, the FP32 rows, a copy of the points and the plan (error bounds,
- * key ranges, distance band).  It is charged to the context's budget until destroyed. */
+ * a hash table per grid from cell key to its run, the per-point key rows, the FP32 rows, a
+ * copy of the points and the plan (error bounds, key ranges, distance band).  It is charged to the context's budget until destroyed. */
 typedef struct rtg_index rtg_index;
 
 /* Builds the index of points (arguments as rtg_all_pairs; n may be 0).  *out receives a

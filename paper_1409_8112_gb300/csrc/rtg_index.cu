@@ -11,7 +11,8 @@
 //     sequence where the bound leaves the cell open (or for every axis when the query lies
 //     outside the indexed points' bounding box, where E does not hold); a cell outside the
 //     planned key range holds no point;
-//   * the cell's run in the sorted keys by binary search;
+//   * the cell's run in the sorted keys, from a per-grid open-addressing hash table built with
+//     the index (cell key -> first position and length of its run; one or two probes);
 //   * each candidate j: FP32 squared distance outside the band decides, else the FP64 sequence
 //     on the original coordinates (the band likewise only inside the bounding box);
 //   * j is reported by the first grid that puts it in the query's cell (the dedupe of
@@ -44,6 +45,8 @@ struct rtg_index {
   rtg::InstPlan* iplan = nullptr;
   rtg::GridPlan* gplan = nullptr;
   double* T64 = nullptr;
+  unsigned long long* table = nullptr;  // m open-addressing tables of table_cap slots
+  long long table_cap = 0;              // slots per grid (a power of two, at least 2 n)
   double box_lo[rtg::kMaxDim] = {}, box_hi[rtg::kMaxDim] = {};
 };
 
@@ -108,15 +111,80 @@ __device__ bool query_key(const float* qf, bool in_box, const void* q, int dtype
   return ok;
 }
 
-// First position in [lo, hi) whose key is not below `key`.
+constexpr unsigned long long kEmptySlot = ~0ull;
+
+// Slot of a cell key in its grid's table (the splitmix64 finalizer as the mixing function).
+__device__ __forceinline__ unsigned long long key_hash(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+// One thread per sorted position: the head of every run of equal keys enters its grid's table
+// as (first position << 32) | length.  Grid t of the single indexed instance owns positions
+// [t n, (t + 1) n) of the sort.
 template <typename K>
-__device__ __forceinline__ long long lower_pos(const K* __restrict__ keys, long long lo,
-                                               long long hi, K key) {
-  while (lo < hi) {
-    const long long mid = (lo + hi) >> 1;
-    if (keys[mid] < key) lo = mid + 1; else hi = mid;
+__global__ void __launch_bounds__(256) k_index_table(const K* __restrict__ skeys, long long n,
+                                                     int m, unsigned long long* table,
+                                                     long long cap, unsigned int* errors) {
+  const long long N = n * m;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long t = p / n, g0 = t * n, g1 = g0 + n;
+    const K key = skeys[p];
+    if (p > g0 && skeys[p - 1] == key) continue;  // not a run head
+    // run end: galloping, then bisection (runs of a large cell can be long)
+    long long lo = p + 1, step = 1, hi = lo;
+    while (true) {
+      hi = lo + step;
+      if (hi >= g1) {
+        hi = g1;
+        break;
+      }
+      if (skeys[hi] != key) break;
+      lo = hi + 1;
+      step <<= 1;
+    }
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (skeys[mid] == key) lo = mid + 1; else hi = mid;
+    }
+    const unsigned long long word = ((unsigned long long)p << 32) | (unsigned long long)(lo - p);
+    unsigned long long* tab = table + t * cap;
+    unsigned long long slot = key_hash((unsigned long long)key) & (unsigned long long)(cap - 1);
+    bool placed = false;
+    for (long long probe = 0; probe < cap; ++probe) {  // at most half full: ends early
+      if (atomicCAS(tab + slot, kEmptySlot, word) == kEmptySlot) {
+        placed = true;
+        break;
+      }
+      slot = (slot + 1) & (unsigned long long)(cap - 1);
+    }
+    if (!placed) atomicOr(errors, kErrLargeOverflow);
   }
-  return lo;
+}
+
+// [first, end) of the run of `key` in grid t's part of the sort, or an empty range.
+template <typename K>
+__device__ __forceinline__ void find_run(const K* __restrict__ skeys,
+                                         const unsigned long long* __restrict__ tab,
+                                         long long cap, K key, long long* lo, long long* hi) {
+  unsigned long long slot = key_hash((unsigned long long)key) & (unsigned long long)(cap - 1);
+  *lo = *hi = 0;
+  for (long long probe = 0; probe < cap; ++probe) {
+    const unsigned long long w = __ldg(tab + slot);
+    if (w == kEmptySlot) return;
+    const long long first = (long long)(w >> 32);
+    if (skeys[first] == key) {
+      *lo = first;
+      *hi = first + (long long)(w & 0xffffffffull);
+      return;
+    }
+    slot = (slot + 1) & (unsigned long long)(cap - 1);
+  }
 }
 
 // WRITE = false: row_cnt[k] = number of answers of query k.  WRITE = true: the answers go to
@@ -125,7 +193,8 @@ template <typename K, int DPAD, bool WRITE>
 __global__ void __launch_bounds__(kIndexThreads) k_index_query(
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const GridPlan* __restrict__ gplan, const double* __restrict__ T64,
-    const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N,
+    const K* __restrict__ skeys, const uint32_t* __restrict__ svals,
+    const unsigned long long* __restrict__ table, long long cap,
     const K* __restrict__ key_mat, int m, const float* __restrict__ pf,
     const void* __restrict__ queries, int dtype, long long nq, QueryBox box,
     unsigned int* row_cnt, const OutSlot* out, Status* st) {
@@ -167,18 +236,12 @@ __global__ void __launch_bounds__(kIndexThreads) k_index_query(
     if (lane < m) {
       has0 = query_key<K, DPAD>(qf, in_box, queries, dtype, kq, I, gplan[lane],
                                 T64 + I.T0 + (size_t)lane * tstride, &key0);
-      if (has0) {
-        lo0 = lower_pos(skeys, 0, N, key0);
-        hi0 = key0 == ~(K)0 ? N : lower_pos(skeys, lo0, N, (K)(key0 + 1));
-      }
+      if (has0) find_run(skeys, table + (long long)lane * cap, cap, key0, &lo0, &hi0);
     }
     if (lane + 32 < m) {
       has1 = query_key<K, DPAD>(qf, in_box, queries, dtype, kq, I, gplan[lane + 32],
                                 T64 + I.T0 + (size_t)(lane + 32) * tstride, &key1);
-      if (has1) {
-        lo1 = lower_pos(skeys, 0, N, key1);
-        hi1 = key1 == ~(K)0 ? N : lower_pos(skeys, lo1, N, (K)(key1 + 1));
-      }
+      if (has1) find_run(skeys, table + (long long)(lane + 32) * cap, cap, key1, &lo1, &hi1);
     }
     const float2 band = IP.filter_on && in_box ? make_float2(IP.s_lo, IP.s_hi)
                                                : make_float2(-1.0f, __int_as_float(0x7f800000));
@@ -250,7 +313,8 @@ void query_launch(const rtg_index* ix, const void* q, long long nq, const QueryB
   if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
   if (blocks < 1) blocks = 1;
   k_index_query<K, DPAD, WRITE><<<(unsigned)blocks, kIndexThreads, 0, s>>>(
-      ix->inst, ix->iplan, ix->gplan, ix->T64, (const K*)ix->skeys, ix->svals, ix->N,
+      ix->inst, ix->iplan, ix->gplan, ix->T64, (const K*)ix->skeys, ix->svals, ix->table,
+      ix->table_cap,
       (const K*)ix->key_mat, ix->m, ix->pf, q, ix->dtype, nq, box, row_cnt, out, st);
 }
 
@@ -333,7 +397,11 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
                b_inst = align256(sizeof(rtg::Inst)), b_ip = align256(sizeof(rtg::InstPlan)),
                b_gp = align256(sizeof(rtg::GridPlan) * (size_t)m),
                b_T = align256(sizeof(double) * (size_t)m * (it.d * it.d + it.d));
-  const size_t total = b_pts + b_pf + b_kr + b_sk + b_sv + b_inst + b_ip + b_gp + b_T;
+  long long cap = 1;
+  while (cap < 2 * (long long)it.n) cap <<= 1;  // at most half full: short probe runs
+  ix->table_cap = cap;
+  const size_t b_tab = align256(sizeof(unsigned long long) * (size_t)cap * m);
+  const size_t total = b_pts + b_pf + b_kr + b_sk + b_sv + b_inst + b_ip + b_gp + b_T + b_tab;
   if ((s = alloc_out_on(c, c->stream, total, &ix->mem)) != RTG_OK) {
     delete ix;
     return s;
@@ -355,6 +423,7 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
   ix->iplan = (rtg::InstPlan*)take(b_ip);
   ix->gplan = (rtg::GridPlan*)take(b_gp);
   ix->T64 = (double*)take(b_T);
+  ix->table = (unsigned long long*)take(b_tab);
   rtg::Inst I = c->h_inst[0];
   const void* src_pts = I.pts;
   I.pts = ix->pts;
@@ -379,7 +448,28 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
                 cudaMemcpyDeviceToDevice)) != RTG_OK ||
       (s = copy(ix->inst, &I, sizeof(I), cudaMemcpyHostToDevice)) != RTG_OK ||
       (s = copy(hb, c->bbox.p, sizeof(hb), cudaMemcpyDeviceToHost)) != RTG_OK ||
-      (s = cuda_ok(c, cudaStreamSynchronize(st), "index copy")) != RTG_OK) {
+      (s = cuda_ok(c, cudaMemsetAsync(ix->table, 0xff, sizeof(unsigned long long) * (size_t)cap * m,
+                                      st),
+                   "index table")) != RTG_OK ||
+      (s = cuda_ok(c, cudaMemsetAsync(&((rtg::Status*)c->status.p)->errors, 0,
+                                      sizeof(unsigned int), st),
+                   "index table")) != RTG_OK) {
+    free_index(c, ix);
+    return s;
+  }
+  {
+    long long blocks = (ix->N + 255) / 256;
+    if (blocks > 16LL * c->num_sms) blocks = 16LL * c->num_sms;
+    unsigned int* errors = &((rtg::Status*)c->status.p)->errors;
+    if (ix->key64)
+      rtg::k_index_table<unsigned long long><<<(unsigned)blocks, 256, 0, st>>>(
+          (const unsigned long long*)ix->skeys, it.n, m, ix->table, cap, errors);
+    else
+      rtg::k_index_table<uint32_t><<<(unsigned)blocks, 256, 0, st>>>(
+          (const uint32_t*)ix->skeys, it.n, m, ix->table, cap, errors);
+  }
+  if ((s = cuda_ok(c, cudaGetLastError(), "index table")) != RTG_OK ||
+      (s = read_status(c)) != RTG_OK || (s = check_errors(c, ~0u)) != RTG_OK) {
     free_index(c, ix);
     return s;
   }

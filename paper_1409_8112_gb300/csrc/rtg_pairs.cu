@@ -61,27 +61,6 @@ __device__ __forceinline__ double exact_dist2(const void* pts, int dtype, long l
   return s;
 }
 
-__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int* total,
-                                                        unsigned int* sbuf) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned int x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sbuf[warp] = x;
-  __syncthreads();
-  unsigned int wpre = 0, tot = 0;
-  for (int w = 0; w < nw; ++w) {
-    const unsigned int c = sbuf[w];
-    if (w < warp) wpre += c;
-    tot += c;
-  }
-  __syncthreads();
-  *total = tot;
-  return wpre + x - v;
-}
-
 __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v,
                                                                 unsigned long long* total,
                                                                 unsigned long long* sbuf) {
@@ -369,7 +348,6 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   __syncthreads();
 
   const unsigned int full = 0xffffffffu;
-  const unsigned int lt = (1u << lane) - 1u;
   const unsigned int le = lane == 31 ? full : ((2u << lane) - 1u);
   const long long nspans = (N + span - 1) / span;
   Tally tl;

@@ -17,8 +17,9 @@
 //     on the original coordinates (the band likewise only inside the bounding box);
 //   * j is reported by the first grid that puts it in the query's cell (the dedupe of
 //     Sec. III-B by key rows), so every answer appears once.
-// One warp per query.  Two passes: count the answers, scan the counts into row pointers, write
-// the answers, then sort each row (the pair path's row sort).
+// One thread per query for indexes of light cells, one warp per query (32 candidates at a time)
+// for dense ones.  Two passes: count the answers, scan the counts into row pointers, write the
+// answers, then sort each row (the pair path's row sort).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,6 +48,7 @@ struct rtg_index {
   double* T64 = nullptr;
   unsigned long long* table = nullptr;  // m open-addressing tables of table_cap slots
   long long table_cap = 0;              // slots per grid (a power of two, at least 2 n)
+  bool thread_queries = true;  // light cells: one thread per query, else one warp per query
   double box_lo[rtg::kMaxDim] = {}, box_hi[rtg::kMaxDim] = {};
 };
 
@@ -305,10 +307,113 @@ __global__ void __launch_bounds__(kIndexThreads) k_index_query(
   if (lane == 0 && rechecks) atomicAdd(&st->dist_rechecks, (unsigned long long)rechecks);
 }
 
+// One thread per query, for indexes whose cells hold few points (a warp per query would leave
+// most lanes idle): the thread walks the m grids in order, keeping the query's keys for the
+// first-grid rule, and writes its own row.
+template <typename K, int DPAD, bool WRITE>
+__global__ void __launch_bounds__(kIndexThreads) k_index_query_thread(
+    const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
+    const GridPlan* __restrict__ gplan, const double* __restrict__ T64,
+    const K* __restrict__ skeys, const uint32_t* __restrict__ svals,
+    const unsigned long long* __restrict__ table, long long cap,
+    const K* __restrict__ key_mat, int m, const float* __restrict__ pf,
+    const void* __restrict__ queries, int dtype, long long nq, QueryBox box,
+    unsigned int* row_cnt, const OutSlot* out, Status* st) {
+  const Inst I = inst[0];
+  const InstPlan IP = iplan[0];
+  const int d = I.d, tstride = d * d + d;
+  unsigned int rechecks = 0;
+  for (long long kq = blockIdx.x * (long long)blockDim.x + threadIdx.x; kq < nq;
+       kq += (long long)gridDim.x * blockDim.x) {
+    float qf[DPAD];
+    bool in_box = true, finite = true;
+#pragma unroll
+    for (int l = 0; l < DPAD; ++l) {
+      qf[l] = 0.0f;
+      if (l < d) {
+        const double x = coord(queries, dtype, kq, d, l);
+        finite &= isfinite(x);
+        in_box &= x >= box.lo[l] && x <= box.hi[l];
+        qf[l] = dtype == 0 ? __double2float_rn(x) : (float)x;
+        finite &= isfinite(qf[l]);
+      }
+    }
+    if (!finite) {
+      atomicOr(&st->errors, kErrNonFinite);
+      if (!WRITE) row_cnt[kq] = 0u;
+      continue;
+    }
+    const float2 band = IP.filter_on && in_box ? make_float2(IP.s_lo, IP.s_hi)
+                                               : make_float2(-1.0f, __int_as_float(0x7f800000));
+    K keyq[kMaxGrids];
+    unsigned long long has = 0;  // grids whose planned range holds the query's cell
+    unsigned int found = 0;
+    long long obase = 0;
+    if (WRITE) obase = out->row_ptr[kq];
+    for (int t = 0; t < m; ++t) {
+      if (!query_key<K, DPAD>(qf, in_box, queries, dtype, kq, I, gplan[t],
+                              T64 + I.T0 + (size_t)t * tstride, &keyq[t]))
+        continue;
+      has |= 1ull << t;
+      long long lo, hi;
+      find_run(skeys, table + (long long)t * cap, cap, keyq[t], &lo, &hi);
+      for (long long pos = lo; pos < hi; ++pos) {
+        const unsigned int j = svals[pos];
+        float sf = 0.0f;
+        const float4* pj = reinterpret_cast<const float4*>(pf + (size_t)j * DPAD);
+#pragma unroll
+        for (int v = 0; v < DPAD / 4; ++v) {
+          const float4 y = __ldg(pj + v);
+          float e = qf[4 * v] - y.x;
+          sf = fmaf(e, e, sf);
+          e = qf[4 * v + 1] - y.y;
+          sf = fmaf(e, e, sf);
+          e = qf[4 * v + 2] - y.z;
+          sf = fmaf(e, e, sf);
+          e = qf[4 * v + 3] - y.w;
+          sf = fmaf(e, e, sf);
+        }
+        if (sf > band.y) continue;
+        if (sf >= band.x) {
+          double s2 = 0.0;
+          for (int l = 0; l < d; ++l) {
+            const double e = __dsub_rn(coord(queries, dtype, kq, d, l),
+                                       coord(I.pts, dtype, (long long)j, d, l));
+            s2 = __fma_rn(e, e, s2);
+          }
+          ++rechecks;
+          if (!(s2 <= IP.rr)) continue;
+        }
+        // reported by the first grid that puts j in the query's cell
+        bool earlier = false;
+        for (int u = 0; u < t && !earlier; ++u)
+          earlier = ((has >> u) & 1ull) && key_mat[(size_t)j * m + u] == keyq[u];
+        if (earlier) continue;
+        if (WRITE) out->col[obase + found] = (int)j;
+        ++found;
+      }
+    }
+    if (!WRITE) row_cnt[kq] = found;
+  }
+  for (int o = 16; o > 0; o >>= 1) rechecks += __shfl_xor_sync(0xffffffffu, rechecks, o);
+  if ((threadIdx.x & 31) == 0 && rechecks)
+    atomicAdd(&st->dist_rechecks, (unsigned long long)rechecks);
+}
+
 template <typename K, int DPAD, bool WRITE>
 void query_launch(const rtg_index* ix, const void* q, long long nq, const QueryBox& box,
                   unsigned int* row_cnt, const OutSlot* out, Status* st, int num_sms,
                   cudaStream_t s) {
+  if (ix->thread_queries) {
+    long long blocks = (nq + kIndexThreads - 1) / kIndexThreads;
+    if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+    if (blocks < 1) blocks = 1;
+    k_index_query_thread<K, DPAD, WRITE><<<(unsigned)blocks, kIndexThreads, 0, s>>>(
+        ix->inst, ix->iplan, ix->gplan, ix->T64, (const K*)ix->skeys, ix->svals, ix->table,
+        ix->table_cap, (const K*)ix->key_mat, ix->m, ix->pf, q, ix->dtype, nq, box, row_cnt,
+        out, st);
+    return;
+  }
   long long blocks = (nq + kIndexThreads / 32 - 1) / (kIndexThreads / 32);
   if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
   if (blocks < 1) blocks = 1;
@@ -378,6 +483,9 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
   rtg_status s = build(c, q, &tmp);
   if (s != RTG_OK) return s;
   const int key_bits = tmp.stats.key_bits;
+  // candidates per sorted position: about how many points share a cell with a query
+  const double cand_per_pos =
+      it.n > 0 ? (double)tmp.stats.total_candidates / ((double)it.n * m) : 0.0;
   release_out(c, &tmp);
   rtg_index* ix = new rtg_index();
   ix->n = it.n;
@@ -387,6 +495,7 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
   ix->dpad = rtg::dpad_for(it.d);
   ix->key64 = key_bits > 32;
   ix->N = (long long)it.n * m;
+  ix->thread_queries = cand_per_pos < 4.0;
   if (it.n == 0) {  // nothing was planned: every query has an empty answer
     *out = ix;
     return RTG_OK;

@@ -87,6 +87,23 @@ def test_shift_only_grids_and_wider_cells(ctx):
     ix.close()
 
 
+def test_dense_cells_take_warp_queries(ctx):
+    # a tight cluster: cells of hundreds of points, so the index answers with a warp per query
+    rng = np.random.default_rng(97)
+    d, m, n = 3, 4, 6000
+    pts = np.clip(rng.normal(0.5, 0.02, (n, d)), 0.0, 1.0)
+    r = 0.03
+    T = gen.transforms(98, d, m, r)
+    ix = ctx.index(pts, r, T, r)
+    q = np.concatenate([np.clip(rng.normal(0.5, 0.03, (300, d)), 0.0, 1.0), pts[:30]])
+    res = ix.query(q)
+    ref = oracle.rtg_query(pts, r, T, r, q)
+    _compare(res, ref)
+    assert ref.nnz > 300 * 50  # dense answers
+    res.release()
+    ix.close()
+
+
 def test_empty_cases_and_errors(ctx):
     d, m = 3, 4
     pts = gen.points_uniform(95, 1000, d)

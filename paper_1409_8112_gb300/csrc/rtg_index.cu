@@ -671,7 +671,7 @@ rtg_status index_query(rtg_ctx* c, const rtg_index* ix, const void* queries, int
     c->h_slot->col_cap = nnz;
     cudaMemcpyAsync(c->out_slot.p, c->h_slot, sizeof(rtg::OutSlot), cudaMemcpyHostToDevice, st);
     rtg::launch_index_query<true>(ix, q, nq, box, a.row_cnt, a.out, a.st, c->num_sms, st);
-    rtg::launch_rowsort(a, st);
+    rtg::launch_rowsort(a, st, ix->n);  // answers are indexed-point indices
   }
   if ((s = cuda_ok(c, cudaGetLastError(), "index query")) != RTG_OK ||
       (s = read_status(c)) != RTG_OK || (s = check_errors(c, ~0u)) != RTG_OK) {

@@ -317,7 +317,8 @@ int launch_scatter(const BuildArgs& a, cudaStream_t s);
 // Bit-matrix dedupe: row counts from the matrices, then (after the scan) the columns.
 int launch_bits_count(const BuildArgs& a, cudaStream_t s);
 int launch_bits_write(const BuildArgs& a, cudaStream_t s);
-int launch_rowsort(const BuildArgs& a, cudaStream_t s);
+// Sorts every row of the output CSR; column values lie in [0, col_bound) (-1: a.n_total).
+int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound = -1);
 
 size_t sort_tiles_for(long long N, int items);
 size_t tc_tiles_bytes(long long n);

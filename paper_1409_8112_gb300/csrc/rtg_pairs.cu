@@ -61,6 +61,29 @@ __device__ __forceinline__ double exact_dist2(const void* pts, int dtype, long l
   return s;
 }
 
+// Exclusive scan of one value per thread over the block (a multiple of 32 threads, at most
+// 1024); sbuf holds one word per warp.
+__device__ __forceinline__ unsigned int block_excl_scan_any(unsigned int v, unsigned int* total,
+                                                            unsigned int* sbuf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sbuf[warp] = x;
+  __syncthreads();
+  unsigned int wpre = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    const unsigned int c = sbuf[w];
+    if (w < warp) wpre += c;
+    tot += c;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + x - v;
+}
+
 __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v,
                                                                 unsigned long long* total,
                                                                 unsigned long long* sbuf) {
@@ -1106,20 +1129,73 @@ __device__ __forceinline__ void warp_sort_row(int* a, int len) {
   }
 }
 
-// One warp per queued row of 33 .. kWarpRowMax entries.
-constexpr int kRowSmem = 8192;
+constexpr int kRowSmem = 16384;       // entries of a long row sorted in shared memory (64 KB)
+constexpr int kRowSortThreads = 256;  // threads of a block of the queued-row sort
+constexpr int kRowRadixMax = kRowSmem;  // longest row of the radix path
+
+// Stable LSD radix sort, 4-bit digits, of one row of len non-negative values below 2^bits:
+// the passes alternate between `row` and the buffer sm, and the result ends in `row` (the
+// row in global memory with a shared buffer, or two halves of the shared buffer).  Thread t owns the contiguous chunk [t C, (t + 1) C); its digit
+// counts sit in column t of cnt (16 x blockDim entries, digit major), whose exclusive scan in
+// that order gives every thread its output offsets, so equal digits keep their order.
+__device__ void block_radix_row(int* row, int* sm, unsigned short* cnt, unsigned int* sbuf,
+                                int len, int bits) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int C = (len + T - 1) / T;
+  const int beg = min(len, tid * C), end = min(len, beg + C);
+  int* src = row;
+  int* dst = sm;
+  for (int shift = 0; shift < bits; shift += 4) {
+#pragma unroll
+    for (int dg = 0; dg < 16; ++dg) cnt[dg * T + tid] = 0;
+    for (int x = beg; x < end; ++x) ++cnt[((src[x] >> shift) & 15) * T + tid];
+    __syncthreads();
+    // exclusive scan of the 16 T counts in digit-major order: thread t takes entries
+    // [16 t, 16 t + 16) of that order
+    unsigned int v[16], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      v[q] = cnt[16 * tid + q];
+      sum += v[q];
+    }
+    unsigned int total;
+    unsigned int run = block_excl_scan_any(sum, &total, sbuf);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      cnt[16 * tid + q] = (unsigned short)run;
+      run += v[q];
+    }
+    __syncthreads();
+    for (int x = beg; x < end; ++x) {
+      const int val = src[x];
+      unsigned short& o = cnt[((val >> shift) & 15) * T + tid];
+      dst[o] = val;
+      ++o;
+    }
+    __syncthreads();
+    int* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != row) {  // an odd number of passes: the result is in the shared buffer
+    for (int x = tid; x < len; x += T) row[x] = src[x];
+  }
+}
 
 // The queued rows: first one block per row of more than kWarpRowMax entries (bitonic sort in
 // shared memory, or in place when the row is longer than the buffer), then one warp per row of
-// kSmallCell + 1 .. kWarpRowMax entries (register sort).
-__global__ void __launch_bounds__(256) k_rowsort_queued(const OutSlot* out, long long n,
-                                                        const unsigned int* __restrict__ row_queue,
-                                                        const unsigned int* long_count,
-                                                        const unsigned int* mid_count) {
+// kSmallCell + 1 .. kWarpRowMax entries (register sort).  Rows of dense clusters run to
+// thousands of entries: a 64 KB buffer per block keeps them out of global memory, with three
+// blocks per SM working on different rows.
+__global__ void __launch_bounds__(kRowSortThreads) k_rowsort_queued(
+    const OutSlot* out, long long n, const unsigned int* __restrict__ row_queue,
+    const unsigned int* long_count, const unsigned int* mid_count, int bits) {
   const long long* __restrict__ row_ptr = out->row_ptr;
   int* col = out->col;
   const long long col_cap = out->col_cap;
-  __shared__ int buf[kRowSmem];
+  extern __shared__ int buf[];  // kRowSmem entries, then the radix counts
+  unsigned short* rcnt = reinterpret_cast<unsigned short*>(buf + kRowSmem);  // 16 x blockDim
+  __shared__ unsigned int rsbuf[kRowSortThreads / 32];
   const unsigned int cnt = *long_count;
   for (unsigned int k = blockIdx.x; k < cnt; k += gridDim.x) {
     const unsigned int row = row_queue[n - 1 - k];
@@ -1128,7 +1204,14 @@ __global__ void __launch_bounds__(256) k_rowsort_queued(const OutSlot* out, long
     long long L = 1;
     while (L < len) L <<= 1;
     __syncthreads();
-    if (L <= kRowSmem) {
+    if (len <= kRowSmem / 2) {  // both buffers in shared memory
+      for (long long x = threadIdx.x; x < len; x += blockDim.x) buf[x] = col[b + x];
+      __syncthreads();
+      block_radix_row(buf, buf + kRowSmem / 2, rcnt, rsbuf, (int)len, bits);
+      for (long long x = threadIdx.x; x < len; x += blockDim.x) col[b + x] = buf[x];
+    } else if (len <= kRowRadixMax) {  // passes alternate between the row and the buffer
+      block_radix_row(col + b, buf, rcnt, rsbuf, (int)len, bits);
+    } else if (L <= kRowSmem) {
       for (long long x = threadIdx.x; x < L; x += blockDim.x) buf[x] = x < len ? col[b + x] : INT_MAX;
       __syncthreads();
       for (long long kk = 2; kk <= L; kk <<= 1) {
@@ -1411,13 +1494,27 @@ int launch_scatter(const BuildArgs& a, cudaStream_t s) {
   return 1;
 }
 
-int launch_rowsort(const BuildArgs& a, cudaStream_t s) {
+int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound) {
   const unsigned blocks = (unsigned)((a.n_total + 255) / 256);
   unsigned int* long_count = &a.st->long_rows;
   unsigned int* mid_count = &a.st->mid_rows;
   k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, mid_count, long_count);
-  k_rowsort_queued<<<(unsigned)(4 * a.num_sms), 256, 0, s>>>(a.out, a.n_total, a.row_cnt,
-                                                              long_count, mid_count);
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem =
+      (size_t)kRowSmem * sizeof(int) + 16 * kRowSortThreads * sizeof(unsigned short);
+  const long long bound = col_bound >= 0 ? col_bound : a.n_total;  // columns lie below it
+  int bits = 1;
+  while (bits < 31 && (1LL << bits) < bound) ++bits;
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    cudaFuncSetAttribute(k_rowsort_queued, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  k_rowsort_queued<<<(unsigned)(3 * a.num_sms), kRowSortThreads, smem, s>>>(a.out, a.n_total,
+                                                                            a.row_cnt,
+                                                              long_count, mid_count, bits);
   return 2;
 }
 

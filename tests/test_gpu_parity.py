@@ -114,6 +114,16 @@ def test_many_grids_high_dimension(ctx):
     assert ref.csr.nnz > 0
 
 
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_rows_of_thousands_of_entries(ctx, symmetric):
+    # every pair within r: rows of up to n - 1 entries take the block radix row sort
+    n, d = 3000, 3
+    pts = gen.points_uniform(14, n, d) * 0.01
+    T = gen.transforms(15, d, 2, 0.1)
+    st, ref = run_and_compare(ctx, pts, 0.1, T, 0.1, symmetric=symmetric)
+    assert ref.csr.nnz == n * (n - 1) // 2
+
+
 def test_download_into_caller_arrays(ctx):
     import torch
     pts = gen.points_uniform(12, 4000, 3)

@@ -718,6 +718,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
   __shared__ __align__(16) float sa[kTL * DPAD];
   __shared__ __align__(16) float sb[kTL * DPAD];
   __shared__ uint32_t ia[kTL], ib[kTL];
+  // the first t keys of each member's key row for the ownership test (64 bytes a row at
+  // most; rows kLK + 1 apart so that neighbouring rows fall in different banks)
+  constexpr int kLK = 64 / (int)sizeof(K);
+  __shared__ K ska[kTL * (kLK + 1)], skb[kTL * (kLK + 1)];
   __shared__ unsigned long long s_emit[kPairThreads / 32][kWarpEmit];
   __shared__ unsigned int s_tally[4];
   if (threadIdx.x < 4) s_tally[threadIdx.x] = 0;
@@ -743,6 +747,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
     const long long bi = k - bj * (bj + 1) / 2;
     const unsigned int a0 = (unsigned int)bi * kTL, b0 = (unsigned int)bj * kTL;
     const unsigned int na = min((unsigned int)kTL, s - a0), nb = min((unsigned int)kTL, s - b0);
+    const int tg = (int)cell.grid;
+    const bool kst = tg <= kLK;  // key rows staged (else read from global memory)
     __syncthreads();
     for (unsigned int x = threadIdx.x; x < 2 * kTL; x += blockDim.x) {
       const bool first = x < kTL;
@@ -754,6 +760,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
         float4* dst = reinterpret_cast<float4*>((first ? sa : sb) + xx * DPAD);
 #pragma unroll
         for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+        if (kst) {
+          const K* kr = key_mat + (size_t)idx * m;
+          K* kd = (first ? ska : skb) + xx * (kLK + 1);
+          for (int u = 0; u < tg; ++u) kd[u] = __ldg(kr + u);
+        }
       }
     }
     __syncthreads();
@@ -766,10 +777,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
         const uint32_t ix = ia[x];
         i = min(ix, iy);
         j = max(ix, iy);
-        keep = decide_pair<K, DPAD, MODE>(i, j, (int)cell.grid, sa + x * DPAD, sb + y * DPAD,
-                                          key_mat + (size_t)ix * m, key_mat + (size_t)iy * m,
-                                          inst + cell.inst, iplan + cell.inst, band, dtype, tl,
-                                          sk.near_r);
+        keep = decide_pair<K, DPAD, MODE>(
+            i, j, tg, sa + x * DPAD, sb + y * DPAD,
+            kst ? ska + x * (kLK + 1) : key_mat + (size_t)ix * m,
+            kst ? skb + y * (kLK + 1) : key_mat + (size_t)iy * m, inst + cell.inst,
+            iplan + cell.inst, band, dtype, tl, sk.near_r);
       }
       if (MODE == kBits) deliver_bits(keep, i, j, inst + cell.inst, sk);
       else if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
@@ -964,49 +976,44 @@ __global__ void __launch_bounds__(256) k_scatter(const unsigned long long* __res
   const long long col_cap = out->col_cap;
   const long long cnt = min((long long)st->emitted, cap);
   bool overflow = false;
-  // four independent pairs per thread and step: their row-pointer loads and cursor atomics
-  // are in flight together
+  // four independent pairs per thread and step, their row-pointer loads and cursor atomics in
+  // flight together; lanes whose pairs share a row (a dense cell emits runs of them) take
+  // consecutive slots with one atomic
   constexpr int U = 4;
+  const unsigned int full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned int lt = (1u << lane) - 1u;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k0 < cnt;
-       k0 += U * stride) {
+  for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w0 < cnt;
+       w0 += U * stride) {  // warp-uniform
     unsigned long long pr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const long long k = k0 + u * stride;
+      const long long k = w0 + lane + u * stride;
       pr[u] = k < cnt ? pairs[k] : ~0ull;
     }
-    long long base[U];
-    unsigned int slot[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (pr[u] != ~0ull) {
-        const unsigned int i = (unsigned int)(pr[u] >> 32);
-        base[u] = row_ptr[i];
-        slot[u] = atomicAdd(&row_cnt[i], 1u);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (pr[u] != ~0ull) {
-        const long long pi = base[u] + slot[u];
-        if (pi < col_cap) col[pi] = (int)(unsigned int)pr[u]; else overflow = true;
-      }
-    }
-    if (symmetric) {
+    for (int side = 0; side < (symmetric ? 2 : 1); ++side) {
+      long long base[U];
+      unsigned int slot[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (pr[u] != ~0ull) {
-          const unsigned int j = (unsigned int)pr[u];
-          base[u] = row_ptr[j];
-          slot[u] = atomicAdd(&row_cnt[j], 1u);
-        }
+        const bool has = pr[u] != ~0ull;
+        const unsigned int row =
+            has ? (side == 0 ? (unsigned int)(pr[u] >> 32) : (unsigned int)pr[u]) : 0xffffffffu;
+        const unsigned int peers = __match_any_sync(full, row);
+        const int leader = __ffs(peers) - 1;
+        unsigned int b0 = 0;
+        if (has && lane == leader) b0 = atomicAdd(&row_cnt[row], (unsigned int)__popc(peers));
+        b0 = __shfl_sync(full, b0, leader);
+        slot[u] = b0 + (unsigned int)__popc(peers & lt);
+        base[u] = has ? row_ptr[row] : 0;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (pr[u] != ~0ull) {
-          const long long pj = base[u] + slot[u];
-          if (pj < col_cap) col[pj] = (int)(pr[u] >> 32); else overflow = true;
+          const long long pos = base[u] + slot[u];
+          const int v = side == 0 ? (int)(unsigned int)pr[u] : (int)(pr[u] >> 32);
+          if (pos < col_cap) col[pos] = v; else overflow = true;
         }
       }
     }

@@ -174,11 +174,11 @@ def measured_peaks():
 # profiled workloads and, for the sort, the variant the profiled run used
 # (digit bits, keys per tile, look-back).  None where the kernels changed after the capture.
 NCU_TRAFFIC = {
-    (100000, "fp64"): {"prep": 4868096, "keys": 3687168, "sort": {(8, 3072, 1): 26571264},
-                       "pairs": 13303296, "scan": 414976, "scatter": 4855552, "rowsort": 2717696},
-    (1000000, "fp32"): {"prep": 24069120, "keys": 69164800, "sort": {(8, 3072, 0): 454946816},
-                        "pairs": 329201408, "scan": 4017920, "scatter": 89130240,
-                        "rowsort": 32138752},
+    (100000, "fp64"): {"prep": 4868608, "keys": 3685888, "sort": {(8, 3072, 1): 26609408},
+                       "pairs": 13299456, "scan": 415232, "scatter": 4854784, "rowsort": 2706432},
+    (1000000, "fp32"): {"prep": 24102656, "keys": 69185536, "sort": {(8, 3072, 0): 455094784},
+                        "pairs": 329081088, "scan": 4024832, "scatter": 89386752,
+                        "rowsort": 32143104},
 }
 
 

@@ -501,8 +501,9 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
     return RTG_OK;
   }
   const size_t esz = dtype == RTG_DTYPE_F64 ? 8 : 4, kb = ix->key64 ? 8 : 4;
-  const size_t b_pts = align256((size_t)it.n * it.d * esz), b_pf = align256((size_t)it.n * ix->dpad * 4),
-               b_kr = align256((size_t)ix->N * kb), b_sk = b_kr, b_sv = align256((size_t)ix->N * 4),
+  const size_t b_pts = align256((size_t)it.n * it.d * esz),
+               b_pf = align256((size_t)it.n * ix->dpad * 4), b_kr = align256((size_t)ix->N * kb),
+               b_sk = b_kr, b_sv = align256((size_t)ix->N * 4),
                b_inst = align256(sizeof(rtg::Inst)), b_ip = align256(sizeof(rtg::InstPlan)),
                b_gp = align256(sizeof(rtg::GridPlan) * (size_t)m),
                b_T = align256(sizeof(double) * (size_t)m * (it.d * it.d + it.d));
@@ -543,14 +544,15 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
   auto copy = [&](void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
     return cuda_ok(c, cudaMemcpyAsync(dst, src, bytes, kind, st), "index copy");
   };
-  if ((s = copy(ix->pts, src_pts, (size_t)it.n * it.d * esz, cudaMemcpyDeviceToDevice)) != RTG_OK ||
-      (s = copy(ix->pf, c->pf.p, (size_t)it.n * ix->dpad * 4, cudaMemcpyDeviceToDevice)) != RTG_OK ||
-      (s = copy(ix->key_mat, c->key_mat.p, (size_t)ix->N * kb, cudaMemcpyDeviceToDevice)) != RTG_OK ||
+  const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+  if ((s = copy(ix->pts, src_pts, (size_t)it.n * it.d * esz, d2d)) != RTG_OK ||
+      (s = copy(ix->pf, c->pf.p, (size_t)it.n * ix->dpad * 4, d2d)) != RTG_OK ||
+      (s = copy(ix->key_mat, c->key_mat.p, (size_t)ix->N * kb, d2d)) != RTG_OK ||
       (s = copy(ix->skeys, sorted ? c->keys1.p : c->keys0.p, (size_t)ix->N * kb,
                 cudaMemcpyDeviceToDevice)) != RTG_OK ||
       (s = copy(ix->svals, sorted ? c->vals1.p : c->vals0.p, (size_t)ix->N * 4,
                 cudaMemcpyDeviceToDevice)) != RTG_OK ||
-      (s = copy(ix->iplan, c->iplan.p, sizeof(rtg::InstPlan), cudaMemcpyDeviceToDevice)) != RTG_OK ||
+      (s = copy(ix->iplan, c->iplan.p, sizeof(rtg::InstPlan), d2d)) != RTG_OK ||
       (s = copy(ix->gplan, c->gplan.p, sizeof(rtg::GridPlan) * (size_t)m,
                 cudaMemcpyDeviceToDevice)) != RTG_OK ||
       (s = copy(ix->T64, c->T64.p, sizeof(double) * (size_t)m * (it.d * it.d + it.d),

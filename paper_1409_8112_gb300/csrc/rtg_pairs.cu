@@ -1142,9 +1142,10 @@ constexpr int kRowRadixMax = kRowSmem;  // longest row of the radix path
 
 // Stable LSD radix sort, 4-bit digits, of one row of len non-negative values below 2^bits:
 // the passes alternate between `row` and the buffer sm, and the result ends in `row` (the
-// row in global memory with a shared buffer, or two halves of the shared buffer).  Thread t owns the contiguous chunk [t C, (t + 1) C); its digit
-// counts sit in column t of cnt (16 x blockDim entries, digit major), whose exclusive scan in
-// that order gives every thread its output offsets, so equal digits keep their order.
+// row in global memory with a shared buffer, or two halves of the shared buffer).  Thread t
+// owns the contiguous chunk [t C, (t + 1) C); its digit counts sit in column t of cnt
+// (16 x blockDim entries, digit major), whose exclusive scan in that order gives every thread
+// its output offsets, so equal digits keep their order.
 __device__ void block_radix_row(int* row, int* sm, unsigned short* cnt, unsigned int* sbuf,
                                 int len, int bits) {
   const int tid = threadIdx.x, T = blockDim.x;

@@ -328,7 +328,8 @@ int oracle_rtg_query(const void* pts, int dtype, int64_t n, int d, double r, con
   const int stride = d * d + d;
   std::vector<std::unordered_set<uint32_t>> sets((size_t)nq);
   std::vector<int64_t> q(d);
-  for (int t = 0; t < m; ++t) {
+  const int grids = MUTANT(9) ? 1 : m;  // mutant 9: a query sees only the first grid
+  for (int t = 0; t < grids; ++t) {
     const double* R = T + (size_t)t * stride;
     const double* s = R + d * d;
     std::map<std::vector<int64_t>, std::vector<uint32_t>> U;

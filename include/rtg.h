@@ -275,8 +275,8 @@ rtg_status rtg_query_neighbors(rtg_ctx* ctx, const rtg_csr* graph, const int32_t
 typedef struct rtg_index rtg_index;
 
 /* Builds the index of points (arguments as rtg_all_pairs; n may be 0).  *out receives a
- * handle owned by the caller, valid for this context until rtg_index_destroy.  Synchronous.
- * Errors as rtg_all_pairs. */
+ * handle owned by the caller, usable with this context only, until rtg_index_destroy (call it
+ * before rtg_destroy of the context).  Synchronous.  Errors as rtg_all_pairs. */
 rtg_status rtg_index_create(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
                             int64_t n, int d, double r, const double* transforms, int m,
                             double cell_side, rtg_index** out);
@@ -287,12 +287,14 @@ rtg_status rtg_index_create(rtg_ctx* ctx, const void* points, int dtype, int poi
  * it: squared distance on the original coordinates <= fl(r * r), the same FP64 sequence and
  * the same FP32 filter with FP64 recheck as the build.  out is a library-owned device CSR
  * with nq rows (out->symmetric = 0); free it with rtg_release.  Synchronous.
- * Errors: RTG_E_INVALID (NULL arguments, nq < 0 or nq >= 2^31, a query coordinate not finite
- * or beyond the FP32 range), RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT. */
+ * Errors: RTG_E_INVALID (NULL arguments, an index of another context, nq < 0 or
+ * nq >= 2^31, a query coordinate not finite or beyond the FP32 range), RTG_E_BUDGET,
+ * RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT. */
 rtg_status rtg_index_query(rtg_ctx* ctx, const rtg_index* index, const void* queries,
                            int queries_on_device, int64_t nq, rtg_csr* out);
 
-/* Frees the index's device memory (stream ordered) and the handle.  NULL is ignored. */
+/* Frees the index's device memory (stream ordered) and the handle.  NULL, or an index of
+ * another context, is ignored. */
 void rtg_index_destroy(rtg_ctx* ctx, rtg_index* index);
 
 /* Grid parameters chosen by rtg_tune_params. */

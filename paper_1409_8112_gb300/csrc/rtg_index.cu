@@ -30,6 +30,7 @@
 #include "rtg_host.h"
 
 struct rtg_index {
+  const rtg_ctx* owner = nullptr;  // the context that made it (its pool holds the memory)
   int64_t n = 0;
   int d = 0, m = 0, dtype = 0, dpad = 4;
   bool key64 = false;
@@ -488,6 +489,7 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
       it.n > 0 ? (double)tmp.stats.total_candidates / ((double)it.n * m) : 0.0;
   release_out(c, &tmp);
   rtg_index* ix = new rtg_index();
+  ix->owner = c;
   ix->n = it.n;
   ix->d = it.d;
   ix->m = m;
@@ -596,6 +598,7 @@ rtg_status index_query(rtg_ctx* c, const rtg_index* ix, const void* queries, int
                        int64_t nq, rtg_csr* out) {
   const cudaStream_t st = c->stream;
   std::memset(out, 0, sizeof(*out));
+  if (ix->owner != c) return fail(c, RTG_E_INVALID, "the index belongs to another context");
   rtg_status s;
   void* rp = nullptr;
   if ((s = alloc_out_on(c, st, sizeof(int64_t) * (size_t)(nq + 1), &rp)) != RTG_OK) return s;
@@ -686,6 +689,7 @@ rtg_status index_query(rtg_ctx* c, const rtg_index* ix, const void* queries, int
 }
 
 void index_destroy(rtg_ctx* c, rtg_index* ix) {
+  if (ix->owner != c) return;  // not this context's: its owner frees it
   free_index(c, ix);
   cudaStreamSynchronize(c->stream);
 }

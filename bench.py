@@ -163,7 +163,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic bytes per build for each timed phase (lower-bound model; see DESIGN.md):
+# Algorithmic bytes per build for each timed phase (lower-bound model):
 #   sort  : each pass reads and writes the N (key, index) pairs; with digits wider than 8 bits
 #           a histogram kernel first reads the N keys once (8-bit digits are counted by the key
 #           kernel as it writes the keys)

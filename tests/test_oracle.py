@@ -78,7 +78,7 @@ def test_shift_only_flag_gives_identity():
 
 
 def test_radius_for_expected_degree():
-    # r^d * zeta_d * n = 2 ln n; the survey's check value for n = 1e5, d = 6.
+    # r^d * zeta_d * n = 2 ln n, with zeta_6 = pi^3 / 6; for n = 1e5, d = 6, r = 0.188287.
     r = gen.radius_for_degree(100000, 6)
     assert abs(r - 0.18829) < 1e-5
     assert abs(r ** 6 * np.pi ** 3 / 6 * 100000 - 2 * np.log(100000)) < 1e-9

@@ -43,6 +43,11 @@ constexpr size_t kMaxGraphs = 32;  // executable graphs kept per context (one pe
 
 void rtg::set_last_error(const char* msg) { g_err = msg; }
 
+std::mutex& rtg::launch_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+
 namespace rtghost {
 
 std::string& last_error_text() { return g_err; }

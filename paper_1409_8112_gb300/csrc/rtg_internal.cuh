@@ -25,6 +25,8 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 namespace rtg {
 
 constexpr int kMaxDim = 16;
@@ -319,6 +321,11 @@ int launch_bits_count(const BuildArgs& a, cudaStream_t s);
 int launch_bits_write(const BuildArgs& a, cudaStream_t s);
 // Sorts every row of the output CSR; column values lie in [0, col_bound) (-1: a.n_total).
 int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound = -1);
+
+// Guards the per-device caches of kernel attributes (shared-memory limits, occupancy) that
+// the launch code keeps in statics: builds of several contexts may launch from several host
+// threads at once (the serving lanes).
+std::mutex& launch_attr_mutex();
 
 size_t sort_tiles_for(long long N, int items);
 size_t tc_tiles_bytes(long long n);

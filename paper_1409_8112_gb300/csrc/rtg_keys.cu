@@ -560,9 +560,13 @@ void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
   static size_t attr_smem[64] = {};  // largest size granted so far, per device
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
-    cudaFuncSetAttribute(k_keys<K, DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
+  {
+    std::lock_guard<std::mutex> lk(launch_attr_mutex());
+    if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
+      cudaFuncSetAttribute(k_keys<K, DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
+    }
   }
   k_keys<K, DPAD><<<(unsigned)a.blocks, kPointBlock, smem, s>>>(
       a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st, (K*)a.key_mat,

@@ -1321,12 +1321,15 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   auto kern = stage_rows ? k_pairs_warp<K, DPAD, MODE, true> : k_pairs_warp<K, DPAD, MODE, false>;
-  if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
-    cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
+  {
+    std::lock_guard<std::mutex> lk(launch_attr_mutex());
+    if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
+      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
+    }
   }
   kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(
       sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
@@ -1339,17 +1342,22 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
     // cells pays for a single wave of blocks that find nothing to do
     static bool mattr[64] = {};
     static int mocc[64] = {};
-    if (dev >= 0 && dev < 64 && !mattr[dev]) {
-      cudaFuncSetAttribute(k_pairs_medium<K, DPAD, MODE>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
-      int occ = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_medium<K, DPAD, MODE>,
-                                                        kMediumWarps * 32, msmem) != cudaSuccess)
-        occ = 0;
-      mocc[dev] = occ;
-      mattr[dev] = true;
+    int mper = 2;
+    {
+      std::lock_guard<std::mutex> lk(launch_attr_mutex());
+      if (dev >= 0 && dev < 64 && !mattr[dev]) {
+        cudaFuncSetAttribute(k_pairs_medium<K, DPAD, MODE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_medium<K, DPAD, MODE>,
+                                                          kMediumWarps * 32,
+                                                          msmem) != cudaSuccess)
+          occ = 0;
+        mocc[dev] = occ;
+        mattr[dev] = true;
+      }
+      if (dev >= 0 && dev < 64 && mocc[dev] > 0) mper = mocc[dev];
     }
-    const int mper = (dev >= 0 && dev < 64 && mocc[dev] > 0) ? mocc[dev] : 2;
     k_pairs_medium<K, DPAD, MODE><<<(unsigned)(mper * a.num_sms), kMediumWarps * 32, msmem, s>>>(
         sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
         make_sink(a));
@@ -1510,6 +1518,7 @@ int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound) {
   static bool attr[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
+  std::unique_lock<std::mutex> lk(launch_attr_mutex());
   const size_t smem =
       (size_t)kRowSmem * sizeof(int) + 16 * kRowSortThreads * sizeof(unsigned short);
   const long long bound = col_bound >= 0 ? col_bound : a.n_total;  // columns lie below it
@@ -1520,6 +1529,7 @@ int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound) {
                          (int)smem);
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
+  lk.unlock();
   k_rowsort_queued<<<(unsigned)(3 * a.num_sms), kRowSortThreads, smem, s>>>(a.out, a.n_total,
                                                                             a.row_cnt,
                                                               long_count, mid_count, bits);

@@ -444,6 +444,7 @@ template <typename F>
 void set_smem_once(F* kern, size_t smem, bool* done /*64*/) {
   int dev = 0;
   cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(launch_attr_mutex());
   if (dev >= 0 && dev < 64 && done[dev]) return;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (dev >= 0 && dev < 64) done[dev] = true;

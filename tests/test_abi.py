@@ -66,3 +66,18 @@ def test_create_without_gpu_reports_cuda_error():
     with pytest.raises(rtg.RTGError) as e:
         rtg.rtg_create(0)
     assert e.value.status == rtg.RTG_E_CUDA
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the public header compiles as strict C99 (no C++ in it)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "rtg.h"\n'
+                   'int main(void) { return rtg_status_string(RTG_OK) ? 0 : 1; }\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

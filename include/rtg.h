@@ -104,6 +104,12 @@ typedef struct {
   double max_abs_err_d2; /* tensor-core brute force: max |tile d^2 - FP64 d^2| over the pairs
                             the tiles did not reject */
   double band;           /* tensor-core brute force: half-width of the FP64 band around r^2 */
+  int64_t phase_bytes[8]; /* device-memory bytes each phase must read and write by its design
+                             (the phases of phase_us; [7] is their sum): the points, FP32 rows,
+                             key rows, every sort pass's keys and indices, the gathered rows,
+                             the emitted pairs, row counts and the CSR.  Cache hits and
+                             re-reads are not counted */
+  int64_t bytes_moved;    /* = phase_bytes[7] */
 } rtg_stats;
 
 typedef struct {
@@ -176,9 +182,17 @@ rtg_status rtg_transforms_generate(uint64_t seed, int d, int m, double cell_side
  *   flags      RTG_FLAG_SYMMETRIC, RTG_FLAG_TIMING
  *   out        receives a library-owned device CSR; free it with rtg_release
  * Errors: RTG_E_INVALID (n < 0 or n >= 2^31, n * m >= 2^31, d outside [1,16], m outside
- * [1,64], r or c not positive and finite, a non-finite coordinate or transform entry, a
- * coordinate beyond the FP32 range), RTG_E_KEY_OVERFLOW,
- * RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT.  n in {0, 1} gives an empty CSR. */
+ * [1,64], r or c not positive and finite, a non-finite coordinate or transform entry),
+ * RTG_E_KEY_OVERFLOW, RTG_E_BUDGET, RTG_E_NOMEM, RTG_E_CUDA, RTG_E_TIMEOUT.  n in {0, 1}
+ * gives an empty CSR.
+ * Limits beyond the paper's problem statement: n * m < 2^31, because every (point, grid)
+ * element of the sort has a 32-bit position; and the composite sort key spends, besides the
+ * mixed-radix cell key of each grid, log2 of the number of (instance, grid) blocks on a base
+ * that keeps the grids (and instances of a batch) apart, so RTG_E_KEY_OVERFLOW comes when the
+ * sum over grids of the cell-key ranges exceeds 2^64, not when one grid's range does.
+ * FP64 coordinates beyond the FP32 range are accepted: the FP32 filters cannot bound them,
+ * so the cell indices and distances whose error bounds they enter are decided in FP64
+ * (slower, same set). */
 rtg_status rtg_all_pairs(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
                          int64_t n, int d, double r, const double* transforms, int m,
                          double cell_side, uint32_t flags, rtg_csr* out);
@@ -221,10 +235,11 @@ rtg_status rtg_brute_force(rtg_ctx* ctx, const void* points, int dtype, int poin
  * Scratch: one file-scope device array of about 4.4 MiB (status counters, plan, FP32 rows of
  * up to 65536 points with d <= 16, row counts), held by every GPU that loads the library
  * until the process exits.  The first call on a device, with that device current, looks up
- * the array's device address; make that first call before any stream capture.  Every call on
- * a device shares the array and leaves its contents behind: calls that overlap on the GPU
- * (from different streams or threads) race and give undefined counts.  Nothing here calls
- * cudaMalloc, cudaFree or an allocating library routine.
+ * the array's device address; that first call must come before any stream capture.  Every
+ * call synchronises `stream` and copies the count back to host memory before it returns.
+ * Every call on a device shares the array and leaves its contents behind: calls that overlap
+ * on the GPU (from different streams or threads) race and give undefined counts.  Nothing
+ * here calls cudaMalloc, cudaFree or an allocating library routine.
  * Errors: RTG_E_INVALID (n > 65536, d outside [1,16], r not positive and finite, NULL
  * pointers, a non-finite coordinate), RTG_E_CUDA, RTG_E_TIMEOUT; text via
  * rtg_last_error(NULL). */
@@ -319,6 +334,25 @@ typedef struct {
 rtg_status rtg_tune_params(rtg_ctx* ctx, const void* points, int dtype, int points_on_device,
                            int64_t n, int d, double r, double target_recall, uint64_t seed,
                            uint32_t flags, rtg_param_choice* out);
+
+/* Failure-path testing (the paper has no counterpart).  Every device wait of the library
+ * (look-back chains of the sort and of the CSR row scan, the tensor-core kernel's wait for
+ * its MMAs) is bounded: after wait_limit iterations (0 = the default, 2^22; the tensor-core
+ * wait takes 16 times that) it gives up, flags the build and lets its kernel return, the call
+ * returns RTG_E_TIMEOUT and the context stays usable.  inject makes chosen waits wait for
+ * something that never happens, so that this path runs on demand:
+ *   RTG_INJECT_SORT_WAIT  look-back sort passes wait for an epoch no tile publishes
+ *   RTG_INJECT_SCAN_WAIT  the CSR row scan waits for predecessors that never publish
+ *   RTG_INJECT_TC_WAIT    the tensor-core brute force waits on a barrier nothing arrives on
+ * fail_alloc_after > 0 makes the fail_alloc_after-th device allocation of ctx from now on
+ * fail once with RTG_E_NOMEM.  inject = 0 and fail_alloc_after = 0 restore normal operation.
+ * Nothing here faults a GPU: each hook only makes a bounded wait or an allocation give up.
+ * Errors: RTG_E_INVALID (NULL ctx, unknown bits, wait_limit >= 2^31). */
+#define RTG_INJECT_SORT_WAIT 1u
+#define RTG_INJECT_SCAN_WAIT 2u
+#define RTG_INJECT_TC_WAIT 4u
+rtg_status rtg_set_test_hooks(rtg_ctx* ctx, uint32_t inject, uint32_t wait_limit,
+                              int64_t fail_alloc_after);
 
 /* Free the device memory of a CSR returned by this context and zero *csr. */
 rtg_status rtg_release(rtg_ctx* ctx, rtg_csr* csr);

@@ -34,7 +34,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", f"-DORACLE_MUTANT={mutant}", _SRC, "-o", tmp]
+           "-pthread", "-shared", f"-DORACLE_MUTANT={mutant}", _SRC, "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -90,9 +90,10 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.oracle_cells.argtypes = [vp, i32, i64, i32, vp, i32, dbl, vp, vp]
     lib.oracle_rtg.argtypes = [vp, i32, i64, i32, dbl, vp, i32, dbl, csrp, vp, vp]
     lib.oracle_rtg_query.argtypes = [vp, i32, i64, i32, dbl, vp, i32, dbl, vp, i64, csrp]
+    lib.oracle_rtg_threads.argtypes = [vp, i32, i64, i32, dbl, vp, i32, dbl, i32, csrp]
     lib.oracle_free.argtypes = [csrp]
     for f in (lib.oracle_brute, lib.oracle_exact_grid, lib.oracle_cells, lib.oracle_rtg,
-              lib.oracle_rtg_query):
+              lib.oracle_rtg_query, lib.oracle_rtg_threads):
         f.restype = ctypes.c_int
     lib.oracle_mutant.restype = ctypes.c_int
     _libs[mutant] = lib
@@ -187,6 +188,26 @@ def rtg(points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,
         raise ValueError("oracle_rtg: invalid arguments")
     stats = [{f: int(getattr(st[t], f)) for f, _ in _GridStats._fields_} for t in range(m)]
     return RTGResult(_take(lib, c), stats, int(near_r.value))
+
+
+def rtg_threads(points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,
+                threads: int = 0, mutant: int = 0) -> CSR:
+    """Alg. 1 with the Sec. III-B dedupe on several host threads (grids in parallel, then the
+    merge by row ranges); the same CSR as ``rtg``.  ``threads`` = 0 takes one per hardware
+    thread."""
+    lib = _lib(mutant)
+    p, dt = _points(points)
+    n, d = p.shape
+    T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
+    if T.size % (d * d + d) != 0:
+        raise ValueError("transforms must hold m * (d*d + d) values")
+    m = T.size // (d * d + d)
+    c = _CSR()
+    rc = lib.oracle_rtg_threads(p.ctypes.data, dt, n, d, float(r), T.ctypes.data, m,
+                                float(cell_side), int(threads), ctypes.byref(c))
+    if rc != 0:
+        raise ValueError("oracle_rtg_threads: invalid arguments")
+    return _take(lib, c)
 
 
 def rtg_query(points: np.ndarray, r: float, transforms: np.ndarray, cell_side: float,

@@ -18,6 +18,10 @@
 //                        to cells, go over all pairs inside each non-empty cell, report those
 //                        at distance at most r; duplicates across grids are removed with the
 //                        array of unordered sets of Sec. III-B (slot i holds j > i).
+//   oracle_rtg_threads - the same computation on several host threads: the m grids are
+//                        independent (each thread takes whole grids), and the merge into the
+//                        array of unordered sets is split by row ranges.  Used only for the
+//                        all-core CPU baseline; the tests check it equals oracle_rtg.
 //
 // Arithmetic (the readings of the paper that make the result unique):
 //   * FP32 coordinates are widened exactly to FP64; everything is FP64.
@@ -44,6 +48,7 @@
 #include <unordered_set>
 #include <vector>
 #include <algorithm>
+#include <thread>
 
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
@@ -309,6 +314,67 @@ int oracle_rtg(const void* pts, int dtype, int64_t n, int d, double r, const dou
     }
   }
   if (near_r_out) *near_r_out = near_r;
+  to_csr(sets, out);
+  return 0;
+}
+
+// Alg. 1 as in oracle_rtg, on `threads` host threads (0: one per hardware thread).  Worker w
+// takes grids w, w + threads, ...; each grid's reported pairs (lo << 32 | hi) go to its own
+// list.  The lists are then merged into the array of unordered sets by row ranges, worker w
+// owning rows [w n / threads, (w + 1) n / threads).  The set of pairs, and so the CSR, is the
+// one oracle_rtg returns.
+int oracle_rtg_threads(const void* pts, int dtype, int64_t n, int d, double r, const double* T,
+                       int m, double c, int threads, oracle_csr* out) {
+  if (n < 0 || d < 1 || d > 16 || m < 1 || !(c > 0) || !(r > 0) || !T || !out) return -1;
+  if (threads <= 0) threads = (int)std::thread::hardware_concurrency();
+  if (threads <= 0) threads = 1;
+  std::vector<double> p = widen(pts, dtype, n, d);
+  const double rr = r * r;
+  const int stride = d * d + d;
+  const int grids = MUTANT(7) ? (m > 1 ? m - 1 : 1) : m;
+  std::vector<std::vector<uint64_t>> found((size_t)grids);
+  auto grid_worker = [&](int w) {
+    std::vector<int64_t> q(d);
+    for (int t = w; t < grids; t += threads) {
+      const double* R = T + (size_t)t * stride;
+      const double* s = R + d * d;
+      std::map<std::vector<int64_t>, std::vector<uint32_t>> U;
+      for (int64_t i = 0; i < n; ++i) {
+        cell_of(&p[(size_t)i * d], R, s, d, c, q.data());
+        U[q].push_back((uint32_t)i);
+      }
+      std::vector<uint64_t>& F = found[(size_t)t];
+      for (const auto& cell : U) {
+        const auto& A = cell.second;
+        const size_t sz = A.size();
+        for (size_t a = 0; a < sz; ++a)
+          for (size_t b = MUTANT(8) ? a : a + 1; b < sz; ++b)
+            if (within(dist2(&p[(size_t)A[a] * d], &p[(size_t)A[b] * d], d), rr)) {
+              uint32_t lo = std::min(A[a], A[b]), hi = std::max(A[a], A[b]);
+              if (MUTANT(6)) std::swap(lo, hi);
+              F.push_back(((uint64_t)lo << 32) | hi);
+            }
+      }
+    }
+  };
+  std::vector<std::unordered_set<uint32_t>> sets((size_t)n);
+  auto merge_worker = [&](int w) {
+    const uint64_t lo = (uint64_t)((__int128)n * w / threads);
+    const uint64_t hi = (uint64_t)((__int128)n * (w + 1) / threads);
+    for (const auto& F : found)
+      for (uint64_t pr : F) {
+        const uint64_t i = pr >> 32;
+        if (i >= lo && i < hi) sets[(size_t)i].insert((uint32_t)pr);
+      }
+  };
+  auto run = [&](auto&& fn) {
+    std::vector<std::thread> pool;
+    for (int w = 1; w < threads; ++w) pool.emplace_back(fn, w);
+    fn(0);
+    for (auto& th : pool) th.join();
+  };
+  run(grid_worker);
+  run(merge_worker);
   to_csr(sets, out);
   return 0;
 }

@@ -67,6 +67,11 @@ rtg_status fail(rtg_ctx* ctx, rtg_status s, const std::string& msg) {
 
 size_t total_held(const rtg_ctx* c) { return c->ws_bytes + c->out_bytes; }
 
+// Test hook: the fail_alloc_at-th device allocation of the context fails (once).
+bool injected_alloc_failure(rtg_ctx* c) {
+  return c->fail_alloc_at > 0 && ++c->alloc_calls == c->fail_alloc_at;
+}
+
 // Grow a workspace buffer to at least `bytes` (contents are not kept).
 rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero) {
   if (bytes == 0) bytes = 16;
@@ -75,6 +80,8 @@ rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero) {
   if (c->budget && total_held(c) - b.cap + bytes > c->budget)
     return fail(c, RTG_E_BUDGET, "workspace of " + std::to_string(bytes) +
                                      " bytes exceeds the memory budget");
+  if (injected_alloc_failure(c))
+    return fail(c, RTG_E_NOMEM, "device allocation failed (injected by rtg_set_test_hooks)");
   if (b.p) {
     cudaStreamSynchronize(c->stream);
     cudaFree(b.p);
@@ -101,6 +108,8 @@ rtg_status alloc_out_on(rtg_ctx* c, cudaStream_t s, size_t bytes, void** p) {
     *p = nullptr;
     return RTG_OK;
   }
+  if (injected_alloc_failure(c))
+    return fail(c, RTG_E_NOMEM, "device allocation failed (injected by rtg_set_test_hooks)");
   {
     std::lock_guard<std::mutex> lk(c->live_mu);
     if (c->budget && total_held(c) + bytes > c->budget)
@@ -141,7 +150,7 @@ rtg_status check_errors(rtg_ctx* c, unsigned int mask) {
   const unsigned int e = c->h_status->errors & mask;
   if (!e) return RTG_OK;
   if (e & rtg::kErrNonFinite)
-    return fail(c, RTG_E_INVALID, "a point coordinate is not finite or exceeds the FP32 range");
+    return fail(c, RTG_E_INVALID, "a point coordinate is not finite");
   if (e & rtg::kErrKeyOverflow)
     return fail(c, RTG_E_KEY_OVERFLOW, "the cell index ranges need more than 64 key bits");
   if (e & rtg::kErrTimeout) return fail(c, RTG_E_TIMEOUT, "a bounded device wait ran out");
@@ -403,6 +412,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.bits = bitset ? (unsigned int*)c->bits.p : nullptr;
   a.sort_epoch = (unsigned int*)c->sort_epoch.p;
   a.num_sms = c->num_sms;
+  a.spin_limit = c->spin_limit;
+  a.inject = c->inject;
 
   const ShapeKey key{n_total, B, m, q.dtype, maxd, sym, q.count_only ? 1 : 0};
   auto git = c->guesses.find(key);
@@ -715,6 +726,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       }
     }
     const Status& h = *c->h_status;
+    if (h.errors & rtg::kErrTimeout) {  // whatever else is flagged follows from the timeout
+      release_out(c, out);
+      return fail(c, RTG_E_TIMEOUT, "a bounded device wait ran out");
+    }
     const unsigned int retry = rtg::kErrKeyBits | rtg::kErrPairOverflow;
     if (h.errors & retry) {
       // the launch assumptions were too small: take the device's values and run again
@@ -777,6 +792,38 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     }
     S.launches = launches;
     S.attempts = attempt + 1 - (tuned_now ? 1 : 0);
+    {
+      // bytes each phase reads and writes by its design (phase order of phase_us)
+      const double n_ = (double)n_total, N_ = (double)N, kb = a.key64 ? 8.0 : 4.0;
+      double in_bytes = 0.0;  // the points, n d S over the instances
+      for (int b = 0; b < B; ++b) in_bytes += (double)q.items[b].n * q.items[b].d * (double)esz;
+      const double P = (double)h.pairs, stored = (double)h.nnz;
+      const double rows = n_ * dpad * 4.0;
+      double pb[7] = {};
+      pb[0] = in_bytes + rows + 4.0 * n_;  // points in, FP32 rows and zeroed row counts out
+      if (m > 0) {
+        pb[1] = rows + N_ * kb;            // FP32 rows in, key rows out
+        // the first pass reads the key rows (indices implicit); every pass writes keys and
+        // indices, and the later ones also read them
+        pb[2] = a.passes > 0 ? N_ * kb + N_ * (kb + 4.0) +
+                                   (a.passes - 1) * 2.0 * N_ * (kb + 4.0) +
+                                   (a.sort_bits != 8 ? N_ * kb : 0.0)
+                             : 0.0;
+        pb[3] = N_ * (kb + 4.0) + N_ * dpad * 4.0 + (two_pass ? 0.0 : 8.0 * P);
+      } else {
+        pb[3] = rows + (two_pass ? 0.0 : 8.0 * P);  // brute force: the rows, the pairs out
+      }
+      pb[4] = 4.0 * n_ + 8.0 * (n_ + 1.0);  // row counts in, row pointers out
+      pb[5] = two_pass ? 4.0 * stored : 8.0 * P + 4.0 * stored;  // pairs in, columns out
+      pb[6] = 8.0 * stored;                                      // columns read and written
+      double tot = 0.0;
+      for (int p = 0; p < 7; ++p) {
+        S.phase_bytes[p] = (int64_t)pb[p];
+        tot += pb[p];
+      }
+      S.phase_bytes[7] = (int64_t)tot;
+      S.bytes_moved = (int64_t)tot;
+    }
     {
       float e;
       std::memcpy(&e, &h.tc_max_err_bits, 4);
@@ -842,6 +889,7 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
     const char* g = std::getenv("RTG_GRAPHS");
     c->use_graphs = !(g && std::strcmp(g, "0") == 0);
   }
+
   {
     // a pool of its own for the output CSRs, so that freed blocks stay cached between builds
     cudaMemPoolProps props = {};
@@ -940,6 +988,21 @@ void rtg_destroy(rtg_ctx* c) {
   if (!c) return;
   stop_server(c);
   destroy_ctx(c);
+}
+
+rtg_status rtg_set_test_hooks(rtg_ctx* c, uint32_t inject, uint32_t wait_limit,
+                              int64_t fail_alloc_after) {
+  if (!c) return fail(nullptr, RTG_E_INVALID, "ctx is NULL");
+  if (inject & ~(uint32_t)(RTG_INJECT_SORT_WAIT | RTG_INJECT_SCAN_WAIT | RTG_INJECT_TC_WAIT))
+    return fail(c, RTG_E_INVALID, "unknown hook bits");
+  if (wait_limit >= (1u << 31)) return fail(c, RTG_E_INVALID, "wait_limit must be below 2^31");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->inject = (inject & RTG_INJECT_SORT_WAIT ? rtg::kInjectSortWait : 0u) |
+              (inject & RTG_INJECT_SCAN_WAIT ? rtg::kInjectScanWait : 0u) |
+              (inject & RTG_INJECT_TC_WAIT ? rtg::kInjectTcWait : 0u);
+  c->spin_limit = wait_limit;
+  c->fail_alloc_at = fail_alloc_after > 0 ? c->alloc_calls.load() + fail_alloc_after : 0;
+  return RTG_OK;
 }
 
 rtg_status rtg_release(rtg_ctx* c, rtg_csr* csr) {

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -106,6 +107,13 @@ struct rtg_ctx {
   rtghost::Upload up_inst, up_T;
   rtghost::Server* server = nullptr;  // created by the first rtg_submit
   int last_sorted = 0;  // keys/vals buffer (0 or 1) that holds the last build's sorted keys
+  // Failure-path hooks (rtg_set_test_hooks): the bounded device waits' iteration limit (0:
+  // the default), waits made to wait for something that never happens (rtg::kInject*), and
+  // the number of the device allocation that is made to fail (0: none).
+  unsigned int spin_limit = 0;
+  unsigned int inject = 0;
+  long long fail_alloc_at = 0;
+  std::atomic<long long> alloc_calls{0};
 };
 
 namespace rtghost {

@@ -57,6 +57,22 @@ enum : uint32_t {
   kErrSortRange = 512u      // a sort tile or offset fell outside the keys (internal)
 };
 
+// Bounded device waits (look-back chains, tensor-core commits): iterations before a wait
+// gives up, sets kErrTimeout and lets its kernel return.  A context may set a smaller limit
+// (BuildArgs::spin_limit; 0 takes this one).
+constexpr unsigned int kDefaultSpinLimit = 1u << 22;
+__host__ __device__ inline unsigned int spin_limit_of(unsigned int v) {
+  return v ? v : kDefaultSpinLimit;
+}
+
+// Test hooks (BuildArgs::inject): make one kind of bounded wait wait for something that never
+// happens, so that its timeout path runs.  Nothing faults: the wait gives up after its limit.
+enum : unsigned int {
+  kInjectSortWait = 1u,  // look-back sort passes wait for an epoch no tile publishes
+  kInjectScanWait = 2u,  // the CSR row scan waits for predecessors that never publish
+  kInjectTcWait = 4u     // the tensor-core kernel waits on an mbarrier nothing arrives on
+};
+
 // Cells with more points than this are enumerated by the tiled large-cell kernel.
 constexpr int kSmallCell = 32;
 
@@ -236,6 +252,8 @@ struct BuildArgs {
   int passes;          // radix passes launched
   unsigned int* sort_epoch;  // device counter: look-back epoch base, advanced by every sort
   int num_sms;
+  unsigned int spin_limit;  // bounded waits: iterations before giving up (0: the default)
+  unsigned int inject;      // test hooks (kInject*), 0 in normal use
 };
 
 // With 8-bit digits the key kernel also counts the digits of every radix pass (the sort then

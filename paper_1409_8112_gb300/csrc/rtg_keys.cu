@@ -75,8 +75,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
                                                        PlanArgs pa) {
   // The bounding box only has to contain every coordinate: it is kept in FP32, each value
   // widened by one ulp (the FP32 row is the FP64 value rounded to nearest), so that no FP64
-  // arithmetic runs here.  Finiteness of FP64 input is tested on the exponent bits; values
-  // beyond the FP32 range count as not finite (the FP32 rows could not hold them).
+  // arithmetic runs here.  Finiteness of FP64 input is tested on the exponent bits.  A finite
+  // FP64 value beyond the FP32 range has an infinite FP32 row entry and goes into the box as
+  // the FP64 value itself; the plan's bounds (cell index, distance band) then become infinite
+  // or non-finite for its instance, which sends every decision of that instance to the FP64
+  // sequences.
   __shared__ int s_b;
   __shared__ float smn[kPrepThreads / 32][DPAD], smx[kPrepThreads / 32][DPAD];
   const int b = block_instance<true>(inst, B, blockIdx.x, &s_b);
@@ -101,16 +104,22 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
         float f;
         if (dtype == 0) {
           const double x = __ldg((const double*)I.pts + i * d + l);
-          bad |= ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+          const bool nonfinite = ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+          bad |= nonfinite;
           f = __double2float_rn(x);
-          mn[l] = fminf(mn[l], nextafterf(f, -FLT_MAX));
-          mx[l] = fmaxf(mx[l], nextafterf(f, FLT_MAX));
+          if (isfinite(f)) {
+            mn[l] = fminf(mn[l], nextafterf(f, -FLT_MAX));
+            mx[l] = fmaxf(mx[l], nextafterf(f, FLT_MAX));
+          } else if (!nonfinite) {  // beyond the FP32 range (rare): the FP64 value itself
+            atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 0], enc_double(x));
+            atomicMax(&bbox[((size_t)b * kMaxDim + l) * 2 + 1], ~enc_double(x));
+          }
         } else {
           f = __ldg((const float*)I.pts + i * d + l);
           mn[l] = fminf(mn[l], f);
           mx[l] = fmaxf(mx[l], f);
+          bad |= !isfinite(f);
         }
-        bad |= !isfinite(f);
         row[l] = f;
       }
     }

@@ -99,14 +99,20 @@ extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int
   I.inv_c = 1.0;
   I.inv_cf = 1.0f;
   // the counters and the bounding box must start at zero; the instance record is copied in;
-  // every other region is fully rewritten (plan, point rows) or only incremented and never
-  // read (row counts)
+  // the plan and the point rows are fully rewritten, and the row counts are zeroed by the
+  // prep kernel and then only incremented (the count itself comes from Status.pairs)
   if (cudaMemsetAsync(a.st, 0, sizeof(rtg::Status), s) != cudaSuccess ||
       cudaMemsetAsync(a.bbox, 0, kBoxBytes, s) != cudaSuccess ||
       cudaMemcpyAsync((void*)a.inst, &I, sizeof(I), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(RTG_E_CUDA, "scratch set-up failed");
   rtg::launch_prep_plan(a, s);
   rtg::launch_brute(a, rtg::kCount, s);
+  {
+    // a launch that failed without a sticky error would otherwise leave Status at zero and
+    // report a count of 0
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return fail(RTG_E_CUDA, cudaGetErrorString(le));
+  }
   rtg::Status h;
   std::memset(&h, 0, sizeof(h));
   cudaError_t e = cudaMemcpyAsync(&h, a.st, sizeof(rtg::Status), cudaMemcpyDeviceToHost, s);

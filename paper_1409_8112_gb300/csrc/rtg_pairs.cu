@@ -42,7 +42,6 @@ constexpr int kTL = 128;                   // large-cell tile
 constexpr int kMediumMax = 256;            // large cells up to this size: one warp per cell
 constexpr int kMediumWarps = 4;            // warps per block of the medium-cell kernel
 constexpr int kMediumKeyBytes = 8192;      // per warp: staged key rows of a medium cell
-constexpr unsigned int kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ double load_coord(const void* pts, int dtype, long long i, int d,
                                              int l) {
@@ -355,6 +354,9 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned int s_maxcell;
   __shared__ unsigned int s_tally[4];
+  // a sort that gave up (a bounded wait ran out) or flagged an offset may have left stale
+  // point indices behind: nothing is read through them (the build reports the error)
+  if (st->errors & (kErrTimeout | kErrSortRange)) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   unsigned char* ws = smem + (size_t)wib * warp_bytes;
   unsigned long long* w_emit = reinterpret_cast<unsigned long long*>(ws);
@@ -859,7 +861,8 @@ constexpr int kScanTile = 256 * kScanItems;
 __global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, const OutSlot* out,
                                               long long n, unsigned long long* lookback,
                                               unsigned int* tile_counter, Status* st,
-                                              unsigned int tiles) {
+                                              unsigned int tiles, unsigned int spin_limit,
+                                              unsigned int inject) {
   long long* row_ptr = out->row_ptr;
   __shared__ unsigned long long sbuf[8];
   __shared__ unsigned long long s_base;
@@ -909,11 +912,12 @@ __global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, const OutSl
         // before tile 0 there is nothing: read as an inclusive prefix of zero
         const unsigned long long w =
             q >= 0 ? *reinterpret_cast<const volatile unsigned long long*>(lookback + q) : kPre;
-        const unsigned int flag = (unsigned int)(w >> 62);
+        // (test hook: predecessors read as never published, so the wait runs to its limit)
+        const unsigned int flag = (inject & kInjectScanWait) ? 0u : (unsigned int)(w >> 62);
         const unsigned int pre = __ballot_sync(full, flag == 2);
         const unsigned int upto = pre ? (((pre & (0u - pre)) - 1u) << 1 | 1u) : full;
         if (__ballot_sync(full, flag == 0) & upto) {  // a tile that matters has not published
-          if (++spins > kSpinLimit) {
+          if (++spins > spin_limit) {
             if (lane == 0) atomicOr(&st->errors, kErrTimeout);
             break;
           }
@@ -1420,7 +1424,8 @@ void launch_scan(const BuildArgs& a, cudaStream_t s) {
   const unsigned tiles = (unsigned)((a.n_total + kScanTile - 1) / kScanTile);
   cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
   k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.out, a.n_total, a.scan_lookback,
-                               &a.st->scan_tiles, a.st, tiles);
+                               &a.st->scan_tiles, a.st, tiles, spin_limit_of(a.spin_limit),
+                               a.inject);
 }
 
 namespace {

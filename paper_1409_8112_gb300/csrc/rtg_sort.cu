@@ -47,7 +47,6 @@ struct SortShape {
 #define RTG_SORT_WIN 4  // look-back window: predecessors read per round
 #endif
 constexpr unsigned long long kFlagAgg = 1ull, kFlagPrefix = 2ull;
-constexpr unsigned int kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned long long pack_lb(unsigned long long flag, unsigned int epoch,
                                                       unsigned int value) {
@@ -366,7 +365,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ digit_off,
     unsigned long long* lookback, unsigned int* tile_counter, const unsigned int* epoch_base,
-    int pass, unsigned int* errors) {
+    int pass, unsigned int* errors, unsigned int spin_limit, unsigned int inject) {
   using TR = TileRank<K, BITS, ITEMS>;
   constexpr int D = TR::D, PT = TR::PT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -392,7 +391,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   for (int q = 0; q < PT; ++q)
     st_volatile(lb_tile + tid * PT + q,
                 pack_lb(tile == 0 ? kFlagPrefix : kFlagAgg, epoch, tcount[q]));
-  const unsigned int ep_want = epoch & 0x3fffffffu;
+  // (test hook: an epoch no tile publishes, so every wait runs to its limit)
+  const unsigned int ep_want = (epoch ^ ((inject & kInjectSortWait) ? 0x20000000u : 0u)) & 0x3fffffffu;
 #pragma unroll
   for (int q = 0; q < PT; ++q) {
     const int d = tid * PT + q;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
         if (done) break;
         p -= u;
         if (u == 0 || (u < kWin && p >= 0)) {
-          if (++spins > kSpinLimit) {
+          if (++spins > spin_limit) {
             atomicOr(errors, kErrTimeout);
             break;
           }
@@ -473,7 +473,8 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
     for (int p = 0; p < passes; ++p) {
       k_sort_pass<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
           (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, p * BITS,
-          a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.sort_epoch, p, &a.st->errors);
+          a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.sort_epoch, p, &a.st->errors,
+          spin_limit_of(a.spin_limit), a.inject);
       cur = 1 - cur;
     }
     return cur;

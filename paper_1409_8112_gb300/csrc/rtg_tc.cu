@@ -28,7 +28,9 @@ constexpr int kTcRows = 128;
 constexpr int kTcK = 32;                          // hi (16) + lo (16)
 constexpr int kTcTileBytes = kTcRows * kTcK * 2;  // 8 KB per 128-point tile
 constexpr int kTcThreads = 128;
-constexpr unsigned int kWaitLimit = 1u << 26;
+// MMA completion waits: the context's spin limit times this (a commit takes far longer than
+// one look-back step)
+constexpr unsigned int kTcWaitScale = 16;
 
 __host__ __device__ __forceinline__ int tile_off(int m, int k) {
   return (m / 8) * 512 + (k / 8) * 128 + (m % 8) * 16 + (k % 8) * 2;
@@ -45,6 +47,21 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
   d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;  // next 8 rows
   d |= (uint64_t)1 << 46;                       // descriptor version; no swizzle
   return d;
+}
+
+// Bounded wait for the completion of phase `parity` of the mbarrier at shared address bar;
+// false when the limit ran out first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int limit) {
+  for (unsigned int it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity));
+    if (ok) return true;
+  }
+  return false;
 }
 
 __device__ __forceinline__ double load_coord(const void* pts, int dtype, long long i, int d,
@@ -180,13 +197,15 @@ template <bool BF16, bool EMIT>
 __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
     const unsigned char* __restrict__ tiles, const float* __restrict__ norms,
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
-    const TcPlan* __restrict__ tp, int dtype, Status* st, TcSink sk, long long nt) {
+    const TcPlan* __restrict__ tp, int dtype, Status* st, TcSink sk, long long nt,
+    unsigned int wait_limit, unsigned int inject) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sa = smem;                       // 8 KB
   unsigned char* sb = smem + kTcTileBytes;        // 8 KB
   float* na = reinterpret_cast<float*>(smem + 2 * kTcTileBytes);  // 128
   float* nb = na + kTcRows;                                         // 128
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_idle;  // test hook: a barrier nothing arrives on
   __shared__ uint32_t tmem_base;
   __shared__ unsigned int s_cnt[4];
   __shared__ unsigned int s_err;
@@ -200,6 +219,7 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
   if (tid == 0) {
     s_err = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_idle)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -269,26 +289,18 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&mbar)));
     }
-    // bounded wait for this job's MMAs
-    bool done = false;
-    for (unsigned int it = 0; it < kWaitLimit; ++it) {
-      uint32_t ok;
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-          "selp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(ok)
-          : "r"(smem_u32(&mbar)), "r"(phase));
-      if (ok) {
-        done = true;
-        break;
-      }
-    }
-    phase ^= 1u;
+    // bounded wait for this job's MMAs (the test hook waits on a barrier nothing arrives on)
+    const bool done = mbar_wait(
+        (inject & kInjectTcWait) ? smem_u32(&mbar_idle) : smem_u32(&mbar), phase, wait_limit);
     if (!__syncthreads_and(done)) {
+      // give up: wait (bounded again) for the MMAs in flight, so that the tensor memory they
+      // write is not freed under them, then leave
+      mbar_wait(smem_u32(&mbar), phase, wait_limit);
       if (tid == 0) atomicOr(&st->errors, kErrTimeout);
       timed_out = true;
       break;
     }
+    phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: row `row` of the tile against its 128 columns.  The fast path only builds a
     // mask of the columns the tile does not reject; those (rare) go to the exact check.
@@ -312,7 +324,7 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         d2v[q] = (nrow + nb[c + q]) - 2.0f * __uint_as_float(r[q]);
-        hits |= (d2v[q] <= hi_thr ? 1u : 0u) << q;
+        hits |= (d2v[q] > hi_thr ? 0u : 1u) << q;  // NaN (overflowed tiles) goes to FP64
       }
       hits &= valid;
       if (hits) {
@@ -391,7 +403,9 @@ int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* til
       if (dev >= 0 && dev < 64) attr[dev] = smem;                                              \
     }                                                                                          \
     k_brute_tc<B, E><<<grid, kTcThreads, smem, s>>>(tiles, norms, a.inst, a.iplan, tp, a.dtype, \
-                                                    a.st, sk, nt);                             \
+                                                    a.st, sk, nt,                              \
+                                                    spin_limit_of(a.spin_limit) * kTcWaitScale, \
+                                                    a.inject);                                 \
   } while (0)
   if (grid > 0) {
     if (bf16 && emit) RTG_TC_LAUNCH(true, true);

@@ -33,6 +33,10 @@ RTG_FLAG_TC_FP16 = 16
 RTG_FLAG_TC_BF16 = 32
 RTG_FLAG_BITSET = 64
 
+RTG_INJECT_SORT_WAIT = 1
+RTG_INJECT_SCAN_WAIT = 2
+RTG_INJECT_TC_WAIT = 4
+
 RTG_DTYPE_F64 = 0
 RTG_DTYPE_F32 = 1
 
@@ -58,7 +62,8 @@ class rtg_stats(ctypes.Structure):
                 ("attempts", ctypes.c_int32), ("sort_digit_bits", ctypes.c_int32),
                 ("sort_tile_keys", ctypes.c_int32), ("sort_lookback", ctypes.c_int32),
                 ("sort_tuned", ctypes.c_int32), ("phase_us", ctypes.c_double * 8),
-                ("max_abs_err_d2", ctypes.c_double), ("band", ctypes.c_double)]
+                ("max_abs_err_d2", ctypes.c_double), ("band", ctypes.c_double),
+                ("phase_bytes", ctypes.c_int64 * 8), ("bytes_moved", ctypes.c_int64)]
 
 
 class rtg_csr(ctypes.Structure):
@@ -141,6 +146,8 @@ _SIGNATURES = {
     "rtg_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64,
                                 ctypes.POINTER(rtg_csr)]),
     "rtg_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr)]),
+    "rtg_set_test_hooks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_int64]),
     "rtg_csr_download": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rtg_csr),
                                         ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -266,6 +273,11 @@ def rtg_wait(ctx, ticket: int, timeout_us: int = -1) -> rtg_csr:
     return out
 
 
+def rtg_set_test_hooks(ctx, inject: int = 0, wait_limit: int = 0,
+                       fail_alloc_after: int = 0) -> None:
+    _check(lib().rtg_set_test_hooks(ctx, inject, wait_limit, fail_alloc_after), ctx)
+
+
 def rtg_release(ctx, csr: rtg_csr) -> None:
     _check(lib().rtg_release(ctx, ctypes.byref(csr)), ctx)
 
@@ -306,6 +318,8 @@ def stats_dict(s: rtg_stats, m: int) -> dict:
                  "lookback": int(s.sort_lookback), "tuned": int(s.sort_tuned)},
         "phase_us": {p: float(s.phase_us[i]) for i, p in enumerate(PHASES)},
         "max_abs_err_d2": float(s.max_abs_err_d2), "band": float(s.band),
+        "phase_bytes": {p: int(s.phase_bytes[i]) for i, p in enumerate(PHASES)},
+        "bytes_moved": int(s.bytes_moved),
     }
 
 

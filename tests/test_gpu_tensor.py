@@ -42,17 +42,3 @@ def test_tc_offset_coordinates(ctx):
         rp, col = res.download()
         ex = oracle.brute(pts, r)
         assert np.array_equal(rp, ex.row_ptr) and np.array_equal(col, ex.col)
-
-
-@pytest.mark.parametrize("tensor", ["fp16", "bf16"])
-def test_tc_brute_count_precision_sample(ctx, tensor):
-    # the precision workload's brute-force sample: n = 200,000 points of U[0,1]^6 stored
-    # FP32 with r for expected degree 2 ln n
-    n, d = 200000, 6
-    pts = gen.points_uniform(2, n, d, np.float32)
-    r = gen.radius_for_degree(n, d)
-    tc = ctx.brute_force(pts, r, count_only=True, tensor=tensor)
-    cuda = ctx.brute_force(pts, r, count_only=True)
-    assert tc.nnz == cuda.nnz
-    assert tc.nnz == oracle.exact_grid(pts, r).nnz
-    assert tc.stats["max_abs_err_d2"] < tc.stats["band"]

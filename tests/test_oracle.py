@@ -82,3 +82,18 @@ def test_radius_for_expected_degree():
     r = gen.radius_for_degree(100000, 6)
     assert abs(r - 0.18829) < 1e-5
     assert abs(r ** 6 * np.pi ** 3 / 6 * 100000 - 2 * np.log(100000)) < 1e-9
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_oracle_equals_serial(threads):
+    # The all-core CPU baseline runs oracle_rtg_threads: grids on several threads, the merge
+    # split by row ranges.  It must give the serial oracle's CSR exactly, including a case
+    # with more threads than grids and rows.
+    for seed, n, d, m, c_mul in [(0, 3000, 3, 5, 1.0), (1, 2000, 6, 8, 1.3), (2, 5, 2, 4, 1.0)]:
+        pts = gen.points_uniform(seed, n, d)
+        r = gen.radius_for_degree(max(n, 2), d)
+        T = gen.transforms(seed, d, m, c_mul * r)
+        a = oracle.rtg(pts, r, T, c_mul * r).csr
+        b = oracle.rtg_threads(pts, r, T, c_mul * r, threads)
+        assert np.array_equal(a.row_ptr, b.row_ptr)
+        assert np.array_equal(a.col, b.col)

@@ -6,6 +6,7 @@ failure has already run every other test.  It must pass alone in a fresh process
 import numpy as np
 import pytest
 
+import oracle
 from paper_1409_8112_gb300 import gen, rtg
 
 pytestmark = pytest.mark.gpu
@@ -15,9 +16,11 @@ def test_noalloc_count_matches_brute_force_on_consecutive_calls():
     import torch
 
     stream = torch.cuda.current_stream()
-    # two calls in a row on different inputs (the second smaller, so stale scratch from the
-    # first call would show), each against the existing entry point
-    cases = [(60000, 6, np.float64, 1), (9000, 3, np.float32, 2)]
+    # calls in a row on different inputs, each against the existing entry point; every call
+    # is smaller than the one before, so stale scratch from an earlier call would show.  The
+    # first fills the static scratch to its limit (65536 points of 16 coordinates, the
+    # widest FP32 rows).
+    cases = [(65536, 16, np.float32, 3), (60000, 6, np.float64, 1), (9000, 3, np.float32, 2)]
     with rtg.Context(0) as ctx:
         for n, d, dt, seed in cases:
             pts = gen.points_uniform(seed, n, d, dt)
@@ -39,3 +42,16 @@ def test_noalloc_rejects_sizes_beyond_the_static_limit():
         rtg.rtg_brute_count_noalloc(dev.data_ptr(), rtg.RTG_DTYPE_F64, 65537, 3, 0.1)
     assert e.value.status == rtg.RTG_E_INVALID
     assert "65536" in rtg.lib().rtg_last_error(None).decode()
+
+
+def test_noalloc_count_matches_the_cpu_oracle():
+    import torch
+
+    # a small case against the CPU oracle's brute force (independent of the GPU kernels)
+    n, d = 1500, 5
+    pts = gen.points_uniform(11, n, d)
+    r = gen.radius_for_degree(n, d, 20.0)
+    dev = torch.from_numpy(pts).cuda()
+    torch.cuda.synchronize()
+    got = rtg.rtg_brute_count_noalloc(dev.data_ptr(), rtg.RTG_DTYPE_F64, n, d, r)
+    assert got == oracle.brute(pts, r).nnz > 0

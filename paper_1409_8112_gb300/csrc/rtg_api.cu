@@ -278,7 +278,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   c->h_inst.assign(B, Inst{});
   long long p0 = 0, blk0 = 0, pblk0 = 0, T0 = 0, bits_words = 0;
   const bool bitset = (q.flags & RTG_FLAG_BITSET) != 0 && m > 0;
-  int maxd = 1;
+  int maxd = 1, mind = RTG_MAX_DIM;
   for (int b = 0; b < B; ++b) {
     const rtg_instance& it = q.items[b];
     Inst& I = c->h_inst[b];
@@ -301,6 +301,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     pblk0 += (it.n + rtg::kPrepPoints - 1) / rtg::kPrepPoints;
     T0 += (long long)m * (it.d * it.d + it.d);
     maxd = std::max(maxd, it.d);
+    mind = std::min(mind, it.d);
   }
   const long long n_total = p0;
   out->n = n_total;
@@ -394,6 +395,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.m = m;
   a.dtype = q.dtype;
   a.dpad = dpad;
+  a.d_common = mind == maxd ? maxd : 0;
   a.symmetric = sym;
   a.n_total = n_total;
   a.blocks = blk0;
@@ -552,7 +554,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         sorted = rtg::launch_sort(a, st);
         l += (a.passes > 0 && N > 1) ? (rtg::hist_in_keys(a) ? 0 : 1) +
                                            (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
-                                     : 0;
+                                     : 1;  // the identity copy when there is nothing to sort
       } else if (timing) {
         mark(2);
       }

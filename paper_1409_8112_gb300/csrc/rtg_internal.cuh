@@ -215,6 +215,7 @@ struct BuildArgs {
   int m;              // grids per instance (0: brute force)
   int dtype;          // 0 FP64, 1 FP32 (common to the batch)
   int dpad;           // padded row width (common to the batch)
+  int d_common;       // d of every instance when they share one, else 0
   int symmetric;
   long long n_total;  // sum of n
   long long blocks;   // per-point kernel blocks (sum of ceil(n / kPointBlock))
@@ -227,9 +228,10 @@ struct BuildArgs {
   const double* T64;         // device, packed transforms
   Status* st;
   float* pf;          // n_total x dpad
-  void* key_mat;      // n_total x m keys
-  void* keys[2];      // N composite keys, ping-pong
-  uint32_t* vals[2];  // N global point indices, ping-pong
+  void* key_mat;      // n_total x m keys, point-major: position g m + t holds point g's key
+                      // in grid t (also the first sort pass's input; its index is g)
+  void* keys[2];      // N composite keys, ping-pong outputs of the sort passes
+  uint32_t* vals[2];  // N global point indices, ping-pong outputs of the sort passes
   unsigned long long* lookback;  // sort: look-back words, or per-(digit, tile) counts (u32)
   unsigned int* hist;            // passes * digits counts (kSortCountWords)
   unsigned int* digit_off;       // passes * digits exclusive digit offsets

@@ -401,9 +401,8 @@ template <typename K, int DPAD>
 __global__ void __launch_bounds__(kPointBlock) k_keys(
     const Inst* __restrict__ inst, int B, int m, int dtype, const float* __restrict__ pf,
     const double* __restrict__ T64, const GridPlan* __restrict__ gplan, InstPlan* iplan,
-    const unsigned long long* bbox, Status* st, K* __restrict__ key_mat, K* __restrict__ comp,
-    uint32_t* __restrict__ vals, int hist_passes, unsigned int* hist, unsigned int* digit_off,
-    unsigned int* sort_epoch) {
+    const unsigned long long* bbox, Status* st, K* __restrict__ key_mat, int hist_passes,
+    unsigned int* hist, unsigned int* digit_off, unsigned int* sort_epoch) {
   __shared__ int s_b;
   __shared__ unsigned int s_hist[kMaxPasses * 256];  // 8-bit digit counts of every pass
   for (int x = threadIdx.x; x < hist_passes * 256; x += blockDim.x) s_hist[x] = 0;
@@ -452,7 +451,6 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
     }
     const int tstride = d * d + d;
     K* krow = s_krow + threadIdx.x * (m + 1);
-    const long long pos0 = I.p0 * m + i;
     const int dv = valid ? d : 0;
     for (int t = 0; t < m; ++t) {  // every lane takes every grid (warp votes below)
       K key = (K)sbase[t];
@@ -499,9 +497,6 @@ __global__ void __launch_bounds__(kPointBlock) k_keys(
       }
       if (valid) {
         krow[t] = key;
-        const long long pos = pos0 + (long long)t * I.n;
-        comp[pos] = key;
-        vals[pos] = (uint32_t)g;
         near_cnt += near ? 1u : 0u;
       }
       // digit counts: the low digits of neighbouring points differ, so only the top digit
@@ -579,8 +574,278 @@ void keys_impl(const BuildArgs& a, int maxd, cudaStream_t s) {
   }
   k_keys<K, DPAD><<<(unsigned)a.blocks, kPointBlock, smem, s>>>(
       a.inst, a.B, a.m, a.dtype, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st, (K*)a.key_mat,
-      (K*)a.keys[0], a.vals[0], hist_in_keys(a) ? a.passes : 0, a.hist, a.digit_off,
-      a.sort_epoch);
+      hist_in_keys(a) ? a.passes : 0, a.hist, a.digit_off, a.sort_epoch);
+}
+
+// Keys with one thread per (point, grid): for instances that share d <= 6.  Each thread keeps
+// its grid's FP32 rotation and shift in registers for the whole block (the grid of a thread
+// never changes), so the inner loop is the d x d FMAs and the floor test; the per-axis error
+// bound and key layout come from shared memory, stored axis-major so that the different grids
+// of a warp read different banks.  A block's threads write consecutive key-row words.  The
+// arithmetic, bounds and FP64 fallback are those of k_keys.  With 32-bit keys the cell offsets
+// are formed modulo 2^32, which is exact for every index inside the planned range (the range
+// check then only guards the plan itself).
+constexpr int kKeyLaneThreads = 256;
+
+// Per (axis, grid) record of k_keys_lanes.
+template <typename K>
+struct __align__(16) LaneAxis {
+  float E;
+  unsigned int pad;
+  K qlo, ext, stride;
+};
+template <>
+struct __align__(16) LaneAxis<uint32_t> {
+  float E;
+  uint32_t qlo, ext, stride;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Chunk c of the per-point numbering (kPointBlock points, blk0 offsets per instance): its
+// instance, first global point and point count.
+struct ChunkInfo {
+  int b, npts;
+  long long g0, i0;
+};
+__device__ __forceinline__ ChunkInfo chunk_info(const Inst* __restrict__ inst, int B,
+                                                long long c) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].blk0 <= c) lo = mid; else hi = mid - 1;
+  }
+  ChunkInfo ci;
+  ci.b = lo;
+  ci.i0 = (c - inst[lo].blk0) * (long long)kPointBlock;
+  ci.g0 = inst[lo].p0 + ci.i0;
+  ci.npts = (int)min((long long)kPointBlock, (long long)inst[lo].n - ci.i0);
+  return ci;
+}
+
+// One thread: start the bulk copy of chunk ci's FP32 rows (contiguous, 16-byte multiples)
+// into dst, completing on bar.
+__device__ __forceinline__ void stage_rows(const float* pf, int dpad, const ChunkInfo& ci,
+                                           float* dst, uint64_t* bar) {
+  const unsigned int bytes = (unsigned int)ci.npts * (unsigned int)dpad * 4u;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(pf + ci.g0 * dpad), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier bar.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned int limit) {
+  for (unsigned int it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <typename K, int D>
+__global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
+    const Inst* __restrict__ inst, int B, int m, int dtype, int dpad,
+    const float* __restrict__ pf, const double* __restrict__ T64,
+    const GridPlan* __restrict__ gplan, InstPlan* iplan, const unsigned long long* bbox,
+    Status* st, K* __restrict__ key_mat, long long chunks, int hist_passes, unsigned int* hist,
+    unsigned int* digit_off, unsigned int* sort_epoch, unsigned int wait_limit) {
+  constexpr int DP = D <= 4 ? 4 : 8;  // padded row width of the FP32 rows
+  __shared__ unsigned int s_hist[kMaxPasses * 256];  // 8-bit digit counts of every pass
+  __shared__ __align__(16) float s_rows[2][kPointBlock * DP];  // double-buffered chunk rows
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ ChunkInfo s_info[2];
+  extern __shared__ __align__(16) unsigned char smem[];
+  LaneAxis<K>* s_ax = reinterpret_cast<LaneAxis<K>*>(smem);  // [axis][grid]
+  for (int x = threadIdx.x; x < hist_passes * 256; x += blockDim.x) s_hist[x] = 0;
+  const long long stride_c = gridDim.x;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("fence.proxy.async.shared::cta;");
+    if ((long long)blockIdx.x < chunks) {
+      s_info[0] = chunk_info(inst, B, blockIdx.x);
+      stage_rows(pf, dpad, s_info[0], s_rows[0], &s_bar[0]);
+    }
+  }
+  __syncthreads();
+  const int P = kKeyLaneThreads / m;  // points per step of the block
+  const int t = (int)threadIdx.x % m, slot = (int)threadIdx.x / m;
+  const bool lane_on = slot < P;
+  float R[D][D], sf[D];
+  K base = 0;
+  int cur_b = -1;
+  const GridPlan* G = nullptr;
+  Inst I;
+  // phase: parity to wait for, per buffer; pending (thread 0): copies issued, not yet consumed
+  unsigned int near_cnt = 0, rechecks = 0, phase = 0, pending = 1u;
+  bool range_err = false, timed_out = false;
+  // persistent: the block takes 128-point chunks gridDim apart, their rows staged one chunk
+  // ahead by bulk copies, and reloads its plan only when a chunk is of another instance
+  int k = 0;
+  for (long long chunk = blockIdx.x; chunk < chunks; chunk += stride_c, ++k) {
+    const int buf = k & 1;
+    const ChunkInfo ci = s_info[buf];
+    if (threadIdx.x == 0 && chunk + stride_c < chunks) {
+      // the other buffer was last read before the previous iteration's closing barrier
+      s_info[buf ^ 1] = chunk_info(inst, B, chunk + stride_c);
+      stage_rows(pf, dpad, s_info[buf ^ 1], s_rows[buf ^ 1], &s_bar[buf ^ 1]);
+      pending |= 2u >> buf;  // the copy into buffer buf ^ 1 is in flight
+    }
+    if (ci.b != cur_b) {  // block-uniform
+      const GridPlan* Gb = gplan + (size_t)ci.b * m;
+      for (int x = threadIdx.x; x < D * m; x += blockDim.x) {
+        const int a = x / m, g = x - a * m;
+        LaneAxis<K> r;
+        r.E = Gb[g].E[a];
+        r.qlo = (K)Gb[g].qlo[a];
+        r.ext = (K)Gb[g].ext[a];
+        r.stride = (K)Gb[g].stride[a];
+        s_ax[x] = r;
+      }
+      I = inst[ci.b];
+      G = Gb + t;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+#pragma unroll
+        for (int l = 0; l < D; ++l) R[a][l] = G->Rf[a * kMaxDim + l];
+        sf[a] = G->sf[a];
+      }
+      base = (K)G->base;
+      cur_b = ci.b;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && chunk == I.blk0) plan_band(ci.b, I, dtype, bbox, iplan);
+    // this chunk's rows
+    const bool ok = mbar_wait_bounded(&s_bar[buf], (phase >> buf) & 1u, wait_limit);
+    if (!__syncthreads_and(ok)) {
+      timed_out = true;
+      break;
+    }
+    phase ^= 1u << buf;
+    pending &= ~(1u << buf);
+    const float inv_c = I.inv_cf;
+    const float* rows = s_rows[buf];
+    K* out = key_mat + ci.g0 * m + (long long)(slot * m + t);  // this thread's first word
+    for (int p0 = 0; p0 < ci.npts; p0 += P, out += P * m) {  // block-uniform
+      const int p = p0 + slot;
+      const bool valid = lane_on && p < ci.npts;
+      const int pp = valid ? p : 0;
+      float x[DP];
+#pragma unroll
+      for (int v = 0; v < DP / 4; ++v) {
+        const float4 q = *reinterpret_cast<const float4*>(rows + pp * dpad + 4 * v);
+        x[4 * v] = q.x;
+        x[4 * v + 1] = q.y;
+        x[4 * v + 2] = q.z;
+        x[4 * v + 3] = q.w;
+      }
+      K key = base;
+      unsigned int redo = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float y = sf[a];
+#pragma unroll
+        for (int l = 0; l < D; ++l) y = fmaf(R[a][l], x[l], y);
+        const LaneAxis<K> ax = s_ax[a * m + t];
+        const float u = y * inv_c;
+        const float f = floorf(u);
+        // certain when [u - E, u + E], rounded outwards, holds no cell wall (as in k_keys)
+        const bool certain = __fsub_rd(u, ax.E) >= f && __fadd_ru(u, ax.E) < f + 1.0f;
+        const K off = (K)(long long)(int)f - ax.qlo;
+        const bool out = off >= ax.ext;
+        if (!certain) redo |= 1u << a;
+        if (certain && out) range_err = true;
+        key += (certain && !out) ? off * ax.stride : (K)0;
+      }
+      if (!valid) redo = 0;
+      bool near = false;
+      while (redo) {  // rare: the FP64 reference sequence decides these axes
+        const int a = __ffs(redo) - 1;
+        redo &= redo - 1;
+        const long long q = exact_cell(I.pts, dtype, ci.i0 + pp, D,
+                                       T64 + I.T0 + (size_t)t * (D * D + D), a, I.c, &near);
+        ++rechecks;
+        const long long off = q - G->qlo[a];
+        if ((unsigned long long)off >= G->ext[a]) {
+          range_err = true;
+        } else {
+          key += (K)off * (K)G->stride[a];
+        }
+      }
+      if (valid) {
+        *out = key;
+        near_cnt += near ? 1u : 0u;
+        const unsigned int lo = (unsigned int)key, hi = (unsigned int)((unsigned long long)key >> 32);
+#pragma unroll
+        for (int q = 0; q < kMaxPasses; ++q)  // digit q is byte q of the key
+          if (q < hist_passes)
+            atomicAdd(&s_hist[q * 256 + __byte_perm(q < 4 ? lo : hi, 0u, 0x4440u + (q & 3))], 1u);
+      }
+    }
+    __syncthreads();  // rows[buf], s_info[buf] and s_ax are rewritten later
+  }
+  if (timed_out) {
+    // a staged copy may still be in flight: wait for it (bounded) before the block exits
+    if (threadIdx.x == 0) {
+      atomicOr(&st->errors, kErrTimeout);
+      for (int q = 0; q < 2; ++q)
+        if ((pending >> q) & 1u) mbar_wait_bounded(&s_bar[q], (phase >> q) & 1u, wait_limit);
+    }
+    return;  // the digit counts stay incomplete; the build reports the timeout
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    near_cnt += __shfl_xor_sync(0xffffffffu, near_cnt, o);
+    rechecks += __shfl_xor_sync(0xffffffffu, rechecks, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (near_cnt) atomicAdd(&st->near_wall, (unsigned long long)near_cnt);
+    if (rechecks) atomicAdd(&st->key_rechecks, (unsigned long long)rechecks);
+  }
+  if (range_err) atomicOr(&st->errors, kErrKeyRange);
+  __syncthreads();
+  if (hist_passes > 0)
+    finish_digit_count256(s_hist, hist_passes, hist, digit_off, &st->hist_ticket, sort_epoch);
+}
+
+template <typename K, int D>
+void keys_lanes_launch(const BuildArgs& a, cudaStream_t s) {
+  const size_t smem = sizeof(LaneAxis<K>) * (size_t)D * a.m;  // at most 16 KB
+  // two resident blocks per SM (the register budget), each looping over chunks
+  long long grid = 2LL * a.num_sms;
+  if (grid > a.blocks) grid = a.blocks;
+  k_keys_lanes<K, D><<<(unsigned)grid, kKeyLaneThreads, smem, s>>>(
+      a.inst, a.B, a.m, a.dtype, a.dpad, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st,
+      (K*)a.key_mat, a.blocks, hist_in_keys(a) ? a.passes : 0, a.hist, a.digit_off,
+      a.sort_epoch, spin_limit_of(a.spin_limit) * 16u);
+}
+
+template <typename K>
+bool keys_lanes(const BuildArgs& a, cudaStream_t s) {
+  if (a.m < 1 || a.m > kKeyLaneThreads) return false;
+  switch (a.d_common) {
+    case 1: keys_lanes_launch<K, 1>(a, s); return true;
+    case 2: keys_lanes_launch<K, 2>(a, s); return true;
+    case 3: keys_lanes_launch<K, 3>(a, s); return true;
+    case 4: keys_lanes_launch<K, 4>(a, s); return true;
+    case 5: keys_lanes_launch<K, 5>(a, s); return true;
+    case 6: keys_lanes_launch<K, 6>(a, s); return true;
+    default: return false;  // wider rows would not fit the register budget
+  }
 }
 
 }  // namespace
@@ -602,6 +867,7 @@ int launch_prep_plan(const BuildArgs& a, cudaStream_t s) {
 }
 
 void launch_keys(const BuildArgs& a, cudaStream_t s) {
+  if (a.key64 ? keys_lanes<unsigned long long>(a, s) : keys_lanes<uint32_t>(a, s)) return;
   const int maxd = a.dpad;  // rows staged per grid never exceed the padded width
   if (a.key64) {
     switch (a.dpad) {

@@ -246,9 +246,11 @@ struct TileRank {
     s_whist = reinterpret_cast<unsigned short*>(s_gbase + D);
   }
 
+  // vin == nullptr: the input is the point-major key-row array, whose position pos holds
+  // point pos / m (vdiv = ceil(2^64 / m), exact for pos < 2^31; m = 1 passes vdiv = 0).
   __device__ void rank(const K* __restrict__ kin, const uint32_t* __restrict__ vin, long long N,
                        long long tile_base, int shift, unsigned int (&tcount)[PT],
-                       unsigned int* sbuf) {
+                       unsigned int* sbuf, unsigned long long vdiv) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned int* wz = reinterpret_cast<unsigned int*>(s_whist);
     for (int x = tid; x < kSortWarps * D / 2; x += kSortThreads) wz[x] = 0;
@@ -262,7 +264,8 @@ struct TileRank {
       const long long pos = wbase + j * 32 + lane;
       if (pos < N) {
         key[j] = kin[pos];
-        val[j] = vin[pos];
+        val[j] = vin ? vin[pos]
+                     : (vdiv ? (uint32_t)__umul64hi((unsigned long long)pos, vdiv) : (uint32_t)pos);
       } else {
         key[j] = (K)0;
         val[j] = 0;
@@ -343,7 +346,7 @@ template <typename K, int BITS, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ offs,
-    unsigned int tiles, unsigned int* errors) {
+    unsigned int tiles, unsigned int* errors, unsigned long long vdiv) {
   using TR = TileRank<K, BITS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned int sbuf[kSortWarps];
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
     tr.s_gbase[x] = offs[(size_t)x * tiles + blockIdx.x];
   const long long tile_base = (long long)blockIdx.x * TR::kTile;
   unsigned int tcount[TR::PT];
-  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf);
+  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
   __syncthreads();
   tr.write(kout, vout, N, tile_base, shift, errors);
 }
@@ -365,7 +368,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ digit_off,
     unsigned long long* lookback, unsigned int* tile_counter, const unsigned int* epoch_base,
-    int pass, unsigned int* errors, unsigned int spin_limit, unsigned int inject) {
+    int pass, unsigned int* errors, unsigned int spin_limit, unsigned int inject,
+    unsigned long long vdiv) {
   using TR = TileRank<K, BITS, ITEMS>;
   constexpr int D = TR::D, PT = TR::PT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   const unsigned int epoch = *epoch_base + (unsigned int)pass;
   const long long tile_base = (long long)tile * TR::kTile;
   unsigned int tcount[PT];
-  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf);
+  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
   // publish this tile's counts, then look back digit by digit
   unsigned long long* lb_tile = lookback + (size_t)tile * D;
 #pragma unroll
@@ -450,49 +454,70 @@ void set_smem_once(F* kern, size_t smem, bool* done /*64*/) {
   if (dev >= 0 && dev < 64) done[dev] = true;
 }
 
+// Identity "sort" (no key bits to sort): the key rows as they are, with their point indices.
+template <typename K>
+__global__ void __launch_bounds__(256) k_sort_identity(const K* __restrict__ kin, long long N,
+                                                       unsigned long long vdiv,
+                                                       K* __restrict__ kout,
+                                                       uint32_t* __restrict__ vout) {
+  for (long long pos = blockIdx.x * 256LL + threadIdx.x; pos < N; pos += 256LL * gridDim.x) {
+    kout[pos] = kin[pos];
+    vout[pos] = vdiv ? (uint32_t)__umul64hi((unsigned long long)pos, vdiv) : (uint32_t)pos;
+  }
+}
+
+// The first pass reads the point-major key rows (indices implicit) and writes buffer 0; pass
+// p > 0 reads buffer (p - 1) & 1 and writes p & 1.  Returns the buffer holding the result.
 template <typename K, int BITS, int ITEMS>
 int sort_impl(const BuildArgs& a, cudaStream_t s) {
   using SS = SortShape<K, BITS, ITEMS>;
   constexpr int D = SS::kDigits;
   const long long N = a.n_total * a.m;
   const int passes = a.passes;
-  if (passes <= 0 || N <= 1) return 0;
+  const unsigned long long vdiv = a.m > 1 ? ~0ull / (unsigned long long)a.m + 1ull : 0ull;
+  if (N <= 0) return 0;
+  if (passes <= 0 || N <= 1) {
+    long long blocks = (N + 255) / 256;
+    if (blocks > 8LL * a.num_sms) blocks = 8LL * a.num_sms;
+    k_sort_identity<K><<<(unsigned)blocks, 256, 0, s>>>((const K*)a.key_mat, N, vdiv,
+                                                        (K*)a.keys[0], a.vals[0]);
+    return 0;
+  }
   long long hb = (N + kSortThreads - 1) / kSortThreads;
   if (hb > 4LL * a.num_sms) hb = 4LL * a.num_sms;
   if (!hist_in_keys(a)) {  // else the key kernel has counted the digits
     static bool hist_attr[64] = {};
     set_smem_once(k_sort_hist<K, BITS>, (size_t)kSortCountWords * 4, hist_attr);
     k_sort_hist<K, BITS><<<(unsigned)hb, kSortThreads, (size_t)passes * D * 4, s>>>(
-        (const K*)a.keys[0], N, passes, a.hist, a.digit_off, &a.st->hist_ticket, a.sort_epoch);
+        (const K*)a.key_mat, N, passes, a.hist, a.digit_off, &a.st->hist_ticket, a.sort_epoch);
   }
   const unsigned tiles = (unsigned)((N + SS::kTile - 1) / SS::kTile);
-  int cur = 0;
+  auto src_k = [&](int p) { return p == 0 ? (const K*)a.key_mat : (const K*)a.keys[(p - 1) & 1]; };
+  auto src_v = [&](int p) { return p == 0 ? (const uint32_t*)nullptr : a.vals[(p - 1) & 1]; };
   if (a.sort_mode == kSortLookback) {
     static bool attr[64] = {};
     set_smem_once(k_sort_pass<K, BITS, ITEMS>, SS::kSmem, attr);
     for (int p = 0; p < passes; ++p) {
       k_sort_pass<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
-          (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, p * BITS,
+          src_k(p), src_v(p), (K*)a.keys[p & 1], a.vals[p & 1], N, p * BITS,
           a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.sort_epoch, p, &a.st->errors,
-          spin_limit_of(a.spin_limit), a.inject);
-      cur = 1 - cur;
+          spin_limit_of(a.spin_limit), a.inject, vdiv);
     }
-    return cur;
+    return (passes - 1) & 1;
   }
   static bool attr[64] = {};
   set_smem_once(k_sort_downsweep<K, BITS, ITEMS>, SS::kSmem, attr);
   unsigned int* counts = (unsigned int*)a.lookback;  // D * tiles words
   for (int p = 0; p < passes; ++p) {
     const int shift = p * BITS;
-    k_sort_upsweep<K, BITS, ITEMS><<<tiles, kSortThreads, 0, s>>>((const K*)a.keys[cur], N, shift,
-                                                                  counts, tiles);
+    k_sort_upsweep<K, BITS, ITEMS><<<tiles, kSortThreads, 0, s>>>(src_k(p), N, shift, counts,
+                                                                  tiles);
     k_sort_scan<<<D, 1024, 0, s>>>(counts, tiles, a.digit_off + p * D);
     k_sort_downsweep<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
-        (const K*)a.keys[cur], a.vals[cur], (K*)a.keys[1 - cur], a.vals[1 - cur], N, shift,
-        counts, tiles, &a.st->errors);
-    cur = 1 - cur;
+        src_k(p), src_v(p), (K*)a.keys[p & 1], a.vals[p & 1], N, shift, counts, tiles,
+        &a.st->errors, vdiv);
   }
-  return cur;
+  return (passes - 1) & 1;
 }
 
 template <typename K, int BITS>

@@ -95,9 +95,10 @@ typedef struct {
   int32_t sort_passes;   /* radix passes run */
   int32_t launches;      /* kernels this build launched */
   int32_t attempts;      /* 1, or more when a launch assumption had to be corrected */
-  int32_t sort_digit_bits; /* radix digit width used (8, 10 or 11; autotuned per shape) */
+  int32_t sort_digit_bits; /* radix digit width used (8, 9, 10 or 11; autotuned per shape) */
   int32_t sort_tile_keys;  /* keys per sort tile (2048, 3072 or 4096; autotuned) */
-  int32_t sort_lookback;   /* 1: single-kernel look-back passes, 0: reduce-then-scan */
+  int32_t sort_lookback;   /* 1: single-kernel look-back passes, 0: reduce-then-scan,
+                              2: every pass in one cooperative launch */
   int32_t sort_tuned;      /* 1 when the sort variant was measured on this device */
   double phase_us[8];    /* with RTG_FLAG_TIMING: prep+plan, keys, sort, pairs, scan,
                             scatter (or write), rowsort, total (microseconds, device events) */

@@ -552,9 +552,12 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         l += 1;
         if (timing) mark(2);
         sorted = rtg::launch_sort(a, st);
-        l += (a.passes > 0 && N > 1) ? (rtg::hist_in_keys(a) ? 0 : 1) +
-                                           (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes
-                                     : 1;  // the identity copy when there is nothing to sort
+        l += (a.passes > 0 && N > 1)
+                 ? (rtg::hist_in_keys(a) ? 0 : 1) +
+                       (a.sort_mode == rtg::kSortCoop
+                            ? 1
+                            : (a.sort_mode == rtg::kSortLookback ? 1 : 3) * a.passes)
+                 : 1;  // the identity copy when there is nothing to sort
       } else if (timing) {
         mark(2);
       }
@@ -786,7 +789,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     S.sort_passes = m > 0 ? a.passes : 0;
     S.sort_digit_bits = m > 0 ? a.sort_bits : 0;
     S.sort_tile_keys = m > 0 ? 256 * a.sort_items : 0;
-    S.sort_lookback = m > 0 && a.sort_mode == rtg::kSortLookback ? 1 : 0;
+    S.sort_lookback =
+        m > 0 ? (a.sort_mode == rtg::kSortLookback ? 1 : (a.sort_mode == rtg::kSortCoop ? 2 : 0))
+              : 0;
     {
       const auto it = c->sort_tune.find(SortKey(N, g.key_bits));
       S.sort_tuned = m > 0 && it != c->sort_tune.end() && it->second.cfg.bits == g.sort.bits &&

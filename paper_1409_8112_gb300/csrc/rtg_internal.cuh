@@ -33,7 +33,7 @@ constexpr int kMaxDim = 16;
 constexpr int kMaxGrids = 64;
 constexpr int kMaxPasses = 8;  // radix passes of the narrowest digit (8 bits) over a 64-bit key
 // Digit widths and tile sizes the radix sort is compiled for.
-constexpr int kSortBitsChoices[] = {8, 10, 11};
+constexpr int kSortBitsChoices[] = {8, 9, 10, 11};
 constexpr int kSortItemsChoices[] = {8, 12, 16};
 constexpr int kSortCountWords = 6 * 2048;  // passes * digits, largest over the digit widths
 __host__ __device__ inline int sort_passes_for(int key_bits, int radix_bits) {
@@ -84,12 +84,14 @@ enum Mode : int { kCount = 0, kWrite = 1, kEmit = 2, kBits = 3 };
 // Largest instance the bit-matrix dedupe takes (n x ceil(n/32) words: 32 MB at this n).
 constexpr int kBitsetMaxN = 16384;
 
-// Radix pass strategies.
-enum SortMode : int { kSortLookback = 0, kSortReduceScan = 1 };
+// Radix pass strategies.  kSortCoop: every pass in one cooperative launch (one tile per
+// block, all blocks resident), the passes' offsets from per-tile counts scanned between
+// bounded grid barriers.
+enum SortMode : int { kSortLookback = 0, kSortReduceScan = 1, kSortCoop = 2 };
 
 // One compiled variant of the sort and its pass strategy.
 struct SortConfig {
-  int bits = 8;   // digit width: 8, 10 or 11
+  int bits = 8;   // digit width: 8, 9, 10 or 11
   int items = 8;  // keys per thread: 8, 12 or 16 (tiles of 256 * items keys)
   int mode = kSortReduceScan;
 };
@@ -115,6 +117,8 @@ struct Status {
   unsigned long long max_cell;
   unsigned int sort_tiles[kMaxPasses];
   unsigned int span_next[2];  // pair enumeration: next unclaimed span (count/emit, write)
+  unsigned int coop_count;  // single-launch sort: blocks arrived at the current grid barrier
+  unsigned int coop_gen;    // single-launch sort: grid barriers completed
   unsigned int long_rows;  // rows queued for the block row sort
   unsigned int mid_rows;   // rows queued for the warp row sort
   unsigned int tc_max_err_bits;  // tensor-core path: max |FP32 d^2 - FP64 d^2| (float bits)
@@ -258,9 +262,19 @@ struct BuildArgs {
   unsigned int inject;      // test hooks (kInject*), 0 in normal use
 };
 
-// With 8-bit digits the key kernel also counts the digits of every radix pass (the sort then
-// needs no histogram kernel).
-inline bool hist_in_keys(const BuildArgs& a) { return a.sort_bits == 8 && a.passes > 0; }
+// The key kernel with one thread per (point, grid) serves instances that share d <= 6.
+inline bool keys_by_lanes(const BuildArgs& a) {
+  return a.d_common >= 1 && a.d_common <= 6 && a.m >= 1 && a.m <= 256;
+}
+// Digit counts kept in shared memory by that kernel (words), at most.
+constexpr int kLaneHistWords = 4096;
+// The key kernel also counts the digits of every radix pass (the sort then needs no histogram
+// kernel): 8-bit digits always, other widths when the lane kernel runs and the counts fit.
+inline bool hist_in_keys(const BuildArgs& a) {
+  if (a.passes <= 0) return false;
+  if (a.sort_bits == 8) return true;
+  return keys_by_lanes(a) && a.passes * (1 << a.sort_bits) <= kLaneHistWords;
+}
 
 // Radix digit counting shared by the key and histogram kernels (256 digits per pass).  Adds one
 // per valid lane; a warp whose lanes share one digit (the high digits of neighbouring keys)
@@ -325,6 +339,53 @@ __device__ __forceinline__ void finish_digit_count256(const unsigned int* sh, in
   }
 }
 
+// finish_digit_count256 for digits of `bits` bits (D = 2^bits per pass, counts sh[p * D + d]);
+// a block of 256 threads.
+__device__ __forceinline__ void finish_digit_count_bits(const unsigned int* sh, int passes,
+                                                        int bits, unsigned int* hist,
+                                                        unsigned int* digit_off,
+                                                        unsigned int* ticket,
+                                                        unsigned int* epoch) {
+  __shared__ unsigned int s_w[8];
+  __shared__ bool s_last;
+  const int tid = threadIdx.x, nt = blockDim.x, D = 1 << bits;
+  for (int x = tid; x < passes * D; x += nt)
+    if (sh[x]) atomicAdd(&hist[x], sh[x]);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int per = D / nt, lane = tid & 31, warp = tid >> 5;  // D >= nt = 256
+  for (int p = 0; p < passes; ++p) {
+    unsigned int sum = 0;
+    for (int q = 0; q < per; ++q) sum += __ldcg(&hist[p * D + tid * per + q]);
+    unsigned int x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    unsigned int run = x - sum;
+    for (int w = 0; w < warp; ++w) run += s_w[w];
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+      const unsigned int v = __ldcg(&hist[p * D + tid * per + q]);
+      digit_off[p * D + tid * per + q] = run;
+      run += v;
+      hist[p * D + tid * per + q] = 0;  // ready for the next sort
+    }
+  }
+  if (tid == 0) {
+    *ticket = 0;
+    unsigned int e = *epoch + kMaxPasses;  // a fresh look-back epoch, never 0
+    if ((e & 0x3fffffffu) < (unsigned int)kMaxPasses) e = 1;
+    *epoch = e;
+  }
+}
+
 // FP32 rows, zeroed row counters, bounding boxes and the plan (in the prep kernel's last block
 // for small batches); returns the kernels launched.
 int launch_prep_plan(const BuildArgs& a, cudaStream_t s);
@@ -348,6 +409,8 @@ int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound = -1)
 std::mutex& launch_attr_mutex();
 
 size_t sort_tiles_for(long long N, int items);
+// Whether the single-launch sort can run this variant: every tile's block resident at once.
+bool sort_coop_fits(long long N, int bits, int items, int num_sms, bool key64);
 size_t tc_tiles_bytes(long long n);
 // tensor-core brute force (instance 0 only); returns kernels launched
 int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* tiles, float* norms,

@@ -661,16 +661,17 @@ __global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
     const Inst* __restrict__ inst, int B, int m, int dtype, int dpad,
     const float* __restrict__ pf, const double* __restrict__ T64,
     const GridPlan* __restrict__ gplan, InstPlan* iplan, const unsigned long long* bbox,
-    Status* st, K* __restrict__ key_mat, long long chunks, int hist_passes, unsigned int* hist,
-    unsigned int* digit_off, unsigned int* sort_epoch, unsigned int wait_limit) {
+    Status* st, K* __restrict__ key_mat, long long chunks, int hist_passes, int hist_bits,
+    unsigned int* hist, unsigned int* digit_off, unsigned int* sort_epoch,
+    unsigned int wait_limit) {
   constexpr int DP = D <= 4 ? 4 : 8;  // padded row width of the FP32 rows
-  __shared__ unsigned int s_hist[kMaxPasses * 256];  // 8-bit digit counts of every pass
+  __shared__ unsigned int s_hist[kLaneHistWords];  // digit counts of every pass
   __shared__ __align__(16) float s_rows[2][kPointBlock * DP];  // double-buffered chunk rows
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ ChunkInfo s_info[2];
   extern __shared__ __align__(16) unsigned char smem[];
   LaneAxis<K>* s_ax = reinterpret_cast<LaneAxis<K>*>(smem);  // [axis][grid]
-  for (int x = threadIdx.x; x < hist_passes * 256; x += blockDim.x) s_hist[x] = 0;
+  for (int x = threadIdx.x; x < hist_passes << hist_bits; x += blockDim.x) s_hist[x] = 0;
   const long long stride_c = gridDim.x;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[0])));
@@ -790,11 +791,20 @@ __global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
       if (valid) {
         *out = key;
         near_cnt += near ? 1u : 0u;
-        const unsigned int lo = (unsigned int)key, hi = (unsigned int)((unsigned long long)key >> 32);
+        if (hist_bits == 8) {
+          const unsigned int lo = (unsigned int)key,
+                             hi = (unsigned int)((unsigned long long)key >> 32);
 #pragma unroll
-        for (int q = 0; q < kMaxPasses; ++q)  // digit q is byte q of the key
-          if (q < hist_passes)
-            atomicAdd(&s_hist[q * 256 + __byte_perm(q < 4 ? lo : hi, 0u, 0x4440u + (q & 3))], 1u);
+          for (int q = 0; q < kMaxPasses; ++q)  // digit q is byte q of the key
+            if (q < hist_passes)
+              atomicAdd(&s_hist[q * 256 + __byte_perm(q < 4 ? lo : hi, 0u, 0x4440u + (q & 3))],
+                        1u);
+        } else {
+          const unsigned int dm = (1u << hist_bits) - 1u;
+#pragma unroll 1
+          for (int q = 0; q < hist_passes; ++q)
+            atomicAdd(&s_hist[(q << hist_bits) + ((unsigned int)(key >> (hist_bits * q)) & dm)], 1u);
+        }
       }
     }
     __syncthreads();  // rows[buf], s_info[buf] and s_ax are rewritten later
@@ -819,7 +829,8 @@ __global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
   if (range_err) atomicOr(&st->errors, kErrKeyRange);
   __syncthreads();
   if (hist_passes > 0)
-    finish_digit_count256(s_hist, hist_passes, hist, digit_off, &st->hist_ticket, sort_epoch);
+    finish_digit_count_bits(s_hist, hist_passes, hist_bits, hist, digit_off, &st->hist_ticket,
+                            sort_epoch);
 }
 
 template <typename K, int D>
@@ -830,13 +841,13 @@ void keys_lanes_launch(const BuildArgs& a, cudaStream_t s) {
   if (grid > a.blocks) grid = a.blocks;
   k_keys_lanes<K, D><<<(unsigned)grid, kKeyLaneThreads, smem, s>>>(
       a.inst, a.B, a.m, a.dtype, a.dpad, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st,
-      (K*)a.key_mat, a.blocks, hist_in_keys(a) ? a.passes : 0, a.hist, a.digit_off,
-      a.sort_epoch, spin_limit_of(a.spin_limit) * 16u);
+      (K*)a.key_mat, a.blocks, hist_in_keys(a) ? a.passes : 0, a.sort_bits, a.hist,
+      a.digit_off, a.sort_epoch, spin_limit_of(a.spin_limit) * 16u);
 }
 
 template <typename K>
 bool keys_lanes(const BuildArgs& a, cudaStream_t s) {
-  if (a.m < 1 || a.m > kKeyLaneThreads) return false;
+  if (!keys_by_lanes(a)) return false;
   switch (a.d_common) {
     case 1: keys_lanes_launch<K, 1>(a, s); return true;
     case 2: keys_lanes_launch<K, 2>(a, s); return true;

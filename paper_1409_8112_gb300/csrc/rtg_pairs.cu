@@ -60,6 +60,25 @@ __device__ __forceinline__ double exact_dist2(const void* pts, int dtype, long l
   return s;
 }
 
+// Asynchronous global -> shared copies (cp.async): a thread issues all of its copies and waits
+// once, so the gathers of a position's row and key row are in flight together.
+__device__ __forceinline__ uint32_t smem_u32addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32addr(dst)), "l"(src)
+               : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32addr(dst)), "l"(src),
+               "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Exclusive scan of one value per thread over the block (a multiple of 32 threads, at most
 // 1024); sbuf holds one word per warp.
 __device__ __forceinline__ unsigned int block_excl_scan_any(unsigned int v, unsigned int* total,
@@ -144,7 +163,7 @@ __device__ __forceinline__ float2 band_of(const InstPlan& IP) {
 
 // Decide one candidate pair (i < j, global indices) of grid t of instance I; ki and kj are the
 // two points' key rows (shared or global memory); band is band_of(IP).
-template <typename K, int DPAD, int MODE>
+template <typename K, int DPAD, int MODE, bool VEC = false>
 __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int t, const float* pa,
                                             const float* pb, const K* ki, const K* kj,
                                             const Inst* __restrict__ Ip,
@@ -169,12 +188,28 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
   // a batch issued together), stopping at the first batch with a match: a close pair usually
   // shares a cell in one of the first grids
   if (MODE != kBits) {
-    for (int u0 = 0; u0 < t; u0 += 4) {
-      bool earlier = false;
+    if (VEC) {
+      // rows 16-byte aligned: 16 bytes of each row per load
+      constexpr int kpv = 16 / (int)sizeof(K);
+      for (int u0 = 0; u0 < t; u0 += kpv) {
+        const uint4 va = *reinterpret_cast<const uint4*>(ki + u0);
+        const uint4 vb = *reinterpret_cast<const uint4*>(kj + u0);
+        const K* xa = reinterpret_cast<const K*>(&va);
+        const K* xb = reinterpret_cast<const K*>(&vb);
+        bool earlier = false;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (u0 + q < t) earlier |= ki[u0 + q] == kj[u0 + q];
-      if (earlier) return false;
+        for (int q = 0; q < kpv; ++q)
+          if (u0 + q < t) earlier |= xa[q] == xb[q];
+        if (earlier) return false;
+      }
+    } else {
+      for (int u0 = 0; u0 < t; u0 += 4) {
+        bool earlier = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (u0 + q < t) earlier |= ki[u0 + q] == kj[u0 + q];
+        if (earlier) return false;
+      }
     }
   }
   if (MODE != kWrite && MODE != kBits) ++tl.owned;
@@ -295,14 +330,26 @@ __device__ __forceinline__ int find_bt(unsigned long long key,
 }
 
 // Key rows are staged in shared memory when a row (m keys) is at most this many bytes.
-// Staged rows are m + 1 keys apart so that neighbouring rows fall in different banks.
 constexpr int kMaxStagedRow = 128;
 
-// Bytes of one warp's shared-memory region in k_pairs_warp.
+// Keys between staged key rows in k_pairs_warp: a multiple of 16 bytes (the ownership test
+// reads four 32-bit or two 64-bit keys per load), plus 16 bytes when the row would otherwise
+// be a multiple of 128 bytes, so that neighbouring rows start in different banks.
+template <typename K>
+__host__ __device__ inline int staged_row_stride(int m) {
+  constexpr int kpv = 16 / (int)sizeof(K);
+  int st = (m + kpv - 1) / kpv * kpv;
+  if ((st * (int)sizeof(K)) % 128 == 0) st += kpv;
+  return st;
+}
+
+// Bytes of one warp's shared-memory region in k_pairs_warp (the staged key rows first, so
+// that they are 16-byte aligned).
 template <typename K, int DPAD>
 __host__ __device__ inline int warp_region_bytes(int m, bool stage_rows) {
-  const int b = kWarpEmit * 8 + kRing * DPAD * 4 + (stage_rows ? kRing * (m + 1) * (int)sizeof(K) : 0) +
-                kRing * 4 + 3 * 32 * 4;
+  const int b = kWarpEmit * 8 + kRing * DPAD * 4 +
+                (stage_rows ? kRing * staged_row_stride<K>(m) * (int)sizeof(K) : 0) + kRing * 4 +
+                3 * 32 * 4;
   return (b + 15) & ~15;
 }
 
@@ -362,7 +409,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   unsigned long long* w_emit = reinterpret_cast<unsigned long long*>(ws);
   float* w_pt = reinterpret_cast<float*>(ws + kWarpEmit * 8);
   K* w_rows = reinterpret_cast<K*>(w_pt + kRing * DPAD);
-  const int rstride = m + 1;
+  const int rstride = staged_row_stride<K>(m);
   uint32_t* w_idx = reinterpret_cast<uint32_t*>(w_rows + (STAGE ? kRing * rstride : 0));
   int* w_excl = reinterpret_cast<int*>(w_idx + kRing);  // per lane: first pair of the lane
   int* w_hrel = w_excl + 32;                             // per lane: cell head - chunk start
@@ -478,14 +525,17 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
       if (active) {
         const int slot = (int)((P0 + p) & (kRing - 1));
         w_idx[slot] = vc;
-        const float4* src = reinterpret_cast<const float4*>(pf + (size_t)vc * DPAD);
-        float4* dst = reinterpret_cast<float4*>(w_pt + slot * DPAD);
+        // the FP32 row and the first t keys of the key row, copied asynchronously (all of a
+        // lane's gathers in flight at once; waited for below)
+        const float* src = pf + (size_t)vc * DPAD;
+        float* dst = w_pt + slot * DPAD;
 #pragma unroll
-        for (int v = 0; v < DPAD / 4; ++v) dst[v] = __ldg(src + v);
+        for (int v = 0; v < DPAD / 4; ++v) cp_async16(dst + 4 * v, src + 4 * v);
         if (STAGE) {
           const int t = (int)(mycell & 0xffu);
           const K* kr = key_mat + (size_t)vc * m;
-          for (int u = 0; u < t; ++u) w_rows[slot * rstride + u] = __ldg(kr + u);
+          K* kd = w_rows + slot * rstride;
+          for (int u = 0; u < t; ++u) cp_async_small<(int)sizeof(K)>(kd + u, kr + u);
         }
         if (MODE != kWrite) {
           const int g = (int)(mycell & 0xffu);
@@ -498,6 +548,8 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
           maxcell = max(maxcell, (unsigned int)np + 1u);
         }
       }
+      cp_async_wait_all();  // this lane's staged rows have landed (visible to the warp at
+                            // the __syncwarp below)
       // pairs of this chunk, spread over the lanes
       int incl = np;
 #pragma unroll
@@ -533,8 +585,9 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
             const K* ka = STAGE ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
             const K* kb = STAGE ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
             const float2 band = one_inst ? span_band : band_of(iplan[ib_]);
-            keep = decide_pair<K, DPAD, MODE>(i, j, t, w_pt + sa * DPAD, w_pt + sb * DPAD, ka, kb,
-                                              inst + ib_, iplan + ib_, band, dtype, tl, sk.near_r);
+            keep = decide_pair<K, DPAD, MODE, STAGE>(i, j, t, w_pt + sa * DPAD, w_pt + sb * DPAD,
+                                                     ka, kb, inst + ib_, iplan + ib_, band, dtype,
+                                                     tl, sk.near_r);
           }
           if (MODE == kBits) {
             deliver_bits(keep, i, j, inst + pinst, sk);

@@ -2,7 +2,7 @@
 // (Alg. 1 of arXiv:1409.8112 associates each point with its cell; the sort makes every cell
 // a contiguous run).  Stable.
 //
-// Compile-time variants: digit width BITS (8, 10 or 11 bits per pass, so a key of b bits takes
+// Compile-time variants: digit width BITS (8, 9, 10 or 11 bits per pass, so a key of b bits takes
 // ceil(b / BITS) passes) and ITEMS keys per thread (tiles of 256 * ITEMS keys).  The
 // autotuner in the host code picks one variant and one pass strategy per shape.
 //
@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 
 #include "rtg_internal.cuh"
+
+#include <mutex>
 
 namespace rtg {
 
@@ -442,6 +444,94 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   tr.write(kout, vout, N, tile_base, shift, errors);
 }
 
+// Grid-wide barrier of a cooperative launch (every block resident), bounded: false when the
+// other blocks did not all arrive within `limit` polls (the caller then leaves; kErrTimeout).
+__device__ __forceinline__ bool coop_grid_sync(unsigned int* count, unsigned int* gen,
+                                               unsigned int limit, unsigned int* errors) {
+  __shared__ bool s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g = *reinterpret_cast<volatile unsigned int*>(gen);
+    __threadfence();
+    bool ok = true;
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      *reinterpret_cast<volatile unsigned int*>(count) = 0u;  // every block has arrived
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned int spins = 0;
+      while (*reinterpret_cast<volatile unsigned int*>(gen) == g) {
+        if (++spins > limit) {
+          ok = false;
+          atomicOr(errors, kErrTimeout);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok;
+}
+
+// Every pass in one launch, one tile per block (the host launches it cooperatively, so all
+// tiles are resident): a block ranks its tile into shared memory and publishes the tile's digit
+// counts (counts[digit * tiles + tile]); after a grid barrier the blocks turn the count
+// columns into output offsets (one digit column per block at a time, a block-wide scan over
+// the tiles, plus the digit's global start); after a second barrier every block writes its
+// ranked tile; a third barrier ends the pass.  No look-back chains, no per-pass launches.
+template <typename K, int BITS, int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_sort_coop(
+    const K* __restrict__ key_rows, K* kbuf0, K* kbuf1, uint32_t* vbuf0, uint32_t* vbuf1,
+    long long N, int passes, const unsigned int* __restrict__ digit_off, unsigned int* counts,
+    unsigned int tiles, Status* st, unsigned int spin_limit, unsigned long long vdiv) {
+  using TR = TileRank<K, BITS, ITEMS>;
+  constexpr int D = TR::D, PT = TR::PT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int sbuf[kSortWarps];
+  TR tr(smem);
+  const unsigned int tile = blockIdx.x;
+  const long long tile_base = (long long)tile * TR::kTile;
+  const int tid = threadIdx.x;
+  unsigned int* errors = &st->errors;
+  for (int p = 0; p < passes; ++p) {
+    const K* kin = p == 0 ? key_rows : ((p - 1) & 1 ? kbuf1 : kbuf0);
+    const uint32_t* vin = p == 0 ? nullptr : ((p - 1) & 1 ? vbuf1 : vbuf0);
+    K* kout = p & 1 ? kbuf1 : kbuf0;
+    uint32_t* vout = p & 1 ? vbuf1 : vbuf0;
+    const int shift = p * BITS;
+    unsigned int tcount[PT];
+    tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf, p == 0 ? vdiv : 0ull);
+#pragma unroll
+    for (int q = 0; q < PT; ++q) counts[(size_t)(tid * PT + q) * tiles + tile] = tcount[q];
+    if (!coop_grid_sync(&st->coop_count, &st->coop_gen, spin_limit, errors)) return;
+    // digit columns: exclusive scan over the tiles, offset by the digit's start
+    for (int d = blockIdx.x; d < D; d += gridDim.x) {
+      unsigned int* col = counts + (size_t)d * tiles;
+      unsigned int carry = digit_off[p * D + d];
+      for (unsigned int b = 0; b < tiles; b += kSortThreads) {
+        const unsigned int t = b + tid;
+        const unsigned int v = t < tiles ? col[t] : 0u;
+        unsigned int tot;
+        const unsigned int ex = block_excl_scan_256(v, &tot, sbuf);
+        if (t < tiles) col[t] = carry + ex;
+        carry += tot;
+      }
+    }
+    if (!coop_grid_sync(&st->coop_count, &st->coop_gen, spin_limit, errors)) return;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+      const int d = tid * PT + q;
+      tr.s_gbase[d] = __ldcg(counts + (size_t)d * tiles + tile);
+    }
+    __syncthreads();
+    tr.write(kout, vout, N, tile_base, shift, errors);
+    if (!coop_grid_sync(&st->coop_count, &st->coop_gen, spin_limit, errors)) return;
+  }
+}
+
 // Sets a kernel's dynamic shared-memory limit once per device (static shared memory adds to
 // the dynamic part, so the limit is raised whatever the size).
 template <typename F>
@@ -492,6 +582,29 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
         (const K*)a.key_mat, N, passes, a.hist, a.digit_off, &a.st->hist_ticket, a.sort_epoch);
   }
   const unsigned tiles = (unsigned)((N + SS::kTile - 1) / SS::kTile);
+  // (a single-launch choice whose tiles cannot all be resident runs as reduce-then-scan, which
+  // uses the same scratch)
+  if (a.sort_mode == kSortCoop && sort_coop_fits(N, BITS, ITEMS, a.num_sms, sizeof(K) == 8)) {
+    static bool attr[64] = {};
+    set_smem_once(k_sort_coop<K, BITS, ITEMS>, SS::kSmem, attr);
+    void* args[] = {(void*)&a.key_mat, (void*)&a.keys[0], (void*)&a.keys[1], (void*)&a.vals[0],
+                    (void*)&a.vals[1], (void*)&N, (void*)&passes, (void*)&a.digit_off,
+                    (void*)&a.lookback, (void*)&tiles, (void*)&a.st, nullptr, (void*)&vdiv};
+    const unsigned int limit = spin_limit_of(a.spin_limit);
+    args[11] = (void*)&limit;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles);
+    cfg.blockDim = dim3(kSortThreads);
+    cfg.dynamicSmemBytes = SS::kSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr_coop[1];
+    attr_coop[0].id = cudaLaunchAttributeCooperative;
+    attr_coop[0].val.cooperative = 1;
+    cfg.attrs = attr_coop;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelExC(&cfg, (const void*)k_sort_coop<K, BITS, ITEMS>, args);
+    return (passes - 1) & 1;
+  }
   auto src_k = [&](int p) { return p == 0 ? (const K*)a.key_mat : (const K*)a.keys[(p - 1) & 1]; };
   auto src_v = [&](int p) { return p == 0 ? (const uint32_t*)nullptr : a.vals[(p - 1) & 1]; };
   if (a.sort_mode == kSortLookback) {
@@ -532,13 +645,60 @@ int sort_items(const BuildArgs& a, cudaStream_t s) {
 template <typename K>
 int sort_width(const BuildArgs& a, cudaStream_t s) {
   switch (a.sort_bits) {
+    case 9: return sort_items<K, 9>(a, s);
     case 10: return sort_items<K, 10>(a, s);
     case 11: return sort_items<K, 11>(a, s);
     default: return sort_items<K, 8>(a, s);
   }
 }
 
+// Blocks of the single-launch sort that can be resident at once (0 if it cannot launch).
+template <typename K, int BITS, int ITEMS>
+int coop_resident(int num_sms) {
+  static int occ[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(launch_attr_mutex());
+  if (dev >= 0 && dev < 64 && occ[dev]) return occ[dev] * num_sms;
+  using SS = SortShape<K, BITS, ITEMS>;
+  cudaFuncSetAttribute(k_sort_coop<K, BITS, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)SS::kSmem);
+  int o = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sort_coop<K, BITS, ITEMS>, kSortThreads,
+                                                    SS::kSmem) != cudaSuccess)
+    o = 0;
+  cudaGetLastError();
+  if (dev >= 0 && dev < 64) occ[dev] = o;
+  return o * num_sms;
+}
+
+template <typename K, int BITS>
+int coop_resident_items(int items, int num_sms) {
+  switch (items) {
+    case 12: return coop_resident<K, BITS, 12>(num_sms);
+    case 16: return coop_resident<K, BITS, 16>(num_sms);
+    default: return coop_resident<K, BITS, 8>(num_sms);
+  }
+}
+
+template <typename K>
+int coop_resident_bits(int bits, int items, int num_sms) {
+  switch (bits) {
+    case 9: return coop_resident_items<K, 9>(items, num_sms);
+    case 10: return coop_resident_items<K, 10>(items, num_sms);
+    case 11: return coop_resident_items<K, 11>(items, num_sms);
+    default: return coop_resident_items<K, 8>(items, num_sms);
+  }
+}
+
 }  // namespace
+
+bool sort_coop_fits(long long N, int bits, int items, int num_sms, bool key64) {
+  const long long tiles = (long long)sort_tiles_for(N, items);
+  const int res = key64 ? coop_resident_bits<unsigned long long>(bits, items, num_sms)
+                        : coop_resident_bits<uint32_t>(bits, items, num_sms);
+  return tiles >= 1 && tiles <= res;
+}
 
 size_t sort_tiles_for(long long N, int items) {
   const long long t = (long long)kSortThreads * items;

@@ -1,5 +1,6 @@
-// Autotuner of the radix sort: digit width (8, 10 or 11 bits per pass), tile size (256 x 8, 12
-// or 16 keys) and pass strategy (look-back or reduce-then-scan).  On the first build of a
+// Autotuner of the radix sort: digit width (8, 9, 10 or 11 bits per pass), tile size (256 x 8, 12
+// or 16 keys) and pass strategy (look-back, reduce-then-scan, or all passes in one cooperative
+// launch when every tile fits on the GPU at once).  On the first build of a
 // shape whose sort is large enough to matter it times every variant twice on the build's own
 // keys and keeps the fastest, per (sorted elements, key bits), in the context and, when
 // RTG_TUNE_CACHE names a file, in a JSON cache shared by later contexts and processes.
@@ -21,11 +22,16 @@ namespace {
 
 constexpr int kTuneReps = 2;
 
-std::vector<rtg::SortConfig> candidates() {
+// Every compiled variant; the single-launch strategy only where all of its tiles can be
+// resident at once (num_sms = 0: every variant, for sizing the scratch).
+std::vector<rtg::SortConfig> candidates(long long N = 0, int num_sms = 0, bool key64 = false) {
   std::vector<rtg::SortConfig> v;
   for (int bits : rtg::kSortBitsChoices)
     for (int items : rtg::kSortItemsChoices)
-      for (int mode : {rtg::kSortLookback, rtg::kSortReduceScan}) {
+      for (int mode : {rtg::kSortLookback, rtg::kSortReduceScan, rtg::kSortCoop}) {
+        if (mode == rtg::kSortCoop && num_sms > 0 &&
+            !rtg::sort_coop_fits(N, bits, items, num_sms, key64))
+          continue;
         rtg::SortConfig c;
         c.bits = bits;
         c.items = items;
@@ -60,7 +66,9 @@ bool valid_cfg(const rtg::SortConfig& c) {
   const bool items_ok = std::find(std::begin(rtg::kSortItemsChoices),
                                   std::end(rtg::kSortItemsChoices),
                                   c.items) != std::end(rtg::kSortItemsChoices);
-  return bits_ok && items_ok && (c.mode == rtg::kSortLookback || c.mode == rtg::kSortReduceScan);
+  return bits_ok && items_ok &&
+         (c.mode == rtg::kSortLookback || c.mode == rtg::kSortReduceScan ||
+          c.mode == rtg::kSortCoop);
 }
 
 // Reads the cache file into `out` (entries of this device only).
@@ -171,7 +179,7 @@ void tune_load(rtg_ctx* c) {
 
 rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
                      rtg::SortConfig* out) {
-  const std::vector<rtg::SortConfig> cands = candidates();
+  const std::vector<rtg::SortConfig> cands = candidates(N, a.num_sms, a.key64);
   const int trials = (int)cands.size() * kTuneReps;
   std::vector<cudaEvent_t> ev(2 * (size_t)trials, nullptr);
   for (auto& e : ev)
@@ -187,6 +195,7 @@ rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
     b.sort_mode = cfg.mode;
     b.passes = rtg::sort_passes_for(key_bits, cfg.bits);
     cudaMemsetAsync(&b.st->sort_tiles[0], 0, sizeof(b.st->sort_tiles), st);
+    cudaMemsetAsync(&b.st->coop_count, 0, 2 * sizeof(unsigned int), st);
     rtg::launch_keys(b, st);  // the sort consumes its input buffers
     cudaEventRecord(ev[2 * (size_t)t], st);
     rtg::launch_sort(b, st);

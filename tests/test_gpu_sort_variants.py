@@ -12,8 +12,9 @@ from paper_1409_8112_gb300 import gen, rtg
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(bits, items, mode) for bits in (8, 10, 11) for items in (8, 12, 16)
-            for mode in (0, 1)]
+VARIANTS = [(bits, items, mode) for bits in (8, 9, 10, 11) for items in (8, 12, 16)
+            for mode in (0, 1, 2)]
+LOOKBACK_CODE = {0: 1, 1: 0, 2: 2}  # stats "lookback" of each pass strategy
 
 
 def _context(env):
@@ -73,7 +74,7 @@ def test_sort_variant_bit_exact(variant, case32, case64):
         st = _check(ctx, *case32)
         assert st["key_bits"] <= 32
         assert (st["sort"]["digit_bits"], st["sort"]["tile_keys"], st["sort"]["lookback"]) == \
-            (variant[0], 256 * variant[1], 1 - variant[2])
+            (variant[0], 256 * variant[1], LOOKBACK_CODE[variant[2]])
         assert st["sort_passes"] == -(-st["key_bits"] // variant[0])
         st = _check(ctx, *case64)
         assert st["key_bits"] > 32
@@ -97,7 +98,7 @@ def test_autotuner_measures_once_and_caches(tmp_path, case32):
     assert len(entries) == 1
     e = entries[0]
     assert e["elements"] == 37003 * 8 and e["key_bits"] == st["key_bits"]
-    assert (e["bits"], 256 * e["items"], 1 - e["mode"]) == (
+    assert (e["bits"], 256 * e["items"], LOOKBACK_CODE[e["mode"]]) == (
         st["sort"]["digit_bits"], st["sort"]["tile_keys"], st["sort"]["lookback"])
     assert e["us"] > 0
     # a new context takes the cached choice without measuring again

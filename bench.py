@@ -163,31 +163,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic bytes per build for each timed phase (lower-bound model):
-#   sort  : each pass reads and writes the N (key, index) pairs; with digits wider than 8 bits
-#           a histogram kernel first reads the N keys once (8-bit digits are counted by the key
-#           kernel as it writes the keys)
-#   pairs : reads the N sorted (key, index) pairs, gathers each point's padded FP32 row and
-#           writes 8 bytes per reported pair
-# DRAM bytes (read + write) of each phase's kernels per build, from ncu
-# (profiles/dram_rtg_all_pairs_n100k_and_n1m.md; cold replays, one build), for the two
-# profiled workloads and, for the sort, the variant the profiled run used
-# (digit bits, keys per tile, look-back).  None where the kernels changed after the capture.
-NCU_TRAFFIC = {
-    (100000, "fp64"): {"prep": 4868608, "keys": 3685888, "sort": {(8, 3072, 1): 26609408},
-                       "pairs": 13299456, "scan": 415232, "scatter": 4854784, "rowsort": 2706432},
-    (1000000, "fp32"): {"prep": 24102656, "keys": 69185536, "sort": {(8, 3072, 0): 455094784},
-                        "pairs": 329081088, "scan": 4024832, "scatter": 89386752,
-                        "rowsort": 32143104},
-}
+# Algorithmic bytes per build of the two phases a roofline is reported for:
+#   pairs : the survey's per-grid model of in-cell enumeration, summed over the m grids:
+#           the sorted (key, index) of every (point, grid) element, a gather of each point's
+#           coordinates in the input's own width (d * S bytes), and 8 bytes per emitted pair
+#           (each reported pair is emitted once, by its first grid)
+#   sort  : every radix pass reads and writes the N (key, index) elements (the first pass
+#           reads the key rows only: indices are implicit), plus one read of the keys by a
+#           histogram kernel when the key kernel did not count the digits
+# DRAM bytes (read + write) of each phase's kernels per build, from ncu, for the profiled
+# workloads and, for the sort, the variant the profiled run used (digit bits, keys per tile,
+# look-back code).  None where the kernels changed after the capture.
+NCU_TRAFFIC = {}
 
 
-def phase_bytes(n, d, m, key_bytes, passes, dpad, pairs, digit_bits=8):
+def phase_bytes(n, d, m, key_bytes, passes, coord_bytes, pairs, hist_read=False):
     N = n * m
-    hist_read = N * key_bytes if digit_bits != 8 else 0
     return {
-        "sort": hist_read + passes * 2 * N * (key_bytes + 4),
-        "pairs": N * (key_bytes + 4) + N * dpad * 4 + 8 * pairs,
+        "sort": (N * key_bytes if hist_read else 0) + N * key_bytes + N * (key_bytes + 4) +
+                max(0, passes - 1) * 2 * N * (key_bytes + 4),
+        "pairs": N * (key_bytes + 4) + N * d * coord_bytes + 8 * pairs,
     }
 
 
@@ -198,30 +193,19 @@ def ncu_traffic(n, dtype, phase, sort_cfg):
     return t
 
 
-def run_ours(args):
+def measure_build(ctx, stream, flush, args, pts, T, r, dtype_name, ws, rank, clocks=None):
+    """Device-timed builds (inputs resident), their phases and roofline, and the end-to-end
+    rate through the C ABI with host points and a CSR download.  Returns the fields of a
+    bench record."""
     import torch
     import torch.distributed as dist
-    from paper_1409_8112_gb300 import rtg
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    pts, T, r = workload()
     n, d = pts.shape
     m = T.shape[0]
-    # torch and the library share one stream: inputs made by torch need no cross-stream wait
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    ctx = rtg.Context(local, stream=stream.cuda_stream)
     dev_pts = torch.from_numpy(pts).cuda()
-    flush = L2Flush()
-
     # recall against the exact set (device brute force), outside the timed region
     exact = ctx.brute_force(dev_pts, r, count_only=True)
     exact_pairs = exact.nnz
     exact.release()
-
     for k in range(args.warmup):
         for timing in (False, True):  # both launch plans (with and without phase events)
             res = ctx.all_pairs(dev_pts, r, T, r, timing=timing)
@@ -229,8 +213,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
+    if clocks is not None:
+        clocks.start()
 
     def steps(timing):
         out_ms, out_ph, info = [], [], {}
@@ -247,7 +231,8 @@ def run_ours(args):
             if timing:
                 out_ph.append(st["phase_us"])
             info = {"pairs": res.nnz, "launches": st["launches"], "key_bits": st["key_bits"],
-                    "passes": st["sort_passes"], "sort": st["sort"]}
+                    "passes": st["sort_passes"], "sort": st["sort"],
+                    "phase_bytes": st["phase_bytes"]}
             res.release()
         return out_ms, out_ph, info
 
@@ -261,21 +246,19 @@ def run_ours(args):
     # the same steps again with phase events (they cost about 30 us a build), for the roofline
     _, phases, _ = steps(True)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks is not None else None
     pairs, launches = info["pairs"], info["launches"]
     key_bytes = 8 if info["key_bits"] > 32 else 4
     passes = info["passes"]
     sort_cfg = dict(info["sort"], key_bits=info["key_bits"], passes=passes)
     total_ms = max_over_ranks(float(np.sum(step_ms)), ws)
     ms_per_step = total_ms / args.steps
-    value = job_throughput(pairs, args.steps, ws, total_ms)
 
     # end to end through the C ABI with host buffers (pinned) and the CSR copied back
-    import torch as _t
-    host_pts = _t.from_numpy(pts).pin_memory()
+    host_pts = torch.from_numpy(pts).pin_memory()
     # pinned result buffers, reused by every step (the download is then a direct DMA)
-    host_rp = _t.empty(n + 1, dtype=_t.int64).pin_memory().numpy()
-    host_col = _t.empty(max(pairs, 1), dtype=_t.int32).pin_memory().numpy()
+    host_rp = torch.empty(n + 1, dtype=torch.int64).pin_memory().numpy()
+    host_col = torch.empty(max(pairs, 1), dtype=torch.int32).pin_memory().numpy()
     # the first calls with host points build this shape's launch plan and CUDA graph: warm-up
     e2e_ms = []
     e2e_warm = max(3, args.warmup)
@@ -295,25 +278,24 @@ def run_ours(args):
 
     # roofline of the dominant phase (per-phase device events over the timed region)
     mean_phase = {p: float(np.mean([ph[p] for ph in phases])) for p in phases[0]}
-    dpad = 4 if d <= 4 else (8 if d <= 8 else 16)
-    pb = phase_bytes(n, d, m, key_bytes, passes, dpad, pairs, sort_cfg.get("digit_bits", 8))
+    pb = phase_bytes(n, d, m, key_bytes, passes, pts.dtype.itemsize, pairs)
     dom = max(pb, key=lambda p: mean_phase[p])
     peak, peak_kind = measured_peaks()
     achieved = pb[dom] / (mean_phase[dom] * 1e-6) / 1e9
-    traffic = ncu_traffic(n, WORKLOAD.get("dtype", "fp64"), dom, sort_cfg)
-    kernels = {"sort": "one k_sort_pass per radix pass (look-back) or upsweep, scan and "
-                       "downsweep per pass (autotuned variant); k_sort_hist for digits over 8 bits",
+    traffic = ncu_traffic(n, dtype_name, dom, sort_cfg)
+    kernels = {"sort": "one k_sort_pass per radix pass (look-back), upsweep + scan + downsweep "
+                       "per pass, or one k_sort_coop launch (autotuned variant)",
                "pairs": "k_pairs_warp + k_pairs_medium + k_large_setup + k_pairs_large"}[dom]
     roofline = {"bound": "hbm", "kernel": dom, "kernels": kernels, "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "algorithmic_bytes": pb[dom], "launch_us": round(mean_phase[dom], 2)}
-
-    line = {
-        "metric": METRIC, "value": round(value, 1), "unit": "pairs/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic", "config": WORKLOAD,
+                "algorithmic_bytes": pb[dom], "launch_us": round(mean_phase[dom], 2),
+                "bytes_model": "pairs: N (key + index) + N d S gather + 8 per pair (survey "
+                               "per-grid model); sort: per radix pass read + write of the N "
+                               "(key, index) elements"}
+    return {
+        "value": round(job_throughput(pairs, args.steps, ws, total_ms), 1),
+        "ms_per_step": round(ms_per_step, 4), "total_ms": total_ms,
         "builds_per_s": round(args.steps * ws / (total_ms / 1e3), 2),
         "pairs_per_build": pairs, "exact_pairs": exact_pairs,
         "recall": round(pairs / exact_pairs, 5) if exact_pairs else 1.0,
@@ -321,15 +303,60 @@ def run_ours(args):
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
         "wall_s_timed_region": round(wall_s, 3),
         "phase_us": {p: round(v, 2) for p, v in mean_phase.items()},
-        "phase_note": "device phases from CUDA events on the library's stream, in a second pass of "
-                      "the same steps (phase events add about 30 us a build, so the timed steps "
-                      "run without them)",
-        "sort": sort_cfg,
-        "roofline": roofline,
+        "phase_bytes_model": info["phase_bytes"],
+        "sort": sort_cfg, "roofline": roofline,
         "e2e": {"value": round(e2e_value, 1), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(float(np.mean(e2e_ms)), 4)},
         "clocks": clk, "gpu_launches": launches * args.steps,
     }
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1409_8112_gb300 import rtg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pts, T, r = workload()
+    # torch and the library share one stream: inputs made by torch need no cross-stream wait
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = rtg.Context(local, stream=stream.cuda_stream)
+    flush = L2Flush()
+    rec = measure_build(ctx, stream, flush, args, pts, T, r, WORKLOAD.get("dtype", "fp64"), ws,
+                        rank, clocks=ClockSampler(local))
+    line = {
+        "metric": METRIC, "value": rec["value"], "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic", "config": WORKLOAD,
+    }
+    for k in ("builds_per_s", "pairs_per_build", "exact_pairs", "recall", "p50_ms", "p99_ms",
+              "wall_s_timed_region", "phase_us", "sort", "roofline", "e2e", "clocks",
+              "gpu_launches"):
+        line[k] = rec[k]
+    line["phase_note"] = ("device phases from CUDA events on the library's stream, in a second "
+                          "pass of the same steps (phase events add about 30 us a build, so the "
+                          "timed steps run without them)")
+    if args.config3 and WORKLOAD["n"] == 100000:
+        # the 1,000,000-point FP32 build, measured in the same run with the same protocol
+        set_workload(1000000, "fp32")
+        p3, T3, r3 = workload()
+        set_workload(100000, "fp64")
+        c3 = measure_build(ctx, stream, flush, args, p3, T3, r3, "fp32", ws, rank,
+                           clocks=ClockSampler(local))
+        line["config3"] = {
+            "workload": "rtg_all_pairs n=1000000 d=6 fp32 uniform[0,1]^6 r=2lnn-degree m=8 c=r "
+                        "seed0",
+            "metric": METRIC, "unit": "pairs/s", "dtype": "f32+f64", "steps": args.steps,
+            **{k: c3[k] for k in ("value", "ms_per_step", "builds_per_s", "pairs_per_build",
+                                  "exact_pairs", "recall", "p50_ms", "p99_ms", "phase_us",
+                                  "sort", "roofline", "e2e", "clocks", "gpu_launches")},
+        }
+        line["gpu_launches"] += c3["gpu_launches"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pts, T, r, budget_s=args.cpu_seconds)
     ctx.close()
@@ -906,6 +933,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config3", dest="config3", action="store_false",
+                    help="leave out the 1,000,000-point FP32 sub-record of the default line")
     ap.add_argument("--workload", default="build",
                     choices=["build", "batch", "serve", "precision", "table2", "query",
                              "points_query", "params", "bitset"],

@@ -814,7 +814,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         // indices, and the later ones also read them
         pb[2] = a.passes > 0 ? N_ * kb + N_ * (kb + 4.0) +
                                    (a.passes - 1) * 2.0 * N_ * (kb + 4.0) +
-                                   (a.sort_bits != 8 ? N_ * kb : 0.0)
+                                   (rtg::hist_in_keys(a) ? 0.0 : N_ * kb)
                              : 0.0;
         pb[3] = N_ * (kb + 4.0) + N_ * dpad * 4.0 + (two_pass ? 0.0 : 8.0 * P);
       } else {

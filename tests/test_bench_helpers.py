@@ -5,25 +5,28 @@ import bench
 
 
 def test_phase_bytes_model():
-    n, d, m, kb, passes, dpad, pairs = 100000, 6, 8, 4, 4, 8, 456724
+    n, d, m, kb, passes, pairs = 100000, 6, 8, 4, 4, 456724
     N = n * m
-    pb = bench.phase_bytes(n, d, m, kb, passes, dpad, pairs)
-    # 8-bit digits: counted by the key kernel, so no extra read of the keys
-    assert pb["sort"] == passes * 2 * N * (kb + 4)
-    assert pb["pairs"] == N * (kb + 4) + N * dpad * 4 + 8 * pairs
-    # wider digits: a histogram kernel reads the keys once more
-    pb11 = bench.phase_bytes(n, d, m, kb, 3, dpad, pairs, digit_bits=11)
-    assert pb11["sort"] == N * kb + 3 * 2 * N * (kb + 4)
+    # FP64 coordinates: the pairs model gathers d * 8 bytes per (point, grid) element
+    pb = bench.phase_bytes(n, d, m, kb, passes, 8, pairs)
+    assert pb["pairs"] == N * (kb + 4) + N * d * 8 + 8 * pairs
+    # the first pass reads only the key rows; every pass writes keys and indices
+    assert pb["sort"] == N * kb + N * (kb + 4) + (passes - 1) * 2 * N * (kb + 4)
+    # a histogram kernel reads the keys once more
+    pbh = bench.phase_bytes(n, d, m, kb, 3, 4, pairs, hist_read=True)
+    assert pbh["sort"] == N * kb + N * kb + N * (kb + 4) + 2 * 2 * N * (kb + 4)
+    assert pbh["pairs"] == N * (kb + 4) + N * d * 4 + 8 * pairs
 
 
-def test_traffic_lookup_by_workload_and_sort_variant():
+def test_traffic_lookup_by_workload_and_sort_variant(monkeypatch):
     cfg = {"digit_bits": 8, "tile_keys": 3072, "lookback": 1}
-    t = bench.ncu_traffic(100000, "fp64", "sort", cfg)
-    assert isinstance(t, int) and t > 0
+    monkeypatch.setattr(bench, "NCU_TRAFFIC",
+                        {(100000, "fp64"): {"pairs": 123, "sort": {(8, 3072, 1): 456}}})
+    assert bench.ncu_traffic(100000, "fp64", "sort", cfg) == 456
     # a variant that was not captured has no traffic figure
     assert bench.ncu_traffic(100000, "fp64", "sort", dict(cfg, tile_keys=2048)) is None
     assert bench.ncu_traffic(123, "fp64", "pairs", cfg) is None
-    assert bench.ncu_traffic(100000, "fp64", "pairs", cfg) > 0
+    assert bench.ncu_traffic(100000, "fp64", "pairs", cfg) == 123
 
 
 def test_whole_job_throughput_counts_every_replica():

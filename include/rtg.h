@@ -56,8 +56,12 @@ typedef enum {
 #define RTG_FLAG_TIMING 4u     /* rtg_all_pairs: fill rtg_stats.phase_us (adds events) */
 #define RTG_FLAG_TWO_PASS 8u   /* enumerate twice (count, then write in place) instead of
                                   holding a pair buffer: less memory, more time */
-#define RTG_FLAG_TC_FP16 16u   /* rtg_brute_force: distances from FP16 tensor-core tiles */
-#define RTG_FLAG_TC_BF16 32u   /* rtg_brute_force: distances from BF16 tensor-core tiles */
+#define RTG_FLAG_TC_FP16 16u   /* rtg_brute_force: distances from FP16 tensor-core tiles;
+                                  rtg_all_pairs / rtg_batch_all_pairs: cells of more than 256
+                                  points are filtered by FP16 tensor-core tiles (pairs the tile
+                                  proves beyond r are dropped, every other pair is decided as
+                                  without the flag: the same set) */
+#define RTG_FLAG_TC_BF16 32u   /* as RTG_FLAG_TC_FP16 with BF16 tiles */
 #define RTG_FLAG_BITSET 64u    /* small instances (n <= 16384 each): dedupe through an n x n
                                   bit matrix per instance (the flattened bit array of
                                   Sec. III-B) instead of the first-grid rule; same output */
@@ -180,7 +184,8 @@ rtg_status rtg_transforms_generate(uint64_t seed, int d, int m, double cell_side
  *   r          reporting radius (> 0, finite)
  *   transforms host pointer, m*(d*d+d) doubles as produced by rtg_transforms_generate
  *   cell_side  grid cell side c (> 0, finite); the paper takes c = c~ r with c~ > 1
- *   flags      RTG_FLAG_SYMMETRIC, RTG_FLAG_TIMING
+ *   flags      RTG_FLAG_SYMMETRIC, RTG_FLAG_TIMING, RTG_FLAG_TWO_PASS, RTG_FLAG_BITSET,
+ *              RTG_FLAG_TC_FP16 or RTG_FLAG_TC_BF16 (dense cells on tensor-core tiles)
  *   out        receives a library-owned device CSR; free it with rtg_release
  * Errors: RTG_E_INVALID (n < 0 or n >= 2^31, n * m >= 2^31, d outside [1,16], m outside
  * [1,64], r or c not positive and finite, a non-finite coordinate or transform entry),

@@ -416,6 +416,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.num_sms = c->num_sms;
   a.spin_limit = c->spin_limit;
   a.inject = c->inject;
+  a.tc_cells = m > 0 ? ((q.flags & RTG_FLAG_TC_BF16) ? 2 : ((q.flags & RTG_FLAG_TC_FP16) ? 1 : 0))
+                     : 0;
 
   const ShapeKey key{n_total, B, m, q.dtype, maxd, sym, q.count_only ? 1 : 0};
   auto git = c->guesses.find(key);

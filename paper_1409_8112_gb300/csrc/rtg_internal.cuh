@@ -258,6 +258,8 @@ struct BuildArgs {
   int passes;          // radix passes launched
   unsigned int* sort_epoch;  // device counter: look-back epoch base, advanced by every sort
   int num_sms;
+  int tc_cells;             // cells of more than 256 points on the tensor cores: 0 off,
+                            // 1 FP16 halves, 2 BF16 halves
   unsigned int spin_limit;  // bounded waits: iterations before giving up (0: the default)
   unsigned int inject;      // test hooks (kInject*), 0 in normal use
 };

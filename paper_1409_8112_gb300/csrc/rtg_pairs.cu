@@ -28,6 +28,10 @@
 #include <climits>
 
 #include "rtg_internal.cuh"
+#include "rtg_tc.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace rtg {
 
@@ -228,6 +232,24 @@ __device__ __forceinline__ bool decide_pair(unsigned int i, unsigned int j, int 
   }
   if (keep && MODE != kWrite) ++tl.pairs;
   return keep;
+}
+
+// A candidate that a tensor-core tile proved to be within r (its tile d^2 is below the band
+// minus the tile error bound): only the ownership test remains (as in decide_pair).
+template <typename K, int MODE>
+__device__ __forceinline__ bool decide_inside(int t, const K* ki, const K* kj, Tally& tl) {
+  if (MODE != kBits) {
+    for (int u0 = 0; u0 < t; u0 += 4) {
+      bool earlier = false;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (u0 + q < t) earlier |= ki[u0 + q] == kj[u0 + q];
+      if (earlier) return false;
+    }
+  }
+  if (MODE != kWrite && MODE != kBits) ++tl.owned;
+  if (MODE != kWrite) ++tl.pairs;
+  return true;
 }
 
 // Deliver a decided pair.  Called by all 32 lanes of a warp together (keep may be false).
@@ -848,6 +870,283 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_large(
   flush_tally<MODE>(tl, st, s_tally);
 }
 
+// Dense cells on the tensor cores (the in-cell distance test of Alg. 1 as d^2 = |x|^2 +
+// |y|^2 - 2 x.y tiles): the jobs of k_pairs_large, a 128 x 128 pair of member tiles each.
+// The members' FP32 rows are centred on the cell's first member and split into half-precision
+// hi + lo; three K = 16 tcgen05 MMAs (hi.hi + hi.lo + lo.hi) accumulate x.y in FP32 in tensor
+// memory.  A pair is rejected on the tile only when its tile d^2 exceeds the FP32 band's upper
+// end plus 1.25 times the tile error bound (tc_error_bound with M the job's largest centred
+// coordinate), so the tile is only a filter: every other pair is decided exactly as on the
+// CUDA cores (FP32 outside the band, the FP64 sequence inside), then tested for ownership and
+// emitted.  The reported set is unchanged.  4 warps, 128 TMEM columns per block.
+constexpr int kLTcK = 32;                          // hi (16) + lo (16) halves per member
+constexpr int kLTcTileBytes = kTL * kLTcK * 2;     // 8 KB per 128-member tile
+
+template <typename K, int DPAD>
+struct LargeTcSmem {
+  static constexpr int kLK = 64 / (int)sizeof(K);  // staged keys per member (as k_pairs_large)
+  static constexpr size_t kTiles = 2 * (size_t)kLTcTileBytes;
+  static constexpr size_t kRows = 2 * (size_t)kTL * DPAD * 4;
+  static constexpr size_t kKeys = 2 * (size_t)kTL * (kLK + 1) * sizeof(K);
+  static constexpr size_t kBytes = kTiles + kRows + kKeys + 2 * kTL * 4 /*idx*/ +
+                                   2 * kTL * 4 /*norms*/ + 4 * kWarpEmit * 8 + 1024 /*align*/;
+};
+
+template <typename K, int DPAD, int MODE, bool BF16>
+__global__ void __launch_bounds__(128) k_pairs_large_tc(
+    const uint32_t* __restrict__ svals, const float* __restrict__ pf, int dtype,
+    const K* __restrict__ key_mat, int m, const Inst* __restrict__ inst,
+    const InstPlan* __restrict__ iplan, Status* st, const LargeCell* __restrict__ large,
+    unsigned int cap, const unsigned long long* job_off, Sink sk, unsigned int wait_limit,
+    unsigned int inject) {
+  using SM = LargeTcSmem<K, DPAD>;
+  constexpr int kLK = SM::kLK;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* ta = smem;
+  unsigned char* tb = ta + kLTcTileBytes;
+  float* ra = reinterpret_cast<float*>(tb + kLTcTileBytes);
+  float* rb = ra + kTL * DPAD;
+  K* ska = reinterpret_cast<K*>(rb + kTL * DPAD);
+  K* skb = ska + kTL * (kLK + 1);
+  uint32_t* ia = reinterpret_cast<uint32_t*>(skb + kTL * (kLK + 1));
+  uint32_t* ib = ia + kTL;
+  float* na = reinterpret_cast<float*>(ib + kTL);
+  float* nb = na + kTL;
+  unsigned long long* s_emit = reinterpret_cast<unsigned long long*>(nb + kTL);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_idle;  // test hook: a barrier nothing arrives on
+  __shared__ uint32_t tmem_base;
+  __shared__ unsigned int s_tally[4];
+  __shared__ float s_thr, s_thr_in;
+  __shared__ unsigned int s_mbits[4];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
+  const unsigned long long J = L ? job_off[L] : 0;
+  if ((unsigned long long)blockIdx.x >= J) return;  // no job for this block: no TMEM either
+  if (tid < 4) s_tally[tid] = 0;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_idle)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) |
+                         ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  unsigned long long* w_emit = s_emit + (size_t)warp * kWarpEmit;
+  unsigned int ecnt = 0;
+  Tally tl;
+  uint32_t phase = 0;
+  for (unsigned long long job = blockIdx.x; job < J; job += gridDim.x) {
+    long long el = 0, eh = (long long)L - 1;
+    while (el < eh) {
+      const long long mid = (el + eh + 1) >> 1;
+      if (job_off[mid] <= job) el = mid; else eh = mid - 1;
+    }
+    const LargeCell cell = large[el];
+    const Inst& I = inst[cell.inst];
+    const int d = I.d;
+    const float2 band = band_of(iplan[cell.inst]);
+    const unsigned int s = cell.size;
+    const long long k = (long long)(job - job_off[el]);
+    long long bj = (long long)((sqrt(8.0 * (double)k + 1.0) - 1.0) * 0.5);
+    while (bj * (bj + 1) / 2 > k) --bj;
+    while ((bj + 1) * (bj + 2) / 2 <= k) ++bj;
+    const long long bi = k - bj * (bj + 1) / 2;
+    const unsigned int a0 = (unsigned int)bi * kTL, b0 = (unsigned int)bj * kTL;
+    const unsigned int nA = min((unsigned int)kTL, s - a0), nB = min((unsigned int)kTL, s - b0);
+    const int tg = (int)cell.grid;
+    const bool kst = tg <= kLK;
+    // stage member tid of each side: index, FP32 row, centred hi/lo halves, norm, key row
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // the previous job's epilogue is done with shared memory and TMEM
+    const uint32_t i0 = svals[cell.start];  // the centre: the cell's first member
+    float cen[DPAD];
+#pragma unroll
+    for (int v = 0; v < DPAD / 4; ++v) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(pf + (size_t)i0 * DPAD) + v);
+      cen[4 * v] = q.x;
+      cen[4 * v + 1] = q.y;
+      cen[4 * v + 2] = q.z;
+      cen[4 * v + 3] = q.w;
+    }
+    float mloc = 0.0f;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      const unsigned int nn = side ? nB : nA, base = side ? b0 : a0;
+      unsigned char* tile = side ? tb : ta;
+      float* rows = side ? rb : ra;
+      K* keys = side ? skb : ska;
+      uint32_t* ids = side ? ib : ia;
+      float* norms = side ? nb : na;
+      const bool ok = (unsigned int)tid < nn;
+      const uint32_t idx = ok ? svals[cell.start + base + tid] : i0;
+      ids[tid] = idx;
+      float x[DPAD];
+      const float4* src = reinterpret_cast<const float4*>(pf + (size_t)idx * DPAD);
+#pragma unroll
+      for (int v = 0; v < DPAD / 4; ++v) {
+        const float4 q = __ldg(src + v);
+        reinterpret_cast<float4*>(rows + tid * DPAD)[v] = q;
+        x[4 * v] = q.x;
+        x[4 * v + 1] = q.y;
+        x[4 * v + 2] = q.z;
+        x[4 * v + 3] = q.w;
+      }
+      float nrm = 0.0f;
+#pragma unroll
+      for (int l = 0; l < 16; ++l) {
+        float xc = 0.0f;
+        if (l < DPAD && l < d && ok) xc = x[l < DPAD ? l : 0] - cen[l < DPAD ? l : 0];
+        mloc = fmaxf(mloc, fabsf(xc));
+        nrm = fmaf(xc, xc, nrm);
+        if (BF16) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(xc);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(xc - __bfloat162float(h));
+          *reinterpret_cast<__nv_bfloat16*>(tile + tile_off(tid, l)) = h;
+          *reinterpret_cast<__nv_bfloat16*>(tile + tile_off(tid, 16 + l)) = lo;
+        } else {
+          const __half h = __float2half_rn(xc);
+          const __half lo = __float2half_rn(xc - __half2float(h));
+          *reinterpret_cast<__half*>(tile + tile_off(tid, l)) = h;
+          *reinterpret_cast<__half*>(tile + tile_off(tid, 16 + l)) = lo;
+        }
+      }
+      norms[tid] = nrm;
+      if (kst && ok) {
+        const K* kr = key_mat + (size_t)idx * m;
+        K* kd = keys + tid * (kLK + 1);
+        for (int u = 0; u < tg; ++u) kd[u] = __ldg(kr + u);
+      }
+    }
+    // the job's largest centred coordinate (a bound for every staged member), and from it
+    // the rejection threshold: the band's upper end plus 1.25 times the tile error bound
+    float mw = mloc;
+    for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+    if (lane == 0) s_mbits[warp] = __float_as_uint(mw);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const float M = fmaxf(fmaxf(__uint_as_float(s_mbits[0]), __uint_as_float(s_mbits[1])),
+                            fmaxf(__uint_as_float(s_mbits[2]), __uint_as_float(s_mbits[3]))) *
+                      (1.0f + 0x1.0p-20f);
+      const double E = tc_error_bound((double)M, d, BF16);
+      s_thr = isinf(band.y) ? band.y : __double2float_ru((double)band.y + 1.25 * E);
+      // certainly within r below this (the band's lower end less the error bound); with the
+      // FP32 filter off (band.x < 0) nothing is
+      s_thr_in = band.x < 0.0f ? -1.0f : __double2float_rd((double)band.x - 1.25 * E);
+      // hi.hi + hi.lo + lo.hi: A parts (0, 0, 1), B parts (0, 1, 0); 256 bytes per part
+      const uint32_t aa = smem_u32(ta), bb = smem_u32(tb);
+      const uint32_t asel[3] = {0u, 0u, 256u}, bsel[3] = {0u, 256u, 0u};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const uint64_t ad = make_desc(aa + asel[q]);
+        const uint64_t bd = make_desc(bb + bsel[q]);
+        const uint32_t acc = q > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar)));
+    }
+    const bool done = mbar_wait(
+        (inject & kInjectTcWait) ? smem_u32(&mbar_idle) : smem_u32(&mbar), phase, wait_limit);
+    if (!__syncthreads_and(done)) {
+      // give up: wait (bounded again) for the MMAs in flight before the tensor memory is freed
+      mbar_wait(smem_u32(&mbar), phase, wait_limit);
+      if (tid == 0) atomicOr(&st->errors, kErrTimeout);
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const float thr = s_thr, thr_in = s_thr_in;
+    // epilogue: warp w holds rows 32w..32w+31 (members a0 + row); 32 columns at a time
+    const int row = warp * 32 + lane;
+    const float nrow = na[row];
+    const bool row_ok = (unsigned int)row < nA;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTL; c0 += 32) {
+      uint32_t rr[32];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, rr);
+      uint32_t hits = 0, inside = 0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float d2 = (nrow + nb[c0 + q]) - 2.0f * __uint_as_float(rr[q]);
+        hits |= (d2 > thr ? 0u : 1u) << q;  // NaN (non-finite tiles) is kept
+        inside |= (d2 < thr_in ? 1u : 0u) << q;
+      }
+      // valid columns: members b0 + col < s, and a0 + row < b0 + col
+      {
+        const long long lo = (long long)a0 + row - (long long)b0 - c0 + 1;  // first valid q
+        const long long hi = (long long)nB - c0;                           // q < hi
+        const int q0 = (int)max(0LL, min(32LL, lo)), q1 = (int)max(0LL, min(32LL, hi));
+        const uint32_t vm = q1 > q0 ? ((q1 - q0 == 32 ? 0xffffffffu : ((1u << (q1 - q0)) - 1u)) << q0)
+                                    : 0u;
+        hits &= row_ok ? vm : 0u;
+      }
+      // transpose the warp's 32 x 32 hit block (lane = row -> lane = column), so that the
+      // lanes of a step share one row member: the emitted pairs of a step share their row,
+      // as in k_pairs_large (the scatter then takes their slots with one atomic)
+      inside &= hits;
+      uint32_t colmask = 0, colin = 0;  // bit w: row 32 warp + w (not rejected, proved inside)
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t b = __ballot_sync(0xffffffffu, (hits >> q) & 1u);
+        const uint32_t bi2 = __ballot_sync(0xffffffffu, (inside >> q) & 1u);
+        if (lane == q) {
+          colmask = b;
+          colin = bi2;
+        }
+      }
+      uint32_t any = __reduce_or_sync(0xffffffffu, colmask);
+      const int col = c0 + lane;
+      const uint32_t iy = ib[col];
+      while (any) {  // rows where some column has a pair that the tile did not reject
+        const int w = __ffs(any) - 1;
+        any &= any - 1;
+        const int rw = warp * 32 + w;
+        bool keep = false;
+        unsigned int i = 0, j = 0;
+        if ((colmask >> w) & 1u) {
+          const uint32_t ix = ia[rw];
+          i = min(ix, iy);
+          j = max(ix, iy);
+          const K* kx = kst ? ska + rw * (kLK + 1) : key_mat + (size_t)ix * m;
+          const K* ky = kst ? skb + col * (kLK + 1) : key_mat + (size_t)iy * m;
+          keep = ((colin >> w) & 1u)
+                     ? decide_inside<K, MODE>(tg, kx, ky, tl)
+                     : decide_pair<K, DPAD, MODE>(i, j, tg, ra + rw * DPAD, rb + col * DPAD, kx,
+                                                  ky, inst + cell.inst, iplan + cell.inst, band,
+                                                  dtype, tl, sk.near_r);
+        }
+        if (MODE == kBits) deliver_bits(keep, i, j, inst + cell.inst, sk);
+        else if (MODE == kEmit) warp_emit(keep, i, j, w_emit, ecnt, sk);
+        else deliver<MODE>(keep, i, j, sk, tl);
+      }
+    }
+  }
+  if (MODE == kEmit && ecnt) warp_flush(w_emit, ecnt, sk);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  flush_tally<MODE>(tl, st, s_tally);
+}
+
 // Exact set of Sec. I: every pair (i < j) of one instance checked, in 128 x 128 tiles
 // (bi <= bj), with the same FP32 filter and FP64 recheck as the in-cell path.
 constexpr int kBT = 128;
@@ -1261,6 +1560,7 @@ __global__ void __launch_bounds__(kRowSortThreads) k_rowsort_queued(
   extern __shared__ int buf[];  // kRowSmem entries, then the radix counts
   unsigned short* rcnt = reinterpret_cast<unsigned short*>(buf + kRowSmem);  // 16 x blockDim
   __shared__ unsigned int rsbuf[kRowSortThreads / 32];
+  __shared__ int s_lo, s_hi;
   const unsigned int cnt = *long_count;
   for (unsigned int k = blockIdx.x; k < cnt; k += gridDim.x) {
     const unsigned int row = row_queue[n - 1 - k];
@@ -1268,7 +1568,63 @@ __global__ void __launch_bounds__(kRowSortThreads) k_rowsort_queued(
     if (b + len > col_cap) continue;  // uniform across the block: same row for all threads
     long long L = 1;
     while (L < len) L <<= 1;
-    __syncthreads();
+    // Dense rows (columns within a span of at most 64 per entry, as in clustered builds): a
+    // bit per value of the span in shared memory, set and then read back in order, which
+    // costs span / 32 + len steps instead of one radix pass per 4 bits of the columns.
+    {
+      int lo = INT_MAX, hi = -1;
+      for (long long x = threadIdx.x; x < len; x += blockDim.x) {
+        const int v = col[b + x];
+        lo = min(lo, v);
+        hi = max(hi, v);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      __syncthreads();  // the previous row is done with buf, s_lo and s_hi
+      if (threadIdx.x == 0) {
+        s_lo = INT_MAX;
+        s_hi = -1;
+      }
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+      }
+      __syncthreads();
+      lo = s_lo;
+      hi = s_hi;
+      const long long span = (long long)hi - lo + 1;
+      if (span >= 1 && span <= 32LL * kRowSmem && span <= 64 * len) {
+        unsigned int* bm = reinterpret_cast<unsigned int*>(buf);
+        const int words = (int)((span + 31) >> 5);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+        __syncthreads();
+        for (long long x = threadIdx.x; x < len; x += blockDim.x) {
+          const int v = col[b + x] - lo;
+          atomicOr(&bm[v >> 5], 1u << (v & 31));
+        }
+        __syncthreads();
+        // thread t reads a contiguous stretch of words; a block scan of the bit counts gives
+        // each stretch's first output position
+        const int per = (words + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int w0 = min(words, (int)threadIdx.x * per), w1 = min(words, w0 + per);
+        unsigned int c = 0;
+        for (int w = w0; w < w1; ++w) c += (unsigned int)__popc(bm[w]);
+        unsigned int total;
+        long long pos = b + block_excl_scan_any(c, &total, rsbuf);
+        for (int w = w0; w < w1; ++w) {
+          unsigned int word = bm[w];
+          while (word) {
+            const int bit = __ffs(word) - 1;
+            word &= word - 1;
+            col[pos++] = lo + w * 32 + bit;
+          }
+        }
+        continue;
+      }
+    }
     if (len <= kRowSmem / 2) {  // both buffers in shared memory
       for (long long x = threadIdx.x; x < len; x += blockDim.x) buf[x] = col[b + x];
       __syncthreads();
@@ -1354,6 +1710,28 @@ void brute_impl(const BuildArgs& a, cudaStream_t s) {
                                                       make_sink(a));
 }
 
+// The dense-cell jobs on the tensor cores (FP16 or BF16 halves), 4 blocks of 128 threads per
+// SM (128 TMEM columns each).
+template <typename K, int DPAD, int MODE>
+void large_tc_launch(const BuildArgs& a, const uint32_t* sv, cudaStream_t s) {
+  using SM = LargeTcSmem<K, DPAD>;
+  const bool bf16 = a.tc_cells == 2;
+  auto kern = bf16 ? k_pairs_large_tc<K, DPAD, MODE, true> : k_pairs_large_tc<K, DPAD, MODE, false>;
+  static bool attr[64][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(launch_attr_mutex());
+    if (dev < 0 || dev >= 64 || !attr[dev][bf16]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::kBytes);
+      if (dev >= 0 && dev < 64) attr[dev][bf16] = true;
+    }
+  }
+  kern<<<(unsigned)(4 * a.num_sms), 128, SM::kBytes, s>>>(
+      sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
+      a.large_job_off, make_sink(a), spin_limit_of(a.spin_limit) * 16u, a.inject);
+}
+
 template <typename K, int DPAD, int MODE>
 void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   const long long N = a.n_total * a.m;
@@ -1420,6 +1798,12 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
         make_sink(a));
   }
   if (MODE != kWrite) k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
+  if constexpr (MODE != kBits) {
+    if (a.tc_cells) {
+      large_tc_launch<K, DPAD, MODE>(a, sv, s);
+      return;
+    }
+  }
   k_pairs_large<K, DPAD, MODE><<<(unsigned)(4 * a.num_sms), kPairThreads, 0, s>>>(
       sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
       a.large_job_off, make_sink(a));

@@ -19,6 +19,7 @@
 #include <cfloat>
 
 #include "rtg_internal.cuh"
+#include "rtg_tc.cuh"
 
 namespace rtg {
 
@@ -31,38 +32,6 @@ constexpr int kTcThreads = 128;
 // MMA completion waits: the context's spin limit times this (a commit takes far longer than
 // one look-back step)
 constexpr unsigned int kTcWaitScale = 16;
-
-__host__ __device__ __forceinline__ int tile_off(int m, int k) {
-  return (m / 8) * 512 + (k / 8) * 128 + (m % 8) * 16 + (k % 8) * 2;
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;  // next core matrix along K
-  d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;  // next 8 rows
-  d |= (uint64_t)1 << 46;                       // descriptor version; no swizzle
-  return d;
-}
-
-// Bounded wait for the completion of phase `parity` of the mbarrier at shared address bar;
-// false when the limit ran out first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int limit) {
-  for (unsigned int it = 0; it < limit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity));
-    if (ok) return true;
-  }
-  return false;
-}
 
 __device__ __forceinline__ double load_coord(const void* pts, int dtype, long long i, int d,
                                              int l) {
@@ -89,13 +58,7 @@ __global__ void k_tc_plan(const Inst* __restrict__ inst, const unsigned long lon
   //   FP32 accumulation of 48 terms 2 * 48 * 2^-24 * 2 d M^2, times 4 for an unknown order
   //   norms (two sums of d squares) 2 d 2^-24 d M^2
   //   epilogue (two roundings)      3 2^-24 (4 d M^2)
-  const double u16 = bf16 ? 0x1.0p-8 : 0x1.0p-11;
-  const double u32 = 0x1.0p-24;
-  const double dd = (double)d, M2 = M * M;
-  const double E = 8.0 * sqrt(dd) * u32 * M * 2.0 * sqrt(dd) * M +
-                   2.0 * (2.0 * dd * M2 * (2.0 * u16 * u16 + 0x1.0p-22) + 2.0 * dd * 0x1.0p-25 * M) +
-                   4.0 * 2.0 * 48.0 * u32 * 2.0 * dd * M2 + 2.0 * dd * u32 * dd * M2 +
-                   3.0 * u32 * 4.0 * dd * M2;
+  const double E = tc_error_bound(M, d, bf16 != 0);
   const double rr = iplan[0].rr;
   const double band = fmax(1e-3 * rr, 1.25 * E);
   tp->band = band;
@@ -144,19 +107,6 @@ struct TcSink {
   unsigned long long* emitted;
   int symmetric;
 };
-
-__device__ __forceinline__ void tc_ld32(uint32_t addr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
-}
 
 __device__ __noinline__ double exact_dist2(const void* pts, int dtype, long long i, long long j,
                                            int d) {

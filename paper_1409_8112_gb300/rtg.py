@@ -463,7 +463,10 @@ class Context:
 
     def all_pairs(self, points, r: float, transforms: np.ndarray, cell_side: float,
                   symmetric: bool = False, timing: bool = False, two_pass: bool = False,
-                  bitset: bool = False) -> Result:
+                  bitset: bool = False, tensor: str | None = None) -> Result:
+        """Alg. 1 over the grids of `transforms`; tensor = "fp16" or "bf16" takes the
+        distances of cells of more than 256 points from tensor-core tiles (a filter; the
+        reported set is the same)."""
         ptr, code, on_dev, n, d, keep = _points_arg(points)
         self._after_producer(keep)
         T = np.ascontiguousarray(transforms, dtype=np.float64).reshape(-1)
@@ -472,6 +475,12 @@ class Context:
         m = T.size // (d * d + d)
         flags = ((RTG_FLAG_SYMMETRIC if symmetric else 0) | (RTG_FLAG_TIMING if timing else 0) |
                  (RTG_FLAG_TWO_PASS if two_pass else 0) | (RTG_FLAG_BITSET if bitset else 0))
+        if tensor == "fp16":
+            flags |= RTG_FLAG_TC_FP16
+        elif tensor == "bf16":
+            flags |= RTG_FLAG_TC_BF16
+        elif tensor is not None:
+            raise ValueError("tensor must be 'fp16', 'bf16' or None")
         csr = rtg_all_pairs(self.handle, ptr, code, on_dev, n, d, float(r), T, m,
                             float(cell_side), flags)
         del keep

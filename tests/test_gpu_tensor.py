@@ -42,3 +42,25 @@ def test_tc_offset_coordinates(ctx):
         rp, col = res.download()
         ex = oracle.brute(pts, r)
         assert np.array_equal(rp, ex.row_ptr) and np.array_equal(col, ex.col)
+
+
+@pytest.mark.parametrize("tensor", ["fp16", "bf16"])
+@pytest.mark.parametrize("sigma,n,d,dtype", [(0.01, 6000, 3, np.float32),
+                                             (0.02, 8000, 6, np.float64),
+                                             (0.05, 9000, 6, np.float32),
+                                             (0.05, 5000, 12, np.float32)])
+def test_dense_cells_on_tensor_cores_match_oracle(ctx, tensor, sigma, n, d, dtype):
+    # clustered points (8 Gaussians): cells of hundreds to thousands of points, whose pairs go
+    # through the tensor-core tiles; the set must equal the oracle's and the build without
+    # the tiles, candidate counts included
+    pts = gen.points_mixture(70 + d, n, d, k=8, sigma=sigma, dtype=dtype)
+    r = gen.radius_for_degree(n, d, 6.0)
+    T = gen.transforms(70 + d, d, 4, r)
+    res = ctx.all_pairs(pts, r, T, r, tensor=tensor)
+    rp, col = res.download()
+    st = res.stats
+    res.release()
+    ref = oracle.rtg(pts, r, T, r)
+    assert np.array_equal(rp, ref.csr.row_ptr) and np.array_equal(col, ref.csr.col)
+    assert st["candidates"] == [s["candidates"] for s in ref.stats]
+    assert st["large_cells"] > 0 and st["max_cell"] > 256

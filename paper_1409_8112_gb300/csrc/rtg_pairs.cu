@@ -64,25 +64,6 @@ __device__ __forceinline__ double exact_dist2(const void* pts, int dtype, long l
   return s;
 }
 
-// Asynchronous global -> shared copies (cp.async): a thread issues all of its copies and waits
-// once, so the gathers of a position's row and key row are in flight together.
-__device__ __forceinline__ uint32_t smem_u32addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32addr(dst)), "l"(src)
-               : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32addr(dst)), "l"(src),
-               "n"(BYTES)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 // Exclusive scan of one value per thread over the block (a multiple of 32 threads, at most
 // 1024); sbuf holds one word per warp.
 __device__ __forceinline__ unsigned int block_excl_scan_any(unsigned int v, unsigned int* total,

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <type_traits>
 
 #include "rtg_internal.cuh"
 #include "rtg_tc.cuh"
@@ -41,7 +42,8 @@ __device__ __forceinline__ double load_coord(const void* pts, int dtype, long lo
 
 // Band, thresholds and centre for instance 0 (one thread).
 __global__ void k_tc_plan(const Inst* __restrict__ inst, const unsigned long long* bbox,
-                          const InstPlan* __restrict__ iplan, TcPlan* tp, Status* st, int bf16) {
+                          const InstPlan* __restrict__ iplan, TcPlan* tp, Status* st, int bf16,
+                          int fold) {
   const Inst I = inst[0];
   const int d = I.d;
   double M = 0.0;
@@ -58,7 +60,7 @@ __global__ void k_tc_plan(const Inst* __restrict__ inst, const unsigned long lon
   //   FP32 accumulation of 48 terms 2 * 48 * 2^-24 * 2 d M^2, times 4 for an unknown order
   //   norms (two sums of d squares) 2 d 2^-24 d M^2
   //   epilogue (two roundings)      3 2^-24 (4 d M^2)
-  const double E = tc_error_bound(M, d, bf16 != 0);
+  const double E = fold ? tc_error_bound_folded(M, d, bf16 != 0) : tc_error_bound(M, d, bf16 != 0);
   const double rr = iplan[0].rr;
   const double band = fmax(1e-3 * rr, 1.25 * E);
   tp->band = band;
@@ -68,16 +70,28 @@ __global__ void k_tc_plan(const Inst* __restrict__ inst, const unsigned long lon
   tp->hi = __double2float_ru(rr + band);
 }
 
-// Half-precision hi/lo rows in the tile layout, and FP32 norms of the centred points.
-template <bool BF16>
+// Half-precision hi/lo rows in the tile layout, and FP32 norms of the centred points.  FOLD
+// (d <= 12): the tiles come in two versions, the A operand's ([-2 x, |x|^2 hi, |x|^2 lo, 1, 1]
+// in the hi block) and the B operand's ([x, 1, 1, |y|^2 hi, |y|^2 lo]), so that the MMAs
+// accumulate |x|^2 + |y|^2 - 2 x.y; the norms array is then not read.
+template <bool BF16, bool FOLD>
 __global__ void __launch_bounds__(256) k_tc_prep(const Inst* __restrict__ inst, int dtype,
                                                  const TcPlan* __restrict__ tp,
                                                  unsigned char* __restrict__ tiles,
                                                  float* __restrict__ norms, long long n_pad) {
+  using H = typename std::conditional<BF16, __nv_bfloat16, __half>::type;
+  auto to_h = [](float v) -> H {
+    if constexpr (BF16) return __float2bfloat16_rn(v); else return __float2half_rn(v);
+  };
+  auto to_f = [](H v) -> float {
+    if constexpr (BF16) return __bfloat162float(v); else return __half2float(v);
+  };
   const Inst I = inst[0];
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
+  const long long ntile = n_pad / kTcRows;
   unsigned char* tile = tiles + (i / kTcRows) * (long long)kTcTileBytes;
+  unsigned char* tileB = FOLD ? tile + ntile * (long long)kTcTileBytes : tile;
   const int m = (int)(i % kTcRows);
   float nrm = 0.0f;
   for (int k = 0; k < 16; ++k) {
@@ -85,17 +99,27 @@ __global__ void __launch_bounds__(256) k_tc_prep(const Inst* __restrict__ inst, 
     if (i < I.n && k < I.d)
       xc = __double2float_rn(__dsub_rn(load_coord(I.pts, dtype, i, I.d, k), tp->center[k]));
     nrm = fmaf(xc, xc, nrm);
-    if (BF16) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(xc);
-      const __nv_bfloat16 l = __float2bfloat16_rn(xc - __bfloat162float(h));
-      *reinterpret_cast<__nv_bfloat16*>(tile + tile_off(m, k)) = h;
-      *reinterpret_cast<__nv_bfloat16*>(tile + tile_off(m, 16 + k)) = l;
-    } else {
-      const __half h = __float2half_rn(xc);
-      const __half l = __float2half_rn(xc - __half2float(h));
-      *reinterpret_cast<__half*>(tile + tile_off(m, k)) = h;
-      *reinterpret_cast<__half*>(tile + tile_off(m, 16 + k)) = l;
+    const H h = to_h(xc);
+    const H l = to_h(xc - to_f(h));
+    // A version: -2 x (exact scaling by a power of two)
+    *reinterpret_cast<H*>(tile + tile_off(m, k)) = FOLD ? to_h(-2.0f * to_f(h)) : h;
+    *reinterpret_cast<H*>(tile + tile_off(m, 16 + k)) = FOLD ? to_h(-2.0f * to_f(l)) : l;
+    if (FOLD) {
+      *reinterpret_cast<H*>(tileB + tile_off(m, k)) = h;
+      *reinterpret_cast<H*>(tileB + tile_off(m, 16 + k)) = l;
     }
+  }
+  if (FOLD) {
+    const int d = I.d;  // slots d .. d + 3 of the hi block are free (d <= 12)
+    const H nh = to_h(nrm), nl = to_h(nrm - to_f(nh)), one = to_h(1.0f);
+    *reinterpret_cast<H*>(tile + tile_off(m, d)) = nh;
+    *reinterpret_cast<H*>(tile + tile_off(m, d + 1)) = nl;
+    *reinterpret_cast<H*>(tile + tile_off(m, d + 2)) = one;
+    *reinterpret_cast<H*>(tile + tile_off(m, d + 3)) = one;
+    *reinterpret_cast<H*>(tileB + tile_off(m, d)) = one;
+    *reinterpret_cast<H*>(tileB + tile_off(m, d + 1)) = one;
+    *reinterpret_cast<H*>(tileB + tile_off(m, d + 2)) = nh;
+    *reinterpret_cast<H*>(tileB + tile_off(m, d + 3)) = nl;
   }
   norms[i] = nrm;
 }
@@ -141,19 +165,49 @@ __device__ __noinline__ void tc_candidate(float d2, long long gi, long long gj, 
   if (sk.symmetric) atomicAdd(&sk.row_cnt[j], 1u);
 }
 
+// Candidates queued per warp before their exact check.  A chunk with more candidates than this
+// (dense inputs: up to 32 x 32) is decided by its lanes directly.
+constexpr int kTcQueue = 256 + 32;
+
+// Decides the qn queued candidates of a warp, 32 at a time (one per lane).  Called by all lanes.
+__device__ __forceinline__ void tc_drain(const unsigned int* q_i, const unsigned int* q_j,
+                                         const float* q_d, unsigned int qn, int lane,
+                                         const Inst& I, const InstPlan& IP, int dtype,
+                                         float lo_thr, const TcSink& sk, bool emit,
+                                         unsigned int& pairs, unsigned int& rechecks,
+                                         unsigned int& near_r, float& max_err, bool& overflow) {
+  __syncwarp();
+  for (unsigned int b = 0; b < qn; b += 32) {
+    const unsigned int e = b + lane;
+    if (e < qn)
+      tc_candidate(q_d[e], (long long)q_i[e], (long long)q_j[e], I, IP, dtype, lo_thr, sk, emit,
+                   pairs, rechecks, near_r, max_err, overflow);
+  }
+  __syncwarp();
+}
+
 // Persistent: each CTA walks a contiguous range of tile pairs (bi <= bj) in bi-major order,
 // so the A tile is reloaded only when bi changes.
-template <bool BF16, bool EMIT>
+template <bool BF16, bool EMIT, bool FOLD>
 __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
     const unsigned char* __restrict__ tiles, const float* __restrict__ norms,
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const TcPlan* __restrict__ tp, int dtype, Status* st, TcSink sk, long long nt,
     unsigned int wait_limit, unsigned int inject) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sa = smem;                       // 8 KB
-  unsigned char* sb = smem + kTcTileBytes;        // 8 KB
-  float* na = reinterpret_cast<float*>(smem + 2 * kTcTileBytes);  // 128
-  float* nb = na + kTcRows;                                         // 128
+  // double-buffered operand tiles and norms: the next job's are copied in while this job's
+  // MMAs and epilogue run
+  unsigned char* sa2 = smem;                                         // 2 x 8 KB
+  unsigned char* sb2 = smem + 2 * kTcTileBytes;                      // 2 x 8 KB
+  float* na2 = reinterpret_cast<float*>(smem + 4 * kTcTileBytes);   // 2 x 128
+  float* nb2 = na2 + 2 * kTcRows;                                    // 2 x 128
+  const float* nb = nullptr;  // this job's column norms
+  // per warp: the candidate queue (rows, columns, tile d^2), after the norms
+  unsigned int* q_i = reinterpret_cast<unsigned int*>(nb2 + 2 * kTcRows) +
+                      (size_t)(threadIdx.x >> 5) * 3 * kTcQueue;
+  unsigned int* q_j = q_i + kTcQueue;
+  float* q_d = reinterpret_cast<float*>(q_j + kTcQueue);
+  unsigned int qn = 0;  // entries queued (warp-uniform)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ __align__(8) uint64_t mbar_idle;  // test hook: a barrier nothing arrives on
   __shared__ uint32_t tmem_base;
@@ -198,29 +252,48 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
     bi = lo;
     bj = bi + (j0 - (bi * nt - bi * (bi - 1) / 2));
   }
-  long long loaded_a = -1;
   uint32_t phase = 0;
   bool timed_out = false;
   unsigned int tl_pairs = 0, tl_rechecks = 0, tl_near = 0;
   bool overflow = false;
   float max_err = 0.0f;
+  // asynchronous copy of tile t and its norms into buffer `buf` of a side (16-byte copies)
+  // (FOLD: the B operand's tiles follow the A operand's, and the norms are in the tiles)
+  const unsigned char* tilesB = FOLD ? tiles + nt * (long long)kTcTileBytes : tiles;
+  auto stage = [&](const unsigned char* src, unsigned char* side, float* nside, long long t,
+                   int buf) {
+    const unsigned char* g = src + t * (long long)kTcTileBytes;
+    unsigned char* dst = side + buf * kTcTileBytes;
+    for (int x = tid; x < kTcTileBytes / 16; x += kTcThreads) cp_async16(dst + 16 * x, g + 16 * x);
+    if (!FOLD) cp_async_small<4>(nside + buf * kTcRows + tid, norms + t * kTcRows + tid);
+  };
+  int abuf = 0, bbuf = 0;
+  if (j0 < j1) {
+    stage(tiles, sa2, na2, bi, 0);
+    stage(tilesB, sb2, nb2, bj, 0);
+  }
   for (long long job = j0; job < j1 && !timed_out; ++job) {
-    // stage the operand tiles (16-byte copies) and norms
-    const uint4* gb = reinterpret_cast<const uint4*>(tiles + bj * (long long)kTcTileBytes);
-    for (int x = tid; x < kTcTileBytes / 16; x += kTcThreads)
-      reinterpret_cast<uint4*>(sb)[x] = __ldg(gb + x);
-    nb[tid] = __ldg(norms + bj * kTcRows + tid);
-    if (bi != loaded_a) {
-      const uint4* ga = reinterpret_cast<const uint4*>(tiles + bi * (long long)kTcTileBytes);
-      for (int x = tid; x < kTcTileBytes / 16; x += kTcThreads)
-        reinterpret_cast<uint4*>(sa)[x] = __ldg(ga + x);
-      na[tid] = __ldg(norms + bi * kTcRows + tid);
-      loaded_a = bi;
-    }
+    cp_async_wait_all();  // this job's tiles (copied during the previous job) have landed
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    unsigned char* sa = sa2 + abuf * kTcTileBytes;
+    unsigned char* sb = sb2 + bbuf * kTcTileBytes;
+    const float* na = na2 + abuf * kTcRows;
+    nb = nb2 + bbuf * kTcRows;
+    // the next job's tiles go to the other buffers while this job runs
+    long long ni = bi, nj = bj + 1;
+    if (nj == nt) {
+      ++ni;
+      nj = ni;
+    }
+    const bool more = job + 1 < j1;
+    const bool new_a = ni != bi;
+    if (more) {
+      if (new_a) stage(tiles, sa2, na2, ni, abuf ^ 1);
+      stage(tilesB, sb2, nb2, nj, bbuf ^ 1);
+    }
     if (tid == 0) {
       // hi.hi + hi.lo + lo.hi: A parts (0, 0, 1), B parts (0, 1, 0); 256 bytes per part
       const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
@@ -273,25 +346,66 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
       uint32_t hits = 0;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        d2v[q] = (nrow + nb[c + q]) - 2.0f * __uint_as_float(r[q]);
+        d2v[q] = FOLD ? __uint_as_float(r[q])
+                      : (nrow + nb[c + q]) - 2.0f * __uint_as_float(r[q]);
         hits |= (d2v[q] > hi_thr ? 0u : 1u) << q;  // NaN (overflowed tiles) goes to FP64
       }
       hits &= valid;
-      if (hits) {
+      // queue this chunk's candidates (the warp's shared-memory queue, kept across jobs) and
+      // decide them 32 at a time, one per lane, so that the FP64 checks and their global
+      // loads run in parallel instead of one lane at a time
+      const unsigned int nh = (unsigned int)__popc(hits);
+      unsigned int incl = nh;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total > (unsigned int)kTcQueue) {
 #pragma unroll
         for (int q = 0; q < 32; ++q)
           if (hits & (1u << q))
             tc_candidate(d2v[q], gi, colbase + q, I, IP, dtype, lo_thr, sk, EMIT, tl_pairs,
                          tl_rechecks, tl_near, max_err, overflow);
+      } else if (total) {
+        if (qn + total > (unsigned int)kTcQueue) {  // room for the chunk: decide the queue first
+          tc_drain(q_i, q_j, q_d, qn, lane, I, IP, dtype, lo_thr, sk, EMIT, tl_pairs,
+                   tl_rechecks, tl_near, max_err, overflow);
+          qn = 0;
+        }
+        unsigned int pos = qn + incl - nh;
+        if (hits) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (hits & (1u << q)) {
+              q_i[pos] = (unsigned int)gi;
+              q_j[pos] = (unsigned int)(colbase + q);
+              q_d[pos] = d2v[q];
+              ++pos;
+            }
+        }
+        qn += total;
+        __syncwarp();
+        while (qn >= 32) {  // the newest 32 entries, one per lane
+          const unsigned int e = qn - 32 + lane;
+          tc_candidate(q_d[e], (long long)q_i[e], (long long)q_j[e], I, IP, dtype, lo_thr, sk,
+                       EMIT, tl_pairs, tl_rechecks, tl_near, max_err, overflow);
+          qn -= 32;
+          __syncwarp();
+        }
       }
-    }
+            }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // TMEM and shared tiles are reused by the next job
-    if (++bj == nt) {
-      ++bi;
-      bj = bi;
-    }
+    // (the barrier at the top of the next job separates this epilogue from its MMAs)
+    bi = ni;
+    bj = nj;
+    if (new_a) abuf ^= 1;
+    bbuf ^= 1;
   }
+  cp_async_wait_all();  // no copy of this block is left in flight
+  if (qn)  // the candidates still queued
+    tc_drain(q_i, q_j, q_d, qn, lane, I, IP, dtype, lo_thr, sk, EMIT, tl_pairs, tl_rechecks,
+             tl_near, max_err, overflow);
   // tallies
   for (int o = 16; o > 0; o >>= 1) {
     tl_pairs += __shfl_xor_sync(0xffffffffu, tl_pairs, o);
@@ -320,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads) k_brute_tc(
 
 size_t tc_tiles_bytes(long long n) {
   const long long nt = (n + kTcRows - 1) / kTcRows;
-  return (size_t)nt * kTcTileBytes;
+  return 2 * (size_t)nt * kTcTileBytes;  // A and B versions (norms folded into the MMA)
 }
 
 int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* tiles, float* norms,
@@ -328,34 +442,46 @@ int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* til
   const long long n = a.n_total;
   const long long nt = (n + kTcRows - 1) / kTcRows;
   const long long n_pad = nt * kTcRows;
-  k_tc_plan<<<1, 1, 0, s>>>(a.inst, a.bbox, a.iplan, tp, a.st, bf16 ? 1 : 0);
-  if (bf16)
-    k_tc_prep<true><<<(unsigned)((n_pad + 255) / 256), 256, 0, s>>>(a.inst, a.dtype, tp, tiles,
-                                                                    norms, n_pad);
+  // the norms ride in the MMA when 4 slots of the K = 16 hi block are free (d <= 12)
+  const bool fold = a.dpad <= 16 && a.d_common >= 1 && a.d_common <= 12;
+  k_tc_plan<<<1, 1, 0, s>>>(a.inst, a.bbox, a.iplan, tp, a.st, bf16 ? 1 : 0, fold ? 1 : 0);
+  const unsigned pblocks = (unsigned)((n_pad + 255) / 256);
+  if (bf16 && fold)
+    k_tc_prep<true, true><<<pblocks, 256, 0, s>>>(a.inst, a.dtype, tp, tiles, norms, n_pad);
+  else if (bf16)
+    k_tc_prep<true, false><<<pblocks, 256, 0, s>>>(a.inst, a.dtype, tp, tiles, norms, n_pad);
+  else if (fold)
+    k_tc_prep<false, true><<<pblocks, 256, 0, s>>>(a.inst, a.dtype, tp, tiles, norms, n_pad);
   else
-    k_tc_prep<false><<<(unsigned)((n_pad + 255) / 256), 256, 0, s>>>(a.inst, a.dtype, tp, tiles,
-                                                                     norms, n_pad);
+    k_tc_prep<false, false><<<pblocks, 256, 0, s>>>(a.inst, a.dtype, tp, tiles, norms, n_pad);
   TcSink sk{a.row_cnt, a.pair_buf, a.pair_cap, &a.st->emitted, a.symmetric};
   // 4 CTAs per SM at most: 128 TMEM columns each fill the 512 columns of an SM.  The dynamic
-  // shared memory (two tiles, norms, padding to 50 KB) enforces that occupancy.
+  // shared memory (two tiles, norms, the warps' candidate queues, padding to 50 KB) enforces
+  // that occupancy.
   const size_t smem = 50 * 1024;
   const long long jobs = nt * (nt + 1) / 2;
   const unsigned grid = (unsigned)(jobs < 4LL * a.num_sms ? jobs : 4LL * a.num_sms);
   const bool emit = mode == kEmit;
-#define RTG_TC_LAUNCH(B, E)                                                                    \
+#define RTG_TC_LAUNCH1(B, E, F)                                                                \
   do {                                                                                         \
     static size_t attr[64] = {};                                                               \
     int dev = 0;                                                                               \
     cudaGetDevice(&dev);                                                                       \
     if (dev < 0 || dev >= 64 || attr[dev] < smem) {                                            \
-      cudaFuncSetAttribute(k_brute_tc<B, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+      cudaFuncSetAttribute(k_brute_tc<B, E, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                            (int)smem);                                                         \
       if (dev >= 0 && dev < 64) attr[dev] = smem;                                              \
     }                                                                                          \
-    k_brute_tc<B, E><<<grid, kTcThreads, smem, s>>>(tiles, norms, a.inst, a.iplan, tp, a.dtype, \
+    k_brute_tc<B, E, F><<<grid, kTcThreads, smem, s>>>(tiles, norms, a.inst, a.iplan, tp,       \
+                                                       a.dtype,                                \
                                                     a.st, sk, nt,                              \
                                                     spin_limit_of(a.spin_limit) * kTcWaitScale, \
                                                     a.inject);                                 \
+  } while (0)
+#define RTG_TC_LAUNCH(B, E)             \
+  do {                                   \
+    if (fold) RTG_TC_LAUNCH1(B, E, true); \
+    else RTG_TC_LAUNCH1(B, E, false);     \
   } while (0)
   if (grid > 0) {
     if (bf16 && emit) RTG_TC_LAUNCH(true, true);
@@ -364,6 +490,7 @@ int launch_brute_tc(const BuildArgs& a, bool bf16, Mode mode, unsigned char* til
     else RTG_TC_LAUNCH(false, false);
   }
 #undef RTG_TC_LAUNCH
+#undef RTG_TC_LAUNCH1
   return grid > 0 ? 3 : 2;
 }
 

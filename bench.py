@@ -232,7 +232,7 @@ def measure_build(ctx, stream, flush, args, pts, T, r, dtype_name, ws, rank, clo
                 out_ph.append(st["phase_us"])
             info = {"pairs": res.nnz, "launches": st["launches"], "key_bits": st["key_bits"],
                     "passes": st["sort_passes"], "sort": st["sort"],
-                    "phase_bytes": st["phase_bytes"]}
+                    "phase_bytes": st["phase_bytes"], "enumeration": st["enumeration"]}
             res.release()
         return out_ms, out_ph, info
 
@@ -304,7 +304,7 @@ def measure_build(ctx, stream, flush, args, pts, T, r, dtype_name, ws, rank, clo
         "wall_s_timed_region": round(wall_s, 3),
         "phase_us": {p: round(v, 2) for p, v in mean_phase.items()},
         "phase_bytes_model": info["phase_bytes"],
-        "sort": sort_cfg, "roofline": roofline,
+        "sort": sort_cfg, "enumeration": info["enumeration"], "roofline": roofline,
         "e2e": {"value": round(e2e_value, 1), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(float(np.mean(e2e_ms)), 4)},
         "clocks": clk, "gpu_launches": launches * args.steps,
@@ -335,8 +335,8 @@ def run_ours(args):
         "dtype": "f32+f64", "data": "synthetic", "config": WORKLOAD,
     }
     for k in ("builds_per_s", "pairs_per_build", "exact_pairs", "recall", "p50_ms", "p99_ms",
-              "wall_s_timed_region", "phase_us", "sort", "roofline", "e2e", "clocks",
-              "gpu_launches"):
+              "wall_s_timed_region", "phase_us", "sort", "enumeration", "roofline", "e2e",
+              "clocks", "gpu_launches"):
         line[k] = rec[k]
     line["phase_note"] = ("device phases from CUDA events on the library's stream, in a second "
                           "pass of the same steps (phase events add about 30 us a build, so the "
@@ -354,7 +354,8 @@ def run_ours(args):
             "metric": METRIC, "unit": "pairs/s", "dtype": "f32+f64", "steps": args.steps,
             **{k: c3[k] for k in ("value", "ms_per_step", "builds_per_s", "pairs_per_build",
                                   "exact_pairs", "recall", "p50_ms", "p99_ms", "phase_us",
-                                  "sort", "roofline", "e2e", "clocks", "gpu_launches")},
+                                  "sort", "enumeration", "roofline", "e2e", "clocks",
+                                  "gpu_launches")},
         }
         line["gpu_launches"] += c3["gpu_launches"]
     if rank == 0 and not args.no_cpu_baseline:
@@ -505,6 +506,7 @@ def run_batch(args):
         "speedup_vs_one_build_per_roadmap": round(sms / ms, 3),
         "phase_us": {k2: round(v, 1) for k2, v in st["phase_us"].items()},
         "key_bits": st["key_bits"], "sort_passes": st["sort_passes"], "sort": st["sort"],
+        "enumeration": st["enumeration"],
         "gpu_launches": st["launches"] * args.steps,
     }
     ctx.close()
@@ -541,6 +543,9 @@ def serve_trace(count, rate, nmax, seed=7):
 
 
 def run_serve(args):
+    """The request server on a Poisson trace (continuous batching over lanes, budget
+    admission), then the same trace one build per request through rtg_all_pairs (no batching,
+    no overlap): the same pair sets, so the same recall, and pairs/s for both."""
     import torch
     from paper_1409_8112_gb300 import rtg
     torch.cuda.set_device(0)
@@ -558,8 +563,8 @@ def run_serve(args):
         if t0 > now:
             time.sleep(t0 - now)
         tickets.append(ctx.submit(pts, r, T, r))
-    lat, pairs, rejected = [], 0, 0
-    for tk in tickets:
+    lat, pairs, rejected, served_idx, slack = [], 0, 0, [], []
+    for k, tk in enumerate(tickets):
         try:
             res = ctx.wait(tk, m=8)
         except rtg.RTGError as e:
@@ -567,10 +572,35 @@ def run_serve(args):
                 rejected += 1
                 continue
             raise
-        lat.append(res.stats["phase_us"]["total"] / 1e3)
+        st = res.stats
+        lat.append(st["phase_us"]["total"] / 1e3)
         pairs += res.nnz
+        served_idx.append(k)
+        if st["mem_estimate"] > 0:
+            slack.append(st["mem_peak"] / st["mem_estimate"])
         res.release()
     makespan = time.perf_counter() - start
+    # the same trace one request at a time, each a plain synchronous build (host points in),
+    # the requests the budget refuses included (they fail there too)
+    plain_ctx = rtg.Context(0, mem_budget_bytes=budget)
+    for k in served_idx[:4]:
+        _, pts, r, T = trace[k]
+        plain_ctx.all_pairs(pts, r, T, r).release()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_pairs, plain_refused = 0, 0
+    for _, pts, r, T in trace:
+        try:
+            res = plain_ctx.all_pairs(pts, r, T, r)
+        except rtg.RTGError as e:
+            if e.status == rtg.RTG_E_BUDGET:
+                plain_refused += 1
+                continue
+            raise
+        plain_pairs += res.nnz
+        res.release()
+    plain_s = time.perf_counter() - t0
+    plain_ctx.close()
     line = {
         "metric": METRIC, "value": round(pairs / makespan, 1), "unit": "pairs/s", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
@@ -582,6 +612,20 @@ def run_serve(args):
         "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat else None,
         "builds_per_s": round(len(lat) / makespan, 2), "makespan_s": round(makespan, 3),
         "pairs": pairs,
+        "one_build_per_request": {
+            "pairs_per_s": round(plain_pairs / plain_s, 1), "pairs": plain_pairs,
+            "refused_budget": plain_refused,
+            "builds_per_s": round((len(trace) - plain_refused) / plain_s, 2),
+            "seconds": round(plain_s, 3),
+            "note": "the whole trace back to back (no arrival times), one synchronous "
+                    "rtg_all_pairs each, host points in; every build is exact, so the recall "
+                    "of each request is the same as served"},
+        "served_vs_one_by_one": round((pairs / makespan) / (plain_pairs / plain_s), 3),
+        "admission_slack": {
+            "peak_over_estimate_median": round(float(np.median(slack)), 3) if slack else None,
+            "peak_over_estimate_max": round(float(np.max(slack)), 3) if slack else None,
+            "note": "device bytes a batch needed (the workspace its build asked for and its "
+                    "block CSR) over the batch's admission estimate"},
     }
     ctx.close()
     print(json.dumps(line), flush=True)

@@ -115,6 +115,14 @@ typedef struct {
                              the emitted pairs, row counts and the CSR.  Cache hits and
                              re-reads are not counted */
   int64_t bytes_moved;    /* = phase_bytes[7] */
+  int32_t pairs_spans_per_warp; /* in-cell enumeration: sorted-position spans per resident
+                                   warp (autotuned per shape) */
+  int32_t dense_cell_min;       /* cells of more points than this take the tiled kernels
+                                   (autotuned per shape: 64, 128 or 256) */
+  int32_t pairs_tuned;          /* 1 when the two above were measured on this device */
+  int64_t mem_estimate;         /* served results: the admission estimate of their batch */
+  int64_t mem_peak;             /* served results: device bytes their batch needed (the
+                                   workspace its build asked for and its block CSR) */
 } rtg_stats;
 
 typedef struct {

@@ -76,6 +76,7 @@ bool injected_alloc_failure(rtg_ctx* c) {
 rtg_status ensure(rtg_ctx* c, DevBuf& b, size_t bytes, bool zero) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
+  c->ws_need += bytes;
   if (b.cap >= bytes) return RTG_OK;
   if (c->budget && total_held(c) - b.cap + bytes > c->budget)
     return fail(c, RTG_E_BUDGET, "workspace of " + std::to_string(bytes) +
@@ -268,6 +269,7 @@ rtg_status graph_for(rtg_ctx* c, const ShapeKey& key, const rtg::BuildArgs& a, b
 
 rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   cudaStream_t st = c->stream;
+  c->ws_need = 0;
   const bool timing = (q.flags & RTG_FLAG_TIMING) != 0;
   const int sym = (q.flags & RTG_FLAG_SYMMETRIC) ? 1 : 0;
   const int B = q.count, m = q.m;
@@ -452,7 +454,11 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         g.sort = it->second.cfg;
         g.sorted_cfg = true;
       } else if (c->autotune && N >= kTuneMinElements) {
-        tune_now = true;
+        // measured on the second build of a shape (a repeated shape pays for the trials; a
+        // stream of distinct shapes, as in serving, is never held up by them); the first
+        // build takes the default and leaves the choice open
+        if (known) tune_now = true;
+        else g.sort = sort_default(N, c->num_sms);
       } else {
         g.sort = sort_default(N, c->num_sms);
         g.sorted_cfg = true;
@@ -466,7 +472,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     // pair enumeration: one static span per warp for light cells (fewest span set-ups); more,
     // smaller spans claimed dynamically when the shape's cells held many candidates, so that
     // warps with heavy spans do not trail
-    a.spans_per_warp = g.cand_per_pos < 0.0f ? 2 : (g.cand_per_pos >= 3.0f ? 4 : 1);
+    a.spans_per_warp = g.pairs_tuned ? g.spans_per_warp
+                                     : (g.cand_per_pos < 0.0f ? 2 : (g.cand_per_pos >= 3.0f ? 4 : 1));
+    a.dense_min = g.pairs_tuned ? g.dense_min : 0;
     if (m > 0) {
       const size_t ksz = a.key64 ? 8 : 4;
       if ((s = ensure(c, c->key_mat, (size_t)N * ksz)) != RTG_OK) return s;
@@ -501,6 +509,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         if ((s = tune_sort(c, a, N, g.key_bits, &best)) != RTG_OK) return s;
         g.sort = best;
         g.sorted_cfg = true;
+        // and the enumeration knobs, on the keys sorted with that variant
+        if ((s = tune_pairs(c, a, best, g.key_bits, &g.spans_per_warp, &g.dense_min)) != RTG_OK)
+          return s;
+        g.pairs_tuned = true;
         tuned_now = true;
         continue;
       }
@@ -801,6 +813,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     }
     S.launches = launches;
     S.attempts = attempt + 1 - (tuned_now ? 1 : 0);
+    S.pairs_spans_per_warp = m > 0 ? a.spans_per_warp : 0;
+    S.dense_cell_min = m > 0 ? (a.dense_min > 0 ? a.dense_min : 256) : 0;
+    S.pairs_tuned = m > 0 && g.pairs_tuned ? 1 : 0;
     {
       // bytes each phase reads and writes by its design (phase order of phase_us)
       const double n_ = (double)n_total, N_ = (double)N, kb = a.key64 ? 8.0 : 4.0;

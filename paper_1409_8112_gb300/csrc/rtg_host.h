@@ -39,6 +39,9 @@ struct ShapeGuess {
   bool sorted_cfg = false;  // sort chosen (tuned or default) for this shape
   rtg::SortConfig sort;
   float cand_per_pos = -1.0f;  // in-cell candidates per sorted position at the last build
+  bool pairs_tuned = false;    // enumeration knobs measured for this shape
+  int spans_per_warp = 0;      // (tuned) spans per resident warp
+  int dense_min = 0;           // (tuned) cells of more points take the tiled kernels
 };
 
 // A build's launch sequence captured once and replayed for later builds of the same shape.
@@ -89,6 +92,7 @@ struct rtg_ctx {
   cudaMemPool_t pool = nullptr;     // output CSRs (stream ordered, kept cached)
   cudaEvent_t ev[8] = {};
   size_t ws_bytes = 0;
+  size_t ws_need = 0;  // workspace bytes the current build asked for (at most ws_bytes)
   size_t out_bytes = 0;
   uint64_t next_handle = 1;
   std::unordered_map<uint64_t, size_t> live;  // CSR handle -> bytes
@@ -141,6 +145,10 @@ rtg::SortConfig sort_default(long long N, int num_sms);
 // JSON cache.  Needs a's buffers sized for any variant.
 rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
                      rtg::SortConfig* out);
+// Times the in-cell enumeration of a's keys (sorted with cfg) for each (spans per warp,
+// dense-cell threshold) candidate and returns the fastest.
+rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg, int key_bits,
+                      int* spans_per_warp, int* dense_min);
 size_t sort_scratch_bytes(long long N, const rtg::SortConfig& cfg);  // look-back / counts
 size_t sort_scratch_bytes_max(long long N);
 void tune_load(rtg_ctx* c);

@@ -215,6 +215,7 @@ struct OutSlot {
 // ---- launch arguments ----------------------------------------------------------------------
 struct BuildArgs {
   int spans_per_warp;  // pair enumeration: spans per resident warp (1: static, one each)
+  int dense_min;       // cells of more points than this take the tiled kernels (0: 256)
   int B;              // instances
   int m;              // grids per instance (0: brute force)
   int dtype;          // 0 FP64, 1 FP32 (common to the batch)
@@ -404,6 +405,9 @@ int launch_bits_count(const BuildArgs& a, cudaStream_t s);
 int launch_bits_write(const BuildArgs& a, cudaStream_t s);
 // Sorts every row of the output CSR; column values lie in [0, col_bound) (-1: a.n_total).
 int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound = -1);
+// Status fields the pair kernels accumulate between launches (large-cell list, span counters),
+// cleared so that the enumeration can be run again (the autotuner's trials).
+void reset_pairs_state(const BuildArgs& a, cudaStream_t s);
 
 // Guards the per-device caches of kernel attributes (shared-memory limits, occupancy) that
 // the launch code keeps in statics: builds of several contexts may launch from several host

@@ -652,12 +652,13 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   flush_tally<MODE>(tl, st, s_tally);
 }
 
-// Job offsets for the tiled kernel: a cell of more than kMediumMax points and T =
-// ceil(size / kTL) tiles has T (T + 1) / 2 tile pairs; smaller cells have none (the
+// Job offsets for the tiled kernel: a cell of more than dense_min (<= kMediumMax) points and
+// T = ceil(size / kTL) tiles has T (T + 1) / 2 tile pairs; smaller cells have none (the
 // medium-cell kernel takes them).
 __global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restrict__ large,
                                                       unsigned int cap, Status* st,
-                                                      unsigned long long* job_off) {
+                                                      unsigned long long* job_off,
+                                                      unsigned int dense_min) {
   __shared__ unsigned long long sbuf[32];
   __shared__ unsigned long long carry;
   const unsigned long long L = min(st->large_cells, (unsigned long long)cap);
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(1024) k_large_setup(const LargeCell* __restric
   for (unsigned long long base = 0; base < L; base += blockDim.x) {
     const unsigned long long e = base + threadIdx.x;
     const unsigned long long T =
-        e < L && large[e].size > (unsigned int)kMediumMax ? (large[e].size + kTL - 1) / kTL : 0;
+        e < L && large[e].size > dense_min ? (large[e].size + kTL - 1) / kTL : 0;
     const unsigned long long v = T * (T + 1) / 2;
     unsigned long long tot;
     const unsigned long long ex = block_excl_scan64(v, &tot, sbuf);
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(kMediumWarps * 32) k_pairs_medium(
     const uint32_t* __restrict__ svals, const float* __restrict__ pf, int dtype,
     const K* __restrict__ key_mat, int m, const Inst* __restrict__ inst,
     const InstPlan* __restrict__ iplan, Status* st, const LargeCell* __restrict__ large,
-    unsigned int cap, Sink sk) {
+    unsigned int cap, Sink sk, unsigned int dense_min) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_emit[kMediumWarps][kWarpEmit];
   __shared__ unsigned int s_tally[4];
@@ -711,7 +712,7 @@ __global__ void __launch_bounds__(kMediumWarps * 32) k_pairs_medium(
   for (unsigned long long e = (unsigned long long)blockIdx.x * kMediumWarps + wib; e < L; e += W) {
     const LargeCell cell = large[e];
     const unsigned int s = cell.size;
-    if (s > (unsigned int)kMediumMax) continue;  // warp-uniform
+    if (s > dense_min) continue;  // warp-uniform (the tiled kernels take it)
     const int t = (int)cell.grid, kst = t + 1;  // staged keys per member (odd stride)
     const bool kstage = (size_t)s * kst * sizeof(K) <= (size_t)kMediumKeyBytes;
     for (unsigned int x = lane; x < s; x += 32) {
@@ -1691,6 +1692,13 @@ void brute_impl(const BuildArgs& a, cudaStream_t s) {
                                                       make_sink(a));
 }
 
+// Cells of more points than this go to the tiled kernels (the tuned value, else kMediumMax;
+// never above kMediumMax, the medium kernel's staging capacity).
+inline unsigned int dense_min_of(const BuildArgs& a) {
+  return a.dense_min > 0 && a.dense_min <= kMediumMax ? (unsigned int)a.dense_min
+                                                      : (unsigned int)kMediumMax;
+}
+
 // The dense-cell jobs on the tensor cores (FP16 or BF16 halves), 4 blocks of 128 threads per
 // SM (128 TMEM columns each).
 template <typename K, int DPAD, int MODE>
@@ -1776,9 +1784,10 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
     }
     k_pairs_medium<K, DPAD, MODE><<<(unsigned)(mper * a.num_sms), kMediumWarps * 32, msmem, s>>>(
         sv, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.st, a.large, a.large_cap,
-        make_sink(a));
+        make_sink(a), dense_min_of(a));
   }
-  if (MODE != kWrite) k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off);
+  if (MODE != kWrite)
+    k_large_setup<<<1, 1024, 0, s>>>(a.large, a.large_cap, a.st, a.large_job_off, dense_min_of(a));
   if constexpr (MODE != kBits) {
     if (a.tc_cells) {
       large_tc_launch<K, DPAD, MODE>(a, sv, s);
@@ -1815,6 +1824,13 @@ int launch_pairs(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s) 
     case 8: return pairs_impl<uint32_t, 8>(a, sorted_buf, mode, s);
     default: return pairs_impl<uint32_t, 16>(a, sorted_buf, mode, s);
   }
+}
+
+void reset_pairs_state(const BuildArgs& a, cudaStream_t s) {
+  cudaMemsetAsync(&a.st->large_cells, 0, sizeof(a.st->large_cells), s);
+  cudaMemsetAsync(&a.st->large_jobs, 0, sizeof(a.st->large_jobs), s);
+  cudaMemsetAsync(&a.st->span_next[0], 0, sizeof(a.st->span_next), s);
+  cudaMemsetAsync(&a.st->emitted, 0, sizeof(a.st->emitted), s);
 }
 
 int launch_brute(const BuildArgs& a, Mode mode, cudaStream_t s) {

@@ -227,6 +227,22 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
     release_out(lc, &blk);
     return s;
   }
+  // the admission estimate of this batch against what the batch needed (the workspace its
+  // build asked for and the block CSR): the slack of the estimate, reported with every result
+  int64_t mem_est = 0, mem_peak = 0;
+  {
+    long long npts = 0, nd = 0;
+    int maxd = 1;
+    for (Ticket* t : batch) {
+      npts += t->n;
+      nd += t->n * t->d;
+      maxd = std::max(maxd, t->d);
+    }
+    mem_est = (int64_t)estimate(npts, nd, batch[0]->m, maxd, batch[0]->dtype);
+    // what this batch needed: the workspace its build asked for and its block CSR
+    mem_peak = (int64_t)lc->ws_need + (int64_t)(sizeof(int64_t) * (blk.n + 1)) +
+               (int64_t)(sizeof(int32_t) * blk.nnz);
+  }
   cudaStream_t st = lc->stream;
   // entry offsets of each request in the block-diagonal CSR
   void* dtmp = nullptr;
@@ -290,6 +306,8 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
         std::chrono::duration<double, std::micro>(t->t_start - t->t_submit).count();
     t->result.stats.phase_us[7] =
         std::chrono::duration<double, std::micro>(now - t->t_submit).count();
+    t->result.stats.mem_estimate = mem_est;
+    t->result.stats.mem_peak = mem_peak;
   }
   return RTG_OK;
 }

@@ -3,7 +3,10 @@
 // launch when every tile fits on the GPU at once).  On the first build of a
 // shape whose sort is large enough to matter it times every variant twice on the build's own
 // keys and keeps the fastest, per (sorted elements, key bits), in the context and, when
-// RTG_TUNE_CACHE names a file, in a JSON cache shared by later contexts and processes.
+// RTG_TUNE_CACHE names a file, in a JSON cache shared by later contexts and processes.  The same
+// first build also times the in-cell enumeration over spans per warp {1, 2, 4} and the
+// dense-cell threshold {64, 128, 256} on the sorted keys and keeps the fastest (in the
+// context).
 // The sort is stable in every variant, so the choice never changes a result.
 #include <cuda_runtime.h>
 
@@ -224,6 +227,55 @@ rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
   te.us = best[k];
   c->sort_tune[SortKey(N, key_bits)] = te;
   save_cache(c);
+  return RTG_OK;
+}
+
+rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg, int key_bits,
+                      int* spans_per_warp, int* dense_min) {
+  static const int kSpans[] = {1, 2, 4};
+  static const int kDense[] = {64, 128, 256};
+  constexpr int kCands = 9;
+  const cudaStream_t st = c->stream;
+  rtg::BuildArgs b = a;
+  b.sort_bits = cfg.bits;
+  b.sort_items = cfg.items;
+  b.sort_mode = cfg.mode;
+  b.passes = rtg::sort_passes_for(key_bits, cfg.bits);
+  cudaMemsetAsync(&b.st->sort_tiles[0], 0, sizeof(b.st->sort_tiles), st);
+  cudaMemsetAsync(&b.st->coop_count, 0, 2 * sizeof(unsigned int), st);
+  rtg::launch_keys(b, st);
+  const int sorted = rtg::launch_sort(b, st);
+  std::vector<cudaEvent_t> ev(2 * kCands * kTuneReps, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess)
+      return fail(c, RTG_E_CUDA, "tune: cudaEventCreate failed");
+  for (int rep = 0; rep < kTuneReps; ++rep)
+    for (int k = 0; k < kCands; ++k) {
+      b.spans_per_warp = kSpans[k / 3];
+      b.dense_min = kDense[k % 3];
+      rtg::reset_pairs_state(b, st);
+      cudaEventRecord(ev[2 * (rep * kCands + k)], st);
+      rtg::launch_pairs(b, sorted, rtg::kCount, st);
+      cudaEventRecord(ev[2 * (rep * kCands + k) + 1], st);
+    }
+  cudaError_t e = cudaStreamSynchronize(st);
+  double best[kCands];
+  for (double& x : best) x = 1e30;
+  if (e == cudaSuccess)
+    for (int rep = 0; rep < kTuneReps; ++rep)
+      for (int k = 0; k < kCands; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[2 * (rep * kCands + k)], ev[2 * (rep * kCands + k) + 1]) ==
+            cudaSuccess)
+          best[k] = std::min(best[k], (double)ms);
+      }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return fail(c, RTG_E_CUDA, std::string("tune: ") + cudaGetErrorString(e));
+  int k = 0;
+  for (int q = 1; q < kCands; ++q)
+    if (best[q] < best[k]) k = q;
+  *spans_per_warp = kSpans[k / 3];
+  *dense_min = kDense[k % 3];
   return RTG_OK;
 }
 

@@ -63,7 +63,10 @@ class rtg_stats(ctypes.Structure):
                 ("sort_tile_keys", ctypes.c_int32), ("sort_lookback", ctypes.c_int32),
                 ("sort_tuned", ctypes.c_int32), ("phase_us", ctypes.c_double * 8),
                 ("max_abs_err_d2", ctypes.c_double), ("band", ctypes.c_double),
-                ("phase_bytes", ctypes.c_int64 * 8), ("bytes_moved", ctypes.c_int64)]
+                ("phase_bytes", ctypes.c_int64 * 8), ("bytes_moved", ctypes.c_int64),
+                ("pairs_spans_per_warp", ctypes.c_int32), ("dense_cell_min", ctypes.c_int32),
+                ("pairs_tuned", ctypes.c_int32), ("mem_estimate", ctypes.c_int64),
+                ("mem_peak", ctypes.c_int64)]
 
 
 class rtg_csr(ctypes.Structure):
@@ -320,6 +323,9 @@ def stats_dict(s: rtg_stats, m: int) -> dict:
         "max_abs_err_d2": float(s.max_abs_err_d2), "band": float(s.band),
         "phase_bytes": {p: int(s.phase_bytes[i]) for i, p in enumerate(PHASES)},
         "bytes_moved": int(s.bytes_moved),
+        "enumeration": {"spans_per_warp": int(s.pairs_spans_per_warp),
+                  "dense_cell_min": int(s.dense_cell_min), "tuned": int(s.pairs_tuned)},
+        "mem_estimate": int(s.mem_estimate), "mem_peak": int(s.mem_peak),
     }
 
 

@@ -87,10 +87,15 @@ def test_autotuner_measures_once_and_caches(tmp_path, case32):
     path = str(tmp_path / "tune.json")
     ctx = _context({"RTG_TUNE_CACHE": path})
     try:
-        st = _check(ctx, *case32)  # 296,024 keys: measured on the first build
+        st0 = _check(ctx, *case32)  # 296,024 keys: the first build takes the default
+        assert st0["sort"]["tuned"] == 0 and st0["enumeration"]["tuned"] == 0
+        st = _check(ctx, *case32)  # and the second measures every variant
         assert st["sort"]["tuned"] == 1 and st["attempts"] == 1
+        assert st["enumeration"]["tuned"] == 1
+        assert st["enumeration"]["spans_per_warp"] in (1, 2, 4)
+        assert st["enumeration"]["dense_cell_min"] in (64, 128, 256)
         st2 = _check(ctx, *case32)
-        assert st2["sort"] == st["sort"]
+        assert st2["sort"] == st["sort"] and st2["enumeration"] == st["enumeration"]
     finally:
         ctx.close()
     doc = json.load(open(path))

@@ -174,7 +174,11 @@ def measured_peaks():
 # DRAM bytes (read + write) of each phase's kernels per build, from ncu, for the profiled
 # workloads and, for the sort, the variant the profiled run used (digit bits, keys per tile,
 # look-back code).  None where the kernels changed after the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_pairs_warp, one launch (the medium and tiled kernels of the phase move under 1 MB)
+    (100000, "fp64"): {"pairs": 13245952},
+    (1000000, "fp32"): {"pairs": 331352832},
+}
 
 
 def phase_bytes(n, d, m, key_bytes, passes, coord_bytes, pairs, hist_read=False):
@@ -631,6 +635,61 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_clustered(args):
+    """Clustered point sets (8 Gaussians, sigma 0.05, clipped to [0,1]^d; the serving
+    workload's points) with r for expected degree 2 ln n under uniform density, m = 8, c = r,
+    FP32: dense cells of thousands of points.  Each is built with the CUDA-core tiles and with
+    the tensor-core tiles (FP16, BF16) for its cells of more than 256 points."""
+    import torch
+    from paper_1409_8112_gb300 import gen, rtg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = rtg.Context(0, stream=stream.cuda_stream)
+    flush = L2Flush()
+    out = {}
+    for n, d in ((200000, 6), (50000, 9), (100000, 3)):
+        pts = torch.from_numpy(gen.points_mixture(5, n, d, k=8, sigma=0.05,
+                                                  dtype=np.float32)).cuda()
+        r = gen.radius_for_degree(n, d)
+        T = gen.transforms(5, d, 8, r)
+        rec = {}
+        for tensor in (None, "fp16", "bf16"):
+            for _ in range(args.warmup):
+                ctx.all_pairs(pts, r, T, r, tensor=tensor).release()
+            ms, ph = [], []
+            for k in range(args.steps):
+                flush(k)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = ctx.all_pairs(pts, r, T, r, tensor=tensor)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                pairs = res.nnz
+                res.release()
+            res = ctx.all_pairs(pts, r, T, r, tensor=tensor, timing=True)
+            st = res.stats
+            res.release()
+            rec[tensor or "cuda_cores"] = {
+                "ms": round(float(np.mean(ms)), 3), "pairs": pairs,
+                "pairs_per_s": round(pairs / (np.mean(ms) / 1e3), 1),
+                "max_cell": st["max_cell"], "large_cells": st["large_cells"],
+                "phase_ms": {p: round(v / 1e3, 3) for p, v in st["phase_us"].items()}}
+        out[f"n{n}_d{d}"] = rec
+    head = out["n200000_d6"]["cuda_cores"]
+    line = {
+        "metric": METRIC, "value": head["pairs_per_s"], "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "clustered: 8 Gaussians sigma 0.05 fp32, r=2lnn-degree (uniform), "
+                               "m=8, c=r, seed 5; n=200000 d=6 (headline), 50000 d=9, "
+                               "100000 d=3", "l2": L2_NOTE},
+        "builds": out,
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_table2(args):
     """Shift-only RTG with the paper's Table II parameters (Sec. IV-A): d = 6, m = 20 grids,
     c = 1.35 r, r from Eq. 2, n uniform points in [0,1]^6 (FP64, seed 0).  Reported pairs/s
@@ -981,7 +1040,7 @@ def main():
                     help="leave out the 1,000,000-point FP32 sub-record of the default line")
     ap.add_argument("--workload", default="build",
                     choices=["build", "batch", "serve", "precision", "table2", "query",
-                             "points_query", "params", "bitset"],
+                             "points_query", "params", "bitset", "clustered"],
                     help="build: the headline single-roadmap workload; batch: 512 roadmaps "
                          "batched vs one by one; serve: a Poisson request trace")
     ap.add_argument("--requests", type=int, default=400)
@@ -1013,6 +1072,8 @@ def main():
         run_params(args)
     elif args.workload == "bitset":
         run_bitset(args)
+    elif args.workload == "clustered":
+        run_clustered(args)
     else:
         run_ours(args)
 

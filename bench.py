@@ -546,10 +546,77 @@ def serve_trace(count, rate, nmax, seed=7):
             for i, (t, n, d) in enumerate(serve_shapes(count, rate, nmax, seed))]
 
 
+def serve_run(ctx, trace, arrivals):
+    """Submits the trace to the request server (at its arrival times, or all at once) while a
+    client thread claims each result as soon as it is done (polling the outstanding tickets),
+    so that no finished result holds memory.  Returns the served records and the makespan."""
+    import queue
+    import threading
+    from paper_1409_8112_gb300 import rtg
+    submitted = queue.Queue()
+    rec = {"lat": [], "pairs": 0, "rejected": 0, "served": [], "slack": [], "corrected": 0}
+    failure = []
+
+    def claim():
+        outstanding, left = {}, len(trace)
+        while left:
+            while True:
+                try:
+                    k, tk = submitted.get_nowait()
+                except queue.Empty:
+                    break
+                outstanding[k] = tk
+            done = 0
+            for k in list(outstanding):
+                try:
+                    res = ctx.poll(outstanding[k], m=8)
+                except rtg.RTGError as e:
+                    del outstanding[k]
+                    left -= 1
+                    done += 1
+                    if e.status == rtg.RTG_E_BUDGET:
+                        rec["rejected"] += 1
+                        continue
+                    failure.append(e)
+                    return
+                if res is None:
+                    continue
+                del outstanding[k]
+                left -= 1
+                done += 1
+                st = res.stats
+                rec["corrected"] += st["attempts"] > 1
+                rec["lat"].append(st["phase_us"]["total"] / 1e3)
+                rec["pairs"] += res.nnz
+                rec["served"].append(k)
+                if st["mem_estimate"] > 0:
+                    rec["slack"].append(st["mem_peak"] / st["mem_estimate"])
+                res.release()
+            if not done:
+                time.sleep(0.0005)
+
+    claimer = threading.Thread(target=claim)
+    start = time.perf_counter()
+    claimer.start()
+    for k, (t0, pts, r, T) in enumerate(trace):
+        if arrivals:
+            now = time.perf_counter() - start
+            if t0 > now:
+                time.sleep(t0 - now)
+        submitted.put((k, ctx.submit(pts, r, T, r)))
+    claimer.join()
+    if failure:
+        raise failure[0]
+    rec["makespan"] = time.perf_counter() - start
+    return rec
+
+
 def run_serve(args):
     """The request server on a Poisson trace (continuous batching over lanes, budget
-    admission), then the same trace one build per request through rtg_all_pairs (no batching,
-    no overlap): the same pair sets, so the same recall, and pairs/s for both."""
+    admission): latency at that load; then the same requests submitted at once (the server's
+    capacity), and the same trace one build per request through rtg_all_pairs (no batching,
+    no overlap).  Every build is exact, so each request has the same pair set (the same
+    recall) in every form, and pairs/s compare directly."""
     import torch
     from paper_1409_8112_gb300 import rtg
     torch.cuda.set_device(0)
@@ -560,39 +627,17 @@ def run_serve(args):
     for t0, pts, r, T in trace[:4]:
         res = ctx.wait(ctx.submit(pts, r, T, r), m=8)
         res.release()
-    start = time.perf_counter()
-    tickets = []
-    for t0, pts, r, T in trace:
-        now = time.perf_counter() - start
-        if t0 > now:
-            time.sleep(t0 - now)
-        tickets.append(ctx.submit(pts, r, T, r))
-    lat, pairs, rejected, served_idx, slack = [], 0, 0, [], []
-    for k, tk in enumerate(tickets):
-        try:
-            res = ctx.wait(tk, m=8)
-        except rtg.RTGError as e:
-            if e.status == rtg.RTG_E_BUDGET:
-                rejected += 1
-                continue
-            raise
-        st = res.stats
-        lat.append(st["phase_us"]["total"] / 1e3)
-        pairs += res.nnz
-        served_idx.append(k)
-        if st["mem_estimate"] > 0:
-            slack.append(st["mem_peak"] / st["mem_estimate"])
-        res.release()
-    makespan = time.perf_counter() - start
+    poisson = serve_run(ctx, trace, arrivals=True)
+    burst = serve_run(ctx, trace, arrivals=False)
     # the same trace one request at a time, each a plain synchronous build (host points in),
     # the requests the budget refuses included (they fail there too)
     plain_ctx = rtg.Context(0, mem_budget_bytes=budget)
-    for k in served_idx[:4]:
+    for k in poisson["served"][:4]:
         _, pts, r, T = trace[k]
         plain_ctx.all_pairs(pts, r, T, r).release()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain_pairs, plain_refused = 0, 0
+    plain_pairs, plain_refused, plain_corrected = 0, 0, 0
     for _, pts, r, T in trace:
         try:
             res = plain_ctx.all_pairs(pts, r, T, r)
@@ -602,29 +647,45 @@ def run_serve(args):
                 continue
             raise
         plain_pairs += res.nnz
+        plain_corrected += res.stats["attempts"] > 1
         res.release()
     plain_s = time.perf_counter() - t0
     plain_ctx.close()
+    lat, slack = poisson["lat"], poisson["slack"]
     line = {
-        "metric": METRIC, "value": round(pairs / makespan, 1), "unit": "pairs/s", "n_gpus": 1,
+        "metric": METRIC, "value": round(poisson["pairs"] / poisson["makespan"], 1),
+        "unit": "pairs/s", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"serving: Poisson {args.rate}/s, {args.requests} requests, n "
                                f"log-uniform [1e3,{args.nmax}], d in 2..12, 8-Gaussian mixture "
                                "sigma 0.05 fp32, r=2lnn-degree (uniform), m=8, budget 64 GiB"},
-        "served": len(lat), "rejected_budget": rejected,
+        "served": len(lat), "rejected_budget": poisson["rejected"],
         "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat else None,
         "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat else None,
-        "builds_per_s": round(len(lat) / makespan, 2), "makespan_s": round(makespan, 3),
-        "pairs": pairs,
+        "builds_per_s": round(len(lat) / poisson["makespan"], 2),
+        "makespan_s": round(poisson["makespan"], 3), "pairs": poisson["pairs"],
+        "served_corrected": poisson["corrected"],
+        "capacity": {
+            "pairs_per_s": round(burst["pairs"] / burst["makespan"], 1),
+            "pairs": burst["pairs"], "served": len(burst["lat"]),
+            "rejected_budget": burst["rejected"],
+            "builds_per_s": round(len(burst["lat"]) / burst["makespan"], 2),
+            "seconds": round(burst["makespan"], 3), "corrected": burst["corrected"],
+            "note": "the same requests submitted at once (no arrival times): the server "
+                    "saturated"},
         "one_build_per_request": {
             "pairs_per_s": round(plain_pairs / plain_s, 1), "pairs": plain_pairs,
             "refused_budget": plain_refused,
             "builds_per_s": round((len(trace) - plain_refused) / plain_s, 2),
-            "seconds": round(plain_s, 3),
+            "seconds": round(plain_s, 3), "corrected": plain_corrected,
             "note": "the whole trace back to back (no arrival times), one synchronous "
-                    "rtg_all_pairs each, host points in; every build is exact, so the recall "
-                    "of each request is the same as served"},
-        "served_vs_one_by_one": round((pairs / makespan) / (plain_pairs / plain_s), 3),
+                    "rtg_all_pairs each, host points in"},
+        "served_vs_one_by_one": round((burst["pairs"] / burst["makespan"]) /
+                                      (plain_pairs / plain_s), 3),
+        "comparison_note": "capacity (all requests at once) over one build per request, "
+                           "pairs/s; every build is exact, so recall is equal",
+        "corrected_note": "builds that had to correct a launch assumption (a pair buffer "
+                          "sized for fewer pairs: a second enumeration writes the columns)",
         "admission_slack": {
             "peak_over_estimate_median": round(float(np.median(slack)), 3) if slack else None,
             "peak_over_estimate_max": round(float(np.max(slack)), 3) if slack else None,

@@ -428,6 +428,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   const bool two_pass_flag = (q.flags & RTG_FLAG_TWO_PASS) != 0;
 
   bool tuned_now = false;
+  int recovered = 0;  // columns written by a second enumeration after a pair-buffer overflow
   for (int attempt = 0; attempt < 5; ++attempt) {
     int launches = 0;
     if (m > 0 && !known && attempt == 0) {
@@ -530,12 +531,21 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
 
     // pair buffer for EMIT; COUNT then WRITE when asked, when only counting, or when the buffer
     // would not fit the budget
-    if (g.pair_cap <= 0) g.pair_cap = std::max<long long>(4096, n_total * 16);
+    if (g.pair_cap <= 0) {
+      g.pair_cap = std::max<long long>(4096, n_total * 16);
+      const auto h = c->ppp_hint.find(maxd);
+      if (h != c->ppp_hint.end() && m > 0)
+        g.pair_cap = std::max(g.pair_cap, (long long)(1.25 * h->second * (double)n_total) + 4096);
+    }
     bool two_pass = two_pass_flag || q.count_only || bitset;
     if (!two_pass) {
       const size_t need = (size_t)g.pair_cap * 8;
-      if (c->budget && total_held(c) - c->pair_buf.cap + need + need / (sym ? 1 : 2) > c->budget)
+      if (c->budget && total_held(c) - c->pair_buf.cap + need + need / (sym ? 1 : 2) > c->budget) {
         two_pass = true;
+        // the count-then-write form needs no pair buffer: a large one from an earlier build
+        // would only crowd the columns out of the budget
+        free_buf(c, c->pair_buf);
+      }
     }
     const bool tc = m == 0 && (q.flags & (RTG_FLAG_TC_FP16 | RTG_FLAG_TC_BF16)) != 0;
     if (tc) {
@@ -656,6 +666,59 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
           return fail(c, RTG_E_CUDA, std::string("build: ") + cudaGetErrorString(e));
         }
       }
+      // An undersized pair buffer (the first build of a shape, or more pairs than its last
+      // build): every pair was still counted in its row and the scan has placed the rows, so
+      // only the columns are missing.  A second enumeration writes them straight into their
+      // rows, as the two-pass form does, instead of running the whole build again.
+      const unsigned int ovf = rtg::kErrPairOverflow | rtg::kErrColOverflow;
+      const unsigned int herr = c->h_status->errors;
+      if ((herr & rtg::kErrPairOverflow) && !(herr & ~ovf)) {
+        const long long nnz = (long long)c->h_status->nnz;
+        const size_t old_bytes = sizeof(int32_t) * (size_t)a.col_cap;
+        cudaFreeAsync(out->col, st);
+        {
+          std::lock_guard<std::mutex> lk(c->live_mu);
+          c->live[out->handle] -= old_bytes;
+          c->out_bytes -= old_bytes;
+        }
+        out->col = nullptr;
+        a.col = nullptr;
+        a.col_cap = 0;
+        // the pair buffer holds nothing the write pass needs
+        if (c->budget && total_held(c) + sizeof(int32_t) * (size_t)nnz > c->budget)
+          free_buf(c, c->pair_buf);
+        a.pair_buf = nullptr;
+        a.pair_cap = 0;
+        void* cp = nullptr;
+        if ((s = alloc_out(c, sizeof(int32_t) * (size_t)nnz, &cp)) != RTG_OK) {
+          release_out(c, out);
+          return s;
+        }
+        out->col = (int32_t*)cp;
+        {
+          std::lock_guard<std::mutex> lk(c->live_mu);
+          c->live[out->handle] += sizeof(int32_t) * (size_t)nnz;
+        }
+        a.col = (int*)cp;
+        a.col_cap = nnz;
+        // the overflow flags go; the fill cursors (used by the scatter, then by the row sort's
+        // queues) and the row-sort queue counts start again from zero
+        RTG_CUDA(c, cudaMemsetAsync(&a.st->errors, 0, sizeof(a.st->errors), st));
+        RTG_CUDA(c, cudaMemsetAsync(a.row_cnt, 0, sizeof(unsigned int) * (size_t)n_total, st));
+        RTG_CUDA(c, cudaMemsetAsync(&a.st->long_rows, 0, sizeof(a.st->long_rows), st));
+        RTG_CUDA(c, cudaMemsetAsync(&a.st->mid_rows, 0, sizeof(a.st->mid_rows), st));
+        set_slot();
+        launches += pairs(rtg::kWrite);
+        if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[6], st));
+        launches += rtg::launch_rowsort(a, st);
+        if (timing) RTG_CUDA(c, cudaEventRecord(c->ev[7], st));
+        RTG_CUDA(c, cudaGetLastError());
+        if ((s = read_status(c)) != RTG_OK) {
+          release_out(c, out);
+          return s;
+        }
+        ++recovered;
+      }
     } else if (bitset) {
       // bit-matrix dedupe (Sec. III-B): every reported candidate sets its bit; rows come out
       // of the matrices already sorted
@@ -772,6 +835,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     }
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
+    if (m > 0 && n_total > 0 && !q.count_only) {
+      double& hint = c->ppp_hint[maxd];
+      hint = std::max(0.9 * hint, (double)h.pairs / (double)n_total);
+    }
     {
       double cand = 0.0;
       for (int t = 0; t < m && t < RTG_MAX_GRIDS; ++t) cand += (double)h.candidates[t];
@@ -812,7 +879,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
                      it->second.cfg.items == g.sort.items && it->second.cfg.mode == g.sort.mode;
     }
     S.launches = launches;
-    S.attempts = attempt + 1 - (tuned_now ? 1 : 0);
+    S.attempts = attempt + 1 - (tuned_now ? 1 : 0) + recovered;
     S.pairs_spans_per_warp = m > 0 ? a.spans_per_warp : 0;
     S.dense_cell_min = m > 0 ? (a.dense_min > 0 ? a.dense_min : 256) : 0;
     S.pairs_tuned = m > 0 && g.pairs_tuned ? 1 : 0;
@@ -937,6 +1004,19 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
   }
   *out = c;
   return RTG_OK;
+}
+
+void trim_workspace(rtg_ctx* c) {
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->pts,      &c->pf,        &c->key_mat, &c->keys0,    &c->keys1,
+                    &c->vals0,    &c->vals1,     &c->lookback, &c->row_cnt, &c->scan_lb,
+                    &c->large,    &c->large_job, &c->pair_buf, &c->tc_tiles, &c->tc_norms};
+  for (DevBuf* b : bufs) free_buf(c, *b);
+  // captured graphs name the freed buffers (a replay needs the same pointers, so none would
+  // replay; they go now rather than when their shape comes back)
+  while (!c->graphs.empty()) drop_graph(c, c->graphs.begin()->first);
+  if (c->pool) cudaMemPoolTrimTo(c->pool, 0);
 }
 
 void destroy_ctx(rtg_ctx* c) {

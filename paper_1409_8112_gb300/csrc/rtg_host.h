@@ -97,6 +97,9 @@ struct rtg_ctx {
   uint64_t next_handle = 1;
   std::unordered_map<uint64_t, size_t> live;  // CSR handle -> bytes
   std::map<rtghost::ShapeKey, rtghost::ShapeGuess> guesses;
+  // Pairs per point of recent builds, per widest d (decaying maximum): the pair-buffer size of
+  // a shape built for the first time, so that clustered inputs seldom overflow it.
+  std::map<int, double> ppp_hint;
   std::map<rtghost::SortKey, rtghost::TuneEntry> sort_tune;  // autotuner results
   std::string tune_path;                                     // JSON cache ("" = none)
   std::string device_name;
@@ -134,6 +137,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out);
 // A context of the same device with its own stream, workspace and pool (no server).
 rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out);
 void destroy_ctx(rtg_ctx* c);
+// Frees the per-build workspace (points, rows, keys, pair buffer, ...), the captured graphs and
+// the output pool's cached blocks; the next build allocates again.  The caller holds c->mu.
+void trim_workspace(rtg_ctx* c);
 void stop_server(rtg_ctx* c);  // joins the server's threads; frees unclaimed results
 
 // Sort autotuner (rtg_tune.cu).

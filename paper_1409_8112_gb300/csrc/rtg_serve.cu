@@ -2,15 +2,16 @@
 // rtg_wait).  Each request is one run of Alg. 1 of arXiv:1409.8112 over its own points.
 //
 // Requests wait in one FIFO queue.  A few lanes (each an internal context with its own stream,
-// workspace and pool) take the oldest waiting requests that share m, dtype and flags as one
-// batch, build them together with the batch pipeline, and split the block-diagonal result into
-// one device CSR per request.  Lanes run concurrently, so a batch formed from requests that
-// arrived while another batch was on the GPU overlaps with it.
+// workspace and pool) take the oldest waiting request and the later waiting requests that share
+// its m, dtype, flags and d as one batch, build them together with the batch pipeline, and split
+// the block-diagonal result into one device CSR per request.  Lanes run concurrently, so a
+// batch formed from requests that arrived while another batch was on the GPU overlaps with it.
 //
 // Admission by device memory: with a budget B (the context's mem_budget_bytes), a batch starts
 // only when its estimated footprint fits next to everything already held (the context's own
 // memory, the results not yet released, idle lanes' workspaces and running lanes'
-// reservations); the oldest request has priority (nothing overtakes a waiting head).  A lane
+// reservations); the oldest request has priority (nothing overtakes a waiting head; requests
+// of its kind may join its batch ahead of older requests of another kind).  A lane
 // builds with its reservation as its budget; a batch that does not fit is re-queued at the
 // front as single exclusive requests, each of which then runs alone with all free memory, and
 // fails with RTG_E_BUDGET if it still does not fit.
@@ -70,6 +71,8 @@ struct Server {
   bool stop = false;
   int max_batch = 256;
   long long max_points = 1LL << 22;
+  // reported pairs per point of finished batches, per d (decaying maximum; S->mu)
+  std::unordered_map<int, double> ppp;
 };
 
 namespace {
@@ -131,18 +134,38 @@ uint64_t held_except(Server* S, int li) {
   return h;
 }
 
-// Rough peak footprint of a batch (worst-case 64-bit keys; a pair guess of 16 per point).
-uint64_t estimate(long long npts, long long nd, int m, int maxd, int dtype) {
+// Rough peak footprint of a batch (worst-case 64-bit keys; pairs per point as finished batches
+// of the same d reported, at least 16).
+uint64_t estimate(long long npts, long long nd, int m, int maxd, int dtype, double ppp) {
   const long long N = npts * m;
-  const long long P = npts * 16;
+  const long long P = (long long)((double)npts * std::max(16.0, 1.25 * ppp));
   const long long dpad = rtg::dpad_for(maxd);
   return (uint64_t)(npts * (dpad * 4 + 4 + 8 + 8) + nd * (dtype == 0 ? 8 : 4) + 33 * N + 16 * P +
                     (1 << 20));
 }
 
+double ppp_of(Server* S, int d) {
+  const auto it = S->ppp.find(d);
+  return it == S->ppp.end() ? 0.0 : it->second;
+}
+
 bool compatible(const Ticket* a, const Ticket* b) {
   return a->m == b->m && a->dtype == b->dtype &&
          ((a->flags ^ b->flags) & RTG_FLAG_SYMMETRIC) == 0;
+}
+
+// Workspaces of idle lanes above this size are freed when the oldest request needs the memory.
+constexpr uint64_t kTrimFloor = 64ull << 20;
+
+// Frees the workspaces of lane li and of the other idle lanes, so that their memory counts as
+// free again.  Called with S->mu held (an idle lane's thread holds no lock of its context).
+void trim_idle(Server* S, int li) {
+  for (int k = 0; k < (int)S->lanes.size(); ++k) {
+    Lane& L = S->lanes[k];
+    if (k != li && L.busy) continue;
+    std::lock_guard<std::mutex> g(L.ctx->mu);
+    if (L.ctx->ws_bytes > kTrimFloor) trim_workspace(L.ctx);
+  }
 }
 
 // Called with S->mu held.  Takes a batch from the front of the queue if one may start on
@@ -153,8 +176,18 @@ bool try_form(Server* S, int li, std::vector<Ticket*>& batch, uint64_t& reservat
   bool others_busy = false;
   for (int k = 0; k < (int)S->lanes.size(); ++k)
     if (k != li && S->lanes[k].busy) others_busy = true;
-  const uint64_t held = held_except(S, li);
-  const uint64_t free_mem = total == 0 ? ~0ull : (total > held ? total - held : 0);
+  uint64_t held = held_except(S, li);
+  uint64_t free_mem = total == 0 ? ~0ull : (total > held ? total - held : 0);
+  if (total != 0 &&
+      (head->exclusive ||
+       estimate(head->n, head->n * head->d, head->m, head->d, head->dtype, ppp_of(S, head->d)) >
+           free_mem)) {
+    // the oldest request does not fit next to what is held: idle lanes give back their
+    // workspaces first
+    trim_idle(S, li);
+    held = held_except(S, li);
+    free_mem = total > held ? total - held : 0;
+  }
   if (head->exclusive) {
     if (others_busy) return false;
     batch.push_back(head);
@@ -162,15 +195,19 @@ bool try_form(Server* S, int li, std::vector<Ticket*>& batch, uint64_t& reservat
     reservation = total == 0 ? 0 : free_mem;
     return true;
   }
+  // the head, then later waiting requests of the same kind (m, dtype, flags and d: a batch of
+  // one dimension needs no padding to its widest member and keeps the shape's key kernel)
   long long npts = 0, nd = 0;
   int maxd = 1;
   uint64_t est = 0;
-  size_t k = 0;
-  for (; k < S->queue.size(); ++k) {
+  std::vector<size_t> take;
+  for (size_t k = 0; k < S->queue.size(); ++k) {
     Ticket* t = S->queue[k];
-    if (t->exclusive || !compatible(t, head)) break;
-    if (k > 0 && ((int)k >= S->max_batch || npts + t->n > S->max_points)) break;
-    const uint64_t e = estimate(npts + t->n, nd + t->n * t->d, t->m, std::max(maxd, t->d), t->dtype);
+    if (k > 0 && (t->exclusive || !compatible(t, head) || t->d != head->d)) continue;
+    if (k > 0 && ((int)take.size() >= S->max_batch || npts + t->n > S->max_points)) break;
+    const uint64_t e =
+        estimate(npts + t->n, nd + t->n * t->d, t->m, std::max(maxd, t->d), t->dtype,
+                 ppp_of(S, head->d));
     if (total != 0 && 2 * e > free_mem && k > 0) break;
     if (total != 0 && e > free_mem) {
       if (k == 0 && !others_busy) {
@@ -188,13 +225,20 @@ bool try_form(Server* S, int li, std::vector<Ticket*>& batch, uint64_t& reservat
     nd += t->n * t->d;
     maxd = std::max(maxd, t->d);
     est = e;
+    take.push_back(k);
   }
-  if (k == 0) return false;
-  for (size_t q = 0; q < k; ++q) {
-    batch.push_back(S->queue.front());
-    S->queue.pop_front();
-  }
-  reservation = total == 0 ? 0 : std::min(free_mem, 2 * est);
+  if (take.empty()) return false;
+  for (size_t q : take) batch.push_back(S->queue[q]);
+  for (auto it = take.rbegin(); it != take.rend(); ++it)
+    S->queue.erase(S->queue.begin() + (std::ptrdiff_t)*it);
+  // The estimate guesses the pairs (clustered points report hundreds of times more than
+  // uniform ones), so a lane reserves an even share of the free memory among the lanes that
+  // are idle now (itself included), and at least twice the estimate: a batch whose pair
+  // buffer would not fit its reservation enumerates twice (count, then write).
+  int idle = 0;
+  for (int q = 0; q < (int)S->lanes.size(); ++q)
+    if (q == li || !S->lanes[q].busy) ++idle;
+  reservation = total == 0 ? 0 : std::min(free_mem, std::max(2 * est, free_mem / (uint64_t)idle));
   return true;
 }
 
@@ -238,7 +282,12 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
       nd += t->n * t->d;
       maxd = std::max(maxd, t->d);
     }
-    mem_est = (int64_t)estimate(npts, nd, batch[0]->m, maxd, batch[0]->dtype);
+    double ppp = 0.0;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      ppp = ppp_of(S, batch[0]->d);
+    }
+    mem_est = (int64_t)estimate(npts, nd, batch[0]->m, maxd, batch[0]->dtype, ppp);
     // what this batch needed: the workspace its build asked for and its block CSR
     mem_peak = (int64_t)lc->ws_need + (int64_t)(sizeof(int64_t) * (blk.n + 1)) +
                (int64_t)(sizeof(int32_t) * blk.nnz);
@@ -298,6 +347,9 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
     for (auto& o : outs) release_out(owner, &o);
     return s;
   }
+  // a lane keeps its workspace for the next batch, unless it has grown past a quarter of the
+  // budget (a large batch's pair buffer): then the memory goes back to the other lanes
+  if (owner->budget && lc->ws_bytes > owner->budget / 4) trim_workspace(lc);
   const auto now = Clock::now();
   for (int b = 0; b < B; ++b) {
     Ticket* t = batch[b];
@@ -340,6 +392,15 @@ void lane_loop(Server* S, int li) {
       L.reservation = 0;
       const bool budget = s == RTG_E_BUDGET || s == RTG_E_NOMEM;
       if (s == RTG_OK) {
+        long long npts = 0, pairs = 0;
+        for (Ticket* t : batch) {  // (a result's stats are its batch's; its nnz is its own)
+          npts += t->n;
+          pairs += t->result.nnz / (t->result.symmetric ? 2 : 1);
+        }
+        if (npts > 0) {
+          double& h = S->ppp[batch[0]->d];
+          h = std::max(0.9 * h, (double)pairs / (double)npts);
+        }
         for (Ticket* t : batch) finish(t, RTG_OK, "");
       } else if (budget && (batch.size() > 1 || !batch[0]->exclusive)) {
         // retry each request alone with all free memory, keeping their order at the front

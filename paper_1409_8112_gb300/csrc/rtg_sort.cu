@@ -250,6 +250,8 @@ struct TileRank {
 
   // vin == nullptr: the input is the point-major key-row array, whose position pos holds
   // point pos / m (vdiv = ceil(2^64 / m), exact for pos < 2^31; m = 1 passes vdiv = 0).
+  // FULL: every position of the tile is below N (all tiles but the last), so no lane tests it.
+  template <bool FULL>
   __device__ void rank(const K* __restrict__ kin, const uint32_t* __restrict__ vin, long long N,
                        long long tile_base, int shift, unsigned int (&tcount)[PT],
                        unsigned int* sbuf, unsigned long long vdiv) {
@@ -264,7 +266,7 @@ struct TileRank {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const long long pos = wbase + j * 32 + lane;
-      if (pos < N) {
+      if (FULL || pos < N) {
         key[j] = kin[pos];
         val[j] = vin ? vin[pos]
                      : (vdiv ? (uint32_t)__umul64hi((unsigned long long)pos, vdiv) : (uint32_t)pos);
@@ -277,7 +279,7 @@ struct TileRank {
     const unsigned int lt = (1u << lane) - 1;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-      const bool valid = wbase + j * 32 + lane < N;
+      const bool valid = FULL || wbase + j * 32 + lane < N;
       const unsigned int dg = (unsigned int)(key[j] >> shift) & (D - 1);
       const unsigned int peers = peer_mask<BITS>(dg, valid);
       const unsigned int before = valid ? wh[dg] : 0u;
@@ -311,7 +313,7 @@ struct TileRank {
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-      const bool valid = wbase + j * 32 + lane < N;
+      const bool valid = FULL || wbase + j * 32 + lane < N;
       if (valid) {
         const unsigned int dg = (unsigned int)(key[j] >> shift) & (D - 1);
         const unsigned int local = s_tdig[dg] + s_whist[warp * D + dg] + rk[j];
@@ -323,12 +325,14 @@ struct TileRank {
 
   // Writes the reordered tile (after a barrier that publishes s_gbase and the tile).  Offsets
   // outside [0, N) (digit counts that do not belong to these keys) are dropped and flagged.
+  template <bool FULL>
   __device__ void write(K* __restrict__ kout, uint32_t* __restrict__ vout, long long N,
                         long long tile_base, int shift, unsigned int* errors) {
     const long long rem = N - tile_base;
-    const int tvalid = rem < kTile ? (int)rem : kTile;
+    const int tvalid = FULL ? kTile : (rem < kTile ? (int)rem : kTile);
     const unsigned int nu = (unsigned int)N;  // the host keeps N below 2^31
     bool bad = false;
+#pragma unroll 4
     for (int x = threadIdx.x; x < tvalid; x += kSortThreads) {
       const K k = s_keys[x];
       const unsigned int dg = (unsigned int)(k >> shift) & (D - 1);
@@ -357,9 +361,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
     tr.s_gbase[x] = offs[(size_t)x * tiles + blockIdx.x];
   const long long tile_base = (long long)blockIdx.x * TR::kTile;
   unsigned int tcount[TR::PT];
-  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
+  const bool full = tile_base + TR::kTile <= N;
+  if (full) tr.template rank<true>(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
+  else tr.template rank<false>(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
   __syncthreads();
-  tr.write(kout, vout, N, tile_base, shift, errors);
+  if (full) tr.template write<true>(kout, vout, N, tile_base, shift, errors);
+  else tr.template write<false>(kout, vout, N, tile_base, shift, errors);
 }
 
 // Single-kernel pass with decoupled look-back (tiles take their index from an atomic
@@ -390,7 +397,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
   const unsigned int epoch = *epoch_base + (unsigned int)pass;
   const long long tile_base = (long long)tile * TR::kTile;
   unsigned int tcount[PT];
-  tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
+  const bool full = tile_base + TR::kTile <= N;
+  if (full) tr.template rank<true>(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
+  else tr.template rank<false>(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
   // publish this tile's counts, then look back digit by digit
   unsigned long long* lb_tile = lookback + (size_t)tile * D;
 #pragma unroll
@@ -441,7 +450,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     tr.s_gbase[d] = digit_off[d] + excl;
   }
   __syncthreads();
-  tr.write(kout, vout, N, tile_base, shift, errors);
+  if (full) tr.template write<true>(kout, vout, N, tile_base, shift, errors);
+  else tr.template write<false>(kout, vout, N, tile_base, shift, errors);
 }
 
 // Grid-wide barrier of a cooperative launch (every block resident), bounded: false when the
@@ -496,6 +506,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_coop(
   const long long tile_base = (long long)tile * TR::kTile;
   const int tid = threadIdx.x;
   unsigned int* errors = &st->errors;
+  const bool full = tile_base + TR::kTile <= N;
   for (int p = 0; p < passes; ++p) {
     const K* kin = p == 0 ? key_rows : ((p - 1) & 1 ? kbuf1 : kbuf0);
     const uint32_t* vin = p == 0 ? nullptr : ((p - 1) & 1 ? vbuf1 : vbuf0);
@@ -503,7 +514,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_coop(
     uint32_t* vout = p & 1 ? vbuf1 : vbuf0;
     const int shift = p * BITS;
     unsigned int tcount[PT];
-    tr.rank(kin, vin, N, tile_base, shift, tcount, sbuf, p == 0 ? vdiv : 0ull);
+    const unsigned long long vd = p == 0 ? vdiv : 0ull;
+    if (full) tr.template rank<true>(kin, vin, N, tile_base, shift, tcount, sbuf, vd);
+    else tr.template rank<false>(kin, vin, N, tile_base, shift, tcount, sbuf, vd);
 #pragma unroll
     for (int q = 0; q < PT; ++q) counts[(size_t)(tid * PT + q) * tiles + tile] = tcount[q];
     if (!coop_grid_sync(&st->coop_count, &st->coop_gen, spin_limit, errors)) return;
@@ -527,7 +540,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_coop(
       tr.s_gbase[d] = __ldcg(counts + (size_t)d * tiles + tile);
     }
     __syncthreads();
-    tr.write(kout, vout, N, tile_base, shift, errors);
+    if (full) tr.template write<true>(kout, vout, N, tile_base, shift, errors);
+    else tr.template write<false>(kout, vout, N, tile_base, shift, errors);
     if (!coop_grid_sync(&st->coop_count, &st->coop_gen, spin_limit, errors)) return;
   }
 }

@@ -18,6 +18,16 @@ def ctx():
     c.close()
 
 
+def symmetric_of(csr, n):
+    """Both (i, j) and (j, i) of every pair of an upper-triangular CSR, rows ascending."""
+    p = csr.pairs()
+    both = np.concatenate([p, p[:, ::-1]])
+    both = both[np.lexsort((both[:, 1], both[:, 0]))]
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, both[:, 0] + 1, 1)
+    return np.cumsum(rp), both[:, 1].astype(np.int32)
+
+
 def run_and_compare(ctx, pts, r, T, c, symmetric=False, on_device=False, check_stats=True):
     arg = pts
     if on_device:
@@ -28,14 +38,7 @@ def run_and_compare(ctx, pts, r, T, c, symmetric=False, on_device=False, check_s
     ref = oracle.rtg(pts, r, T, c)
     want_rp, want_col = ref.csr.row_ptr, ref.csr.col
     if symmetric:
-        p = ref.csr.pairs()
-        both = np.concatenate([p, p[:, ::-1]])
-        order = np.lexsort((both[:, 1], both[:, 0]))
-        both = both[order]
-        want_rp = np.zeros(len(pts) + 1, dtype=np.int64)
-        np.add.at(want_rp, both[:, 0] + 1, 1)
-        want_rp = np.cumsum(want_rp)
-        want_col = both[:, 1].astype(np.int32)
+        want_rp, want_col = symmetric_of(ref.csr, len(pts))
     assert len(rp) == len(want_rp)
     assert np.array_equal(rp, want_rp), "row pointers differ"
     assert np.array_equal(col, want_col), "columns differ"
@@ -336,23 +339,28 @@ def test_two_pass_mode_matches(ctx):
     assert np.array_equal(ra, ref.row_ptr) and np.array_equal(ca, ref.col)
 
 
-def test_launch_assumptions_are_corrected():
-    # same shape, far more pairs the second time: the cached pair-buffer size is too small,
-    # the device reports it and the build is run again
+@pytest.mark.parametrize("symmetric,timing", [(False, False), (True, False), (False, True)])
+def test_launch_assumptions_are_corrected(symmetric, timing):
+    # same shape, far more pairs the second time: the cached pair-buffer size is too small;
+    # the rows are still counted and placed, and a second enumeration writes the columns
+    # into them (no second build); the next build of the shape takes the corrected size
     ctx = rtg.Context(0)
     n, d, m = 6000, 3, 4
     r = 0.05
     T = gen.transforms(7, d, m, r)
     a = gen.points_uniform(7, n, d)
     b = gen.points_mixture(7, n, d, k=2, sigma=0.01, dtype=np.float64)
-    ra = ctx.all_pairs(a, r, T, r)
-    rb = ctx.all_pairs(b, r, T, r)
-    assert rb.stats["attempts"] >= 2
-    got = rb.download()
     ref = oracle.rtg(b, r, T, r).csr
-    assert np.array_equal(got[0], ref.row_ptr) and np.array_equal(got[1], ref.col)
+    want = symmetric_of(ref, n) if symmetric else (ref.row_ptr, ref.col)
+    ra = ctx.all_pairs(a, r, T, r, symmetric=symmetric)
+    for k in range(2):
+        rb = ctx.all_pairs(b, r, T, r, symmetric=symmetric, timing=timing)
+        assert rb.stats["attempts"] == (2 if k == 0 else 1)
+        got = rb.download()
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+        assert rb.stats["pairs"] == ref.nnz
+        rb.release()
     ra.release()
-    rb.release()
     ctx.close()
 
 

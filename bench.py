@@ -621,19 +621,26 @@ def run_serve(args):
     from paper_1409_8112_gb300 import rtg
     torch.cuda.set_device(0)
     budget = 64 << 30
-    ctx = rtg.Context(0, mem_budget_bytes=budget)
     trace = serve_trace(args.requests, args.rate, args.nmax)
-    # warm the lanes with a few requests outside the measurement
-    for t0, pts, r, T in trace[:4]:
-        res = ctx.wait(ctx.submit(pts, r, T, r), m=8)
-        res.release()
+    warm = serve_trace(4, args.rate, args.nmax, seed=99)
+
+    def server():
+        # a fresh server (its lanes warmed with a few other requests), so that every request
+        # of the trace is a shape it has not built before, as in a live stream
+        c = rtg.Context(0, mem_budget_bytes=budget)
+        for t0, pts, r, T in warm:
+            c.wait(c.submit(pts, r, T, r), m=8).release()
+        return c
+
+    ctx = server()
     poisson = serve_run(ctx, trace, arrivals=True)
+    ctx.close()
+    ctx = server()
     burst = serve_run(ctx, trace, arrivals=False)
     # the same trace one request at a time, each a plain synchronous build (host points in),
     # the requests the budget refuses included (they fail there too)
     plain_ctx = rtg.Context(0, mem_budget_bytes=budget)
-    for k in poisson["served"][:4]:
-        _, pts, r, T = trace[k]
+    for _, pts, r, T in warm:
         plain_ctx.all_pairs(pts, r, T, r).release()
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -38,6 +38,9 @@ thread_local std::string g_err;
 // Sorts of fewer elements take the default variant: a measurement would cost more than the
 // best variant could save.
 constexpr long long kTuneMinElements = 1LL << 17;
+// The enumeration knobs are measured only for shapes with at most this many in-cell candidates
+// per sorted position at their previous build.
+constexpr float kTunePairsMaxCand = 16.0f;
 constexpr size_t kMaxGraphs = 32;  // executable graphs kept per context (one per shape)
 }  // namespace
 
@@ -510,10 +513,15 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         if ((s = tune_sort(c, a, N, g.key_bits, &best)) != RTG_OK) return s;
         g.sort = best;
         g.sorted_cfg = true;
-        // and the enumeration knobs, on the keys sorted with that variant
-        if ((s = tune_pairs(c, a, best, g.key_bits, &g.spans_per_warp, &g.dense_min)) != RTG_OK)
-          return s;
-        g.pairs_tuned = true;
+        // and the enumeration knobs, on the keys sorted with that variant, when the shape's
+        // cells are light: each trial enumerates every candidate, and dense (clustered) cells
+        // would make the trials cost seconds
+        if (g.cand_per_pos >= 0.0f && g.cand_per_pos <= kTunePairsMaxCand) {
+          if ((s = tune_pairs(c, a, best, g.key_bits, &g.spans_per_warp, &g.dense_min)) !=
+              RTG_OK)
+            return s;
+          g.pairs_tuned = true;
+        }
         tuned_now = true;
         continue;
       }
@@ -535,7 +543,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       g.pair_cap = std::max<long long>(4096, n_total * 16);
       const auto h = c->ppp_hint.find(maxd);
       if (h != c->ppp_hint.end() && m > 0)
-        g.pair_cap = std::max(g.pair_cap, (long long)(1.25 * h->second * (double)n_total) + 4096);
+        g.pair_cap = std::max(g.pair_cap, (long long)(1.5 * h->second * (double)n_total) + 4096);
     }
     bool two_pass = two_pass_flag || q.count_only || bitset;
     if (!two_pass) {
@@ -1039,7 +1047,7 @@ void destroy_ctx(rtg_ctx* c) {
     if (ev) cudaEventDestroy(ev);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_stage) cudaFreeHost(c->h_stage);
-  if (c->pool) cudaMemPoolDestroy(c->pool);  // outstanding CSRs go with the pool
+  if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);  // outstanding CSRs go with it
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1111,9 +1119,13 @@ rtg_status rtg_set_test_hooks(rtg_ctx* c, uint32_t inject, uint32_t wait_limit,
 
 rtg_status rtg_release(rtg_ctx* c, rtg_csr* csr) {
   if (!c || !csr) return fail(c, RTG_E_INVALID, "NULL argument");
-  std::lock_guard<std::mutex> lk(c->mu);
-  cudaSetDevice(c->device);
-  release_out(c, csr);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    release_out(c, csr);
+  }
+  // a request waiting for memory may fit now
+  notify_server(c);
   return RTG_OK;
 }
 

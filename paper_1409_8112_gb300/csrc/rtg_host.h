@@ -90,6 +90,7 @@ struct rtg_ctx {
   bool use_graphs = true;           // RTG_GRAPHS=0 launches every kernel directly
   std::map<rtghost::ShapeKey, rtghost::GraphEntry> graphs;
   cudaMemPool_t pool = nullptr;     // output CSRs (stream ordered, kept cached)
+  bool own_pool = true;             // false: a serving lane drawing on its owner's pool
   cudaEvent_t ev[8] = {};
   size_t ws_bytes = 0;
   size_t ws_need = 0;  // workspace bytes the current build asked for (at most ws_bytes)
@@ -141,6 +142,7 @@ void destroy_ctx(rtg_ctx* c);
 // the output pool's cached blocks; the next build allocates again.  The caller holds c->mu.
 void trim_workspace(rtg_ctx* c);
 void stop_server(rtg_ctx* c);  // joins the server's threads; frees unclaimed results
+void notify_server(rtg_ctx* c);  // memory was released: waiting requests are considered again
 
 // Sort autotuner (rtg_tune.cu).
 // The variant used without measurement: 8-bit digits, 2048-key tiles, look-back while the

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -70,7 +71,8 @@ struct Server {
   uint64_t next = 1;
   bool stop = false;
   int max_batch = 256;
-  long long max_points = 1LL << 22;
+  long long max_points = 1LL << 20;
+  bool log = false;  // RTG_SERVE_LOG=1: one line per batch on stderr
   // reported pairs per point of finished batches, per d (decaying maximum; S->mu)
   std::unordered_map<int, double> ppp;
 };
@@ -156,6 +158,8 @@ bool compatible(const Ticket* a, const Ticket* b) {
 
 // Workspaces of idle lanes above this size are freed when the oldest request needs the memory.
 constexpr uint64_t kTrimFloor = 64ull << 20;
+// Requests of at least this many points are built alone.
+constexpr long long kAloneMin = 1LL << 17;
 
 // Frees the workspaces of lane li and of the other idle lanes, so that their memory counts as
 // free again.  Called with S->mu held (an idle lane's thread holds no lock of its context).
@@ -204,6 +208,9 @@ bool try_form(Server* S, int li, std::vector<Ticket*>& batch, uint64_t& reservat
   for (size_t k = 0; k < S->queue.size(); ++k) {
     Ticket* t = S->queue[k];
     if (k > 0 && (t->exclusive || !compatible(t, head) || t->d != head->d)) continue;
+    // a request of kAloneMin points or more fills the GPU by itself: it runs alone, and a
+    // batch takes none (a batch that does not fit its memory fails after its enumeration)
+    if (k > 0 && (head->n >= kAloneMin || t->n >= kAloneMin)) continue;
     if (k > 0 && ((int)take.size() >= S->max_batch || npts + t->n > S->max_points)) break;
     const uint64_t e =
         estimate(npts + t->n, nd + t->n * t->d, t->m, std::max(maxd, t->d), t->dtype,
@@ -266,6 +273,16 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
   Request q{items.data(), B, batch[0]->m, batch[0]->dtype, 0, batch[0]->flags, false};
   rtg_csr blk{};
   cudaSetDevice(lc->device);
+  {
+    // the pairs per point every lane has seen for this d size the pair buffer of a new shape
+    double ppp = 0.0;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      ppp = ppp_of(S, batch[0]->d);
+    }
+    double& h = lc->ppp_hint[batch[0]->d];
+    h = std::max(h, ppp);
+  }
   rtg_status s = build(lc, q, &blk);
   if (s != RTG_OK) {
     release_out(lc, &blk);
@@ -291,6 +308,36 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
     // what this batch needed: the workspace its build asked for and its block CSR
     mem_peak = (int64_t)lc->ws_need + (int64_t)(sizeof(int64_t) * (blk.n + 1)) +
                (int64_t)(sizeof(int32_t) * blk.nnz);
+  }
+  if (B == 1) {
+    // a batch of one: its block CSR (from the owner's pool) is the request's CSR, handed to the
+    // owner as it is (no copy, and never two copies in memory)
+    size_t bytes = 0;
+    {
+      std::lock_guard<std::mutex> lk(lc->live_mu);
+      auto it = lc->live.find(blk.handle);
+      if (it != lc->live.end()) {
+        bytes = it->second;
+        lc->out_bytes -= bytes;
+        lc->live.erase(it);
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(owner->live_mu);
+      owner->out_bytes += bytes;
+    }
+    blk.handle = register_out(owner, bytes);
+    if (owner->budget && lc->ws_bytes > owner->budget / 4) trim_workspace(lc);
+    Ticket* t = batch[0];
+    t->result = blk;
+    const auto now = Clock::now();
+    t->result.stats.phase_us[0] =
+        std::chrono::duration<double, std::micro>(t->t_start - t->t_submit).count();
+    t->result.stats.phase_us[7] =
+        std::chrono::duration<double, std::micro>(now - t->t_submit).count();
+    t->result.stats.mem_estimate = mem_est;
+    t->result.stats.mem_peak = mem_peak;
+    return RTG_OK;
   }
   cudaStream_t st = lc->stream;
   // entry offsets of each request in the block-diagonal CSR
@@ -384,7 +431,16 @@ void lane_loop(Server* S, int li) {
         t->t_start = now;
       }
     }
+    const auto t_run = Clock::now();
     const rtg_status s = run_batch(S, S->lanes[li], batch, reservation);
+    if (S->log) {
+      long long npts = 0;
+      for (Ticket* t : batch) npts += t->n;
+      std::fprintf(stderr, "serve lane %d: %zu requests, %lld points, d %d%s, %.3f ms, status %d\n",
+                   li, batch.size(), npts, batch[0]->d, batch[0]->exclusive ? " (alone)" : "",
+                   std::chrono::duration<double, std::milli>(Clock::now() - t_run).count(),
+                   (int)s);
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
       Lane& L = S->lanes[li];
@@ -421,6 +477,7 @@ Server* get_server(rtg_ctx* c) {
   if (c->server) return c->server;
   Server* S = new Server();
   S->owner = c;
+  if (const char* v = std::getenv("RTG_SERVE_LOG")) S->log = std::atoi(v) != 0;
   int lanes = 2;
   if (const char* v = std::getenv("RTG_SERVE_LANES")) lanes = std::max(1, std::min(8, std::atoi(v)));
   S->lanes.resize(lanes);
@@ -431,6 +488,11 @@ Server* get_server(rtg_ctx* c) {
       delete S;
       return nullptr;
     }
+    // the lane's CSRs come from the owner's pool, so that a result handed over as it is
+    // (a batch of one) is the owner's memory like any other result
+    if (lc->pool) cudaMemPoolDestroy(lc->pool);
+    lc->pool = c->pool;
+    lc->own_pool = false;
     S->lanes[k].ctx = lc;
   }
   for (int k = 0; k < lanes; ++k) S->lanes[k].th = std::thread(lane_loop, S, k);
@@ -461,6 +523,13 @@ rtg_status take(rtg_ctx* c, Server* S, uint64_t ticket, rtg_csr* out, bool* pend
 }
 
 }  // namespace
+
+void notify_server(rtg_ctx* c) {
+  Server* S = c->server;
+  if (!S) return;
+  { std::lock_guard<std::mutex> lk(S->mu); }  // a lane between its check and its wait sees it
+  S->cv.notify_all();
+}
 
 void stop_server(rtg_ctx* c) {
   Server* S = c->server;

@@ -124,3 +124,23 @@ def test_autotune_off_takes_the_default(case32):
         assert st["sort"]["digit_bits"] == 8 and st["sort"]["tile_keys"] == 2048
     finally:
         ctx.close()
+
+
+def test_dense_shapes_tune_the_sort_but_not_the_enumeration():
+    # clustered points with cells of hundreds of points (far more than 16 candidates per
+    # sorted position): the second build measures the sort variants only, since every
+    # enumeration trial would enumerate all the candidates
+    n, d, m = 20000, 3, 8
+    pts = gen.points_mixture(23, n, d, k=4, sigma=0.02, dtype=np.float32)
+    r = gen.radius_for_degree(n, d)
+    T = gen.transforms(23, d, m, r)
+    ref = oracle.rtg(pts, r, T, r)
+    ctx = _context({})
+    try:
+        st0 = _check(ctx, pts, r, T, ref)
+        assert st0["total_candidates"] > 16 * n * m
+        st = _check(ctx, pts, r, T, ref)
+        assert st["sort"]["tuned"] == 1
+        assert st["enumeration"]["tuned"] == 0
+    finally:
+        ctx.close()

@@ -38,9 +38,6 @@ thread_local std::string g_err;
 // Sorts of fewer elements take the default variant: a measurement would cost more than the
 // best variant could save.
 constexpr long long kTuneMinElements = 1LL << 17;
-// The enumeration knobs are measured only for shapes with at most this many in-cell candidates
-// per sorted position at their previous build.
-constexpr float kTunePairsMaxCand = 16.0f;
 constexpr size_t kMaxGraphs = 32;  // executable graphs kept per context (one per shape)
 }  // namespace
 
@@ -513,14 +510,15 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         if ((s = tune_sort(c, a, N, g.key_bits, &best)) != RTG_OK) return s;
         g.sort = best;
         g.sorted_cfg = true;
-        // and the enumeration knobs, on the keys sorted with that variant, when the shape's
-        // cells are light: each trial enumerates every candidate, and dense (clustered) cells
-        // would make the trials cost seconds
-        if (g.cand_per_pos >= 0.0f && g.cand_per_pos <= kTunePairsMaxCand) {
+        // and the enumeration knobs, on the keys sorted with that variant, unless the shape
+        // has so many in-cell candidates (clustered points) that the trials, each of which
+        // enumerates every candidate, would cost seconds
+        if (g.cand_per_pos >= 0.0f &&
+            (double)g.cand_per_pos * (double)N <= c->tune_pairs_max_cand) {
           if ((s = tune_pairs(c, a, best, g.key_bits, &g.spans_per_warp, &g.dense_min)) !=
               RTG_OK)
             return s;
-          g.pairs_tuned = true;
+          g.pairs_tuned = g.spans_per_warp > 0;
         }
         tuned_now = true;
         continue;
@@ -541,9 +539,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     // would not fit the budget
     if (g.pair_cap <= 0) {
       g.pair_cap = std::max<long long>(4096, n_total * 16);
-      const auto h = c->ppp_hint.find(maxd);
-      if (h != c->ppp_hint.end() && m > 0)
-        g.pair_cap = std::max(g.pair_cap, (long long)(1.5 * h->second * (double)n_total) + 4096);
+      const double h = m > 0 ? c->ppp_hint.get(maxd) : 0.0;
+      if (h > 0.0)
+        g.pair_cap = std::max(g.pair_cap, (long long)(1.5 * h * (double)n_total) + 4096);
     }
     bool two_pass = two_pass_flag || q.count_only || bitset;
     if (!two_pass) {
@@ -844,8 +842,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
     if (m > 0 && n_total > 0 && !q.count_only) {
-      double& hint = c->ppp_hint[maxd];
-      hint = std::max(0.9 * hint, (double)h.pairs / (double)n_total);
+      c->ppp_hint.put(maxd, (double)h.pairs / (double)n_total);
     }
     {
       double cand = 0.0;

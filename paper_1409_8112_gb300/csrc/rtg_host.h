@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <map>
@@ -71,6 +72,24 @@ struct Request {
 
 struct Server;  // request server of a context (rtg_serve.cu)
 
+// Reported pairs per point of recent builds, per d: a decaying maximum (a figure per size
+// class of n was measured to correct more first builds, not fewer).
+struct PppHints {
+  std::map<int, double> h;
+  double get(int d) const {
+    const auto it = h.find(d);
+    return it == h.end() ? 0.0 : it->second;
+  }
+  void put(int d, double ppp) {
+    double& x = h[d];
+    x = std::max(0.9 * x, ppp);
+  }
+  void raise(int d, double ppp) {
+    double& x = h[d];
+    x = std::max(x, ppp);
+  }
+};
+
 }  // namespace rtghost
 
 struct rtg_ctx {
@@ -98,13 +117,16 @@ struct rtg_ctx {
   uint64_t next_handle = 1;
   std::unordered_map<uint64_t, size_t> live;  // CSR handle -> bytes
   std::map<rtghost::ShapeKey, rtghost::ShapeGuess> guesses;
-  // Pairs per point of recent builds, per widest d (decaying maximum): the pair-buffer size of
-  // a shape built for the first time, so that clustered inputs seldom overflow it.
-  std::map<int, double> ppp_hint;
+  // Pairs per point of recent builds: the pair-buffer size of a shape built for the first
+  // time, so that clustered inputs seldom overflow it.
+  rtghost::PppHints ppp_hint;
   std::map<rtghost::SortKey, rtghost::TuneEntry> sort_tune;  // autotuner results
   std::string tune_path;                                     // JSON cache ("" = none)
   std::string device_name;
   bool autotune = true;
+  // shapes with more in-cell candidates keep the default enumeration knobs (the trials would
+  // each enumerate them all); RTG_TUNE_PAIRS_MAX_CAND
+  double tune_pairs_max_cand = 4.0e9;
   bool sort_forced = false;  // RTG_SORT_VARIANT
   rtg::SortConfig sort_force;
   std::vector<rtg::Inst> h_inst;
@@ -154,7 +176,8 @@ rtg::SortConfig sort_default(long long N, int num_sms);
 rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
                      rtg::SortConfig* out);
 // Times the in-cell enumeration of a's keys (sorted with cfg) for each (spans per warp,
-// dense-cell threshold) candidate and returns the fastest.
+// dense-cell threshold) candidate and returns the fastest; 0, 0 (the defaults) when a first
+// trial takes long.
 rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg, int key_bits,
                       int* spans_per_warp, int* dense_min);
 size_t sort_scratch_bytes(long long N, const rtg::SortConfig& cfg);  // look-back / counts

@@ -73,8 +73,8 @@ struct Server {
   int max_batch = 256;
   long long max_points = 1LL << 20;
   bool log = false;  // RTG_SERVE_LOG=1: one line per batch on stderr
-  // reported pairs per point of finished batches, per d (decaying maximum; S->mu)
-  std::unordered_map<int, double> ppp;
+  // reported pairs per point of finished batches (S->mu)
+  PppHints ppp;
 };
 
 namespace {
@@ -146,10 +146,7 @@ uint64_t estimate(long long npts, long long nd, int m, int maxd, int dtype, doub
                     (1 << 20));
 }
 
-double ppp_of(Server* S, int d) {
-  const auto it = S->ppp.find(d);
-  return it == S->ppp.end() ? 0.0 : it->second;
-}
+double ppp_of(Server* S, int d) { return S->ppp.get(d); }
 
 bool compatible(const Ticket* a, const Ticket* b) {
   return a->m == b->m && a->dtype == b->dtype &&
@@ -280,8 +277,7 @@ rtg_status run_batch(Server* S, Lane& L, std::vector<Ticket*>& batch, uint64_t r
       std::lock_guard<std::mutex> lk(S->mu);
       ppp = ppp_of(S, batch[0]->d);
     }
-    double& h = lc->ppp_hint[batch[0]->d];
-    h = std::max(h, ppp);
+    lc->ppp_hint.raise(batch[0]->d, ppp);
   }
   rtg_status s = build(lc, q, &blk);
   if (s != RTG_OK) {
@@ -453,10 +449,7 @@ void lane_loop(Server* S, int li) {
           npts += t->n;
           pairs += t->result.nnz / (t->result.symmetric ? 2 : 1);
         }
-        if (npts > 0) {
-          double& h = S->ppp[batch[0]->d];
-          h = std::max(0.9 * h, (double)pairs / (double)npts);
-        }
+        if (npts > 0) S->ppp.put(batch[0]->d, (double)pairs / (double)npts);
         for (Ticket* t : batch) finish(t, RTG_OK, "");
       } else if (budget && (batch.size() > 1 || !batch[0]->exclusive)) {
         // retry each request alone with all free memory, keeping their order at the front

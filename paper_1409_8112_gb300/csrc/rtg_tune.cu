@@ -168,6 +168,11 @@ void tune_load(rtg_ctx* c) {
   c->tune_path = p ? p : "";
   const char* off = std::getenv("RTG_AUTOTUNE");
   c->autotune = !(off && std::strcmp(off, "0") == 0);
+  // in-cell candidates above which the enumeration knobs keep their defaults
+  if (const char* v = std::getenv("RTG_TUNE_PAIRS_MAX_CAND")) {
+    const double x = std::atof(v);
+    if (x > 0.0) c->tune_pairs_max_cand = x;
+  }
   c->sort_forced = false;
   if (const char* v = std::getenv("RTG_SORT_VARIANT")) {
     // "bits,items,mode": one variant for every sort of this context (no measurement)
@@ -230,6 +235,9 @@ rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
   return RTG_OK;
 }
 
+// A first enumeration trial longer than this keeps the default knobs.
+constexpr float kTunePairsTrialMaxMs = 25.0f;
+
 rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg, int key_bits,
                       int* spans_per_warp, int* dense_min) {
   static const int kSpans[] = {1, 2, 4};
@@ -249,6 +257,25 @@ rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg,
   for (auto& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess)
       return fail(c, RTG_E_CUDA, "tune: cudaEventCreate failed");
+  {
+    // one trial first: an enumeration that takes long keeps the defaults (the trials would
+    // cost more than the knobs can save)
+    b.spans_per_warp = kSpans[0];
+    b.dense_min = kDense[0];
+    rtg::reset_pairs_state(b, st);
+    cudaEventRecord(ev[0], st);
+    rtg::launch_pairs(b, sorted, rtg::kCount, st);
+    cudaEventRecord(ev[1], st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess || ms > kTunePairsTrialMaxMs) {
+      cudaGetLastError();
+      for (auto& x : ev) cudaEventDestroy(x);
+      *spans_per_warp = 0;
+      *dense_min = 0;
+      return RTG_OK;
+    }
+  }
   for (int rep = 0; rep < kTuneReps; ++rep)
     for (int k = 0; k < kCands; ++k) {
       b.spans_per_warp = kSpans[k / 3];

@@ -19,7 +19,7 @@ LOOKBACK_CODE = {0: 1, 1: 0, 2: 2}  # stats "lookback" of each pass strategy
 
 def _context(env):
     """A context created with the given environment (read at creation)."""
-    keys = ("RTG_SORT_VARIANT", "RTG_TUNE_CACHE", "RTG_AUTOTUNE")
+    keys = ("RTG_SORT_VARIANT", "RTG_TUNE_CACHE", "RTG_AUTOTUNE", "RTG_TUNE_PAIRS_MAX_CAND")
     old = {k: os.environ.get(k) for k in keys}
     try:
         for k in keys:
@@ -126,21 +126,24 @@ def test_autotune_off_takes_the_default(case32):
         ctx.close()
 
 
-def test_dense_shapes_tune_the_sort_but_not_the_enumeration():
-    # clustered points with cells of hundreds of points (far more than 16 candidates per
-    # sorted position): the second build measures the sort variants only, since every
-    # enumeration trial would enumerate all the candidates
+@pytest.mark.parametrize("cap,tuned", [("1e6", 0), (None, 1)])
+def test_enumeration_trials_are_capped_by_candidates(cap, tuned):
+    # clustered points (cells of hundreds of points): above the candidate cap the second build
+    # measures the sort variants only, since every enumeration trial would enumerate all the
+    # candidates; under the default cap (4e9) this shape's enumeration is measured too
     n, d, m = 20000, 3, 8
     pts = gen.points_mixture(23, n, d, k=4, sigma=0.02, dtype=np.float32)
     r = gen.radius_for_degree(n, d)
     T = gen.transforms(23, d, m, r)
     ref = oracle.rtg(pts, r, T, r)
-    ctx = _context({})
+    ctx = _context({"RTG_TUNE_PAIRS_MAX_CAND": cap} if cap else {})
     try:
         st0 = _check(ctx, pts, r, T, ref)
-        assert st0["total_candidates"] > 16 * n * m
+        assert st0["total_candidates"] > 1e6
         st = _check(ctx, pts, r, T, ref)
         assert st["sort"]["tuned"] == 1
-        assert st["enumeration"]["tuned"] == 0
+        assert st["enumeration"]["tuned"] == tuned
+        st2 = _check(ctx, pts, r, T, ref)
+        assert st2["enumeration"] == st["enumeration"]
     finally:
         ctx.close()

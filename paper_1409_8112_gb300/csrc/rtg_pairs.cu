@@ -393,7 +393,9 @@ __device__ long long run_end(const K* __restrict__ skeys, long long N, long long
 #ifndef RTG_PAIRS_MIN_BLOCKS
 #define RTG_PAIRS_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
 #endif
-template <typename K, int DPAD, int MODE, bool STAGE>
+// STAGE: 0 key rows read in place, 1 staged key by key, 2 staged in 16-byte blocks (key rows
+// of a multiple of 16 bytes).
+template <typename K, int DPAD, int MODE, int STAGE>
 __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_warp(
     const K* __restrict__ skeys, const uint32_t* __restrict__ svals, long long N, long long span,
     const float* __restrict__ pf, int dtype, const K* __restrict__ key_mat, int m,
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
   float* w_pt = reinterpret_cast<float*>(ws + kWarpEmit * 8);
   K* w_rows = reinterpret_cast<K*>(w_pt + kRing * DPAD);
   const int rstride = staged_row_stride<K>(m);
-  uint32_t* w_idx = reinterpret_cast<uint32_t*>(w_rows + (STAGE ? kRing * rstride : 0));
+  uint32_t* w_idx = reinterpret_cast<uint32_t*>(w_rows + (STAGE != 0 ? kRing * rstride : 0));
   int* w_excl = reinterpret_cast<int*>(w_idx + kRing);  // per lane: first pair of the lane
   int* w_hrel = w_excl + 32;                             // per lane: cell head - chunk start
   unsigned int* w_cell = reinterpret_cast<unsigned int*>(w_hrel + 32);  // (instance << 8) | grid
@@ -534,7 +536,15 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
         float* dst = w_pt + slot * DPAD;
 #pragma unroll
         for (int v = 0; v < DPAD / 4; ++v) cp_async16(dst + 4 * v, src + 4 * v);
-        if (STAGE) {
+        if (STAGE == 2) {
+          // 16-byte copies covering the first t keys (key rows and staged rows start on 16-byte
+          // boundaries and hold a multiple of 16 bytes, so the copies stay inside both)
+          const int t = (int)(mycell & 0xffu);
+          const K* kr = key_mat + (size_t)vc * m;
+          K* kd = w_rows + slot * rstride;
+          constexpr int kpv = 16 / (int)sizeof(K);
+          for (int u = 0; u < t; u += kpv) cp_async16(kd + u, kr + u);
+        } else if (STAGE == 1) {
           const int t = (int)(mycell & 0xffu);
           const K* kr = key_mat + (size_t)vc * m;
           K* kd = w_rows + slot * rstride;
@@ -585,12 +595,13 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
             const unsigned int cl = w_cell[o];
             const int t = (int)(cl & 0xffu), ib_ = (int)(cl >> 8);
             pinst = ib_;
-            const K* ka = STAGE ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
-            const K* kb = STAGE ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
+            const K* ka = STAGE != 0 ? w_rows + sa * rstride : key_mat + (size_t)ia * m;
+            const K* kb = STAGE != 0 ? w_rows + sb * rstride : key_mat + (size_t)ib * m;
             const float2 band = one_inst ? span_band : band_of(iplan[ib_]);
-            keep = decide_pair<K, DPAD, MODE, STAGE>(i, j, t, w_pt + sa * DPAD, w_pt + sb * DPAD,
-                                                     ka, kb, inst + ib_, iplan + ib_, band, dtype,
-                                                     tl, sk.near_r);
+            keep = decide_pair<K, DPAD, MODE, STAGE != 0>(i, j, t, w_pt + sa * DPAD,
+                                                          w_pt + sb * DPAD, ka, kb, inst + ib_,
+                                                          iplan + ib_, band, dtype, tl,
+                                                          sk.near_r);
           }
           if (MODE == kBits) {
             deliver_bits(keep, i, j, inst + pinst, sk);
@@ -1744,13 +1755,17 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   static size_t attr_smem[64] = {};  // largest size granted so far, per device
   int dev = 0;
   cudaGetDevice(&dev);
-  auto kern = stage_rows ? k_pairs_warp<K, DPAD, MODE, true> : k_pairs_warp<K, DPAD, MODE, false>;
+  const bool rows16 = (a.m * (int)sizeof(K)) % 16 == 0;  // key rows of whole 16-byte blocks
+  auto kern = !stage_rows ? k_pairs_warp<K, DPAD, MODE, 0>
+                          : (rows16 ? k_pairs_warp<K, DPAD, MODE, 2> : k_pairs_warp<K, DPAD, MODE, 1>);
   {
     std::lock_guard<std::mutex> lk(launch_attr_mutex());
     if (dev < 0 || dev >= 64 || smem > attr_smem[dev]) {
-      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, true>,
+      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, 0>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, false>,
+      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, 1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_pairs_warp<K, DPAD, MODE, 2>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (dev >= 0 && dev < 64) attr_smem[dev] = smem;
     }

@@ -497,9 +497,12 @@ class Context:
         """instances: list of (points, r, transforms, cell_side); points all numpy (host) or
         all CUDA tensors, one dtype.  Returns (Result over the block-diagonal CSR, offsets)."""
         items, keep, codes, devs = [], [], set(), set()
+        ordered = set()  # devices whose current stream the library's stream already follows
         for pts, r, T, c in instances:
             ptr, code, on_dev, n, d, kp = _points_arg(pts)
-            self._after_producer(kp)
+            if on_dev and kp.device not in ordered:
+                self._after_producer(kp)  # one wait covers every tensor of that stream
+                ordered.add(kp.device)
             Tc = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
             if Tc.size != m * (d * d + d):
                 raise ValueError("each instance needs m * (d*d + d) transform values")

@@ -431,6 +431,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   int recovered = 0;  // columns written by a second enumeration after a pair-buffer overflow
   for (int attempt = 0; attempt < 5; ++attempt) {
     int launches = 0;
+    a.skip_tail = 0;
     if (m > 0 && !known && attempt == 0) {
       // first build of this shape: read the key width back once
       RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
@@ -610,6 +611,11 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       cudaMemcpyAsync(c->out_slot.p, c->h_slot, sizeof(rtg::OutSlot), cudaMemcpyHostToDevice, st);
     };
     if (!two_pass) {
+      // kernels the last build of this shape gave nothing to do are left out; the kernels
+      // before them flag any work that turns up, and the build runs again with them
+      if (m > 0 && known)
+        a.skip_tail =
+            (g.no_dense ? rtg::kSkipDense : 0) | (g.no_long_rows ? rtg::kSkipLongRows : 0);
       if ((s = ensure(c, c->pair_buf, (size_t)g.pair_cap * 8)) != RTG_OK) return s;
       a.pair_buf = (unsigned long long*)c->pair_buf.p;
       a.pair_cap = g.pair_cap;
@@ -818,10 +824,14 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       release_out(c, out);
       return fail(c, RTG_E_TIMEOUT, "a bounded device wait ran out");
     }
-    const unsigned int retry = rtg::kErrKeyBits | rtg::kErrPairOverflow;
+    const unsigned int retry = rtg::kErrKeyBits | rtg::kErrPairOverflow | rtg::kErrTailSkipped;
     if (h.errors & retry) {
       // the launch assumptions were too small: take the device's values and run again
       release_out(c, out);
+      if (h.errors & rtg::kErrTailSkipped) {
+        g.no_dense = false;
+        g.no_long_rows = false;
+      }
       if (h.errors & rtg::kErrKeyBits) {
         g.key64 = h.sort_bits > 32;
         g.key_bits = (int)h.sort_bits;
@@ -841,6 +851,11 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     }
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
+    if (m > 0 && !bitset) {
+      // with a margin, so that new data of the same shape seldom brings such work back
+      g.no_dense = h.max_cell <= (unsigned long long)rtg::kSkipMargin;
+      g.no_long_rows = h.rows_over_margin == 0;
+    }
     if (m > 0 && n_total > 0 && !q.count_only) {
       c->ppp_hint.put(maxd, (double)h.pairs / (double)n_total);
     }

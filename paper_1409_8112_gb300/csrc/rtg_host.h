@@ -43,6 +43,8 @@ struct ShapeGuess {
   bool pairs_tuned = false;    // enumeration knobs measured for this shape
   int spans_per_warp = 0;      // (tuned) spans per resident warp
   int dense_min = 0;           // (tuned) cells of more points take the tiled kernels
+  bool no_dense = false;       // the last build had no cell of more than 32 points
+  bool no_long_rows = false;   // the last build had no row of more than 32 entries
 };
 
 // A build's launch sequence captured once and replayed for later builds of the same shape.

@@ -54,8 +54,18 @@ enum : uint32_t {
   kErrLargeOverflow = 64u,  // large-cell list full (internal)
   kErrPairOverflow = 128u,  // pair buffer too small (host re-runs bigger)
   kErrQueryRange = 256u,    // a neighbour query names a point outside the graph
-  kErrSortRange = 512u      // a sort tile or offset fell outside the keys (internal)
+  kErrSortRange = 512u,     // a sort tile or offset fell outside the keys (internal)
+  kErrTailSkipped = 1024u   // work for a kernel left out of the launch (host re-runs with it)
 };
+
+// Kernels a build leaves out because the last build of its shape gave them nothing to do
+// (BuildArgs::skip_tail); the kernels before them flag kErrTailSkipped if work turns up.
+constexpr int kSkipDense = 1;     // the medium-cell, large-cell set-up and large-cell kernels
+constexpr int kSkipLongRows = 2;  // the warp and block row sorts
+// A shape whose last build had no cell and no row longer than this leaves those kernels (for
+// more than 32 points or entries) out of its next builds; the margin keeps new data of the
+// same shape from flipping the decision often.
+constexpr int kSkipMargin = 24;
 
 // Bounded device waits (look-back chains, tensor-core commits): iterations before a wait
 // gives up, sets kErrTimeout and lets its kernel return.  A context may set a smaller limit
@@ -121,6 +131,7 @@ struct Status {
   unsigned int coop_gen;    // single-launch sort: grid barriers completed
   unsigned int long_rows;  // rows queued for the block row sort
   unsigned int mid_rows;   // rows queued for the warp row sort
+  unsigned int rows_over_margin;  // 1 if a row holds more than kSkipMargin entries
   unsigned int tc_max_err_bits;  // tensor-core path: max |FP32 d^2 - FP64 d^2| (float bits)
   double tc_band;                // tensor-core path: band used around r^2
 };
@@ -263,6 +274,7 @@ struct BuildArgs {
                             // 1 FP16 halves, 2 BF16 halves
   unsigned int spin_limit;  // bounded waits: iterations before giving up (0: the default)
   unsigned int inject;      // test hooks (kInject*), 0 in normal use
+  int skip_tail;            // kSkipDense | kSkipLongRows: kernels left out of this launch
 };
 
 // The key kernel with one thread per (point, grid) serves instances that share d <= 6.

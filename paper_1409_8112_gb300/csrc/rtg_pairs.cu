@@ -401,7 +401,8 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
     const float* __restrict__ pf, int dtype, const K* __restrict__ key_mat, int m,
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const unsigned long long* __restrict__ bases, int nbt, Status* st, Sink sk,
-    LargeCell* large, unsigned int large_cap, int warp_bytes, unsigned int* span_next) {
+    LargeCell* large, unsigned int large_cap, int warp_bytes, unsigned int* span_next,
+    int skip_dense) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned int s_maxcell;
@@ -501,6 +502,8 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
           const long long e = run_end(skeys, N, P0 + pn, kc);
           lend = (int)min(e - P0, (long long)INT_MAX);
           if (MODE != kWrite) {
+            // the dense-cell kernels were left out of this launch: the host runs it again
+            if (skip_dense) atomicOr(&st->errors, kErrTailSkipped);
             const unsigned long long size = (unsigned long long)(e - (P0 + p));
             const unsigned long long slot = atomicAdd(&st->large_cells, 1ull);
             if (slot < large_cap) {
@@ -1400,14 +1403,22 @@ constexpr int kWarpRowMax = 256;  // rows up to this length are sorted by one wa
 __global__ void __launch_bounds__(256) k_rowsort_thread(const OutSlot* out, long long n,
                                                         unsigned int* row_queue,
                                                         unsigned int* mid_count,
-                                                        unsigned int* long_count) {
+                                                        unsigned int* long_count,
+                                                        unsigned int* errors, int skip_long,
+                                                        unsigned int* rows_over_margin) {
   const long long* __restrict__ row_ptr = out->row_ptr;
   int* col = out->col;
   const long long col_cap = out->col_cap;
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long b = row < n ? row_ptr[row] : 0, len = row < n ? row_ptr[row + 1] - b : 0;
+  // a row near the queued sorts' threshold keeps them in the next build of the shape (one
+  // atomic for a warp that has one)
+  if (__any_sync(0xffffffffu, len > kSkipMargin) && (threadIdx.x & 31) == 0)
+    atomicOr(rows_over_margin, 1u);
   if (row >= n) return;
-  const long long b = row_ptr[row], len = row_ptr[row + 1] - b;
   if (len <= 1 || b + len > col_cap) return;
+  // the queued row sorts were left out of this launch: the host runs it again
+  if (skip_long && len > 32) atomicOr(errors, kErrTailSkipped);
   if (len > kWarpRowMax) {
     row_queue[n - 1 - atomicAdd(long_count, 1u)] = (unsigned int)row;
     return;
@@ -1773,7 +1784,8 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(
       sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
       a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes,
-      &a.st->span_next[MODE == kWrite ? 1 : 0]);
+      &a.st->span_next[MODE == kWrite ? 1 : 0], (a.skip_tail & kSkipDense) ? 1 : 0);
+  if (a.skip_tail & kSkipDense) return;  // (k_pairs_warp flags any dense cell it meets)
   {
     const size_t msmem =
         (size_t)kMediumWarps * kMediumMax * (DPAD * 4 + 4) + (size_t)kMediumWarps * kMediumKeyBytes;
@@ -1816,11 +1828,12 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
 
 template <typename K, int DPAD>
 int pairs_impl(const BuildArgs& a, int sorted_buf, Mode mode, cudaStream_t s) {
+  const bool dense = !(a.skip_tail & kSkipDense);
   switch (mode) {
-    case kCount: pairs_mode<K, DPAD, kCount>(a, sorted_buf, s); return 4;
-    case kWrite: pairs_mode<K, DPAD, kWrite>(a, sorted_buf, s); return 3;
-    case kBits: pairs_mode<K, DPAD, kBits>(a, sorted_buf, s); return 4;
-    default: pairs_mode<K, DPAD, kEmit>(a, sorted_buf, s); return 4;
+    case kCount: pairs_mode<K, DPAD, kCount>(a, sorted_buf, s); return dense ? 4 : 1;
+    case kWrite: pairs_mode<K, DPAD, kWrite>(a, sorted_buf, s); return dense ? 3 : 1;
+    case kBits: pairs_mode<K, DPAD, kBits>(a, sorted_buf, s); return dense ? 4 : 1;
+    default: pairs_mode<K, DPAD, kEmit>(a, sorted_buf, s); return dense ? 4 : 1;
   }
 }
 
@@ -1968,7 +1981,10 @@ int launch_rowsort(const BuildArgs& a, cudaStream_t s, long long col_bound) {
   const unsigned blocks = (unsigned)((a.n_total + 255) / 256);
   unsigned int* long_count = &a.st->long_rows;
   unsigned int* mid_count = &a.st->mid_rows;
-  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, mid_count, long_count);
+  const int skip_long = (a.skip_tail & kSkipLongRows) ? 1 : 0;
+  k_rowsort_thread<<<blocks, 256, 0, s>>>(a.out, a.n_total, a.row_cnt, mid_count, long_count,
+                                          &a.st->errors, skip_long, &a.st->rows_over_margin);
+  if (skip_long) return 1;
   static bool attr[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);

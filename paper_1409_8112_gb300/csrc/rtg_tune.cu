@@ -245,6 +245,7 @@ rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg,
   constexpr int kCands = 9;
   const cudaStream_t st = c->stream;
   rtg::BuildArgs b = a;
+  b.skip_tail = 0;  // every kernel of the enumeration is timed
   b.sort_bits = cfg.bits;
   b.sort_items = cfg.items;
   b.sort_mode = cfg.mode;

@@ -341,9 +341,8 @@ def test_two_pass_mode_matches(ctx):
 
 @pytest.mark.parametrize("symmetric,timing", [(False, False), (True, False), (False, True)])
 def test_launch_assumptions_are_corrected(symmetric, timing):
-    # same shape, far more pairs the second time: the cached pair-buffer size is too small;
-    # the rows are still counted and placed, and a second enumeration writes the columns
-    # into them (no second build); the next build of the shape takes the corrected size
+    # same shape, far more pairs (and dense cells) the second time: the build runs again with
+    # the corrected launch decisions; the next build of the shape takes them at once
     ctx = rtg.Context(0)
     n, d, m = 6000, 3, 4
     r = 0.05
@@ -355,12 +354,60 @@ def test_launch_assumptions_are_corrected(symmetric, timing):
     ra = ctx.all_pairs(a, r, T, r, symmetric=symmetric)
     for k in range(2):
         rb = ctx.all_pairs(b, r, T, r, symmetric=symmetric, timing=timing)
-        assert rb.stats["attempts"] == (2 if k == 0 else 1)
+        # the first build of b runs again with the dense-cell kernels (which a uniform build
+        # of the shape left out), and may then recover an undersized pair buffer
+        assert rb.stats["attempts"] in (2, 3) if k == 0 else rb.stats["attempts"] == 1
         got = rb.download()
         assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
         assert rb.stats["pairs"] == ref.nnz
         rb.release()
     ra.release()
+    ctx.close()
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_overflowed_pair_buffer_is_recovered_without_a_rebuild(symmetric):
+    # a shape first built on clustered points (its dense-cell kernels stay in the launch), then
+    # on denser clustered points: only the pair buffer is too small, so the rows counted by the
+    # enumeration are placed and a second enumeration writes the columns into them
+    ctx = rtg.Context(0)
+    n, d, m = 6000, 3, 4
+    r = 0.05
+    T = gen.transforms(8, d, m, r)
+    a = gen.points_mixture(8, n, d, k=2, sigma=0.02, dtype=np.float64)
+    b = gen.points_mixture(9, n, d, k=2, sigma=0.006, dtype=np.float64)
+    ref = oracle.rtg(b, r, T, r).csr
+    want = symmetric_of(ref, n) if symmetric else (ref.row_ptr, ref.col)
+    ra = ctx.all_pairs(a, r, T, r, symmetric=symmetric)
+    assert ra.stats["large_cells"] > 0
+    rb = ctx.all_pairs(b, r, T, r, symmetric=symmetric)
+    assert rb.stats["attempts"] == 2 and rb.stats["pairs"] > 2 * ra.stats["pairs"]
+    got = rb.download()
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    ra.release()
+    rb.release()
+    ctx.close()
+
+
+def test_kernels_left_out_come_back_when_work_turns_up():
+    # uniform points leave the dense-cell kernels and the queued row sorts out of the next
+    # build of the shape; clustered points of that shape bring them back (the kernels before
+    # them flag the work and the build runs again), and the result is exact either way
+    ctx = rtg.Context(0)
+    n, d, m = 20000, 3, 4
+    r = 0.02
+    T = gen.transforms(10, d, m, r)
+    u = gen.points_uniform(10, n, d)
+    c = gen.points_mixture(10, n, d, k=2, sigma=0.01, dtype=np.float64)
+    for pts, first in ((u, True), (u, False), (c, False), (c, False), (u, False)):
+        res = ctx.all_pairs(pts, r, T, r)
+        got = res.download()
+        st = res.stats
+        res.release()
+        ref = oracle.rtg(pts, r, T, r).csr
+        assert np.array_equal(got[0], ref.row_ptr) and np.array_equal(got[1], ref.col)
+        if pts is u and not first:
+            assert st["max_cell"] <= 24
     ctx.close()
 
 

@@ -177,7 +177,7 @@ def measured_peaks():
 NCU_TRAFFIC = {
     # k_pairs_warp, one launch (the medium and tiled kernels of the phase move under 1 MB)
     (100000, "fp64"): {"pairs": 13242112},
-    (1000000, "fp32"): {"pairs": 331776256},
+    (1000000, "fp32"): {"pairs": 331525632},
 }
 
 

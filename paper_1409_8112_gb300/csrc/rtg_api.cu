@@ -279,6 +279,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   // ---- instance table and packed transforms (host) ----
   c->h_inst.assign(B, Inst{});
   long long p0 = 0, blk0 = 0, pblk0 = 0, T0 = 0, bits_words = 0;
+  long long n_sum = 0;
+  for (int b = 0; b < B; ++b) n_sum += q.items[b].n;
+  const int prep_pts = rtg::prep_points_for(n_sum);
   const bool bitset = (q.flags & RTG_FLAG_BITSET) != 0 && m > 0;
   int maxd = 1, mind = RTG_MAX_DIM;
   for (int b = 0; b < B; ++b) {
@@ -300,7 +303,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     bits_words += it.n * (long long)I.bits_w;
     p0 += it.n;
     blk0 += (it.n + rtg::kPointBlock - 1) / rtg::kPointBlock;
-    pblk0 += (it.n + rtg::kPrepPoints - 1) / rtg::kPrepPoints;
+    pblk0 += (it.n + prep_pts - 1) / prep_pts;
     T0 += (long long)m * (it.d * it.d + it.d);
     maxd = std::max(maxd, it.d);
     mind = std::min(mind, it.d);
@@ -402,6 +405,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.n_total = n_total;
   a.blocks = blk0;
   a.pblocks = pblk0;
+  a.prep_points = prep_pts;
   a.inst = (const Inst*)c->inst.p;
   a.iplan = (InstPlan*)c->iplan.p;
   a.gplan = (GridPlan*)c->gplan.p;

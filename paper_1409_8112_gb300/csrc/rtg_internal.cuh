@@ -41,7 +41,12 @@ __host__ __device__ inline int sort_passes_for(int key_bits, int radix_bits) {
 }
 constexpr int kPointBlock = 128;   // points per block in the per-point kernels
 constexpr int kPrepThreads = 256;
-constexpr int kPrepPoints = 256;   // points per block in the prep kernel
+constexpr int kPrepPoints = 256;   // points per block in the prep kernel (at least; a multiple)
+// Large builds give each prep block more points: fewer blocks adding their bounds to the
+// bounding box (1M points: 37 against 47 us); small ones keep one point per thread.
+__host__ __device__ inline int prep_points_for(long long n_total) {
+  return n_total >= (1LL << 19) ? 4 * kPrepPoints : kPrepPoints;
+}
 
 // Bits of Status::errors.
 enum : uint32_t {
@@ -235,7 +240,8 @@ struct BuildArgs {
   int symmetric;
   long long n_total;  // sum of n
   long long blocks;   // per-point kernel blocks (sum of ceil(n / kPointBlock))
-  long long pblocks;  // prep blocks (sum of ceil(n / kPrepPoints))
+  long long pblocks;  // prep blocks (sum of ceil(n / prep_points))
+  int prep_points;    // points per prep block: prep_points_for(n_total), a multiple of 256
   const Inst* inst;   // device, B entries
   InstPlan* iplan;    // device, B entries
   GridPlan* gplan;    // device, B * m entries

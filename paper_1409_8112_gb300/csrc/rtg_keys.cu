@@ -56,7 +56,8 @@ __device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, G
 // Plan arguments for the prep kernel's last block (small batches plan there, saving two
 // launches on the build's critical path).
 struct PlanArgs {
-  int fuse;  // 1: the last block to finish runs the plan
+  int fuse;    // 1: the last block to finish runs the plan
+  int points;  // points per block (a multiple of the block size)
   int m;
   const double* T64;
   InstPlan* iplan;
@@ -66,7 +67,8 @@ struct PlanArgs {
 };
 
 // FP32 rows of the points, zeroed row counters and the per-instance bounding box;
-// kPrepPoints points per block so that each block adds one bound per axis.
+// pa.points points per block (one or four per thread), so that each block adds one bound per
+// axis.
 template <int DPAD>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ inst, int B,
                                                        int dtype, float* __restrict__ pf,
@@ -92,8 +94,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
     mn[l] = FLT_MAX;
     mx[l] = -FLT_MAX;
   }
-  const long long base = (blockIdx.x - I.pblk0) * (long long)kPrepPoints;
-  for (int q = 0; q < kPrepPoints / kPrepThreads; ++q) {
+  const long long base = (blockIdx.x - I.pblk0) * (long long)pa.points;
+  for (int q = 0; q < pa.points / kPrepThreads; ++q) {
     const long long i = base + q * kPrepThreads + threadIdx.x;
     if (i >= I.n) break;
     float row[DPAD];
@@ -543,6 +545,7 @@ template <int DPAD>
 void prep_impl(const BuildArgs& a, cudaStream_t s) {
   PlanArgs pa;
   pa.fuse = plan_fused(a) ? 1 : 0;
+  pa.points = a.prep_points > 0 ? a.prep_points : kPrepPoints;
   pa.m = a.m;
   pa.T64 = a.T64;
   pa.iplan = a.iplan;

@@ -82,6 +82,7 @@ extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int
   a.dpad = rtg::dpad_for(d);
   a.n_total = n;
   a.blocks = (n + rtg::kPointBlock - 1) / rtg::kPointBlock;
+  a.prep_points = rtg::kPrepPoints;
   a.pblocks = (n + rtg::kPrepPoints - 1) / rtg::kPrepPoints;
   a.st = (rtg::Status*)p;
   a.inst = (const rtg::Inst*)(p + kStatusBytes);

@@ -27,6 +27,17 @@
  * Errors: every entry point returns an rtg_status; nothing is thrown across the ABI.
  * rtg_last_error() gives a text for the last failure on a context.  One context serialises
  * its synchronous calls on its own stream; distinct contexts are independent.
+ *
+ * Environment, read when a context is created (none changes a result):
+ *   RTG_TUNE_CACHE=path       JSON file that keeps the autotuner's sort choices per device
+ *   RTG_AUTOTUNE=0            take the default sort variant and enumeration knobs
+ *   RTG_SORT_VARIANT=b,i,m    force a sort variant: digit bits, keys per thread, strategy
+ *                             (0 look-back, 1 reduce-then-scan, 2 one cooperative launch)
+ *   RTG_TUNE_PAIRS_MAX_CAND=x in-cell candidates above which the enumeration keeps its
+ *                             default knobs (4e9)
+ *   RTG_GRAPHS=0              launch every kernel directly instead of replaying CUDA graphs
+ *   RTG_SERVE_LANES=k         concurrent server lanes (1 to 8, default 2)
+ *   RTG_SERVE_LOG=1           one line per served batch on stderr
  */
 #ifndef RTG_H
 #define RTG_H

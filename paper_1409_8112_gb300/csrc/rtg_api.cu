@@ -340,11 +340,10 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   }
 
   // ---- workspace ----
-  const size_t stat_bytes = (sizeof(Status) + 255) & ~size_t(255);
-  if ((s = ensure(c, c->status, stat_bytes)) != RTG_OK) return s;
+  const size_t bbox_bytes = sizeof(unsigned long long) * B * rtg::kMaxDim * 2;
+  if ((s = ensure(c, c->status, kStatusBytes + bbox_bytes)) != RTG_OK) return s;
   if ((s = ensure(c, c->inst, sizeof(Inst) * B)) != RTG_OK) return s;
   if ((s = ensure(c, c->iplan, sizeof(InstPlan) * B)) != RTG_OK) return s;
-  if ((s = ensure(c, c->bbox, sizeof(unsigned long long) * B * rtg::kMaxDim * 2)) != RTG_OK) return s;
   if (m > 0) {
     if ((s = ensure(c, c->gplan, sizeof(GridPlan) * (size_t)B * m)) != RTG_OK) return s;
     if ((s = ensure(c, c->bases, sizeof(unsigned long long) * ((size_t)B * m + 1))) != RTG_OK) return s;
@@ -410,7 +409,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.iplan = (InstPlan*)c->iplan.p;
   a.gplan = (GridPlan*)c->gplan.p;
   a.bases = (unsigned long long*)c->bases.p;
-  a.bbox = (unsigned long long*)c->bbox.p;
+  a.bbox = bbox_of(c);
   a.T64 = (const double*)c->T64.p;
   a.st = (Status*)c->status.p;
   a.pf = (float*)c->pf.p;
@@ -438,8 +437,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     a.skip_tail = 0;
     if (m > 0 && !known && attempt == 0) {
       // first build of this shape: read the key width back once
-      RTG_CUDA(c, cudaMemsetAsync(a.st, 0, sizeof(Status), st));
-      RTG_CUDA(c, cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st));
+      RTG_CUDA(c, cudaMemsetAsync(a.st, 0, kStatusBytes + bbox_bytes, st));  // and the boxes
       a.passes = rtg::sort_passes_for(64, 8);
       a.sort_bits = 8;
       rtg::launch_prep_plan(a, st);
@@ -578,8 +576,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     auto front = [&]() -> int {
       int l = 0;
       if (timing) mark(0);
-      cudaMemsetAsync(a.st, 0, sizeof(Status), st);
-      cudaMemsetAsync(a.bbox, 0, sizeof(unsigned long long) * B * rtg::kMaxDim * 2, st);
+      cudaMemsetAsync(a.st, 0, kStatusBytes + bbox_bytes, st);  // counters and bounding boxes
       l += rtg::launch_prep_plan(a, st);
       if (timing) mark(1);
       if (m > 0) {
@@ -1020,7 +1017,7 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
   }
   for (auto& ev : c->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e);
-  rtg_status s = ensure(c, c->status, (sizeof(Status) + 255) & ~size_t(255), true);
+  rtg_status s = ensure(c, c->status, kStatusBytes, true);
   if (s != RTG_OK) {
     std::string msg = c->err;
     destroy_ctx(c);
@@ -1048,7 +1045,7 @@ void destroy_ctx(rtg_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   DevBuf* bufs[] = {&c->status,    &c->inst,      &c->iplan,   &c->gplan,   &c->bases,
-                    &c->bbox,      &c->T64,       &c->pts,     &c->pf,      &c->key_mat,
+                    &c->T64,       &c->pts,       &c->pf,      &c->key_mat,
                     &c->keys0,     &c->keys1,     &c->vals0,   &c->vals1,   &c->lookback,
                     &c->hist,      &c->digit_off, &c->row_cnt, &c->scan_lb, &c->large,
                     &c->large_job, &c->pair_buf,  &c->tc_tiles, &c->tc_norms, &c->tc_plan};

@@ -103,7 +103,7 @@ struct rtg_ctx {
   std::mutex mu;       // one build at a time
   std::mutex live_mu;  // output bookkeeping (live, out_bytes)
   std::string err;
-  rtghost::DevBuf status, inst, iplan, gplan, bases, bbox, T64, pts, pf, key_mat, keys0, keys1,
+  rtghost::DevBuf status, inst, iplan, gplan, bases, T64, pts, pf, key_mat, keys0, keys1,
       vals0, vals1, lookback, hist, digit_off, row_cnt, scan_lb, large, large_job, pair_buf,
       tc_tiles, tc_norms, tc_plan, out_slot, sort_epoch, q_idx, bits;
   rtg::Status* h_status = nullptr;  // pinned
@@ -150,6 +150,13 @@ struct rtg_ctx {
 
 namespace rtghost {
 
+// The status buffer holds the Status counters, then the bounding boxes of the build's
+// instances (zeroed together, by one memset, at the start of every build).
+constexpr size_t kStatusBytes = (sizeof(rtg::Status) + 255) & ~size_t(255);
+inline unsigned long long* bbox_of(rtg_ctx* c) {
+  return reinterpret_cast<unsigned long long*>(static_cast<char*>(c->status.p) + kStatusBytes);
+}
+
 rtg_status fail(rtg_ctx* ctx, rtg_status s, const std::string& msg);
 std::string& last_error_text();
 // Output memory of ctx's pool, ordered on stream s; counted in ctx's out_bytes.
@@ -173,8 +180,8 @@ void notify_server(rtg_ctx* c);  // memory was released: waiting requests are co
 // tiles fit in about three waves.
 rtg::SortConfig sort_default(long long N, int num_sms);
 // Sorts the keys of `a` (regenerated by the key kernel before every trial) with every compiled
-// variant and strategy, twice, and returns the fastest; records it in the context's table and
-// JSON cache.  Needs a's buffers sized for any variant.
+// variant and strategy, five times, and returns the one with the lowest median time; records
+// it in the context's table and JSON cache.  Needs a's buffers sized for any variant.
 rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
                      rtg::SortConfig* out);
 // Times the in-cell enumeration of a's keys (sorted with cfg) for each (spans per warp,

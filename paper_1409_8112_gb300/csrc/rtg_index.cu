@@ -560,7 +560,7 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
       (s = copy(ix->T64, c->T64.p, sizeof(double) * (size_t)m * (it.d * it.d + it.d),
                 cudaMemcpyDeviceToDevice)) != RTG_OK ||
       (s = copy(ix->inst, &I, sizeof(I), cudaMemcpyHostToDevice)) != RTG_OK ||
-      (s = copy(hb, c->bbox.p, sizeof(hb), cudaMemcpyDeviceToHost)) != RTG_OK ||
+      (s = copy(hb, bbox_of(c), sizeof(hb), cudaMemcpyDeviceToHost)) != RTG_OK ||
       (s = cuda_ok(c, cudaMemsetAsync(ix->table, 0xff, sizeof(unsigned long long) * (size_t)cap * m,
                                       st),
                    "index table")) != RTG_OK ||

@@ -23,7 +23,13 @@ namespace rtghost {
 
 namespace {
 
-constexpr int kTuneReps = 2;
+constexpr int kTuneReps = 5;  // trials per candidate; the median decides (noise-robust)
+
+double median_of(std::vector<double> v) {
+  if (v.empty()) return 1e30;
+  std::sort(v.begin(), v.end());
+  return v[v.size() / 2];
+}
 
 // Every compiled variant; the single-launch strategy only where all of its tiles can be
 // resident at once (num_sms = 0: every variant, for sizing the scratch).
@@ -210,16 +216,16 @@ rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
     cudaEventRecord(ev[2 * (size_t)t + 1], st);
   }
   cudaError_t e = cudaStreamSynchronize(st);
-  std::vector<double> best(cands.size(), 1e30);
+  std::vector<std::vector<double>> samples(cands.size());
   if (e == cudaSuccess) {
     for (int t = 0; t < trials; ++t) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev[2 * (size_t)t], ev[2 * (size_t)t + 1]) == cudaSuccess) {
-        double& b = best[(size_t)t % cands.size()];
-        b = std::min(b, (double)ms * 1e3);
-      }
+      if (cudaEventElapsedTime(&ms, ev[2 * (size_t)t], ev[2 * (size_t)t + 1]) == cudaSuccess)
+        samples[(size_t)t % cands.size()].push_back((double)ms * 1e3);
     }
   }
+  std::vector<double> best(cands.size());
+  for (size_t i = 0; i < cands.size(); ++i) best[i] = median_of(samples[i]);
   for (auto& x : ev) cudaEventDestroy(x);
   if (e != cudaSuccess)
     return fail(c, RTG_E_CUDA, std::string("tune: ") + cudaGetErrorString(e));
@@ -287,16 +293,17 @@ rtg_status tune_pairs(rtg_ctx* c, rtg::BuildArgs& a, const rtg::SortConfig& cfg,
       cudaEventRecord(ev[2 * (rep * kCands + k) + 1], st);
     }
   cudaError_t e = cudaStreamSynchronize(st);
-  double best[kCands];
-  for (double& x : best) x = 1e30;
+  std::vector<std::vector<double>> samples(kCands);
   if (e == cudaSuccess)
     for (int rep = 0; rep < kTuneReps; ++rep)
       for (int k = 0; k < kCands; ++k) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ev[2 * (rep * kCands + k)], ev[2 * (rep * kCands + k) + 1]) ==
             cudaSuccess)
-          best[k] = std::min(best[k], (double)ms);
+          samples[k].push_back((double)ms);
       }
+  double best[kCands];
+  for (int k = 0; k < kCands; ++k) best[k] = median_of(samples[k]);
   for (auto& x : ev) cudaEventDestroy(x);
   if (e != cudaSuccess) return fail(c, RTG_E_CUDA, std::string("tune: ") + cudaGetErrorString(e));
   int k = 0;

@@ -261,12 +261,13 @@ rtg_status rtg_brute_force(rtg_ctx* ctx, const void* points, int dtype, int poin
  * up to 65536 points with d <= 16, row counts), held by every GPU that loads the library
  * until the process exits.  The first call on a device, with that device current, looks up
  * the array's device address; that first call must come before any stream capture.  Every
- * call synchronises `stream` and copies the count back to host memory before it returns.
+ * call synchronises `stream` and copies the count back to host memory before it returns, so
+ * no call can be made inside a stream capture (RTG_E_INVALID when `stream` is capturing).
  * Every call on a device shares the array and leaves its contents behind: calls that overlap
  * on the GPU (from different streams or threads) race and give undefined counts.  Nothing
  * here calls cudaMalloc, cudaFree or an allocating library routine.
  * Errors: RTG_E_INVALID (n > 65536, d outside [1,16], r not positive and finite, NULL
- * pointers, a non-finite coordinate), RTG_E_CUDA, RTG_E_TIMEOUT; text via
+ * pointers, a non-finite coordinate, a capturing stream), RTG_E_CUDA, RTG_E_TIMEOUT; text via
  * rtg_last_error(NULL). */
 rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int64_t n, int d, double r,
                                    void* stream, uint64_t* count);

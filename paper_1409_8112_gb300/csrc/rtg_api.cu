@@ -341,7 +341,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
 
   // ---- workspace ----
   const size_t bbox_bytes = sizeof(unsigned long long) * B * rtg::kMaxDim * 2;
-  if ((s = ensure(c, c->status, kStatusBytes + bbox_bytes)) != RTG_OK) return s;
+  // counters, bounding boxes and the scan's look-back words, zeroed by one memset per build
+  const size_t front_bytes = kStatusBytes + bbox_bytes + rtg::scan_lookback_bytes(n_total);
+  if ((s = ensure(c, c->status, front_bytes)) != RTG_OK) return s;
   if ((s = ensure(c, c->inst, sizeof(Inst) * B)) != RTG_OK) return s;
   if ((s = ensure(c, c->iplan, sizeof(InstPlan) * B)) != RTG_OK) return s;
   if (m > 0) {
@@ -351,7 +353,6 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   }
   if ((s = ensure(c, c->pf, (size_t)n_total * dpad * 4)) != RTG_OK) return s;
   if ((s = ensure(c, c->row_cnt, (size_t)n_total * 4)) != RTG_OK) return s;
-  if ((s = ensure(c, c->scan_lb, ((size_t)n_total / 4096 + 2) * 8)) != RTG_OK) return s;
   if ((s = ensure(c, c->out_slot, sizeof(rtg::OutSlot))) != RTG_OK) return s;
   if (bitset && (s = ensure(c, c->bits, (size_t)bits_words * 4)) != RTG_OK) return s;
   if ((s = ensure(c, c->sort_epoch, sizeof(unsigned int), true)) != RTG_OK) return s;
@@ -414,7 +415,9 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
   a.st = (Status*)c->status.p;
   a.pf = (float*)c->pf.p;
   a.row_cnt = (unsigned int*)c->row_cnt.p;
-  a.scan_lookback = (unsigned long long*)c->scan_lb.p;
+  a.scan_lookback =
+      reinterpret_cast<unsigned long long*>((char*)c->status.p + kStatusBytes + bbox_bytes);
+  a.scan_zeroed = 1;  // every build path zeroes them with the counters and scans once
   a.out = (const rtg::OutSlot*)c->out_slot.p;
   a.bits = bitset ? (unsigned int*)c->bits.p : nullptr;
   a.sort_epoch = (unsigned int*)c->sort_epoch.p;
@@ -576,7 +579,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     auto front = [&]() -> int {
       int l = 0;
       if (timing) mark(0);
-      cudaMemsetAsync(a.st, 0, kStatusBytes + bbox_bytes, st);  // counters and bounding boxes
+      cudaMemsetAsync(a.st, 0, front_bytes, st);  // counters, boxes, scan look-back words
       l += rtg::launch_prep_plan(a, st);
       if (timing) mark(1);
       if (m > 0) {

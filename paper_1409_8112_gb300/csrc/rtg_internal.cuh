@@ -281,7 +281,16 @@ struct BuildArgs {
   unsigned int spin_limit;  // bounded waits: iterations before giving up (0: the default)
   unsigned int inject;      // test hooks (kInject*), 0 in normal use
   int skip_tail;            // kSkipDense | kSkipLongRows: kernels left out of this launch
+  int scan_zeroed;          // the scan's look-back words were zeroed with the counters
 };
+
+// Row-count scan: 16 counts per thread, 256 threads per tile, one 8-byte look-back word per
+// tile.
+constexpr int kScanItems = 16;
+constexpr int kScanTile = 256 * kScanItems;
+inline size_t scan_lookback_bytes(long long n_total) {
+  return (size_t)((n_total + kScanTile - 1) / kScanTile + 1) * 8;
+}
 
 // The key kernel with one thread per (point, grid) serves instances that share d <= 6.
 inline bool keys_by_lanes(const BuildArgs& a) {

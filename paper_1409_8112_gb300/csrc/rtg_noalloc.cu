@@ -53,6 +53,14 @@ extern "C" rtg_status rtg_brute_count_noalloc(const void* points, int dtype, int
   if (n > 0 && !points) return fail(RTG_E_INVALID, "points is NULL");
   *count = 0;
   if (n < 2) return RTG_OK;
+  {
+    // the call synchronises its stream and reads the count back, neither of which a stream
+    // capture allows
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+      return fail(RTG_E_INVALID, "rtg_brute_count_noalloc cannot run inside a stream capture");
+  }
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)

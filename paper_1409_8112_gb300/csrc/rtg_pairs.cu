@@ -1203,9 +1203,6 @@ __global__ void __launch_bounds__(kPairThreads) k_brute(const float* __restrict_
 // counts are reset to zero so that the scatter or WRITE pass can use them as fill cursors.
 // Each thread holds 16 consecutive counts (vector loads and stores); the first warp of a tile
 // looks back over 32 predecessor tiles at a time, one per lane.
-constexpr int kScanItems = 16;
-constexpr int kScanTile = 256 * kScanItems;
-
 __global__ void __launch_bounds__(256) k_scan(unsigned int* row_cnt, const OutSlot* out,
                                               long long n, unsigned long long* lookback,
                                               unsigned int* tile_counter, Status* st,
@@ -1884,7 +1881,7 @@ int launch_brute(const BuildArgs& a, Mode mode, cudaStream_t s) {
 
 void launch_scan(const BuildArgs& a, cudaStream_t s) {
   const unsigned tiles = (unsigned)((a.n_total + kScanTile - 1) / kScanTile);
-  cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
+  if (!a.scan_zeroed) cudaMemsetAsync(a.scan_lookback, 0, (size_t)tiles * 8, s);
   k_scan<<<tiles, 256, 0, s>>>(a.row_cnt, a.out, a.n_total, a.scan_lookback,
                                &a.st->scan_tiles, a.st, tiles, spin_limit_of(a.spin_limit),
                                a.inject);

@@ -55,3 +55,33 @@ def test_noalloc_count_matches_the_cpu_oracle():
     torch.cuda.synchronize()
     got = rtg.rtg_brute_count_noalloc(dev.data_ptr(), rtg.RTG_DTYPE_F64, n, d, r)
     assert got == oracle.brute(pts, r).nnz > 0
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    import torch
+
+    # the call synchronises its stream and reads the count back, so inside a capture it must
+    # refuse before it issues anything (the capture itself stays valid)
+    n, d = 2000, 4
+    pts = gen.points_uniform(12, n, d)
+    r = gen.radius_for_degree(n, d, 10.0)
+    dev = torch.from_numpy(pts).cuda()
+    side = torch.zeros(16, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = []
+    with torch.cuda.graph(g, stream=s):
+        side.add_(1.0)
+        try:
+            rtg.rtg_brute_count_noalloc(dev.data_ptr(), rtg.RTG_DTYPE_F64, n, d, r, s.cuda_stream)
+            status.append(rtg.RTG_OK)
+        except rtg.RTGError as e:
+            status.append(e.status)
+    g.replay()
+    torch.cuda.synchronize()
+    assert status == [rtg.RTG_E_INVALID]
+    assert float(side[0]) == 1.0
+    # outside the capture the same call counts as before
+    got = rtg.rtg_brute_count_noalloc(dev.data_ptr(), rtg.RTG_DTYPE_F64, n, d, r)
+    assert got == oracle.brute(pts, r).nnz > 0

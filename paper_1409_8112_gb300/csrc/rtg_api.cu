@@ -642,11 +642,17 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       // the whole build as one fixed launch sequence, ending with the status copy-back
       auto emit_build = [&]() -> int {
         int l = 0;
+        // the scan is the first reader of the output slot: its copy runs on the side stream
+        // beside the front and the enumeration, and joins before the scan
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         cudaMemcpyAsync(c->out_slot.p, c->h_slot, sizeof(rtg::OutSlot), cudaMemcpyHostToDevice,
-                        st);
+                        c->side);
+        cudaEventRecord(c->ev_join, c->side);
         l += front();
         l += pairs(rtg::kEmit);
         if (timing) mark(4);
+        cudaStreamWaitEvent(st, c->ev_join, 0);
         rtg::launch_scan(a, st);
         l += 1;
         if (timing) mark(5);
@@ -1020,6 +1026,10 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
   }
   for (auto& ev : c->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(e);
+  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e);
   rtg_status s = ensure(c, c->status, kStatusBytes, true);
   if (s != RTG_OK) {
     std::string msg = c->err;
@@ -1061,6 +1071,9 @@ void destroy_ctx(rtg_ctx* c) {
   if (c->h_slot) cudaFreeHost(c->h_slot);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);  // outstanding CSRs go with it

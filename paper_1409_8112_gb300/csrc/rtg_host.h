@@ -113,6 +113,9 @@ struct rtg_ctx {
   cudaMemPool_t pool = nullptr;     // output CSRs (stream ordered, kept cached)
   bool own_pool = true;             // false: a serving lane drawing on its owner's pool
   cudaEvent_t ev[8] = {};
+  // the output-slot copy runs on a second stream beside the front of the build
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t ws_bytes = 0;
   size_t ws_need = 0;  // workspace bytes the current build asked for (at most ws_bytes)
   size_t out_bytes = 0;

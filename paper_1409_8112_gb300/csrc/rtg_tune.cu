@@ -1,12 +1,13 @@
 // Autotuner of the radix sort: digit width (8, 9, 10 or 11 bits per pass), tile size (256 x 8, 12
 // or 16 keys) and pass strategy (look-back, reduce-then-scan, or all passes in one cooperative
-// launch when every tile fits on the GPU at once).  On the first build of a
-// shape whose sort is large enough to matter it times every variant twice on the build's own
-// keys and keeps the fastest, per (sorted elements, key bits), in the context and, when
-// RTG_TUNE_CACHE names a file, in a JSON cache shared by later contexts and processes.  The same
-// first build also times the in-cell enumeration over spans per warp {1, 2, 4} and the
-// dense-cell threshold {64, 128, 256} on the sorted keys and keeps the fastest (in the
-// context).
+// launch when every tile fits on the GPU at once).  On the second build of a
+// shape it times every variant five times on the build's own keys, each as a replayed CUDA
+// graph (the form the build runs it in, so that variants of several launches are not charged
+// the gaps of direct launches), and keeps the lowest median, per (sorted elements, key bits),
+// in the context and, when RTG_TUNE_CACHE names a file, in a JSON cache shared by later
+// contexts and processes.  The same build also times the in-cell enumeration over spans per
+// warp {1, 2, 4} and the dense-cell threshold {64, 128, 256} on the sorted keys and keeps the
+// fastest (in the context).
 // The sort is stable in every variant, so the choice never changes a result.
 #include <cuda_runtime.h>
 
@@ -194,15 +195,26 @@ void tune_load(rtg_ctx* c) {
 rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
                      rtg::SortConfig* out) {
   const std::vector<rtg::SortConfig> cands = candidates(N, a.num_sms, a.key64);
-  const int trials = (int)cands.size() * kTuneReps;
-  std::vector<cudaEvent_t> ev(2 * (size_t)trials, nullptr);
+  const size_t nc = cands.size();
+  std::vector<cudaEvent_t> ev(2 * nc, nullptr);
+  std::vector<cudaGraphExec_t> exec(nc, nullptr);
+  auto release = [&]() {
+    for (auto& x : exec)
+      if (x) cudaGraphExecDestroy(x);
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+  };
   for (auto& e : ev)
-    if (cudaEventCreate(&e) != cudaSuccess)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      release();
       return fail(c, RTG_E_CUDA, "tune: cudaEventCreate failed");
+    }
   const cudaStream_t st = c->stream;
   const rtg::BuildArgs base = a;
-  for (int t = 0; t < trials; ++t) {
-    const rtg::SortConfig& cfg = cands[(size_t)t % cands.size()];
+  // one trial of candidate i: the keys (the sort consumes its input buffers), then the sort
+  // between two event records; inside a capture the records become event nodes
+  auto trial = [&](size_t i, bool captured) {
+    const rtg::SortConfig& cfg = cands[i];
     rtg::BuildArgs b = base;
     b.sort_bits = cfg.bits;
     b.sort_items = cfg.items;
@@ -210,23 +222,49 @@ rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
     b.passes = rtg::sort_passes_for(key_bits, cfg.bits);
     cudaMemsetAsync(&b.st->sort_tiles[0], 0, sizeof(b.st->sort_tiles), st);
     cudaMemsetAsync(&b.st->coop_count, 0, 2 * sizeof(unsigned int), st);
-    rtg::launch_keys(b, st);  // the sort consumes its input buffers
-    cudaEventRecord(ev[2 * (size_t)t], st);
+    rtg::launch_keys(b, st);
+    if (captured) cudaEventRecordWithFlags(ev[2 * i], st, cudaEventRecordExternal);
+    else cudaEventRecord(ev[2 * i], st);
     rtg::launch_sort(b, st);
-    cudaEventRecord(ev[2 * (size_t)t + 1], st);
+    if (captured) cudaEventRecordWithFlags(ev[2 * i + 1], st, cudaEventRecordExternal);
+    else cudaEventRecord(ev[2 * i + 1], st);
+  };
+  if (c->use_graphs) {
+    for (size_t i = 0; i < nc; ++i) {
+      cudaGetLastError();
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) break;
+      trial(i, true);
+      cudaGraph_t g = nullptr;
+      if (cudaStreamEndCapture(st, &g) != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        continue;
+      }
+      if (cudaGraphInstantiate(&exec[i], g, 0) != cudaSuccess) exec[i] = nullptr;
+      cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // a candidate that could not be captured is timed directly
   }
-  cudaError_t e = cudaStreamSynchronize(st);
-  std::vector<std::vector<double>> samples(cands.size());
-  if (e == cudaSuccess) {
-    for (int t = 0; t < trials; ++t) {
+  std::vector<std::vector<double>> samples(nc);
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < kTuneReps && e == cudaSuccess; ++rep) {
+    for (size_t i = 0; i < nc; ++i) {
+      if (exec[i]) {
+        if ((e = cudaGraphLaunch(exec[i], st)) != cudaSuccess) break;
+      } else {
+        trial(i, false);
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) break;
+    for (size_t i = 0; i < nc; ++i) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev[2 * (size_t)t], ev[2 * (size_t)t + 1]) == cudaSuccess)
-        samples[(size_t)t % cands.size()].push_back((double)ms * 1e3);
+      if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) == cudaSuccess)
+        samples[i].push_back((double)ms * 1e3);
     }
   }
   std::vector<double> best(cands.size());
   for (size_t i = 0; i < cands.size(); ++i) best[i] = median_of(samples[i]);
-  for (auto& x : ev) cudaEventDestroy(x);
+  release();
   if (e != cudaSuccess)
     return fail(c, RTG_E_CUDA, std::string("tune: ") + cudaGetErrorString(e));
   size_t k = 0;

@@ -175,8 +175,9 @@ def measured_peaks():
 # workloads and, for the sort, the variant the profiled run used (digit bits, keys per tile,
 # look-back code).  None where the kernels changed after the capture.
 NCU_TRAFFIC = {
-    # k_pairs_warp, one launch (the medium and tiled kernels of the phase move under 1 MB)
-    (100000, "fp64"): {"pairs": 13242112},
+    # pairs: k_pairs_warp, one launch (the medium and tiled kernels of the phase move under
+    # 1 MB); sort: the k_sort_pass launches of one sort, per (digit bits, tile keys, look-back)
+    (100000, "fp64"): {"pairs": 13242112, "sort": {(8, 3072, 1): 24184064}},
     (1000000, "fp32"): {"pairs": 331525632},
 }
 

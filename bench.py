@@ -113,6 +113,9 @@ class ClockSampler:
         self.lines: list[str] = []
 
     def start(self):
+        """Starts sampling and returns once the first sample is in (at most 10 s): the first
+        nvidia-smi call on a fresh machine initialises NVML and has stalled CUDA calls for
+        over a second, which must not fall into the timed steps."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
@@ -122,10 +125,18 @@ class ClockSampler:
             self.thread.start()
         except FileNotFoundError:
             self.proc = None
+            return
+        t_end = time.perf_counter() + 10.0
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def open_window(self):
+        """The timed region starts: samples from here (less one period) to stop() count."""
+        self.t_open = time.perf_counter()
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -136,9 +147,12 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        t0 = getattr(self, "t_open", None)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if t0 is not None and t < t0 - 0.2:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -207,6 +221,8 @@ def measure_build(ctx, stream, flush, args, pts, T, r, dtype_name, ws, rank, clo
     n, d = pts.shape
     m = T.shape[0]
     dev_pts = torch.from_numpy(pts).cuda()
+    if clocks is not None:
+        clocks.start()  # sampling runs from before the warm-up; only the timed window counts
     # recall against the exact set (device brute force), outside the timed region
     exact = ctx.brute_force(dev_pts, r, count_only=True)
     exact_pairs = exact.nnz
@@ -219,7 +235,7 @@ def measure_build(ctx, stream, flush, args, pts, T, r, dtype_name, ws, rank, clo
     if ws > 1:
         dist.barrier()
     if clocks is not None:
-        clocks.start()
+        clocks.open_window()
 
     def steps(timing):
         out_ms, out_ph, info = [], [], {}

@@ -1,6 +1,6 @@
 """Host-side arithmetic of the benchmark's JSON line (no GPU): the algorithmic bytes of the
-roofline phases, the DRAM-traffic lookup per workload and sort variant, and the whole-job
-throughput of replicas."""
+roofline phases, the DRAM-traffic lookup per workload and sort variant, the whole-job
+throughput of replicas, and the clock samples kept for the timed window."""
 import bench
 
 
@@ -34,3 +34,30 @@ def test_whole_job_throughput_counts_every_replica():
     assert one == 1000 * 10 / 0.005
     assert bench.job_throughput(1000, 10, 4, 5.0) == 4 * one
     assert bench.max_over_ranks(7.5, 1) == 7.5
+
+
+def test_clock_samples_count_only_inside_the_timed_window():
+    import time
+
+    class Done:  # a finished nvidia-smi process
+        def poll(self):
+            return 0
+
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    c = bench.ClockSampler(0)
+    c.proc = Done()
+    now = time.perf_counter()
+    row = "0, {}, 2070, 800, 0x0, Not Active, Not Active, Not Active, {}"
+    # a sample from the warm-up (clock low, power cap active) and two from the timed steps
+    c.lines = [(now - 5.0, row.format(1200, "Active")), (now - 0.05, row.format(2070, "Not Active")),
+               (now, row.format(2055, "Not Active"))]
+    c.open_window()
+    c.t_open = now - 0.1
+    rec = c.stop()
+    assert rec["samples"] == 2 and rec["reasons"] == [] and rec["sm_max_mhz"] == 2070.0
+    assert 2055.0 <= rec["sm_mhz"] <= 2070.0

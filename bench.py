@@ -195,8 +195,9 @@ def measured_peaks():
 # look-back code).  None where the kernels changed after the capture.
 NCU_TRAFFIC = {
     # pairs: k_pairs_warp, one launch (the medium and tiled kernels of the phase move under
-    # 1 MB); sort: the k_sort_pass launches of one sort, per (digit bits, tile keys, look-back)
-    (100000, "fp64"): {"pairs": 13242112, "sort": {(8, 3072, 1): 24184064}},
+    # 1 MB); sort: the k_sort_pass launches of one sort, per (digit bits, tile keys, look-back,
+    # passes)
+    (100000, "fp64"): {"pairs": 13242112, "sort": {(8, 3072, 1, 4): 24184064}},
     (1000000, "fp32"): {"pairs": 331525632},
 }
 
@@ -213,7 +214,8 @@ def phase_bytes(n, d, m, key_bytes, passes, coord_bytes, pairs, hist_read=False)
 def ncu_traffic(n, dtype, phase, sort_cfg):
     t = NCU_TRAFFIC.get((n, dtype), {}).get(phase)
     if phase == "sort" and isinstance(t, dict):
-        t = t.get((sort_cfg.get("digit_bits"), sort_cfg.get("tile_keys"), sort_cfg.get("lookback")))
+        t = t.get((sort_cfg.get("digit_bits"), sort_cfg.get("tile_keys"), sort_cfg.get("lookback"),
+                   sort_cfg.get("passes")))
     return t
 
 

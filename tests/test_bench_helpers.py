@@ -19,12 +19,13 @@ def test_phase_bytes_model():
 
 
 def test_traffic_lookup_by_workload_and_sort_variant(monkeypatch):
-    cfg = {"digit_bits": 8, "tile_keys": 3072, "lookback": 1}
+    cfg = {"digit_bits": 8, "tile_keys": 3072, "lookback": 1, "passes": 4}
     monkeypatch.setattr(bench, "NCU_TRAFFIC",
-                        {(100000, "fp64"): {"pairs": 123, "sort": {(8, 3072, 1): 456}}})
+                        {(100000, "fp64"): {"pairs": 123, "sort": {(8, 3072, 1, 4): 456}}})
     assert bench.ncu_traffic(100000, "fp64", "sort", cfg) == 456
-    # a variant that was not captured has no traffic figure
+    # a variant, or a pass count, that was not captured has no traffic figure
     assert bench.ncu_traffic(100000, "fp64", "sort", dict(cfg, tile_keys=2048)) is None
+    assert bench.ncu_traffic(100000, "fp64", "sort", dict(cfg, passes=3)) is None
     assert bench.ncu_traffic(123, "fp64", "pairs", cfg) is None
     assert bench.ncu_traffic(100000, "fp64", "pairs", cfg) == 123
 

@@ -134,6 +134,12 @@ typedef struct {
   int64_t mem_estimate;         /* served results: the admission estimate of their batch */
   int64_t mem_peak;             /* served results: device bytes their batch needed (the
                                    workspace its build asked for and its block CSR) */
+  int32_t sort_cell_major;      /* 1 when the sort key was the cell index alone (one
+                                   instance, where that saves a radix pass): the sort then
+                                   orders (cell, grid, point) instead of (grid, cell, point);
+                                   the reported pairs are the same */
+  int32_t sort_key_bits;        /* bits the sort ordered: key_bits, or the cell index's when
+                                   sort_cell_major is 1 */
 } rtg_stats;
 
 typedef struct {

@@ -447,13 +447,20 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if ((s = read_status(c)) != RTG_OK) return s;
       if ((s = check_errors(c, rtg::kErrNonFinite | rtg::kErrKeyOverflow)) != RTG_OK) return s;
       g.key_bits = (int)c->h_status->sort_bits;
+      g.cell_bits = (int)c->h_status->cell_bits;
       g.key64 = g.key_bits > 32;
     }
+    // Cell-major sort (one instance, the lane key kernel, 32-bit keys) where leaving the grid
+    // out of the key saves an 8-bit pass; the sorted bits are then the cell index's.
+    const bool cm_ok = c->cell_major && m > 1 && B == 1 && !bitset && !q.grid_major &&
+                       n_total >= 2 && !g.key64 && rtg::keys_by_lanes(a) && g.cell_bits > 0 &&
+                       rtg::sort_passes_for(g.cell_bits, 8) < rtg::sort_passes_for(g.key_bits, 8);
+    const int sort_key_bits = cm_ok ? g.cell_bits : g.key_bits;
     bool tune_now = false;
     if (m > 0 && !g.sorted_cfg) {
       // sort variant: forced, else the autotuner's table, else measure now (large sorts), else
       // the default
-      const auto it = c->sort_tune.find(SortKey(N, g.key_bits));
+      const auto it = c->sort_tune.find(SortKey(N, sort_key_bits));
       if (c->sort_forced) {
         g.sort = c->sort_force;
         g.sorted_cfg = true;
@@ -472,10 +479,16 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       }
     }
     a.key64 = g.key64;
-    a.passes = rtg::sort_passes_for(g.key_bits, g.sort.bits);
     a.sort_bits = g.sort.bits;
     a.sort_items = g.sort.items;
     a.sort_mode = g.sort.mode;
+    // (8-bit digits in separate passes only; the tuner times those forms alone)
+    a.cell_major = 0;
+    if (cm_ok && (tune_now || (g.sort.mode != rtg::kSortCoop && g.sort.bits == 8))) {
+      a.cell_major = 1;
+      a.passes = rtg::sort_passes_for(g.cell_bits, g.sort.bits);
+    }
+    if (!a.cell_major) a.passes = rtg::sort_passes_for(g.key_bits, g.sort.bits);
     // pair enumeration: one static span per warp for light cells (fewest span set-ups); more,
     // smaller spans claimed dynamically when the shape's cells held many candidates, so that
     // warps with heavy spans do not trail
@@ -513,7 +526,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         // measure every sort variant on this build's keys (the plan of the key-width read-back
         // above is in place), then run the build from the start
         rtg::SortConfig best;
-        if ((s = tune_sort(c, a, N, g.key_bits, &best)) != RTG_OK) return s;
+        if ((s = tune_sort(c, a, N, sort_key_bits, &best)) != RTG_OK) return s;
         g.sort = best;
         g.sorted_cfg = true;
         // and the enumeration knobs, on the keys sorted with that variant, unless the shape
@@ -521,7 +534,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         // enumerates every candidate, would cost seconds
         if (g.cand_per_pos >= 0.0f &&
             (double)g.cand_per_pos * (double)N <= c->tune_pairs_max_cand) {
-          if ((s = tune_pairs(c, a, best, g.key_bits, &g.spans_per_warp, &g.dense_min)) !=
+          if ((s = tune_pairs(c, a, best, sort_key_bits, &g.spans_per_warp, &g.dense_min)) !=
               RTG_OK)
             return s;
           g.pairs_tuned = g.spans_per_warp > 0;
@@ -845,6 +858,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       if (h.errors & rtg::kErrKeyBits) {
         g.key64 = h.sort_bits > 32;
         g.key_bits = (int)h.sort_bits;
+        g.cell_bits = (int)h.cell_bits;
       }
       if (h.errors & rtg::kErrPairOverflow)
         g.pair_cap = (long long)((double)h.emitted * 1.05) + 4096;
@@ -858,6 +872,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     if (m > 0) {
       g.key64 = h.sort_bits > 32;
       g.key_bits = (int)h.sort_bits;
+      g.cell_bits = (int)h.cell_bits;
     }
     if (!two_pass)
       g.pair_cap = std::max<long long>((long long)((double)h.emitted * 1.05) + 4096, 4096);
@@ -904,7 +919,7 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
         m > 0 ? (a.sort_mode == rtg::kSortLookback ? 1 : (a.sort_mode == rtg::kSortCoop ? 2 : 0))
               : 0;
     {
-      const auto it = c->sort_tune.find(SortKey(N, g.key_bits));
+      const auto it = c->sort_tune.find(SortKey(N, sort_key_bits));
       S.sort_tuned = m > 0 && it != c->sort_tune.end() && it->second.cfg.bits == g.sort.bits &&
                      it->second.cfg.items == g.sort.items && it->second.cfg.mode == g.sort.mode;
     }
@@ -913,6 +928,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
     S.pairs_spans_per_warp = m > 0 ? a.spans_per_warp : 0;
     S.dense_cell_min = m > 0 ? (a.dense_min > 0 ? a.dense_min : 256) : 0;
     S.pairs_tuned = m > 0 && g.pairs_tuned ? 1 : 0;
+    S.sort_cell_major = m > 0 && a.cell_major ? 1 : 0;
+    S.sort_key_bits = m > 0 ? (a.cell_major ? (int32_t)h.cell_bits : (int32_t)h.sort_bits) : 0;
     {
       // bytes each phase reads and writes by its design (phase order of phase_us)
       const double n_ = (double)n_total, N_ = (double)N, kb = a.key64 ? 8.0 : 4.0;
@@ -923,7 +940,8 @@ rtg_status build(rtg_ctx* c, const Request& q, rtg_csr* out) {
       double pb[7] = {};
       pb[0] = in_bytes + rows + 4.0 * n_;  // points in, FP32 rows and zeroed row counts out
       if (m > 0) {
-        pb[1] = rows + N_ * kb;            // FP32 rows in, key rows out
+        // FP32 rows in, key rows out (and their grid-major copy for a cell-major sort)
+        pb[1] = rows + N_ * kb * (a.cell_major ? 2.0 : 1.0);
         // the first pass reads the key rows (indices implicit); every pass writes keys and
         // indices, and the later ones also read them
         pb[2] = a.passes > 0 ? N_ * kb + N_ * (kb + 4.0) +
@@ -1009,6 +1027,8 @@ rtg_status create_ctx(int device, uint64_t budget, void* stream, rtg_ctx** out) 
   {
     const char* g = std::getenv("RTG_GRAPHS");
     c->use_graphs = !(g && std::strcmp(g, "0") == 0);
+    const char* cm = std::getenv("RTG_CELL_MAJOR");
+    c->cell_major = !(cm && std::strcmp(cm, "0") == 0);
   }
 
   {

@@ -36,6 +36,7 @@ using ShapeKey = std::tuple<long long, int, int, int, int, int, int>;
 struct ShapeGuess {
   bool key64 = true;
   int key_bits = 64;
+  int cell_bits = 0;  // widest grid's cell index range (bits), the key of a cell-major sort
   long long pair_cap = 0;
   bool sorted_cfg = false;  // sort chosen (tuned or default) for this shape
   rtg::SortConfig sort;
@@ -70,6 +71,7 @@ struct Request {
   int points_on_device;
   uint32_t flags;
   bool count_only;
+  bool grid_major = false;  // the sorted keys must come out grid by grid (the index reads them so)
 };
 
 struct Server;  // request server of a context (rtg_serve.cu)
@@ -109,6 +111,7 @@ struct rtg_ctx {
   rtg::Status* h_status = nullptr;  // pinned
   rtg::OutSlot* h_slot = nullptr;   // pinned; copied to out_slot before the output kernels
   bool use_graphs = true;           // RTG_GRAPHS=0 launches every kernel directly
+  bool cell_major = true;           // RTG_CELL_MAJOR=0 keeps the grid in every sort key
   std::map<rtghost::ShapeKey, rtghost::GraphEntry> graphs;
   cudaMemPool_t pool = nullptr;     // output CSRs (stream ordered, kept cached)
   bool own_pool = true;             // false: a serving lane drawing on its owner's pool

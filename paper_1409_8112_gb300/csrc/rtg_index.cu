@@ -480,7 +480,7 @@ rtg_status index_create(rtg_ctx* c, const rtg_instance& it, int m, int dtype, in
   // the sorted keys in the context's workspace
   rtg_csr tmp;
   std::memset(&tmp, 0, sizeof(tmp));
-  const Request q{&it, 1, m, dtype, on_device, 0u, true};
+  const Request q{&it, 1, m, dtype, on_device, 0u, true, true};  // grid t at [t n, (t + 1) n)
   rtg_status s = build(c, q, &tmp);
   if (s != RTG_OK) return s;
   const int key_bits = tmp.stats.key_bits;

@@ -137,6 +137,7 @@ struct Status {
   unsigned int long_rows;  // rows queued for the block row sort
   unsigned int mid_rows;   // rows queued for the warp row sort
   unsigned int rows_over_margin;  // 1 if a row holds more than kSkipMargin entries
+  unsigned int cell_bits;  // bits of the widest grid's cell index range (set by the plan)
   unsigned int tc_max_err_bits;  // tensor-core path: max |FP32 d^2 - FP64 d^2| (float bits)
   double tc_band;                // tensor-core path: band used around r^2
 };
@@ -282,6 +283,13 @@ struct BuildArgs {
   unsigned int inject;      // test hooks (kInject*), 0 in normal use
   int skip_tail;            // kSkipDense | kSkipLongRows: kernels left out of this launch
   int scan_zeroed;          // the scan's look-back words were zeroed with the counters
+  // Cell-major sort (one instance): the sort key is the cell index alone, the first pass reads
+  // a grid-major copy of the cell indices (keys[1], written by the key kernel) with their
+  // grid-major positions as values, and the last pass adds each grid's base back to the key
+  // and turns the position into the point index.  LSD passes are stable, so the output is in
+  // (cell, grid, point) order with every (grid, cell) run contiguous; the key carries
+  // log2(m) bits fewer.
+  int cell_major;
 };
 
 // Row-count scan: 16 counts per thread, 256 threads per tile, one 8-byte look-back word per

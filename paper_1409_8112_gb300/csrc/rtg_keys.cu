@@ -51,7 +51,7 @@ __device__ void plan_axis_item(long long idx, const Inst* __restrict__ inst, int
                                InstPlan* iplan, GridPlan* gplan);
 __device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, GridPlan* gplan,
                                   unsigned long long* bases, Status* st, int passes,
-                                  int radix_bits, int key64);
+                                  int radix_bits, int key64, int cell_major);
 
 // Plan arguments for the prep kernel's last block (small batches plan there, saving two
 // launches on the build's critical path).
@@ -64,6 +64,7 @@ struct PlanArgs {
   GridPlan* gplan;
   unsigned long long* bases;
   int passes, radix_bits, key64;
+  int cell_major;  // the sort keys are cell indices alone (the pass check uses their width)
 };
 
 // FP32 rows of the points, zeroed row counters and the per-instance bounding box;
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const Inst* __restrict__ 
     plan_axis_item(idx, inst, pa.m, dtype, pa.T64, bbox, pa.iplan, pa.gplan);
   if (pa.m == 0) return;
   __syncthreads();
-  plan_ranges_block(inst, B, pa.m, pa.gplan, pa.bases, st, pa.passes, pa.radix_bits, pa.key64);
+  plan_ranges_block(inst, B, pa.m, pa.gplan, pa.bases, st, pa.passes, pa.radix_bits, pa.key64,
+                    pa.cell_major);
 }
 
 // Distance band of instance b (one thread).  The bounding box is read from L2 (it was built
@@ -259,9 +261,12 @@ __device__ void plan_axis_item(long long idx, const Inst* __restrict__ inst, int
   }
   for (int l = d; l < kMaxDim; ++l) G.Rf[k * kMaxDim + l] = 0.0f;
   G.sf[k] = __double2float_rn(s[k]);
-  // Two cells of margin on each side absorb every rounding difference between these sums
-  // and the per-point fma chains (both are far below one cell); 1/c comes from the host.
-  const double qmin = floor(ymin * I.inv_c) - 2.0, qmax = floor(ymax * I.inv_c) + 2.0;
+  // The margin absorbs every rounding difference between these sums and the per-point
+  // chains: both are within (d + 3) 2^-53 A / c < 2^-48 A / c of the exact y / c (d <= 16),
+  // so one cell on each side covers them while A / c < 2^48, and the margin grows with
+  // A / c beyond that; 1/c comes from the host.
+  const double margin = 1.0 + floor(A * I.inv_c * 0x1.0p-48);
+  const double qmin = floor(ymin * I.inv_c) - margin, qmax = floor(ymax * I.inv_c) + margin;
   if (!(qmin > -4.0e18 && qmax < 4.0e18)) {
     G.qlo[k] = 0;
     G.ext[k] = ~0ull;  // flagged as overflow by the range pass
@@ -287,13 +292,15 @@ __global__ void __launch_bounds__(128) k_plan_axes(const Inst* __restrict__ inst
 // multiple of 32, up to 1024.
 __device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, GridPlan* gplan,
                                   unsigned long long* bases, Status* st, int passes,
-                                  int radix_bits, int key64) {
+                                  int radix_bits, int key64, int cell_major) {
   __shared__ unsigned long long sbuf[32];
   __shared__ unsigned long long carry;
   __shared__ int overflow;
+  __shared__ unsigned int s_cbits;  // widest cell index range of one grid (bits)
   if (threadIdx.x == 0) {
     carry = 0;
     overflow = 0;
+    s_cbits = 0;
   }
   __syncthreads();
   const long long total_bt = (long long)B * m;
@@ -321,6 +328,7 @@ __device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, G
       }
       G.range = strd;
       range = strd;
+      if (strd > 1) atomicMax(&s_cbits, 64u - (unsigned)__clzll((long long)(strd - 1)));
     }
     // block exclusive scan of the ranges (with a carry across chunks)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -354,8 +362,10 @@ __device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, G
     const unsigned long long total = carry;
     const unsigned int bits = total <= 1 ? 0u : 64u - (unsigned)__clzll((long long)(total - 1));
     st->sort_bits = bits;
+    st->cell_bits = s_cbits;
     if (overflow) atomicOr(&st->errors, kErrKeyOverflow);
-    if (sort_passes_for((int)bits, radix_bits) > passes || (!key64 && bits > 32))
+    const unsigned int sorted_bits = cell_major ? s_cbits : bits;
+    if (sort_passes_for((int)sorted_bits, radix_bits) > passes || (!key64 && bits > 32))
       atomicOr(&st->errors, kErrKeyBits);
   }
 }
@@ -363,8 +373,9 @@ __device__ void plan_ranges_block(const Inst* __restrict__ inst, int B, int m, G
 __global__ void __launch_bounds__(1024) k_plan_ranges(const Inst* __restrict__ inst, int B, int m,
                                                       GridPlan* gplan,
                                                       unsigned long long* bases, Status* st,
-                                                      int passes, int radix_bits, int key64) {
-  plan_ranges_block(inst, B, m, gplan, bases, st, passes, radix_bits, key64);
+                                                      int passes, int radix_bits, int key64,
+                                                      int cell_major) {
+  plan_ranges_block(inst, B, m, gplan, bases, st, passes, radix_bits, key64, cell_major);
 }
 
 // FP64 reference cell index (the oracle's sequence) for point i, grid data Tt, axis k.
@@ -554,6 +565,7 @@ void prep_impl(const BuildArgs& a, cudaStream_t s) {
   pa.passes = a.passes;
   pa.radix_bits = a.sort_bits;
   pa.key64 = a.key64 ? 1 : 0;
+  pa.cell_major = a.cell_major;
   k_prep<DPAD><<<(unsigned)a.pblocks, kPrepThreads, 0, s>>>(a.inst, a.B, a.dtype, a.pf,
                                                              a.row_cnt, a.bbox, a.st, pa);
 }
@@ -666,7 +678,7 @@ __global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
     const GridPlan* __restrict__ gplan, InstPlan* iplan, const unsigned long long* bbox,
     Status* st, K* __restrict__ key_mat, long long chunks, int hist_passes, int hist_bits,
     unsigned int* hist, unsigned int* digit_off, unsigned int* sort_epoch,
-    unsigned int wait_limit) {
+    unsigned int wait_limit, K* __restrict__ key_gm, long long gm_n) {
   constexpr int DP = D <= 4 ? 4 : 8;  // padded row width of the FP32 rows
   __shared__ unsigned int s_hist[kLaneHistWords];  // digit counts of every pass
   __shared__ __align__(16) float s_rows[2][kPointBlock * DP];  // double-buffered chunk rows
@@ -794,9 +806,13 @@ __global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
       if (valid) {
         *out = key;
         near_cnt += near ? 1u : 0u;
+        // cell-major sort: the digits are those of the cell index, whose grid-major copy the
+        // first pass reads (one instance, so point ci.g0 + p is its own grid-major offset)
+        const K hkey = key_gm ? key - base : key;
+        if (key_gm) key_gm[(long long)t * gm_n + ci.g0 + p] = hkey;
         if (hist_bits == 8) {
-          const unsigned int lo = (unsigned int)key,
-                             hi = (unsigned int)((unsigned long long)key >> 32);
+          const unsigned int lo = (unsigned int)hkey,
+                             hi = (unsigned int)((unsigned long long)hkey >> 32);
 #pragma unroll
           for (int q = 0; q < kMaxPasses; ++q)  // digit q is byte q of the key
             if (q < hist_passes)
@@ -806,7 +822,8 @@ __global__ void __launch_bounds__(kKeyLaneThreads, 2) k_keys_lanes(
           const unsigned int dm = (1u << hist_bits) - 1u;
 #pragma unroll 1
           for (int q = 0; q < hist_passes; ++q)
-            atomicAdd(&s_hist[(q << hist_bits) + ((unsigned int)(key >> (hist_bits * q)) & dm)], 1u);
+            atomicAdd(&s_hist[(q << hist_bits) + ((unsigned int)(hkey >> (hist_bits * q)) & dm)],
+                      1u);
         }
       }
     }
@@ -845,7 +862,8 @@ void keys_lanes_launch(const BuildArgs& a, cudaStream_t s) {
   k_keys_lanes<K, D><<<(unsigned)grid, kKeyLaneThreads, smem, s>>>(
       a.inst, a.B, a.m, a.dtype, a.dpad, a.pf, a.T64, a.gplan, a.iplan, a.bbox, a.st,
       (K*)a.key_mat, a.blocks, hist_in_keys(a) ? a.passes : 0, a.sort_bits, a.hist,
-      a.digit_off, a.sort_epoch, spin_limit_of(a.spin_limit) * 16u);
+      a.digit_off, a.sort_epoch, spin_limit_of(a.spin_limit) * 16u,
+      a.cell_major ? (K*)a.keys[1] : (K*)nullptr, a.n_total);
 }
 
 template <typename K>
@@ -876,7 +894,7 @@ int launch_prep_plan(const BuildArgs& a, cudaStream_t s) {
                                                               a.bbox, a.iplan, a.gplan);
   if (a.m > 0)
     k_plan_ranges<<<1, 1024, 0, s>>>(a.inst, a.B, a.m, a.gplan, a.bases, a.st, a.passes,
-                                     a.sort_bits, a.key64 ? 1 : 0);
+                                     a.sort_bits, a.key64 ? 1 : 0, a.cell_major);
   return a.m > 0 ? 3 : 2;
 }
 

@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
     const Inst* __restrict__ inst, const InstPlan* __restrict__ iplan,
     const unsigned long long* __restrict__ bases, int nbt, Status* st, Sink sk,
     LargeCell* large, unsigned int large_cap, int warp_bytes, unsigned int* span_next,
-    int skip_dense) {
+    int skip_dense, int cell_major) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_gcand[kMaxGrids];
   __shared__ unsigned int s_maxcell;
@@ -444,9 +444,10 @@ __global__ void __launch_bounds__(kPairThreads, RTG_PAIRS_MIN_BLOCKS) k_pairs_wa
     const long long P0 = sp * span;
     const int len = (int)(min(P0 + span, N) - P0);  // owned heads lie in [0, len)
     const int lim = (int)(min(P0 + span + 64, N) - P0);  // positions read lie in [0, lim)
-    // (instance, grid) range of every cell this span can own
+    // (instance, grid) range of every cell this span can own (a cell-major sort leaves the
+    // keys in (cell, grid) order, so a span may hold any grid)
     int bt_lo = 0, bt_hi = nbt - 1;
-    {
+    if (!cell_major) {
       const long long q = lane == 0 ? P0 : P0 + min(len + 32, lim) - 1;
       int v = 0;
       if (lane < 2) v = find_bt((unsigned long long)skeys[q], bases, 0, nbt - 1);
@@ -1781,7 +1782,8 @@ void pairs_mode(const BuildArgs& a, int sorted_buf, cudaStream_t s) {
   kern<<<(unsigned)blocks, kPairThreads, smem, s>>>(
       sk, sv, N, span, a.pf, a.dtype, (const K*)a.key_mat, a.m, a.inst, a.iplan, a.bases,
       a.B * a.m, a.st, make_sink(a), a.large, a.large_cap, wbytes,
-      &a.st->span_next[MODE == kWrite ? 1 : 0], (a.skip_tail & kSkipDense) ? 1 : 0);
+      &a.st->span_next[MODE == kWrite ? 1 : 0], (a.skip_tail & kSkipDense) ? 1 : 0,
+      a.cell_major);
   if (a.skip_tail & kSkipDense) return;  // (k_pairs_warp flags any dense cell it meets)
   {
     const size_t msmem =

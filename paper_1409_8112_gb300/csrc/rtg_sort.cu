@@ -21,6 +21,7 @@
 #include "rtg_internal.cuh"
 
 #include <mutex>
+#include <type_traits>
 
 namespace rtg {
 
@@ -325,9 +326,14 @@ struct TileRank {
 
   // Writes the reordered tile (after a barrier that publishes s_gbase and the tile).  Offsets
   // outside [0, N) (digit counts that do not belong to these keys) are dropped and flagged.
-  template <bool FULL>
+  // REB (last pass of a cell-major sort): the values are grid-major positions q = g n + i;
+  // the key written is the cell index plus grid g's base and the value is the point i
+  // (g = floor(q / n) by a multiply-high with rdiv = ceil(2^64 / n), exact for q, n < 2^31).
+  template <bool FULL, bool REB>
   __device__ void write(K* __restrict__ kout, uint32_t* __restrict__ vout, long long N,
-                        long long tile_base, int shift, unsigned int* errors) {
+                        long long tile_base, int shift, unsigned int* errors,
+                        const unsigned long long* __restrict__ rbases, unsigned int rn,
+                        unsigned long long rdiv) {
     const long long rem = N - tile_base;
     const int tvalid = FULL ? kTile : (rem < kTile ? (int)rem : kTile);
     const unsigned int nu = (unsigned int)N;  // the host keeps N below 2^31
@@ -338,8 +344,15 @@ struct TileRank {
       const unsigned int dg = (unsigned int)(k >> shift) & (D - 1);
       const unsigned int dst = s_gbase[dg] + (unsigned int)x - s_tdig[dg];
       if (dst < nu) {
-        kout[dst] = k;
-        vout[dst] = s_vals[x];
+        if (REB) {
+          const uint32_t q = s_vals[x];
+          const uint32_t g = (uint32_t)__umul64hi((unsigned long long)q, rdiv);
+          kout[dst] = k + (K)__ldg(rbases + g);
+          vout[dst] = q - g * rn;
+        } else {
+          kout[dst] = k;
+          vout[dst] = s_vals[x];
+        }
       } else {
         bad = true;
       }
@@ -348,11 +361,12 @@ struct TileRank {
   }
 };
 
-template <typename K, int BITS, int ITEMS>
+template <typename K, int BITS, int ITEMS, bool REB>
 __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ offs,
-    unsigned int tiles, unsigned int* errors, unsigned long long vdiv) {
+    unsigned int tiles, unsigned int* errors, unsigned long long vdiv,
+    const unsigned long long* __restrict__ rbases, unsigned int rn, unsigned long long rdiv) {
   using TR = TileRank<K, BITS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned int sbuf[kSortWarps];
@@ -365,20 +379,21 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(
   if (full) tr.template rank<true>(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
   else tr.template rank<false>(kin, vin, N, tile_base, shift, tcount, sbuf, vdiv);
   __syncthreads();
-  if (full) tr.template write<true>(kout, vout, N, tile_base, shift, errors);
-  else tr.template write<false>(kout, vout, N, tile_base, shift, errors);
+  if (full) tr.template write<true, REB>(kout, vout, N, tile_base, shift, errors, rbases, rn, rdiv);
+  else tr.template write<false, REB>(kout, vout, N, tile_base, shift, errors, rbases, rn, rdiv);
 }
 
 // Single-kernel pass with decoupled look-back (tiles take their index from an atomic
 // counter, so a tile waits only on tiles already running; each wait is bounded).  Cheaper
 // than reduce-then-scan while all tiles fit in about one wave.
-template <typename K, int BITS, int ITEMS>
+template <typename K, int BITS, int ITEMS, bool REB>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, long long N, int shift, const unsigned int* __restrict__ digit_off,
     unsigned long long* lookback, unsigned int* tile_counter, const unsigned int* epoch_base,
     int pass, unsigned int* errors, unsigned int spin_limit, unsigned int inject,
-    unsigned long long vdiv) {
+    unsigned long long vdiv, const unsigned long long* __restrict__ rbases, unsigned int rn,
+    unsigned long long rdiv) {
   using TR = TileRank<K, BITS, ITEMS>;
   constexpr int D = TR::D, PT = TR::PT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -450,8 +465,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     tr.s_gbase[d] = digit_off[d] + excl;
   }
   __syncthreads();
-  if (full) tr.template write<true>(kout, vout, N, tile_base, shift, errors);
-  else tr.template write<false>(kout, vout, N, tile_base, shift, errors);
+  if (full) tr.template write<true, REB>(kout, vout, N, tile_base, shift, errors, rbases, rn, rdiv);
+  else tr.template write<false, REB>(kout, vout, N, tile_base, shift, errors, rbases, rn, rdiv);
 }
 
 // Grid-wide barrier of a cooperative launch (every block resident), bounded: false when the
@@ -540,8 +555,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_coop(
       tr.s_gbase[d] = __ldcg(counts + (size_t)d * tiles + tile);
     }
     __syncthreads();
-    if (full) tr.template write<true>(kout, vout, N, tile_base, shift, errors);
-    else tr.template write<false>(kout, vout, N, tile_base, shift, errors);
+    if (full) tr.template write<true, false>(kout, vout, N, tile_base, shift, errors, nullptr, 0u, 0ull);
+    else tr.template write<false, false>(kout, vout, N, tile_base, shift, errors, nullptr, 0u, 0ull);
     if (!coop_grid_sync(&st->coop_count, &st->coop_gen, spin_limit, errors)) return;
   }
 }
@@ -598,7 +613,8 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
   const unsigned tiles = (unsigned)((N + SS::kTile - 1) / SS::kTile);
   // (a single-launch choice whose tiles cannot all be resident runs as reduce-then-scan, which
   // uses the same scratch)
-  if (a.sort_mode == kSortCoop && sort_coop_fits(N, BITS, ITEMS, a.num_sms, sizeof(K) == 8)) {
+  if (a.sort_mode == kSortCoop && !a.cell_major &&
+      sort_coop_fits(N, BITS, ITEMS, a.num_sms, sizeof(K) == 8)) {
     static bool attr[64] = {};
     set_smem_once(k_sort_coop<K, BITS, ITEMS>, SS::kSmem, attr);
     void* args[] = {(void*)&a.key_mat, (void*)&a.keys[0], (void*)&a.keys[1], (void*)&a.vals[0],
@@ -619,30 +635,49 @@ int sort_impl(const BuildArgs& a, cudaStream_t s) {
     cudaLaunchKernelExC(&cfg, (const void*)k_sort_coop<K, BITS, ITEMS>, args);
     return (passes - 1) & 1;
   }
-  auto src_k = [&](int p) { return p == 0 ? (const K*)a.key_mat : (const K*)a.keys[(p - 1) & 1]; };
+  // cell-major: the first pass reads the grid-major cell indices (keys[1], consumed before the
+  // second pass overwrites it) with the positions themselves as values, and the last pass
+  // rebases them
+  const K* first = a.cell_major ? (const K*)a.keys[1] : (const K*)a.key_mat;
+  auto src_k = [&](int p) { return p == 0 ? first : (const K*)a.keys[(p - 1) & 1]; };
   auto src_v = [&](int p) { return p == 0 ? (const uint32_t*)nullptr : a.vals[(p - 1) & 1]; };
+  const unsigned long long vd0 = a.cell_major ? 0ull : vdiv;
+  const unsigned int rn = a.cell_major ? (unsigned int)a.n_total : 0u;
+  const unsigned long long rdiv = a.cell_major ? ~0ull / (unsigned long long)a.n_total + 1ull : 0ull;
+  auto rn_of = [&](int p) { return p == passes - 1 ? rn : 0u; };
+  // the rebasing last pass is compiled for 8-bit digits over 32-bit keys only, the one form
+  // the host chooses a cell-major sort with
+  constexpr bool kReb = BITS == 8 && std::is_same<K, uint32_t>::value;
   if (a.sort_mode == kSortLookback) {
-    static bool attr[64] = {};
-    set_smem_once(k_sort_pass<K, BITS, ITEMS>, SS::kSmem, attr);
+    static bool attr[64] = {}, attr_reb[64] = {};
+    set_smem_once(k_sort_pass<K, BITS, ITEMS, false>, SS::kSmem, attr);
+    if constexpr (kReb)
+      if (a.cell_major) set_smem_once(k_sort_pass<K, BITS, ITEMS, kReb>, SS::kSmem, attr_reb);
     for (int p = 0; p < passes; ++p) {
-      k_sort_pass<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
+      auto kern = (kReb && rn_of(p)) ? k_sort_pass<K, BITS, ITEMS, kReb>
+                                     : k_sort_pass<K, BITS, ITEMS, false>;
+      kern<<<tiles, kSortThreads, SS::kSmem, s>>>(
           src_k(p), src_v(p), (K*)a.keys[p & 1], a.vals[p & 1], N, p * BITS,
           a.digit_off + p * D, a.lookback, &a.st->sort_tiles[p], a.sort_epoch, p, &a.st->errors,
-          spin_limit_of(a.spin_limit), a.inject, vdiv);
+          spin_limit_of(a.spin_limit), a.inject, vd0, a.bases, rn_of(p), rdiv);
     }
     return (passes - 1) & 1;
   }
-  static bool attr[64] = {};
-  set_smem_once(k_sort_downsweep<K, BITS, ITEMS>, SS::kSmem, attr);
+  static bool attr[64] = {}, attr_reb[64] = {};
+  set_smem_once(k_sort_downsweep<K, BITS, ITEMS, false>, SS::kSmem, attr);
+  if constexpr (kReb)
+    if (a.cell_major) set_smem_once(k_sort_downsweep<K, BITS, ITEMS, kReb>, SS::kSmem, attr_reb);
   unsigned int* counts = (unsigned int*)a.lookback;  // D * tiles words
   for (int p = 0; p < passes; ++p) {
     const int shift = p * BITS;
     k_sort_upsweep<K, BITS, ITEMS><<<tiles, kSortThreads, 0, s>>>(src_k(p), N, shift, counts,
                                                                   tiles);
     k_sort_scan<<<D, 1024, 0, s>>>(counts, tiles, a.digit_off + p * D);
-    k_sort_downsweep<K, BITS, ITEMS><<<tiles, kSortThreads, SS::kSmem, s>>>(
+    auto down = (kReb && rn_of(p)) ? k_sort_downsweep<K, BITS, ITEMS, kReb>
+                                   : k_sort_downsweep<K, BITS, ITEMS, false>;
+    down<<<tiles, kSortThreads, SS::kSmem, s>>>(
         src_k(p), src_v(p), (K*)a.keys[p & 1], a.vals[p & 1], N, shift, counts, tiles,
-        &a.st->errors, vdiv);
+        &a.st->errors, vd0, a.bases, rn_of(p), rdiv);
   }
   return (passes - 1) & 1;
 }

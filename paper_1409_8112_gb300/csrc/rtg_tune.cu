@@ -194,7 +194,14 @@ void tune_load(rtg_ctx* c) {
 
 rtg_status tune_sort(rtg_ctx* c, rtg::BuildArgs& a, long long N, int key_bits,
                      rtg::SortConfig* out) {
-  const std::vector<rtg::SortConfig> cands = candidates(N, a.num_sms, a.key64);
+  std::vector<rtg::SortConfig> cands = candidates(N, a.num_sms, a.key64);
+  if (a.cell_major) {
+    // a cell-major sort runs 8-bit digits in separate passes (its last pass rebases the keys)
+    std::vector<rtg::SortConfig> keep;
+    for (const rtg::SortConfig& cfg : cands)
+      if (cfg.mode != rtg::kSortCoop && cfg.bits == 8) keep.push_back(cfg);
+    cands.swap(keep);
+  }
   const size_t nc = cands.size();
   std::vector<cudaEvent_t> ev(2 * nc, nullptr);
   std::vector<cudaGraphExec_t> exec(nc, nullptr);

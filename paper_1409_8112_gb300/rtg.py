@@ -66,7 +66,8 @@ class rtg_stats(ctypes.Structure):
                 ("phase_bytes", ctypes.c_int64 * 8), ("bytes_moved", ctypes.c_int64),
                 ("pairs_spans_per_warp", ctypes.c_int32), ("dense_cell_min", ctypes.c_int32),
                 ("pairs_tuned", ctypes.c_int32), ("mem_estimate", ctypes.c_int64),
-                ("mem_peak", ctypes.c_int64)]
+                ("mem_peak", ctypes.c_int64), ("sort_cell_major", ctypes.c_int32),
+                ("sort_key_bits", ctypes.c_int32)]
 
 
 class rtg_csr(ctypes.Structure):
@@ -318,7 +319,8 @@ def stats_dict(s: rtg_stats, m: int) -> dict:
         "pairs": int(s.pairs), "key_bits": int(s.key_bits), "sort_passes": int(s.sort_passes),
         "launches": int(s.launches), "attempts": int(s.attempts),
         "sort": {"digit_bits": int(s.sort_digit_bits), "tile_keys": int(s.sort_tile_keys),
-                 "lookback": int(s.sort_lookback), "tuned": int(s.sort_tuned)},
+                 "lookback": int(s.sort_lookback), "tuned": int(s.sort_tuned),
+                 "cell_major": int(s.sort_cell_major), "sorted_bits": int(s.sort_key_bits)},
         "phase_us": {p: float(s.phase_us[i]) for i, p in enumerate(PHASES)},
         "max_abs_err_d2": float(s.max_abs_err_d2), "band": float(s.band),
         "phase_bytes": {p: int(s.phase_bytes[i]) for i, p in enumerate(PHASES)},

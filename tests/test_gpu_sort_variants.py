@@ -75,7 +75,13 @@ def test_sort_variant_bit_exact(variant, case32, case64):
         assert st["key_bits"] <= 32
         assert (st["sort"]["digit_bits"], st["sort"]["tile_keys"], st["sort"]["lookback"]) == \
             (variant[0], 256 * variant[1], LOOKBACK_CODE[variant[2]])
-        assert st["sort_passes"] == -(-st["key_bits"] // variant[0])
+        # a cell-major sort (8-bit passes only) orders the cell index's bits alone
+        assert st["sort_passes"] == -(-st["sort"]["sorted_bits"] // variant[0])
+        if st["sort"]["cell_major"]:
+            assert variant[0] == 8 and variant[2] != 2
+            assert st["sort"]["sorted_bits"] < st["key_bits"]
+        else:
+            assert st["sort"]["sorted_bits"] == st["key_bits"]
         st = _check(ctx, *case64)
         assert st["key_bits"] > 32
         assert st["sort"]["digit_bits"] == variant[0]
@@ -102,7 +108,7 @@ def test_autotuner_measures_once_and_caches(tmp_path, case32):
     entries = doc["entries"]
     assert len(entries) == 1
     e = entries[0]
-    assert e["elements"] == 37003 * 8 and e["key_bits"] == st["key_bits"]
+    assert e["elements"] == 37003 * 8 and e["key_bits"] == st["sort"]["sorted_bits"]
     assert (e["bits"], 256 * e["items"], LOOKBACK_CODE[e["mode"]]) == (
         st["sort"]["digit_bits"], st["sort"]["tile_keys"], st["sort"]["lookback"])
     assert e["us"] > 0

@@ -194,11 +194,11 @@ def measured_peaks():
 # workloads and, for the sort, the variant the profiled run used (digit bits, keys per tile,
 # look-back code).  None where the kernels changed after the capture.
 NCU_TRAFFIC = {
-    # pairs: k_pairs_warp, one launch (the medium and tiled kernels of the phase move under
-    # 1 MB); sort: the k_sort_pass launches of one sort, per (digit bits, tile keys, look-back,
-    # passes)
-    (100000, "fp64"): {"pairs": 13242112, "sort": {(8, 3072, 1, 4): 24184064}},
-    (1000000, "fp32"): {"pairs": 331525632},
+    # DRAM bytes of the dominant kernel from one ncu capture, per workload; an entry goes when
+    # its kernel changes.  pairs: k_pairs_warp, one launch; sort: the k_sort_pass launches of
+    # one sort, per (digit bits, tile keys, look-back, passes).  The captures of both (13.2 MB
+    # and 331.5 MB for the pairs at 100k and 1M, 24.2 MB for the four-pass 100k sort) predate
+    # the cell-major sort, which changed k_pairs_warp and the sort's order at 100k.
 }
 
 

@@ -36,6 +36,7 @@
  *   RTG_TUNE_PAIRS_MAX_CAND=x in-cell candidates above which the enumeration keeps its
  *                             default knobs (4e9)
  *   RTG_GRAPHS=0              launch every kernel directly instead of replaying CUDA graphs
+ *   RTG_CELL_MAJOR=0          keep the grid in every sort key (no cell-major sort)
  *   RTG_SERVE_LANES=k         concurrent server lanes (1 to 8, default 2)
  *   RTG_SERVE_LOG=1           one line per served batch on stderr
  */

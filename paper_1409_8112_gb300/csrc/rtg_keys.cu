@@ -262,10 +262,10 @@ __device__ void plan_axis_item(long long idx, const Inst* __restrict__ inst, int
   for (int l = d; l < kMaxDim; ++l) G.Rf[k * kMaxDim + l] = 0.0f;
   G.sf[k] = __double2float_rn(s[k]);
   // The margin absorbs every rounding difference between these sums and the per-point
-  // chains: both are within (d + 3) 2^-53 A / c < 2^-48 A / c of the exact y / c (d <= 16),
-  // so one cell on each side covers them while A / c < 2^48, and the margin grows with
-  // A / c beyond that; 1/c comes from the host.
-  const double margin = 1.0 + floor(A * I.inv_c * 0x1.0p-48);
+  // chains: each is within (d + 3) 2^-53 A / c of the exact y / c (d <= 16), so the two
+  // together stay below 2^-47 A / c, less than 1 + floor(2^-46 A / c) cells: one cell on
+  // each side for every A / c below 2^46, more beyond; 1/c comes from the host.
+  const double margin = 1.0 + floor(A * I.inv_c * 0x1.0p-46);
   const double qmin = floor(ymin * I.inv_c) - margin, qmax = floor(ymax * I.inv_c) + margin;
   if (!(qmin > -4.0e18 && qmax < 4.0e18)) {
     G.qlo[k] = 0;

@@ -38,7 +38,7 @@ def _context(cell_major: bool, variant: str | None = None):
 
 @pytest.fixture(scope="module")
 def case100k():
-    # the bench's 100k workload: 27-bit composite keys, 24-bit cell indices (3 passes, not 4)
+    # the 100k workload of bench.py: 26-bit composite keys, 24-bit cell indices (3 passes, not 4)
     n, d, m = 100000, 6, 8
     r = gen.radius_for_degree(n, d)
     pts = gen.points_uniform(0, n, d)
